@@ -1,0 +1,199 @@
+// qld_oracle.cpp -- CPU oracle for quadrature lock-in discrimination (QLD).
+//
+// TEST INFRASTRUCTURE ONLY. This file is the plain, slow, obviously-correct
+// restatement of what the QLD hot path computes, written from the paper's
+// definitions (Methods, "Numerical simulations"; Supplementary Information,
+// "Timing sequence for hybrid parallelisation"). Only the test suite, the
+// smoke check in __graft_entry__ and bench.py's CPU-baseline leg may load it.
+// It shares no code, header, table or helper with the CUDA library, and it
+// never includes anything from it.
+//
+// Conventions (readings of points the paper leaves open):
+//  * Sampling at four samples per modulation period: omega * t_s = pi * s / 2.
+//  * s is the absolute 1-based index of a frame in the stream (Methods:
+//    t_s = s * dt, s = 1, 2, ...). A window of N frames whose first frame
+//    has absolute index s0 covers s = s0 .. s0 + N - 1.
+//  * Quadrature sums (Methods, the equation defining R(j,k)):
+//        S = sum_s I(s) * sin(omega t_s),   C = sum_s I(s) * cos(omega t_s)
+//    computed exactly in int64, from scratch for every window.
+//  * R = sqrt(S^2 + C^2) (Methods); phase = atan2(-S, C), the argument of the
+//    DFT bin k = N/4 under the absolute-index convention (the paper defines no
+//    phase image). S = C = 0 gives phase 0.
+//  * DFT bin (Methods, FFT discrimination): X_k = sum_s I(s) exp(-2 pi i k s / N)
+//    over the window, with (k * s) mod N reduced in integers before the FP64
+//    cos/sin; the map is |X_k|^2.
+//
+// Every array is a window of N frames laid out frame-major: frame i of the
+// window starts at x + i * stride (elements), and pixels 0 .. npix-1 of a
+// frame are contiguous. All arithmetic is int64 or IEEE double.
+
+#include <cmath>
+#include <cstdint>
+#include <thread>
+#include <vector>
+
+namespace {
+
+// Precomputed reference arrays (Methods: "values of sin(omega t_s) and
+// cos(omega t_s) being read from pre-calculated arrays"; SI item 1: tables
+// "appropriate for the choice of lock-in and sampling frequencies"). With
+// omega t_s = pi s / 2 the functions have period 4 in s and take the exact
+// integer values sin(pi r / 2), cos(pi r / 2) for r = s mod 4.
+struct RefTables {
+    int64_t sin_r[4];
+    int64_t cos_r[4];
+    RefTables() {
+        for (int r = 0; r < 4; ++r) {
+            const double arg = M_PI * 0.5 * (double)r;
+            sin_r[r] = (int64_t)std::llround(std::sin(arg));
+            cos_r[r] = (int64_t)std::llround(std::cos(arg));
+        }
+    }
+};
+const RefTables kTables;
+
+inline int residue4(int64_t s) { return (int)(((s % 4) + 4) % 4); }
+
+template <typename T>
+void quadrature_sums(const T* x, int64_t stride, int64_t npix, int N, int64_t s0,
+                     int64_t* S, int64_t* C) {
+    for (int64_t p = 0; p < npix; ++p) {
+        int64_t sin_acc = 0, cos_acc = 0;
+        for (int i = 0; i < N; ++i) {
+            const int64_t s = s0 + i;
+            const int64_t I = (int64_t)x[(int64_t)i * stride + p];
+            sin_acc += I * kTables.sin_r[residue4(s)];
+            cos_acc += I * kTables.cos_r[residue4(s)];
+        }
+        S[p] = sin_acc;
+        C[p] = cos_acc;
+    }
+}
+
+template <typename T>
+void dft_bin(const T* x, int64_t stride, int64_t npix, int N, int64_t s0, int64_t k,
+             double* re, double* im, double* power) {
+    // Per-window twiddles exp(-2 pi i k s / N) for s = s0 .. s0+N-1, with the
+    // angle index (k*s) mod N reduced exactly in integers.
+    std::vector<double> cr(N), ci(N);
+    for (int i = 0; i < N; ++i) {
+        const int64_t s = s0 + i;
+        int64_t m = ((k % N) * (s % N)) % N;
+        if (m < 0) m += N;
+        const double theta = 2.0 * M_PI * (double)m / (double)N;
+        cr[i] = std::cos(theta);
+        ci[i] = -std::sin(theta);
+    }
+    for (int64_t p = 0; p < npix; ++p) {
+        double a = 0.0, b = 0.0;
+        for (int i = 0; i < N; ++i) {
+            const double I = (double)x[(int64_t)i * stride + p];
+            a += I * cr[i];
+            b += I * ci[i];
+        }
+        if (re) re[p] = a;
+        if (im) im[p] = b;
+        if (power) power[p] = a * a + b * b;
+    }
+}
+
+// Splits pixels [0, npix) into nthreads contiguous ranges (rows of the image
+// are contiguous runs of pixels, so this is a row partition) and runs fn on
+// each range in its own std::thread.
+template <typename Fn>
+void run_partitioned(int64_t npix, int nthreads, Fn fn) {
+    if (nthreads <= 1 || npix < 2) {
+        fn((int64_t)0, npix);
+        return;
+    }
+    if ((int64_t)nthreads > npix) nthreads = (int)npix;
+    std::vector<std::thread> pool;
+    pool.reserve(nthreads);
+    const int64_t chunk = (npix + nthreads - 1) / nthreads;
+    for (int t = 0; t < nthreads; ++t) {
+        const int64_t lo = (int64_t)t * chunk;
+        const int64_t hi = lo + chunk < npix ? lo + chunk : npix;
+        if (lo >= hi) break;
+        pool.emplace_back([=] { fn(lo, hi - lo); });
+    }
+    for (auto& th : pool) th.join();
+}
+
+}  // namespace
+
+extern "C" {
+
+// Reference arrays sin(pi r/2), cos(pi r/2), r = 0..3 (Methods; SI item 1).
+void orc_reference_tables(int64_t* sin_r, int64_t* cos_r) {
+    for (int r = 0; r < 4; ++r) {
+        sin_r[r] = kTables.sin_r[r];
+        cos_r[r] = kTables.cos_r[r];
+    }
+}
+
+// Quadrature sums S, C of a window (Methods, definition of R(j,k)), int64.
+// pixfmt 1 = uint8 frames, 2 = uint16 frames. Returns 0, or -1 on bad args.
+int orc_quadrature_sums(const void* x, int pixfmt, int64_t stride, int64_t npix, int N,
+                        int64_t s0, int64_t* S, int64_t* C, int nthreads) {
+    if (!x || !S || !C || N < 1 || npix < 0 || stride < npix) return -1;
+    if (pixfmt == 1) {
+        const uint8_t* xb = (const uint8_t*)x;
+        run_partitioned(npix, nthreads, [&](int64_t lo, int64_t n) {
+            quadrature_sums(xb + lo, stride, n, N, s0, S + lo, C + lo);
+        });
+    } else if (pixfmt == 2) {
+        const uint16_t* xh = (const uint16_t*)x;
+        run_partitioned(npix, nthreads, [&](int64_t lo, int64_t n) {
+            quadrature_sums(xh + lo, stride, n, N, s0, S + lo, C + lo);
+        });
+    } else {
+        return -1;
+    }
+    return 0;
+}
+
+// Amplitude R = [S^2 + C^2]^(1/2) (Methods) and phase atan2(-S, C), FP64.
+// The negation is taken on the integer so that S = 0 gives +0 and the phase
+// lies in (-pi, pi].
+int orc_amplitude_phase(const int64_t* S, const int64_t* C, int64_t npix, double* R,
+                        double* phase) {
+    if (!S || !C || npix < 0) return -1;
+    for (int64_t p = 0; p < npix; ++p) {
+        const double s = (double)S[p];
+        const double c = (double)C[p];
+        if (R) R[p] = std::sqrt(s * s + c * c);
+        if (phase) {
+            if (S[p] == 0 && C[p] == 0) {
+                phase[p] = 0.0;
+            } else {
+                phase[p] = std::atan2((double)(-S[p]), c);
+            }
+        }
+    }
+    return 0;
+}
+
+// DFT bin k of each pixel's time series over the window (Methods, FFT
+// discrimination): X_k = sum_s I(s) exp(-2 pi i k s / N), FP64. Any of re,
+// im, power may be NULL. k is taken modulo N.
+int orc_dft_bin(const void* x, int pixfmt, int64_t stride, int64_t npix, int N, int64_t s0,
+                int64_t k, double* re, double* im, double* power, int nthreads) {
+    if (!x || N < 1 || npix < 0 || stride < npix) return -1;
+    auto off = [](double* a, int64_t lo) { return a ? a + lo : (double*)nullptr; };
+    if (pixfmt == 1) {
+        const uint8_t* xb = (const uint8_t*)x;
+        run_partitioned(npix, nthreads, [&](int64_t lo, int64_t n) {
+            dft_bin(xb + lo, stride, n, N, s0, k, off(re, lo), off(im, lo), off(power, lo));
+        });
+    } else if (pixfmt == 2) {
+        const uint16_t* xh = (const uint16_t*)x;
+        run_partitioned(npix, nthreads, [&](int64_t lo, int64_t n) {
+            dft_bin(xh + lo, stride, n, N, s0, k, off(re, lo), off(im, lo), off(power, lo));
+        });
+    } else {
+        return -1;
+    }
+    return 0;
+}
+
+}  // extern "C"

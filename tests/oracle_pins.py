@@ -1,0 +1,249 @@
+"""Pins for the CPU oracle: facts fixed by the paper's definitions and by
+mathematics, not by the oracle itself.
+
+Each ``pin_*`` function takes an ``oracle.Oracle`` instance and raises
+AssertionError when that oracle disagrees with the pinned fact. They are run
+against the real oracle (tests/test_oracle_pins.py) and against deliberately
+broken copies of it (tests/test_oracle_mutants.py), where every copy must fail
+at least one pin.
+
+Notation (Methods, "Numerical simulations"; four samples per period):
+omega t_s = pi s / 2, sigma_s = sin(pi s / 2) = 1, 0, -1, 0 and
+gamma_s = cos(pi s / 2) = 0, -1, 0, 1 for s mod 4 = 1, 2, 3, 0;
+S = sum sigma_s x_s, C = sum gamma_s x_s, R = sqrt(S^2 + C^2),
+phase = atan2(-S, C); X_k = sum_s x_s exp(-2 pi i k s / N).
+"""
+import math
+import os
+
+import numpy as np
+
+GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
+
+
+def _assert_eq(a, b, what):
+    a = np.asarray(a)
+    b = np.asarray(b)
+    if not np.array_equal(a, b):
+        raise AssertionError("%s: got %r expected %r" % (what, a.ravel()[:8], b.ravel()[:8]))
+
+
+def _assert_close(a, b, rtol, atol, what):
+    a = np.asarray(a, np.float64)
+    b = np.asarray(b, np.float64)
+    if not np.allclose(a, b, rtol=rtol, atol=atol):
+        i = int(np.argmax(np.abs(a - b).ravel()))
+        raise AssertionError("%s: max err at %d: got %r expected %r" % (what, i, a.ravel()[i], b.ravel()[i]))
+
+
+def pin_reference_tables(o):
+    # sin(0), sin(pi/2), sin(pi), sin(3pi/2) and the cosines of the same angles.
+    s, c = o.reference_tables()
+    _assert_eq(s, [0, 1, 0, -1], "sin table")
+    _assert_eq(c, [1, 0, -1, 0], "cos table")
+
+
+# Square wave of height a, high on two consecutive residues of s mod 4, on a
+# background B. Per period the sums are read off sigma/gamma by hand:
+#   high {1,2}: S = a*1 + a*0 = +a,  C = a*0 + a*(-1) = -a, phase = atan2(-a,-a) = -3pi/4
+#   high {2,3}: S = 0 - a     = -a,  C = -a + 0       = -a, phase = atan2( a,-a) = +3pi/4
+#   high {3,0}: S = -a + 0    = -a,  C = 0 + a        = +a, phase = atan2( a, a) = +pi/4
+#   high {0,1}: S = 0 + a     = +a,  C = a + 0        = +a, phase = atan2(-a, a) = -pi/4
+# The background contributes nothing (each table sums to zero over a period),
+# and R = sqrt(2) a P for P = N/4 periods, whatever the phase.
+SQUARE_WAVE_TABLE = {
+    (1, 2): (+1, -1, -3 * math.pi / 4),
+    (2, 3): (-1, -1, +3 * math.pi / 4),
+    (3, 0): (-1, +1, +math.pi / 4),
+    (0, 1): (+1, +1, -math.pi / 4),
+}
+
+
+def pin_square_wave(o):
+    for (r1, r2), (ks, kc, ph) in SQUARE_WAVE_TABLE.items():
+        for N, s0, a, B in [(8, 1, 2, 100), (64, 1, 2, 100), (64, 7, 5, 0), (1024, 1234, 3, 4000),
+                            (12, 3, 255, 0)]:
+            P = N // 4
+            s = np.arange(s0, s0 + N)
+            high = ((s % 4) == r1) | ((s % 4) == r2)
+            x = (B + a * high).astype(np.uint16).reshape(N, 1)
+            S, C, R, phase = o.qld(x, s0=s0)
+            _assert_eq(S, [ks * a * P], "square wave S %s N=%d s0=%d" % ((r1, r2), N, s0))
+            _assert_eq(C, [kc * a * P], "square wave C %s N=%d s0=%d" % ((r1, r2), N, s0))
+            _assert_close(R, [math.sqrt(2.0) * a * P], 1e-14, 0, "square wave R")
+            _assert_close(phase, [ph], 0, 1e-14, "square wave phase")
+
+
+# Integer tone x_s = B + A cos(pi s/2 + phi0) with A cos(phi0) = c and
+# A sin(phi0) = d integers: cos(pi s/2 + phi0) expands to
+# c*cos(pi s/2) - d*sin(pi s/2). Summing over whole periods, where
+# sum sin^2 = sum cos^2 = N/2 and sum sin*cos = sum sin = sum cos = 0:
+#   S = -(N/2) d,  C = (N/2) c,  R = (N/2) sqrt(c^2+d^2) = (N/2) A,  phase = phi0.
+def pin_tone(o):
+    for (c, d) in [(3, 4), (-5, 12), (7, 0), (0, -9), (-8, -6), (1, 1)]:
+        for N, s0 in [(4, 1), (16, 2), (64, 3), (256, 4), (40, 1001)]:
+            s = np.arange(s0, s0 + N, dtype=np.float64)
+            tone = c * np.cos(np.pi * s / 2) - d * np.sin(np.pi * s / 2)
+            x = (100 + np.rint(tone)).astype(np.uint8).reshape(N, 1, 1)
+            S, C, R, phase = o.qld(x, s0=s0)
+            _assert_eq(S.ravel(), [-(N // 2) * d], "tone S (c,d)=%s N=%d s0=%d" % ((c, d), N, s0))
+            _assert_eq(C.ravel(), [(N // 2) * c], "tone C (c,d)=%s N=%d s0=%d" % ((c, d), N, s0))
+            _assert_close(R.ravel(), [(N / 2) * math.hypot(c, d)], 1e-14, 0, "tone R")
+            _assert_close(phase.ravel(), [math.atan2(d, c)], 0, 1e-14, "tone phase")
+
+
+# Constant background, the Nyquist tone B + a(-1)^s and any period-2 sequence
+# carry nothing at f_s/4: S = C = 0 exactly, so R = 0 and phase = 0.
+def pin_zeros(o):
+    rng = np.random.default_rng(5)
+    for N, s0 in [(4, 1), (32, 6), (1024, 99)]:
+        s = np.arange(s0, s0 + N)
+        cols = [np.full(N, 77), 100 + 9 * (-1) ** s]
+        u, v = rng.integers(0, 4096, 2)
+        cols.append(np.where(s % 2 == 0, u, v))
+        x = np.stack(cols, axis=1).astype(np.uint16)
+        S, C, R, phase = o.qld(x, s0=s0)
+        _assert_eq(S, [0, 0, 0], "zeros S")
+        _assert_eq(C, [0, 0, 0], "zeros C")
+        _assert_eq(R, [0.0, 0.0, 0.0], "zeros R")
+        _assert_eq(phase, [0.0, 0.0, 0.0], "zeros phase")
+
+
+# Ramp x_s = s pins the time origin and the signs. Over four frames s0..s0+3,
+# by hand from the tables:
+#   s0 = 1 mod 4: S = 1 - 3 = -2,  C = -2 + 4 = +2
+#   s0 = 2 mod 4: S = -3 + 5 = +2, C = -2 + 4 = +2
+#   s0 = 3 mod 4: S = -3 + 5 = +2, C = 4 - 6  = -2
+#   s0 = 0 mod 4: S = 5 - 7 = -2,  C = 4 - 6  = -2
+# Shifting the block by 4 adds 4 * (table sum) = 0, so a window of P periods
+# gives P times these values.
+RAMP_TABLE = {1: (-2, +2), 2: (+2, +2), 3: (+2, -2), 0: (-2, -2)}
+
+
+def pin_ramp(o):
+    for s0 in [1, 2, 3, 4, 5, 10, 11, 100, 4093]:
+        for N in [4, 8, 64, 256]:
+            x = np.arange(s0, s0 + N).astype(np.uint16).reshape(N, 1)
+            S, C = o.quadrature_sums(x, s0=s0)
+            es, ec = RAMP_TABLE[s0 % 4]
+            P = N // 4
+            _assert_eq(S, [es * P], "ramp S s0=%d N=%d" % (s0, N))
+            _assert_eq(C, [ec * P], "ramp C s0=%d N=%d" % (s0, N))
+
+
+# Against numpy's FFT of the window y_i = x_{s0+i}: Y_k = sum_i y_i e^{-2 pi i k i/N},
+# so the absolute-index bin is X_k = e^{-2 pi i k s0 / N} Y_k.
+def pin_dft_vs_numpy(o):
+    rng = np.random.default_rng(11)
+    for N in [4, 8, 12, 16, 20]:
+        for s0 in [1, 3, 22]:
+            x = rng.integers(0, 4096, size=(N, 5)).astype(np.uint16)
+            Y = np.fft.fft(x.astype(np.float64), axis=0)
+            for k in range(N):
+                re, im, pw = o.dft_bin(x, k, s0=s0)
+                X = Y[k] * np.exp(-2j * np.pi * k * s0 / N)
+                scale = float(x.astype(np.float64).sum())
+                _assert_close(re, X.real, 0, 1e-12 * scale, "dft re N=%d k=%d s0=%d" % (N, k, s0))
+                _assert_close(im, X.imag, 0, 1e-12 * scale, "dft im N=%d k=%d s0=%d" % (N, k, s0))
+                _assert_close(pw, np.abs(Y[k]) ** 2, 1e-12, 1e-12 * scale ** 2, "dft power")
+
+
+# Parseval: sum_k |X_k|^2 = N sum_s x_s^2.
+def pin_parseval(o):
+    rng = np.random.default_rng(12)
+    for N in [4, 8, 16, 24]:
+        x = rng.integers(0, 256, size=(N, 7)).astype(np.uint8)
+        tot = np.zeros(7)
+        for k in range(N):
+            tot += o.dft_bin(x, k, s0=2)[2]
+        _assert_close(tot, N * (x.astype(np.float64) ** 2).sum(axis=0), 1e-12, 0, "parseval")
+
+
+# X_{N/4} = sum x_s (cos(pi s/2) - i sin(pi s/2)) = C - i S, X_0 = sum x_s,
+# X_{N/2} = sum (-1)^s x_s.
+def pin_dft_identities(o):
+    rng = np.random.default_rng(13)
+    for N, s0 in [(8, 1), (64, 5), (1024, 3)]:
+        x = rng.integers(0, 4096, size=(N, 6)).astype(np.uint16)
+        S, C = o.quadrature_sums(x, s0=s0)
+        re, im, pw = o.dft_bin(x, N // 4, s0=s0)
+        scale = float(x.astype(np.float64).sum())
+        _assert_close(re, C, 0, 1e-12 * scale, "X_{N/4} real part = C")
+        _assert_close(im, -S, 0, 1e-12 * scale, "X_{N/4} imaginary part = -S")
+        _assert_close(pw, S.astype(np.float64) ** 2 + C.astype(np.float64) ** 2, 1e-12, 1e-9,
+                      "|X_{N/4}|^2 = S^2 + C^2")
+        re0, im0, _ = o.dft_bin(x, 0, s0=s0)
+        _assert_close(re0, x.astype(np.float64).sum(axis=0), 0, 1e-9, "X_0")
+        _assert_close(im0, 0.0, 0, 1e-9, "X_0 imaginary")
+        sgn = (-1.0) ** np.arange(s0, s0 + N)
+        reh, imh, _ = o.dft_bin(x, N // 2, s0=s0)
+        _assert_close(reh, (sgn[:, None] * x).sum(axis=0), 0, 1e-9 * scale, "X_{N/2}")
+        _assert_close(imh, 0.0, 0, 1e-9 * scale, "X_{N/2} imaginary")
+
+
+def pin_amplitude_phase_cases(o):
+    S = np.array([0, 0, 3, -1, 0, 5, -7], np.int64)
+    C = np.array([0, -4, 4, 0, 9, 0, -7], np.int64)
+    R, ph = o.amplitude_phase(S, C)
+    _assert_close(R, [0, 4, 5, 1, 9, 5, 7 * math.sqrt(2)], 1e-15, 0, "R cases")
+    # S = 0, C < 0 lies on the branch cut: the phase is +pi (range (-pi, pi]).
+    _assert_close(ph, [0, math.pi, math.atan2(-3, 4), math.pi / 2, 0, -math.pi / 2, 3 * math.pi / 4],
+                  0, 1e-15, "phase cases")
+    big = np.array([2 ** 31 - 1], np.int64)
+    Rb, _ = o.amplitude_phase(big, big)
+    _assert_close(Rb, [(2 ** 31 - 1) * math.sqrt(2)], 1e-15, 0, "R at the int32 limit")
+
+
+def pin_threads_agree(o):
+    rng = np.random.default_rng(14)
+    x = rng.integers(0, 65536, size=(32, 1001)).astype(np.uint16)
+    S1, C1 = o.quadrature_sums(x, s0=9, nthreads=1)
+    S4, C4 = o.quadrature_sums(x, s0=9, nthreads=4)
+    _assert_eq(S4, S1, "threaded S")
+    _assert_eq(C4, C1, "threaded C")
+    p1 = o.dft_bin(x, 3, s0=9, nthreads=1)[2]
+    p4 = o.dft_bin(x, 3, s0=9, nthreads=7)[2]
+    _assert_eq(p4, p1, "threaded dft")
+
+
+def load_golden(name):
+    """Parse a tests/golden fixture: '#' comments, then 'key: v v v' lines."""
+    out = {}
+    with open(os.path.join(GOLDEN, name)) as f:
+        for line in f:
+            line = line.split("#", 1)[0].strip()
+            if not line:
+                continue
+            key, vals = line.split(":", 1)
+            out[key.strip()] = [int(v) for v in vals.split()]
+    return out
+
+
+def pin_golden_worked_example(o):
+    g = load_golden("qld_worked_example.txt")
+    N = g["N"][0]
+    npix = g["npix"][0]
+    s0 = g["s0"][0]
+    x = np.array(g["frames"], np.uint16).reshape(N, npix)
+    S, C = o.quadrature_sums(x, s0=s0)
+    _assert_eq(S, g["S"], "golden S")
+    _assert_eq(C, g["C"], "golden C")
+    R, _ = o.amplitude_phase(S, C)
+    _assert_close(R ** 2, g["R2"], 1e-13, 0, "golden R^2")
+    _assert_close(o.dft_bin(x, 0, s0=s0)[0], g["X0"], 0, 1e-9, "golden X_0")
+    _assert_close(o.dft_bin(x, N // 2, s0=s0)[0], g["XN2"], 0, 1e-9, "golden X_{N/2}")
+
+
+ALL_PINS = [
+    pin_reference_tables,
+    pin_square_wave,
+    pin_tone,
+    pin_zeros,
+    pin_ramp,
+    pin_dft_vs_numpy,
+    pin_parseval,
+    pin_dft_identities,
+    pin_amplitude_phase_cases,
+    pin_threads_agree,
+    pin_golden_worked_example,
+]
