@@ -1,0 +1,160 @@
+/* qld.h -- C ABI of the B300 quadrature lock-in discrimination (QLD) library.
+ *
+ * The library computes, for every pixel of a stream of camera frames sampled
+ * at four times the source modulation frequency, the quadrature lock-in sums
+ * of the paper (Methods, "Numerical simulations": the equation for R(j,k))
+ *
+ *     S = sum_{s in window} x_s * sin(pi s / 2),
+ *     C = sum_{s in window} x_s * cos(pi s / 2),
+ *
+ * exactly in int32 over a sliding window of the last N frames, the amplitude
+ * R = sqrt(S^2 + C^2) and phase atan2(-S, C) images, and the single-bin DFT
+ * power |X_k|^2 with X_k = sum_s x_s exp(-2 pi i k s / N) (Methods, the FFT
+ * map the paper compares QLD against).
+ *
+ * Frame index convention: s is the absolute 1-based index of a frame in the
+ * stream (the first frame ever pushed has s = 1; Methods: t_s = s dt,
+ * s = 1, 2, ...). After T frames have been pushed the window is
+ * s = T-N+1 .. T. At four samples per period sin(pi s/2) and cos(pi s/2)
+ * take only the values 0, +1, -1, so S and C are signed sums of frame
+ * values and need no multiplications.
+ *
+ * Memory: all frame, image and sum pointers are DEVICE pointers unless the
+ * function name ends in _host. Frames are laid out [count][H][W], row-major,
+ * contiguous, uint8 (QLD_U8) or uint16 (QLD_U16, 12- or 16-bit data in the
+ * low bits). Images are float32 [H][W]; sums are int32 [H][W]. Any pointer
+ * alignment and any W are accepted (unaligned inputs take a slower scalar
+ * path). The context owns its ring buffer, sums and scratch; the caller owns
+ * every pointer it passes.
+ *
+ * Streams: qld_push_frames and its variants enqueue on the stream they are
+ * given and make it the context's current stream; every other call enqueues
+ * on the context's current stream. All calls are asynchronous with respect
+ * to the host except qld_create, qld_destroy and qld_sync. A frame buffer may
+ * be reused once its push has completed on that stream.
+ *
+ * Errors: functions returning int return QLD_OK (0) or a negative status.
+ * Argument errors are detected synchronously and change no state. A CUDA
+ * error from a launch or copy is returned as QLD_E_CUDA; an error raised
+ * later by the device is reported by the next call or by qld_sync.
+ * qld_last_error() returns the last non-OK status set on the calling thread.
+ *
+ * Threads: there is no internal locking; a context must not be used by two
+ * host threads at once. Distinct contexts are independent.
+ */
+#ifndef QLD_H
+#define QLD_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct qld_ctx qld_ctx;
+
+enum qld_pixfmt { QLD_U8 = 1, QLD_U16 = 2 };
+
+enum qld_status {
+    QLD_OK = 0,
+    QLD_E_INVAL = -1,     /* bad argument */
+    QLD_E_NOMEM = -2,     /* device allocation failed or over the memory budget */
+    QLD_E_NOT_READY = -3, /* fewer than N frames pushed since creation/reset */
+    QLD_E_CUDA = -4,      /* a CUDA runtime error */
+    QLD_E_TIMEOUT = -5    /* a bounded wait ran out */
+};
+
+/* Largest window. With |x| <= 65535, |S|, |C| <= (N/2) * 65535 < 2^31 for
+ * N <= 65536, so the int32 sums are exact. */
+#define QLD_MAX_N 65536
+
+/* Creates a context for H x W frames of the given pixel format and a window
+ * of N frames (SI, "Timing sequence", item 1: the set-up thread allocates
+ * memory and builds the reference tables; SI closing paragraph: a sliding
+ * window needs a buffer of N frames). N must be a positive multiple of 4 and
+ * at most QLD_MAX_N so the window holds whole modulation periods. Allocates
+ * on the current CUDA device a zeroed ring of N frames, the int32 sums and a
+ * twiddle table: see qld_footprint_bytes. Returns NULL on error
+ * (qld_last_error() gives QLD_E_INVAL or QLD_E_NOMEM). Synchronous. */
+qld_ctx* qld_create(int H, int W, int N, int pixfmt);
+
+/* Device bytes qld_create(H, W, N, pixfmt) would allocate, or a negative
+ * status for invalid arguments. */
+long long qld_footprint_bytes(int H, int W, int N, int pixfmt);
+
+/* Caps the device bytes that contexts created afterwards in this process may
+ * hold in total (0 = no cap). qld_create fails with QLD_E_NOMEM when the cap
+ * would be exceeded. Used for admission by memory footprint and to test
+ * allocation failure without exhausting the device. */
+void qld_set_mem_budget(long long bytes);
+long long qld_mem_in_use(void);
+
+/* Frees the context and everything it owns. Waits for its pending work. */
+void qld_destroy(qld_ctx* ctx);
+
+/* Pushes `count` frames (device, [count][H][W]) into the window on `stream`
+ * (a cudaStream_t; NULL = the legacy default stream), frame i getting the
+ * absolute index frames_pushed + 1 + i (SI, "Timing sequence", item 3:
+ * every frame updates the two quadrature accumulators as it arrives). For
+ * each frame s the ring slot s mod N is read (frame s - N, or zero while the
+ * window fills), overwritten with x_s, and the difference x_s - x_{s-N} is
+ * added to S with sign sin(pi s/2) or to C with sign cos(pi s/2). count = 0
+ * is a no-op; count > N behaves as count sequential pushes (only the last N
+ * frames remain). Returns QLD_E_INVAL for a NULL frame pointer with
+ * count > 0 or count < 0. */
+int qld_push_frames(qld_ctx* ctx, const void* frames, int count, void* stream);
+
+/* Writes the amplitude R = sqrt(S^2 + C^2) and phase atan2(-S, C) images
+ * (device float32 [H][W]; either may be NULL) of the current window (Methods,
+ * R(j,k); SI item 3: the components are squared and added after the required
+ * number of frames). Phase is in (-pi, pi], 0 where S = C = 0. Returns
+ * QLD_E_NOT_READY until N frames have been pushed. */
+int qld_image(qld_ctx* ctx, float* amp, float* phase);
+
+/* qld_push_frames followed by qld_image in one kernel: the image is written
+ * while S and C are still in registers. Requires that the window is full
+ * after the push (else QLD_E_NOT_READY and nothing is done). */
+int qld_push_image(qld_ctx* ctx, const void* frames, int count, void* stream, float* amp, float* phase);
+
+/* Writes |X_k|^2 for every pixel (device float32 [H][W]), X_k the DFT bin k
+ * of the pixel's time series over the current window with absolute frame
+ * indices (Methods, the map |F(j,k,omega_q)|^2). 0 <= k < N. Accumulates in
+ * float32 with twiddles rounded from FP64. For k = N/4, X_k = C - iS.
+ * Returns QLD_E_NOT_READY until N frames have been pushed. */
+int qld_fft_bin(qld_ctx* ctx, int k, float* out);
+
+/* Host-buffer variants: frames are read from, and images written to, HOST
+ * memory (pinned memory makes the copies asynchronous). The copies and the
+ * kernels are stream-ordered on the context's stream; results in host memory
+ * are valid after qld_sync. The context allocates a device staging area on
+ * first use (not counted in qld_footprint_bytes). */
+int qld_push_frames_host(qld_ctx* ctx, const void* host_frames, int count, void* stream);
+int qld_image_host(qld_ctx* ctx, float* amp_host, float* phase_host);
+int qld_fft_bin_host(qld_ctx* ctx, int k, float* out_host);
+
+/* Copies the exact int32 sums S and C (device [H][W]; either may be NULL).
+ * Valid at any time (partial sums while the window fills). */
+int qld_get_iq(qld_ctx* ctx, int32_t* S, int32_t* C);
+
+/* Empties the window: zeroes the ring and the sums, frames_pushed = 0. */
+int qld_reset(qld_ctx* ctx);
+
+/* Frames pushed since creation or the last reset. -1 for NULL. */
+long long qld_frames_pushed(const qld_ctx* ctx);
+
+/* Waits for the context's stream; returns any pending CUDA error. */
+int qld_sync(qld_ctx* ctx);
+
+/* The context's current stream (a cudaStream_t). */
+void* qld_stream(const qld_ctx* ctx);
+
+/* Status text; last status set on this thread; version string. */
+const char* qld_strerror(int status);
+int qld_last_error(void);
+const char* qld_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* QLD_H */

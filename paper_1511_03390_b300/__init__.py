@@ -1,0 +1,243 @@
+"""Python binding of the B300 QLD library (libqld.so, C ABI in include/qld.h).
+
+Argument marshalling only: every computation runs in the library's CUDA
+kernels. Device buffers are torch CUDA tensors (or raw integer addresses);
+streams are torch.cuda.Stream objects, raw cudaStream_t integers, or None for
+torch's current stream. The functions carry the C names.
+
+The package refuses to import when libqld.so has not been built: there is no
+fallback path. Build it with ``python -m paper_1511_03390_b300.build``.
+"""
+import ctypes
+import os
+
+from . import build as _build
+
+__all__ = [
+    "QLD_U8", "QLD_U16", "QLD_OK", "QLD_E_INVAL", "QLD_E_NOMEM", "QLD_E_NOT_READY", "QLD_E_CUDA",
+    "QLD_E_TIMEOUT", "QLD_MAX_N", "QLDError", "Context", "qld_create", "qld_destroy", "qld_push_frames",
+    "qld_push_image", "qld_image", "qld_fft_bin", "qld_push_frames_host", "qld_image_host",
+    "qld_fft_bin_host", "qld_get_iq", "qld_reset", "qld_frames_pushed", "qld_sync", "qld_stream",
+    "qld_strerror", "qld_last_error", "qld_version", "qld_footprint_bytes", "qld_set_mem_budget",
+    "qld_mem_in_use", "LIB_PATH", "lib",
+]
+
+QLD_U8, QLD_U16 = 1, 2
+QLD_OK, QLD_E_INVAL, QLD_E_NOMEM, QLD_E_NOT_READY, QLD_E_CUDA, QLD_E_TIMEOUT = 0, -1, -2, -3, -4, -5
+QLD_MAX_N = 65536
+
+LIB_PATH = _build.LIB
+if not os.path.exists(LIB_PATH):
+    raise ImportError("libqld.so is not built (%s); run `python -m paper_1511_03390_b300.build`" % LIB_PATH)
+
+_p = ctypes.c_void_p
+_i = ctypes.c_int
+_ll = ctypes.c_longlong
+
+lib = ctypes.CDLL(LIB_PATH)
+_SIGS = {
+    "qld_create": ([_i, _i, _i, _i], _p),
+    "qld_footprint_bytes": ([_i, _i, _i, _i], _ll),
+    "qld_set_mem_budget": ([_ll], None),
+    "qld_mem_in_use": ([], _ll),
+    "qld_destroy": ([_p], None),
+    "qld_push_frames": ([_p, _p, _i, _p], _i),
+    "qld_push_image": ([_p, _p, _i, _p, _p, _p], _i),
+    "qld_image": ([_p, _p, _p], _i),
+    "qld_fft_bin": ([_p, _i, _p], _i),
+    "qld_push_frames_host": ([_p, _p, _i, _p], _i),
+    "qld_image_host": ([_p, _p, _p], _i),
+    "qld_fft_bin_host": ([_p, _i, _p], _i),
+    "qld_get_iq": ([_p, _p, _p], _i),
+    "qld_reset": ([_p], _i),
+    "qld_frames_pushed": ([_p], _ll),
+    "qld_sync": ([_p], _i),
+    "qld_stream": ([_p], _p),
+    "qld_strerror": ([_i], ctypes.c_char_p),
+    "qld_last_error": ([], _i),
+    "qld_version": ([], ctypes.c_char_p),
+}
+for _name, (_args, _res) in _SIGS.items():
+    _f = getattr(lib, _name)
+    _f.argtypes = _args
+    _f.restype = _res
+
+
+class QLDError(RuntimeError):
+    def __init__(self, status, where):
+        self.status = status
+        super().__init__("%s: %s (%d)" % (where, lib.qld_strerror(status).decode(), status))
+
+
+def _check(rc, where):
+    if rc != QLD_OK:
+        raise QLDError(rc, where)
+    return rc
+
+
+def _addr(buf, nbytes_needed=None, what="buffer"):
+    """Device/host address of a tensor, numpy array or integer (None -> NULL)."""
+    if buf is None:
+        return None
+    if isinstance(buf, int):
+        return buf
+    if hasattr(buf, "data_ptr"):  # torch tensor
+        if not buf.is_contiguous():
+            raise ValueError("%s must be contiguous" % what)
+        if nbytes_needed is not None and buf.numel() * buf.element_size() < nbytes_needed:
+            raise ValueError("%s holds %d bytes, %d needed" % (what, buf.numel() * buf.element_size(),
+                                                               nbytes_needed))
+        return buf.data_ptr()
+    if hasattr(buf, "__array_interface__"):  # numpy array
+        if not buf.flags["C_CONTIGUOUS"]:
+            raise ValueError("%s must be C-contiguous" % what)
+        if nbytes_needed is not None and buf.nbytes < nbytes_needed:
+            raise ValueError("%s holds %d bytes, %d needed" % (what, buf.nbytes, nbytes_needed))
+        return buf.__array_interface__["data"][0]
+    raise TypeError("unsupported %s type %r" % (what, type(buf)))
+
+
+def _stream(stream):
+    if stream is None:
+        import torch
+
+        return torch.cuda.current_stream().cuda_stream
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream
+
+
+class Context:
+    """A qld_ctx handle with its geometry."""
+
+    def __init__(self, handle, H, W, N, pixfmt):
+        self.handle = handle
+        self.H, self.W, self.N, self.pixfmt = H, W, N, pixfmt
+        self.npix = H * W
+        self.frame_bytes = self.npix * pixfmt
+
+    def __del__(self):
+        if getattr(self, "handle", None):
+            try:
+                lib.qld_destroy(self.handle)
+            except Exception:
+                pass
+            self.handle = None
+
+    def destroy(self):
+        if self.handle:
+            lib.qld_destroy(self.handle)
+            self.handle = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.destroy()
+
+
+def _h(ctx):
+    if ctx is None or not ctx.handle:
+        raise ValueError("invalid (destroyed) context")
+    return ctx.handle
+
+
+def qld_create(H, W, N, pixfmt):
+    h = lib.qld_create(int(H), int(W), int(N), int(pixfmt))
+    if not h:
+        raise QLDError(lib.qld_last_error(), "qld_create")
+    return Context(h, int(H), int(W), int(N), int(pixfmt))
+
+
+def qld_destroy(ctx):
+    ctx.destroy()
+
+
+def qld_footprint_bytes(H, W, N, pixfmt):
+    return lib.qld_footprint_bytes(int(H), int(W), int(N), int(pixfmt))
+
+
+def qld_set_mem_budget(nbytes):
+    lib.qld_set_mem_budget(int(nbytes))
+
+
+def qld_mem_in_use():
+    return lib.qld_mem_in_use()
+
+
+def _count_of(frames, count, frame_bytes):
+    if count is not None:
+        return int(count)
+    if hasattr(frames, "shape") and len(frames.shape) >= 1:
+        nbytes = frames.nbytes if hasattr(frames, "nbytes") else frames.numel() * frames.element_size()
+        return nbytes // frame_bytes
+    raise ValueError("count is required when frames is a raw address")
+
+
+def qld_push_frames(ctx, frames, count=None, stream=None):
+    n = _count_of(frames, count, ctx.frame_bytes)
+    a = _addr(frames, n * ctx.frame_bytes, "frames")
+    return _check(lib.qld_push_frames(_h(ctx), a, n, _stream(stream)), "qld_push_frames")
+
+
+def qld_push_image(ctx, frames, count=None, stream=None, amp=None, phase=None):
+    n = _count_of(frames, count, ctx.frame_bytes)
+    a = _addr(frames, n * ctx.frame_bytes, "frames")
+    return _check(lib.qld_push_image(_h(ctx), a, n, _stream(stream), _addr(amp, 4 * ctx.npix, "amp"),
+                                     _addr(phase, 4 * ctx.npix, "phase")), "qld_push_image")
+
+
+def qld_image(ctx, amp=None, phase=None):
+    return _check(lib.qld_image(_h(ctx), _addr(amp, 4 * ctx.npix, "amp"), _addr(phase, 4 * ctx.npix, "phase")),
+                  "qld_image")
+
+
+def qld_fft_bin(ctx, k, out):
+    return _check(lib.qld_fft_bin(_h(ctx), int(k), _addr(out, 4 * ctx.npix, "out")), "qld_fft_bin")
+
+
+def qld_push_frames_host(ctx, frames, count=None, stream=None):
+    n = _count_of(frames, count, ctx.frame_bytes)
+    a = _addr(frames, n * ctx.frame_bytes, "host frames")
+    return _check(lib.qld_push_frames_host(_h(ctx), a, n, _stream(stream)), "qld_push_frames_host")
+
+
+def qld_image_host(ctx, amp=None, phase=None):
+    return _check(lib.qld_image_host(_h(ctx), _addr(amp, 4 * ctx.npix, "amp"), _addr(phase, 4 * ctx.npix, "phase")),
+                  "qld_image_host")
+
+
+def qld_fft_bin_host(ctx, k, out):
+    return _check(lib.qld_fft_bin_host(_h(ctx), int(k), _addr(out, 4 * ctx.npix, "out")), "qld_fft_bin_host")
+
+
+def qld_get_iq(ctx, S=None, C=None):
+    return _check(lib.qld_get_iq(_h(ctx), _addr(S, 4 * ctx.npix, "S"), _addr(C, 4 * ctx.npix, "C")), "qld_get_iq")
+
+
+def qld_reset(ctx):
+    return _check(lib.qld_reset(_h(ctx)), "qld_reset")
+
+
+def qld_frames_pushed(ctx):
+    return lib.qld_frames_pushed(_h(ctx))
+
+
+def qld_sync(ctx):
+    return _check(lib.qld_sync(_h(ctx)), "qld_sync")
+
+
+def qld_stream(ctx):
+    return lib.qld_stream(_h(ctx)) or 0
+
+
+def qld_strerror(status):
+    return lib.qld_strerror(int(status)).decode()
+
+
+def qld_last_error():
+    return lib.qld_last_error()
+
+
+def qld_version():
+    return lib.qld_version().decode()

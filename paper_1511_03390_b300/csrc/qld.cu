@@ -1,0 +1,478 @@
+// qld.cu -- context management and the C ABI declared in include/qld.h.
+//
+// A context owns, in device memory:
+//   ring   N slots of one frame each (slot stride padded to 256 bytes): the
+//          sliding buffer of N frames (SI, closing paragraph);
+//   S, C   int32 quadrature sums, padded to a multiple of 64 pixels
+//          (SI "Timing sequence" item 3: the two 2-D accumulators);
+//   tw     float2 twiddles of the last DFT bin requested (SI item 1: the
+//          pre-calculated sine / cosine tables).
+// Frame s (absolute, 1-based) lives in slot s mod N.
+
+#include <atomic>
+#include <cstdint>
+#include <cstdio>
+#include <cstring>
+#include <cuda_runtime.h>
+
+#include "qld.h"
+#include "qld_kernels.cuh"
+
+struct qld_ctx {
+    int H, W, N, pixfmt, bpp;
+    long long npix;
+    long long npad;         // padded pixel count of S and C
+    long long slot_stride;  // bytes
+    int device;
+    uint8_t* ring;
+    int32_t* S;
+    int32_t* C;
+    float2* tw;
+    int tw_k;               // bin whose twiddles are in tw, -1 if none
+    long long pushed;
+    cudaStream_t stream;
+    long long footprint;
+    // host-buffer variants
+    uint8_t* stage;
+    long long stage_bytes;
+    float* out_dev;
+    long long out_elems;
+};
+
+namespace {
+
+thread_local int g_last_error = QLD_OK;
+std::atomic<long long> g_budget{0};
+std::atomic<long long> g_in_use{0};
+
+int set_err(int st) {
+    if (st != QLD_OK) g_last_error = st;
+    return st;
+}
+
+long long round_up(long long x, long long m) { return (x + m - 1) / m * m; }
+
+bool valid_dims(int H, int W, int N, int pixfmt) {
+    if (H < 1 || W < 1 || N < 4 || N > QLD_MAX_N || (N % 4) != 0) return false;
+    if (pixfmt != QLD_U8 && pixfmt != QLD_U16) return false;
+    const long long npix = (long long)H * W;
+    return npix <= (1ll << 31) - 1;
+}
+
+struct Layout {
+    long long npix, npad, slot_stride, ring_bytes, sums_bytes, tw_bytes, total;
+};
+
+Layout layout_of(int H, int W, int N, int pixfmt) {
+    Layout L;
+    L.npix = (long long)H * W;
+    L.npad = round_up(L.npix, 64);
+    L.slot_stride = round_up(L.npix * pixfmt, 256);
+    L.ring_bytes = L.slot_stride * N;
+    L.sums_bytes = L.npad * (long long)sizeof(int32_t);
+    L.tw_bytes = round_up((long long)N * (long long)sizeof(float2), 256);
+    L.total = L.ring_bytes + 2 * L.sums_bytes + L.tw_bytes;
+    return L;
+}
+
+// Makes the context's device current for the duration of a call.
+struct DeviceGuard {
+    int prev = -1;
+    bool ok = true;
+    explicit DeviceGuard(int dev) {
+        if (cudaGetDevice(&prev) != cudaSuccess) {
+            ok = false;
+            return;
+        }
+        if (prev != dev && cudaSetDevice(dev) != cudaSuccess) ok = false;
+    }
+    ~DeviceGuard() {
+        int cur = -1;
+        if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+    }
+};
+
+// Any CUDA error raised since the last call (launch or asynchronous).
+int pending_error() {
+    const cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? QLD_OK : QLD_E_CUDA;
+}
+
+bool aligned(const void* p, unsigned a) { return ((uintptr_t)p % a) == 0; }
+
+unsigned blocks_for(long long n, int threads) { return (unsigned)((n + threads - 1) / threads); }
+
+template <bool RESET, bool EPI>
+void launch_push_t(const qld_ctx* c, const qldk::PushArgs& a, bool vec) {
+    if (vec) {
+        if (c->pixfmt == QLD_U16)
+            qldk::push_vec_kernel<uint16_t, RESET, EPI><<<blocks_for(a.nvec, 128), 128, 0, c->stream>>>(a);
+        else
+            qldk::push_vec_kernel<uint8_t, RESET, EPI><<<blocks_for(a.nvec, 128), 128, 0, c->stream>>>(a);
+    } else {
+        if (c->pixfmt == QLD_U16)
+            qldk::push_scalar_kernel<uint16_t, RESET, EPI><<<blocks_for(a.npix, 256), 256, 0, c->stream>>>(a);
+        else
+            qldk::push_scalar_kernel<uint8_t, RESET, EPI><<<blocks_for(a.npix, 256), 256, 0, c->stream>>>(a);
+    }
+}
+
+// Enqueues the push of `count` device frames (and, if epi, the image) on
+// c->stream. Arguments are already validated.
+int enqueue_push(qld_ctx* c, const uint8_t* frames, int count, bool epi, float* amp, float* phase) {
+    if (count == 0) return QLD_OK;
+    const long long frame_bytes = c->npix * c->bpp;
+    const bool reset = count >= c->N;
+    const int first = reset ? count - c->N : 0;
+    qldk::PushArgs a;
+    a.frames = frames + (long long)first * frame_bytes;
+    a.frame_stride = frame_bytes;
+    a.nf = reset ? c->N : count;
+    a.s_first = c->pushed + first + 1;
+    a.ring = c->ring;
+    a.slot_stride = c->slot_stride;
+    a.N = c->N;
+    a.S = c->S;
+    a.C = c->C;
+    a.npix = c->npix;
+    a.amp = amp;
+    a.phase = phase;
+    a.out_aligned = (aligned(amp, 16) && aligned(phase, 16)) ? 1 : 0;
+    const bool vec = aligned(a.frames, 16) && (frame_bytes % qldk::kVecBytes) == 0;
+    a.nvec = vec ? frame_bytes / qldk::kVecBytes : c->npix;
+    if (reset) {
+        if (epi) launch_push_t<true, true>(c, a, vec);
+        else launch_push_t<true, false>(c, a, vec);
+    } else {
+        if (epi) launch_push_t<false, true>(c, a, vec);
+        else launch_push_t<false, false>(c, a, vec);
+    }
+    if (cudaGetLastError() != cudaSuccess) return QLD_E_CUDA;
+    c->pushed += count;
+    return QLD_OK;
+}
+
+int enqueue_image(qld_ctx* c, float* amp, float* phase) {
+    if (!amp && !phase) return QLD_OK;
+    const long long nthr = (c->npix + 3) / 4;
+    const int oa = (aligned(amp, 16) && aligned(phase, 16)) ? 1 : 0;
+    qldk::image_kernel<<<blocks_for(nthr, 256), 256, 0, c->stream>>>(c->S, c->C, c->npix, amp, phase, oa);
+    return cudaGetLastError() == cudaSuccess ? QLD_OK : QLD_E_CUDA;
+}
+
+template <typename T>
+void launch_fftbin_t(const qld_ctx* c, float* out, long long nvec) {
+    // Pixel vectors per CTA: 32 (8 time slices) when there are enough pixels
+    // for two CTAs per SM, fewer (more time slices, reduced by warp shuffles)
+    // for small frames so the grid still covers the GPU.
+    int pv_log = 5;
+    while (pv_log > 2 && (nvec + (1ll << pv_log) - 1) / (1ll << pv_log) < 296) --pv_log;
+    const unsigned grid = (unsigned)((nvec + (1ll << pv_log) - 1) >> pv_log);
+    switch (pv_log) {
+        case 5: qldk::fftbin_kernel<T, 5><<<grid, 256, 0, c->stream>>>(c->ring, c->slot_stride, c->N, c->tw, nvec, c->npix, out); break;
+        case 4: qldk::fftbin_kernel<T, 4><<<grid, 256, 0, c->stream>>>(c->ring, c->slot_stride, c->N, c->tw, nvec, c->npix, out); break;
+        case 3: qldk::fftbin_kernel<T, 3><<<grid, 256, 0, c->stream>>>(c->ring, c->slot_stride, c->N, c->tw, nvec, c->npix, out); break;
+        default: qldk::fftbin_kernel<T, 2><<<grid, 256, 0, c->stream>>>(c->ring, c->slot_stride, c->N, c->tw, nvec, c->npix, out); break;
+    }
+}
+
+int enqueue_fft_bin(qld_ctx* c, int k, float* out) {
+    if (c->tw_k != k) {
+        qldk::twiddle_kernel<<<blocks_for(c->N, 256), 256, 0, c->stream>>>(c->tw, c->N, k);
+        if (cudaGetLastError() != cudaSuccess) return QLD_E_CUDA;
+        c->tw_k = k;
+    }
+    const long long nvec = (c->npix * c->bpp + qldk::kVecBytes - 1) / qldk::kVecBytes;
+    if (c->pixfmt == QLD_U16) launch_fftbin_t<uint16_t>(c, out, nvec);
+    else launch_fftbin_t<uint8_t>(c, out, nvec);
+    return cudaGetLastError() == cudaSuccess ? QLD_OK : QLD_E_CUDA;
+}
+
+void free_ctx_memory(qld_ctx* c) {
+    if (c->ring) cudaFree(c->ring);
+    if (c->S) cudaFree(c->S);
+    if (c->C) cudaFree(c->C);
+    if (c->tw) cudaFree(c->tw);
+    if (c->stage) cudaFree(c->stage);
+    if (c->out_dev) cudaFree(c->out_dev);
+    c->ring = nullptr;
+    c->S = c->C = nullptr;
+    c->tw = nullptr;
+    c->stage = nullptr;
+    c->out_dev = nullptr;
+}
+
+int ensure_stage(qld_ctx* c, long long bytes) {
+    if (c->stage_bytes >= bytes) return QLD_OK;
+    if (c->stage) {
+        cudaStreamSynchronize(c->stream);
+        cudaFree(c->stage);
+        c->stage = nullptr;
+        c->stage_bytes = 0;
+    }
+    if (cudaMalloc(&c->stage, (size_t)bytes) != cudaSuccess) {
+        cudaGetLastError();
+        c->stage = nullptr;
+        return QLD_E_NOMEM;
+    }
+    c->stage_bytes = bytes;
+    return QLD_OK;
+}
+
+int ensure_out(qld_ctx* c, long long elems) {
+    if (c->out_elems >= elems) return QLD_OK;
+    if (c->out_dev) {
+        cudaStreamSynchronize(c->stream);
+        cudaFree(c->out_dev);
+        c->out_dev = nullptr;
+        c->out_elems = 0;
+    }
+    if (cudaMalloc(&c->out_dev, (size_t)elems * sizeof(float)) != cudaSuccess) {
+        cudaGetLastError();
+        c->out_dev = nullptr;
+        return QLD_E_NOMEM;
+    }
+    c->out_elems = elems;
+    return QLD_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* qld_version(void) { return "qld 0.1 (sm_103a)"; }
+
+const char* qld_strerror(int st) {
+    switch (st) {
+        case QLD_OK: return "ok";
+        case QLD_E_INVAL: return "invalid argument";
+        case QLD_E_NOMEM: return "out of device memory or over the memory budget";
+        case QLD_E_NOT_READY: return "window not full: fewer than N frames pushed";
+        case QLD_E_CUDA: return "CUDA runtime error";
+        case QLD_E_TIMEOUT: return "bounded wait timed out";
+        default: return "unknown status";
+    }
+}
+
+int qld_last_error(void) { return g_last_error; }
+
+long long qld_footprint_bytes(int H, int W, int N, int pixfmt) {
+    if (!valid_dims(H, W, N, pixfmt)) return QLD_E_INVAL;
+    return layout_of(H, W, N, pixfmt).total;
+}
+
+void qld_set_mem_budget(long long bytes) { g_budget.store(bytes < 0 ? 0 : bytes); }
+
+long long qld_mem_in_use(void) { return g_in_use.load(); }
+
+qld_ctx* qld_create(int H, int W, int N, int pixfmt) {
+    if (!valid_dims(H, W, N, pixfmt)) {
+        set_err(QLD_E_INVAL);
+        return nullptr;
+    }
+    const Layout L = layout_of(H, W, N, pixfmt);
+    // Reserve against the budget before touching the device.
+    const long long budget = g_budget.load();
+    long long prev = g_in_use.fetch_add(L.total);
+    if (budget > 0 && prev + L.total > budget) {
+        g_in_use.fetch_sub(L.total);
+        set_err(QLD_E_NOMEM);
+        return nullptr;
+    }
+    qld_ctx* c = new qld_ctx();
+    std::memset(c, 0, sizeof(*c));
+    c->H = H;
+    c->W = W;
+    c->N = N;
+    c->pixfmt = pixfmt;
+    c->bpp = pixfmt;
+    c->npix = L.npix;
+    c->npad = L.npad;
+    c->slot_stride = L.slot_stride;
+    c->tw_k = -1;
+    c->footprint = L.total;
+    c->stream = nullptr;
+    int st = QLD_OK;
+    if (cudaGetDevice(&c->device) != cudaSuccess) st = QLD_E_CUDA;
+    if (st == QLD_OK && (cudaMalloc(&c->ring, (size_t)L.ring_bytes) != cudaSuccess ||
+                         cudaMalloc(&c->S, (size_t)L.sums_bytes) != cudaSuccess ||
+                         cudaMalloc(&c->C, (size_t)L.sums_bytes) != cudaSuccess ||
+                         cudaMalloc(&c->tw, (size_t)L.tw_bytes) != cudaSuccess)) {
+        st = QLD_E_NOMEM;
+    }
+    if (st == QLD_OK && (cudaMemset(c->ring, 0, (size_t)L.ring_bytes) != cudaSuccess ||
+                         cudaMemset(c->S, 0, (size_t)L.sums_bytes) != cudaSuccess ||
+                         cudaMemset(c->C, 0, (size_t)L.sums_bytes) != cudaSuccess ||
+                         cudaDeviceSynchronize() != cudaSuccess)) {
+        st = QLD_E_CUDA;
+    }
+    if (st != QLD_OK) {
+        cudaGetLastError();
+        free_ctx_memory(c);
+        delete c;
+        g_in_use.fetch_sub(L.total);
+        set_err(st);
+        return nullptr;
+    }
+    return c;
+}
+
+void qld_destroy(qld_ctx* c) {
+    if (!c) return;
+    {
+        DeviceGuard g(c->device);
+        cudaStreamSynchronize(c->stream);
+        free_ctx_memory(c);
+    }
+    g_in_use.fetch_sub(c->footprint);
+    delete c;
+}
+
+int qld_push_frames(qld_ctx* c, const void* frames, int count, void* stream) {
+    if (!c || count < 0 || (count > 0 && !frames)) return set_err(QLD_E_INVAL);
+    if (c->pixfmt == QLD_U16 && !aligned(frames, 2)) return set_err(QLD_E_INVAL);
+    DeviceGuard g(c->device);
+    if (!g.ok) return set_err(QLD_E_CUDA);
+    if (pending_error() != QLD_OK) return set_err(QLD_E_CUDA);
+    c->stream = (cudaStream_t)stream;
+    return set_err(enqueue_push(c, (const uint8_t*)frames, count, false, nullptr, nullptr));
+}
+
+int qld_push_image(qld_ctx* c, const void* frames, int count, void* stream, float* amp, float* phase) {
+    if (!c || count < 0 || (count > 0 && !frames)) return set_err(QLD_E_INVAL);
+    if (c->pixfmt == QLD_U16 && !aligned(frames, 2)) return set_err(QLD_E_INVAL);
+    if (!aligned(amp, 4) || !aligned(phase, 4)) return set_err(QLD_E_INVAL);
+    if (c->pushed + count < c->N) return set_err(QLD_E_NOT_READY);
+    DeviceGuard g(c->device);
+    if (!g.ok) return set_err(QLD_E_CUDA);
+    if (pending_error() != QLD_OK) return set_err(QLD_E_CUDA);
+    c->stream = (cudaStream_t)stream;
+    if (count == 0) return set_err(enqueue_image(c, amp, phase));
+    return set_err(enqueue_push(c, (const uint8_t*)frames, count, amp || phase, amp, phase));
+}
+
+int qld_image(qld_ctx* c, float* amp, float* phase) {
+    if (!c || !aligned(amp, 4) || !aligned(phase, 4)) return set_err(QLD_E_INVAL);
+    if (c->pushed < c->N) return set_err(QLD_E_NOT_READY);
+    DeviceGuard g(c->device);
+    if (!g.ok) return set_err(QLD_E_CUDA);
+    if (pending_error() != QLD_OK) return set_err(QLD_E_CUDA);
+    return set_err(enqueue_image(c, amp, phase));
+}
+
+int qld_fft_bin(qld_ctx* c, int k, float* out) {
+    if (!c || !out || !aligned(out, 4) || k < 0 || k >= (c ? c->N : 0)) return set_err(QLD_E_INVAL);
+    if (c->pushed < c->N) return set_err(QLD_E_NOT_READY);
+    DeviceGuard g(c->device);
+    if (!g.ok) return set_err(QLD_E_CUDA);
+    if (pending_error() != QLD_OK) return set_err(QLD_E_CUDA);
+    return set_err(enqueue_fft_bin(c, k, out));
+}
+
+int qld_push_frames_host(qld_ctx* c, const void* host_frames, int count, void* stream) {
+    if (!c || count < 0 || (count > 0 && !host_frames)) return set_err(QLD_E_INVAL);
+    DeviceGuard g(c->device);
+    if (!g.ok) return set_err(QLD_E_CUDA);
+    if (pending_error() != QLD_OK) return set_err(QLD_E_CUDA);
+    c->stream = (cudaStream_t)stream;
+    if (count == 0) return QLD_OK;
+    const long long frame_bytes = c->npix * c->bpp;
+    // Stage at most 256 MiB (and at least one frame) per copy; larger pushes
+    // run as consecutive chunks, which is the same as one push.
+    long long chunk = (256ll << 20) / frame_bytes;
+    if (chunk < 1) chunk = 1;
+    if (chunk > count) chunk = count;
+    int st = ensure_stage(c, round_up(chunk * frame_bytes, 256));
+    if (st != QLD_OK) return set_err(st);
+    const uint8_t* src = (const uint8_t*)host_frames;
+    for (long long done = 0; done < count; done += chunk) {
+        const long long n = (count - done < chunk) ? count - done : chunk;
+        if (cudaMemcpyAsync(c->stage, src + done * frame_bytes, (size_t)(n * frame_bytes), cudaMemcpyHostToDevice,
+                            c->stream) != cudaSuccess)
+            return set_err(QLD_E_CUDA);
+        st = enqueue_push(c, c->stage, (int)n, false, nullptr, nullptr);
+        if (st != QLD_OK) return set_err(st);
+    }
+    return QLD_OK;
+}
+
+int qld_image_host(qld_ctx* c, float* amp_host, float* phase_host) {
+    if (!c) return set_err(QLD_E_INVAL);
+    if (c->pushed < c->N) return set_err(QLD_E_NOT_READY);
+    if (!amp_host && !phase_host) return QLD_OK;
+    DeviceGuard g(c->device);
+    if (!g.ok) return set_err(QLD_E_CUDA);
+    if (pending_error() != QLD_OK) return set_err(QLD_E_CUDA);
+    const long long n = c->npad;
+    int st = ensure_out(c, 2 * n);
+    if (st != QLD_OK) return set_err(st);
+    float* da = amp_host ? c->out_dev : nullptr;
+    float* dp = phase_host ? c->out_dev + n : nullptr;
+    st = enqueue_image(c, da, dp);
+    if (st != QLD_OK) return set_err(st);
+    const size_t bytes = (size_t)c->npix * sizeof(float);
+    if (amp_host && cudaMemcpyAsync(amp_host, da, bytes, cudaMemcpyDeviceToHost, c->stream) != cudaSuccess)
+        return set_err(QLD_E_CUDA);
+    if (phase_host && cudaMemcpyAsync(phase_host, dp, bytes, cudaMemcpyDeviceToHost, c->stream) != cudaSuccess)
+        return set_err(QLD_E_CUDA);
+    return QLD_OK;
+}
+
+int qld_fft_bin_host(qld_ctx* c, int k, float* out_host) {
+    if (!c || !out_host || k < 0 || k >= c->N) return set_err(QLD_E_INVAL);
+    if (c->pushed < c->N) return set_err(QLD_E_NOT_READY);
+    DeviceGuard g(c->device);
+    if (!g.ok) return set_err(QLD_E_CUDA);
+    if (pending_error() != QLD_OK) return set_err(QLD_E_CUDA);
+    int st = ensure_out(c, 2 * c->npad);
+    if (st != QLD_OK) return set_err(st);
+    st = enqueue_fft_bin(c, k, c->out_dev);
+    if (st != QLD_OK) return set_err(st);
+    if (cudaMemcpyAsync(out_host, c->out_dev, (size_t)c->npix * sizeof(float), cudaMemcpyDeviceToHost,
+                        c->stream) != cudaSuccess)
+        return set_err(QLD_E_CUDA);
+    return QLD_OK;
+}
+
+int qld_get_iq(qld_ctx* c, int32_t* S, int32_t* C) {
+    if (!c || !aligned(S, 4) || !aligned(C, 4)) return set_err(QLD_E_INVAL);
+    DeviceGuard g(c->device);
+    if (!g.ok) return set_err(QLD_E_CUDA);
+    if (pending_error() != QLD_OK) return set_err(QLD_E_CUDA);
+    const size_t bytes = (size_t)c->npix * sizeof(int32_t);
+    if (S && cudaMemcpyAsync(S, c->S, bytes, cudaMemcpyDeviceToDevice, c->stream) != cudaSuccess)
+        return set_err(QLD_E_CUDA);
+    if (C && cudaMemcpyAsync(C, c->C, bytes, cudaMemcpyDeviceToDevice, c->stream) != cudaSuccess)
+        return set_err(QLD_E_CUDA);
+    return QLD_OK;
+}
+
+int qld_reset(qld_ctx* c) {
+    if (!c) return set_err(QLD_E_INVAL);
+    DeviceGuard g(c->device);
+    if (!g.ok) return set_err(QLD_E_CUDA);
+    if (pending_error() != QLD_OK) return set_err(QLD_E_CUDA);
+    if (cudaMemsetAsync(c->ring, 0, (size_t)(c->slot_stride * c->N), c->stream) != cudaSuccess ||
+        cudaMemsetAsync(c->S, 0, (size_t)c->npad * sizeof(int32_t), c->stream) != cudaSuccess ||
+        cudaMemsetAsync(c->C, 0, (size_t)c->npad * sizeof(int32_t), c->stream) != cudaSuccess)
+        return set_err(QLD_E_CUDA);
+    c->pushed = 0;
+    return QLD_OK;
+}
+
+long long qld_frames_pushed(const qld_ctx* c) { return c ? c->pushed : -1; }
+
+int qld_sync(qld_ctx* c) {
+    if (!c) return set_err(QLD_E_INVAL);
+    DeviceGuard g(c->device);
+    if (!g.ok) return set_err(QLD_E_CUDA);
+    if (cudaStreamSynchronize(c->stream) != cudaSuccess) {
+        cudaGetLastError();
+        return set_err(QLD_E_CUDA);
+    }
+    return set_err(pending_error());
+}
+
+void* qld_stream(const qld_ctx* c) { return c ? (void*)c->stream : nullptr; }
+
+}  // extern "C"

@@ -1,0 +1,395 @@
+// qld_kernels.cuh -- sm_103a kernels of the QLD library.
+//
+// Hot path (per pixel, per frame s of the stream, window of N frames):
+//   push:   x_old = ring[s mod N]; ring[s mod N] = x_s; d = x_s - x_old;
+//           S += sin(pi s/2) d, C += cos(pi s/2) d        (int32, exact)
+//   image:  R = sqrt(S^2 + C^2), phase = atan2(-S, C)      (float32)
+//   bin:    X_k = sum_{slots j} ring[j] exp(-2 pi i k j / N), out = |X_k|^2
+// (Methods, "Numerical simulations", the equations for R(j,k) and the FFT
+// map; SI, "Timing sequence" item 3 and the closing paragraph on the sliding
+// buffer of N frames.)
+//
+// All three are HBM-streaming kernels: pixels are independent, frames are
+// contiguous rows, and every thread owns a 16-byte vector of pixels (8 uint16
+// or 16 uint8) so loads and stores are 128-bit and fully coalesced.
+
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace qldk {
+
+constexpr int kVecBytes = 16;
+
+// ---------------------------------------------------------------- helpers --
+
+__device__ __forceinline__ uint4 ld_stream(const void* p) {
+    return __ldcs(reinterpret_cast<const uint4*>(p));
+}
+__device__ __forceinline__ void st_stream(void* p, uint4 v) {
+    __stcs(reinterpret_cast<uint4*>(p), v);
+}
+
+// Pixel q (0-based) of a 16-byte vector as an int.
+template <typename T>
+__device__ __forceinline__ int pix(const uint4& v, int q);
+
+template <>
+__device__ __forceinline__ int pix<uint16_t>(const uint4& v, int q) {
+    const uint32_t w = (q < 2) ? v.x : (q < 4) ? v.y : (q < 6) ? v.z : v.w;
+    return (q & 1) ? (int)(w >> 16) : (int)(w & 0xFFFFu);
+}
+template <>
+__device__ __forceinline__ int pix<uint8_t>(const uint4& v, int q) {
+    const uint32_t w = (q < 4) ? v.x : (q < 8) ? v.y : (q < 12) ? v.z : v.w;
+    return (int)((w >> (8 * (q & 3))) & 0xFFu);
+}
+
+// Pixel q of a 16-byte vector as an exact float: the integer bits are placed
+// in the mantissa of 2^23 by one byte permute, and 2^23 is subtracted (exact
+// for values below 2^23).
+template <typename T>
+__device__ __forceinline__ float pixf(const uint4& v, int q);
+
+template <>
+__device__ __forceinline__ float pixf<uint16_t>(const uint4& v, int q) {
+    const uint32_t w = (q < 2) ? v.x : (q < 4) ? v.y : (q < 6) ? v.z : v.w;
+    const uint32_t b = __byte_perm(w, 0x4B000000u, (q & 1) ? 0x7632u : 0x7610u);
+    return __uint_as_float(b) - 8388608.0f;
+}
+template <>
+__device__ __forceinline__ float pixf<uint8_t>(const uint4& v, int q) {
+    const uint32_t w = (q < 4) ? v.x : (q < 8) ? v.y : (q < 12) ? v.z : v.w;
+    const uint32_t b = __byte_perm(w, 0x4B000000u, 0x7540u | (uint32_t)(q & 3));
+    return __uint_as_float(b) - 8388608.0f;
+}
+
+// Adds d = x_new - x_old of one frame with absolute index residue r = s mod 4
+// to the quadrature sums: sin(pi s/2) = 1, 0, -1, 0 and cos(pi s/2) = 0, -1,
+// 0, 1 for r = 1, 2, 3, 0, so exactly one of S, C changes. r is the same for
+// every thread of a launch, so the switch does not diverge.
+template <typename T, bool HAS_OLD>
+__device__ __forceinline__ void accumulate(int32_t* sacc, int32_t* cacc, const uint4& xn, const uint4& xo, int r) {
+    constexpr int VP = kVecBytes / (int)sizeof(T);
+    switch (r) {
+        case 1:
+#pragma unroll
+            for (int q = 0; q < VP; ++q) sacc[q] += pix<T>(xn, q) - (HAS_OLD ? pix<T>(xo, q) : 0);
+            break;
+        case 2:
+#pragma unroll
+            for (int q = 0; q < VP; ++q) cacc[q] -= pix<T>(xn, q) - (HAS_OLD ? pix<T>(xo, q) : 0);
+            break;
+        case 3:
+#pragma unroll
+            for (int q = 0; q < VP; ++q) sacc[q] -= pix<T>(xn, q) - (HAS_OLD ? pix<T>(xo, q) : 0);
+            break;
+        default:
+#pragma unroll
+            for (int q = 0; q < VP; ++q) cacc[q] += pix<T>(xn, q) - (HAS_OLD ? pix<T>(xo, q) : 0);
+            break;
+    }
+}
+
+// R = sqrt(S^2 + C^2) with S^2 + C^2 formed exactly in 64-bit integers and
+// rounded once to float; phase = atan2(-S, C) with the negation done on the
+// integer so S = 0 gives +0 and the phase stays in (-pi, pi].
+__device__ __forceinline__ float amplitude(int32_t s, int32_t c) {
+    const long long ss = (long long)s * s + (long long)c * c;
+    return sqrtf(__ll2float_rn(ss));
+}
+__device__ __forceinline__ float phase_of(int32_t s, int32_t c) {
+    return atan2f((float)(-s), (float)c);
+}
+
+// ------------------------------------------------------------------- push --
+
+struct PushArgs {
+    const uint8_t* frames;  // first frame applied
+    long long frame_stride; // bytes between consecutive input frames
+    int nf;                 // frames applied
+    long long s_first;      // absolute index of the first applied frame
+    uint8_t* ring;          // N slots
+    long long slot_stride;  // bytes between ring slots (multiple of 256)
+    int N;
+    int32_t* S;             // sums, padded to a multiple of 64 pixels
+    int32_t* C;
+    long long nvec;         // 16-byte vectors per frame (vector path) or pixels (scalar path)
+    long long npix;
+    float* amp;             // epilogue outputs (may be NULL)
+    float* phase;
+    int out_aligned;        // amp and phase are 16-byte aligned (or NULL)
+};
+
+// Vector path: frames 16-byte aligned and frame_stride a multiple of 16.
+// RESET: the window is rebuilt from the applied frames alone (a push of at
+// least N frames), so the sums start at zero and the expiring slots are not
+// read. EPI: also write the amplitude / phase image.
+template <typename T, bool RESET, bool EPI>
+__global__ void __launch_bounds__(128) push_vec_kernel(const PushArgs a) {
+    constexpr int VP = kVecBytes / (int)sizeof(T);
+    const long long v = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (v >= a.nvec) return;
+    const long long off = v * kVecBytes;
+    const long long p0 = v * VP;
+
+    int32_t sacc[VP], cacc[VP];
+    if (RESET) {
+#pragma unroll
+        for (int q = 0; q < VP; ++q) sacc[q] = cacc[q] = 0;
+    } else {
+#pragma unroll
+        for (int q = 0; q < VP; q += 4) {
+            const int4 s4 = *reinterpret_cast<const int4*>(a.S + p0 + q);
+            const int4 c4 = *reinterpret_cast<const int4*>(a.C + p0 + q);
+            sacc[q] = s4.x; sacc[q + 1] = s4.y; sacc[q + 2] = s4.z; sacc[q + 3] = s4.w;
+            cacc[q] = c4.x; cacc[q + 1] = c4.y; cacc[q + 2] = c4.z; cacc[q + 3] = c4.w;
+        }
+    }
+
+    const uint8_t* src = a.frames + off;
+    uint8_t* ring = a.ring + off;
+    int f = 0;
+    // Groups of four frames: all loads are issued before any store so eight
+    // 128-bit loads per thread are in flight.
+    for (; f + 4 <= a.nf; f += 4) {
+        uint4 xn[4], xo[4];
+        long long slot[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const long long s = a.s_first + f + u;
+            slot[u] = s % a.N;
+            xn[u] = ld_stream(src + (long long)(f + u) * a.frame_stride);
+        }
+        if (!RESET) {
+#pragma unroll
+            for (int u = 0; u < 4; ++u) xo[u] = ld_stream(ring + slot[u] * a.slot_stride);
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) st_stream(ring + slot[u] * a.slot_stride, xn[u]);
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+            accumulate<T, !RESET>(sacc, cacc, xn[u], xo[u], (int)((a.s_first + f + u) & 3));
+    }
+    for (; f < a.nf; ++f) {
+        const long long s = a.s_first + f;
+        const long long slot = s % a.N;
+        const uint4 xn = ld_stream(src + (long long)f * a.frame_stride);
+        uint4 xo = make_uint4(0, 0, 0, 0);
+        if (!RESET) xo = ld_stream(ring + slot * a.slot_stride);
+        st_stream(ring + slot * a.slot_stride, xn);
+        accumulate<T, !RESET>(sacc, cacc, xn, xo, (int)(s & 3));
+    }
+
+#pragma unroll
+    for (int q = 0; q < VP; q += 4) {
+        *reinterpret_cast<int4*>(a.S + p0 + q) = make_int4(sacc[q], sacc[q + 1], sacc[q + 2], sacc[q + 3]);
+        *reinterpret_cast<int4*>(a.C + p0 + q) = make_int4(cacc[q], cacc[q + 1], cacc[q + 2], cacc[q + 3]);
+    }
+
+    if (EPI) {
+        if (a.amp) {
+            if (a.out_aligned) {
+#pragma unroll
+                for (int q = 0; q < VP; q += 4)
+                    __stcs(reinterpret_cast<float4*>(a.amp + p0 + q),
+                           make_float4(amplitude(sacc[q], cacc[q]), amplitude(sacc[q + 1], cacc[q + 1]),
+                                       amplitude(sacc[q + 2], cacc[q + 2]), amplitude(sacc[q + 3], cacc[q + 3])));
+            } else {
+#pragma unroll
+                for (int q = 0; q < VP; ++q) a.amp[p0 + q] = amplitude(sacc[q], cacc[q]);
+            }
+        }
+        if (a.phase) {
+            if (a.out_aligned) {
+#pragma unroll
+                for (int q = 0; q < VP; q += 4)
+                    __stcs(reinterpret_cast<float4*>(a.phase + p0 + q),
+                           make_float4(phase_of(sacc[q], cacc[q]), phase_of(sacc[q + 1], cacc[q + 1]),
+                                       phase_of(sacc[q + 2], cacc[q + 2]), phase_of(sacc[q + 3], cacc[q + 3])));
+            } else {
+#pragma unroll
+                for (int q = 0; q < VP; ++q) a.phase[p0 + q] = phase_of(sacc[q], cacc[q]);
+            }
+        }
+    }
+}
+
+// Scalar path for inputs that are not 16-byte aligned or whose frame size is
+// not a multiple of 16 bytes: one pixel per thread.
+template <typename T, bool RESET, bool EPI>
+__global__ void __launch_bounds__(256) push_scalar_kernel(const PushArgs a) {
+    const long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= a.npix) return;
+    int32_t sacc = RESET ? 0 : a.S[p];
+    int32_t cacc = RESET ? 0 : a.C[p];
+    const T* src = reinterpret_cast<const T*>(a.frames) + p;
+    for (int f = 0; f < a.nf; ++f) {
+        const long long s = a.s_first + f;
+        T* slotp = reinterpret_cast<T*>(a.ring + (s % a.N) * a.slot_stride) + p;
+        const int xn = (int)*reinterpret_cast<const T*>(reinterpret_cast<const uint8_t*>(src) +
+                                                        (long long)f * a.frame_stride);
+        const int xo = RESET ? 0 : (int)*slotp;
+        *slotp = (T)xn;
+        const int d = xn - xo;
+        switch ((int)(s & 3)) {
+            case 1: sacc += d; break;
+            case 2: cacc -= d; break;
+            case 3: sacc -= d; break;
+            default: cacc += d; break;
+        }
+    }
+    a.S[p] = sacc;
+    a.C[p] = cacc;
+    if (EPI) {
+        if (a.amp) a.amp[p] = amplitude(sacc, cacc);
+        if (a.phase) a.phase[p] = phase_of(sacc, cacc);
+    }
+}
+
+// ------------------------------------------------------------------ image --
+
+// Four pixels per thread; S and C are padded so the int4 loads stay in bounds.
+__global__ void __launch_bounds__(256) image_kernel(const int32_t* __restrict__ S, const int32_t* __restrict__ C,
+                                                    long long npix, float* __restrict__ amp,
+                                                    float* __restrict__ phase, int out_aligned) {
+    const long long p0 = ((long long)blockIdx.x * blockDim.x + threadIdx.x) * 4;
+    if (p0 >= npix) return;
+    const int4 s4 = *reinterpret_cast<const int4*>(S + p0);
+    const int4 c4 = *reinterpret_cast<const int4*>(C + p0);
+    const int32_t s[4] = {s4.x, s4.y, s4.z, s4.w};
+    const int32_t c[4] = {c4.x, c4.y, c4.z, c4.w};
+    const bool full = out_aligned && p0 + 4 <= npix;
+    if (amp) {
+        if (full) {
+            __stcs(reinterpret_cast<float4*>(amp + p0), make_float4(amplitude(s[0], c[0]), amplitude(s[1], c[1]),
+                                                                     amplitude(s[2], c[2]), amplitude(s[3], c[3])));
+        } else {
+            for (int q = 0; q < 4 && p0 + q < npix; ++q) amp[p0 + q] = amplitude(s[q], c[q]);
+        }
+    }
+    if (phase) {
+        if (full) {
+            __stcs(reinterpret_cast<float4*>(phase + p0), make_float4(phase_of(s[0], c[0]), phase_of(s[1], c[1]),
+                                                                       phase_of(s[2], c[2]), phase_of(s[3], c[3])));
+        } else {
+            for (int q = 0; q < 4 && p0 + q < npix; ++q) phase[p0 + q] = phase_of(s[q], c[q]);
+        }
+    }
+}
+
+// --------------------------------------------------------------- DFT bin --
+
+// Twiddles of bin k for ring slot j: exp(-2 pi i k j / N), with (k j) mod N
+// reduced in integers, evaluated in FP64 and rounded to float. Slot j holds
+// the frame whose absolute index s satisfies s = j (mod N), and
+// exp(-2 pi i k s / N) depends only on (k s) mod N, so slot order needs no
+// window rotation.
+__global__ void twiddle_kernel(float2* __restrict__ tw, int N, int k) {
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= N) return;
+    const long long m = ((long long)k * j) % N;
+    double sn, cs;
+    sincospi(2.0 * (double)m / (double)N, &sn, &cs);
+    tw[j] = make_float2((float)cs, (float)(-sn));
+}
+
+// Pixel-tiled single-bin DFT over the N ring slots. A CTA of 256 threads
+// covers PV = 2^PV_LOG pixel vectors and splits the time axis into 256/PV
+// slices: thread t takes vector t mod PV and frames j = t/PV, t/PV + 256/PV,
+// ... Each thread accumulates in float32, flushing a partial every 16 frames
+// into a running sum to keep rounding small. When PV < 32 one warp holds
+// 32/PV time slices of the same pixels and they are combined with
+// warp shuffles; the 8 warps' partials are then combined in shared memory.
+template <typename T, int PV_LOG>
+__global__ void __launch_bounds__(256) fftbin_kernel(const uint8_t* __restrict__ ring, long long slot_stride, int N,
+                                                     const float2* __restrict__ tw, long long nvec, long long npix,
+                                                     float* __restrict__ out) {
+    constexpr int VP = kVecBytes / (int)sizeof(T);
+    constexpr int PV = 1 << PV_LOG;
+    constexpr int TS = 256 / PV;
+    static_assert(PV >= 4 && PV <= 32, "pixel vectors per CTA must be 4..32");
+    __shared__ float2 red[8][PV * VP];
+
+    const int t = threadIdx.x;
+    const int pv = t & (PV - 1);
+    const int ts = t >> PV_LOG;
+    const long long v = (long long)blockIdx.x * PV + pv;
+
+    float re[VP], im[VP];
+#pragma unroll
+    for (int q = 0; q < VP; ++q) re[q] = im[q] = 0.f;
+
+    if (v < nvec) {
+        const uint8_t* base = ring + v * kVecBytes;
+        int j = ts;
+        while (j < N) {
+            float pr[VP], pi[VP];
+#pragma unroll
+            for (int q = 0; q < VP; ++q) pr[q] = pi[q] = 0.f;
+            // Up to 16 frames (4 groups of 4) into the partial.
+            for (int g = 0; g < 4 && j < N; ++g, j += 4 * TS) {
+                uint4 x[4];
+                float2 w[4];
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    const int jj = j + u * TS;
+                    if (jj < N) {
+                        x[u] = ld_stream(base + (long long)jj * slot_stride);
+                        w[u] = __ldg(tw + jj);
+                    } else {
+                        x[u] = make_uint4(0, 0, 0, 0);
+                        w[u] = make_float2(0.f, 0.f);
+                    }
+                }
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+#pragma unroll
+                    for (int q = 0; q < VP; ++q) {
+                        const float xf = pixf<T>(x[u], q);
+                        pr[q] = fmaf(xf, w[u].x, pr[q]);
+                        pi[q] = fmaf(xf, w[u].y, pi[q]);
+                    }
+                }
+            }
+#pragma unroll
+            for (int q = 0; q < VP; ++q) {
+                re[q] += pr[q];
+                im[q] += pi[q];
+            }
+        }
+    }
+
+    if (PV < 32) {
+#pragma unroll
+        for (int o = 16; o >= PV; o >>= 1) {
+#pragma unroll
+            for (int q = 0; q < VP; ++q) {
+                re[q] += __shfl_xor_sync(0xFFFFFFFFu, re[q], o);
+                im[q] += __shfl_xor_sync(0xFFFFFFFFu, im[q], o);
+            }
+        }
+    }
+    const int warp = t >> 5;
+    const bool rep = (PV >= 32) || (((t & 31) >> PV_LOG) == 0);
+    if (rep) {
+#pragma unroll
+        for (int q = 0; q < VP; ++q) red[warp][pv * VP + q] = make_float2(re[q], im[q]);
+    }
+    __syncthreads();
+    const long long pbase = (long long)blockIdx.x * PV * VP;
+    for (int e = t; e < PV * VP; e += 256) {
+        float a = 0.f, b = 0.f;
+#pragma unroll
+        for (int w = 0; w < 8; ++w) {
+            const float2 r = red[w][e];
+            a += r.x;
+            b += r.y;
+        }
+        const long long p = pbase + e;
+        if (p < npix) out[p] = a * a + b * b;
+    }
+}
+
+}  // namespace qldk
