@@ -1,0 +1,468 @@
+#!/usr/bin/env python3
+"""Throughput of the QLD hot path on B300.
+
+Workload: fog scene (OD 6), 1024x1024 12-bit frames in uint16, window
+N = 1024, sliding by 4 new frames per step. One step is the whole hot path
+over one batch: push the 4 frames into the HBM ring and update the int32
+quadrature sums, write the amplitude and phase images (one fused kernel), and
+write the DFT-bin power image at k = N/4 (the FFT discrimination the paper
+compares QLD against), which reads the whole window.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl cuda|reference]
+
+Prints one JSON line. Under torchrun (N > 1) every rank runs its own camera
+stream on its own GPU (pixels and streams are independent: weak scaling, no
+data-path collective); the step time is the maximum over ranks.
+
+--impl reference times the CPU oracle (plain C++, int64/FP64, recomputing
+every window from scratch) on the host cores on a bounded band of rows.
+"""
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "QLD Gpixel-frames/s and % HBM roofline; p99 frame-to-image latency at 1 B300"
+UNIT = "Gpixel-frames/s"
+H = W = 1024
+N = 1024
+ADV = 4
+OD = 6
+SEED = 1002
+K_BIN = N // 4
+POOL = 2048  # frames resident in HBM (4 GiB), cycled: every step reads fresh frames from DRAM
+WORKLOAD = ("fog scene OD 6, 1024x1024 uint16 (12-bit), N=1024 sliding window advanced 4 frames/step; "
+            "per step: push+amplitude/phase image (fused) and DFT-bin power at k=N/4")
+FALLBACK_HBM_GBS = 6400.0
+
+
+def parse_args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3000)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", choices=["cuda", "reference"], default="cuda")
+    ap.add_argument("--latency-samples", type=int, default=1000)
+    ap.add_argument("--cpu-seconds", type=float, default=12.0, help="budget of the oracle CPU baseline")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--case", choices=["full", "small"], default="full",
+                    help="small: N=256 and a 512-frame pool (1.5 GB on the device) for profiler captures")
+    args = ap.parse_args()
+    if args.case == "small":
+        global N, K_BIN, POOL, WORKLOAD
+        N, POOL = 256, 512
+        K_BIN = N // 4
+        WORKLOAD = WORKLOAD.replace("N=1024", "N=256")
+    return args
+
+
+# --------------------------------------------------------------- helpers ---
+
+def algorithmic_bytes():
+    """Bytes each kernel must move per launch (must-move traffic, not DRAM
+    counters)."""
+    npix = H * W
+    b = 2
+    push_image = ADV * npix * 3 * b + npix * (4 + 4) * 2 + npix * 8  # new+old+ring write; S,C rd+wr; amp+phase
+    fft_bin = N * npix * b + npix * 4  # whole window read once; power image written
+    return {"push_image": push_image, "fft_bin": fft_bin}
+
+
+def measured_hbm_peak():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            return float(json.load(f)["hbm_gbs"]), "measured"
+    except Exception:
+        return FALLBACK_HBM_GBS, "fallback"
+
+
+def kernel_source_sha():
+    h = hashlib.sha256()
+    with open(os.path.join(ROOT, "paper_1511_03390_b300/csrc/qld_kernels.cuh"), "rb") as f:
+        h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def profiled_traffic(kernel):
+    """DRAM bytes per launch from the committed ncu summary of this kernel on
+    this workload, or None if the summary is missing or was taken on other
+    kernel sources."""
+    path = os.path.join(ROOT, "profiles", "%s_fog1024_N%d.txt" % (kernel, N))
+    if not os.path.exists(path):
+        return None
+    vals = {}
+    with open(path) as f:
+        for line in f:
+            if ":" in line:
+                k, v = line.split(":", 1)
+                vals[k.strip()] = v.strip()
+    if vals.get("kernel_source_sha256_16") != kernel_source_sha():
+        return None
+    try:
+        return int(float(vals["dram_bytes_per_launch"]))
+    except (KeyError, ValueError):
+        return None
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 100 ms."""
+
+    FIELDS = ("pci.bus_id,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, bus_id=None):
+        self.bus_id = bus_id
+        self.proc = None
+        self.out = None
+
+    def start(self):
+        try:
+            self.out = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+            self.proc = subprocess.Popen(["nvidia-smi", "--query-gpu=" + self.FIELDS, "--format=csv,noheader,nounits",
+                                          "-lms", "100"], stdout=self.out, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        return self
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.out.flush()
+        self.out.seek(0)
+        rows = [r.split(",") for r in self.out.read().splitlines() if r.strip()]
+        os.unlink(self.out.name)
+        if self.bus_id:
+            mine = [r for r in rows if self.bus_id.lower() in r[0].strip().lower()]
+            rows = mine or rows
+        sm, mx, pw, reasons = [], [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            try:
+                sm.append(float(r[1]))
+                mx.append(float(r[2]))
+                pw.append(float(r[3]))
+            except (ValueError, IndexError):
+                continue
+            for i, n in enumerate(names):
+                if len(r) > 5 + i and r[5 + i].strip() == "Active":
+                    reasons.add(n)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "power_w_max": max(pw), "samples": len(sm),
+                "reasons": sorted(reasons)}
+
+
+def dist_setup():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("gloo")
+    return world, rank, local
+
+
+def dist_max(x, world):
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+
+    t = torch.tensor([float(x)], dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def dist_barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.barrier()
+
+
+# --------------------------------------------------------- oracle timing ---
+
+def oracle_steps(band, rows, nthreads, max_steps, budget_s):
+    """Times the oracle on a band of `rows` image rows: each step recomputes
+    S, C (int64), R and phase (FP64) over the N-frame window ending 4 frames
+    later, and the DFT bin k = N/4 (FP64). Returns per-step seconds."""
+    import oracle
+
+    times = []
+    P = band.shape[0] - N
+    for i in range(max_steps):
+        off = (ADV * (i + 1)) % (P + 1)
+        win = band[off:off + N]
+        t0 = time.perf_counter()
+        S, C = oracle.quadrature_sums(win, s0=off + 1, nthreads=nthreads)
+        oracle.amplitude_phase(S, C)
+        oracle.dft_bin(win, K_BIN, s0=off + 1, nthreads=nthreads)
+        times.append(time.perf_counter() - t0)
+        if sum(times) > budget_s:
+            break
+    return times
+
+
+def cpu_baseline_from_band(band, rows, budget_s, steps=64):
+    nthreads = os.cpu_count() or 1
+    t = oracle_steps(band, rows, nthreads, steps, budget_s)
+    t1 = oracle_steps(band, rows, 1, 2, budget_s / 4)
+    per_step = statistics.median(t)
+    pf = rows * W * ADV
+    return {
+        "value": pf / per_step / 1e9,
+        "unit": UNIT,
+        "cores": nthreads,
+        "kind": "oracle",
+        "sample": ("%d of %d rows (%d px) x %d consecutive windows; per window S,C,R,phase recomputed over "
+                   "N=%d frames and the DFT bin k=N/4, %d threads; value per pixel-frame ingested, scaled "
+                   "from the band" % (rows, H, rows * W, len(t), N, nthreads)),
+        "single_thread_value": pf / statistics.median(t1) / 1e9,
+        "ms_per_step_sample": per_step * 1e3,
+    }
+
+
+# ----------------------------------------------------------- CUDA arm ---
+
+def run_cuda(args, world, rank, local):
+    import torch
+
+    import paper_1511_03390_b300 as q
+    from qldscene import DeviceScene, scene_fog
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    st = torch.cuda.current_stream(dev)
+    sc = scene_fog(OD, seed=SEED, H=H, W=W)
+    ds = DeviceScene(sc, dev)
+    pool = torch.empty((POOL, H, W), dtype=torch.uint16, device=dev)
+    for i in range(0, POOL, 256):
+        ds.generate_into(pool[i:i + 256], i + 1, 256)
+    amp = torch.empty(H * W, dtype=torch.float32, device=dev)
+    ph = torch.empty_like(amp)
+    pw = torch.empty_like(amp)
+
+    ctx = q.qld_create(H, W, N, q.QLD_U16)
+    q.qld_push_frames(ctx, pool[:N], N, st)
+
+    def frames_of(i):
+        j = (N + ADV * i) % POOL
+        return pool[j:j + ADV]
+
+    def step(i):
+        q.qld_push_image(ctx, frames_of(i), ADV, st, amp, ph)
+        q.qld_fft_bin(ctx, K_BIN, pw)
+
+    for i in range(args.warmup):
+        step(i)
+    K = args.steps
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(K)]
+    ev_end = torch.cuda.Event(enable_timing=True)
+    bus = None
+    try:
+        bus = torch.cuda.get_device_properties(dev).pci_bus_id
+    except Exception:
+        pass
+    torch.cuda.synchronize(dev)
+    dist_barrier(world)
+    torch.cuda.synchronize(dev)
+    clocks = ClockSampler(bus).start()
+    n0 = q.qld_launch_count()
+    for i in range(K):
+        ev[i][0].record(st)
+        q.qld_push_image(ctx, frames_of(args.warmup + i), ADV, st, amp, ph)
+        ev[i][1].record(st)
+        q.qld_fft_bin(ctx, K_BIN, pw)
+    ev_end.record(st)
+    ev_end.synchronize()
+    launches = q.qld_launch_count() - n0
+    torch.cuda.synchronize(dev)
+    clk = clocks.stop()
+    dist_barrier(world)
+    total_ms = ev[0][0].elapsed_time(ev_end)
+    push_ms = sum(ev[i][0].elapsed_time(ev[i][1]) for i in range(K))
+    fft_ms = sum(ev[i][1].elapsed_time(ev[i + 1][0] if i + 1 < K else ev_end) for i in range(K))
+    max_ms = dist_max(total_ms, world)
+
+    ab = algorithmic_bytes()
+    peak, peak_kind = measured_hbm_peak()
+    fft_gbs = ab["fft_bin"] * K / (fft_ms * 1e-3) / 1e9
+    push_gbs = ab["push_image"] * K / (push_ms * 1e-3) / 1e9
+    value = world * H * W * ADV * K / (max_ms * 1e-3) / 1e9
+
+    # frame-to-image latency: host call of the fused push (frames already in
+    # HBM) to completion of the image, one sample at a time
+    lat = []
+    e = torch.cuda.Event()
+    for i in range(args.latency_samples):
+        fr = frames_of(args.warmup + K + i)
+        t0 = time.perf_counter()
+        q.qld_push_image(ctx, fr, ADV, st, amp, ph)
+        e.record(st)
+        e.synchronize()
+        lat.append((time.perf_counter() - t0) * 1e6)
+    lat.sort()
+
+    e2e = None
+    if not args.no_e2e:
+        e2e = run_e2e(args, q, torch, dev, st, pool)
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        rows = 64
+        band = pool[:N + ADV * 64, :rows, :].cpu().numpy().reshape(N + ADV * 64, rows * W)
+        cpu = cpu_baseline_from_band(band, rows, args.cpu_seconds)
+
+    ctx.destroy()
+    traffic = profiled_traffic("fftbin")
+    out = {
+        "metric": METRIC,
+        "value": value,
+        "unit": UNIT,
+        "n_gpus": world,
+        "steps": K,
+        "warmup": args.warmup,
+        "ms_per_step": max_ms / K,
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "u16 in, int32 sums, f32 images",
+        "data": "synthetic (seeded scattered-light scene generator)",
+        "config": {"workload": WORKLOAD, "H": H, "W": W, "N": N, "advance": ADV, "pixfmt": "uint16 12-bit",
+                   "od": OD, "dft_bin_k": K_BIN, "parallelism": "one camera stream per GPU" if world > 1 else "1 GPU",
+                   "l2": "inputs larger than L2: 4 GiB frame pool cycled + 2 GiB window read by the DFT bin each step"},
+        "roofline": {"bound": "hbm", "kernel": "fftbin_kernel (qld_fft_bin)", "achieved": fft_gbs, "peak": peak,
+                     "unit": "GB/s", "frac": fft_gbs / peak, "peak_kind": peak_kind,
+                     "algorithmic_bytes_per_launch": ab["fft_bin"], "traffic": traffic},
+        "kernels": {
+            "push_image": {"ms_per_launch": push_ms / K, "algorithmic_bytes": ab["push_image"], "achieved_gbs": push_gbs,
+                           "frac": push_gbs / peak, "qld_only_gpf_s": H * W * ADV / (push_ms / K * 1e-3) / 1e9},
+            "fft_bin": {"ms_per_launch": fft_ms / K, "algorithmic_bytes": ab["fft_bin"], "achieved_gbs": fft_gbs,
+                        "frac": fft_gbs / peak},
+            "share": {"push_image": push_ms / total_ms, "fft_bin": fft_ms / total_ms},
+        },
+        "latency_us": {"p50": lat[len(lat) // 2], "p99": lat[min(len(lat) - 1, int(0.99 * len(lat)))],
+                       "samples": len(lat),
+                       "what": "host call of qld_push_image (4 frames already in HBM) to image complete"}
+        if lat else None,
+        "gpu_launches": launches,
+        "clocks": clk,
+        "e2e": e2e,
+        "cpu_baseline": cpu,
+    }
+    return out
+
+
+def run_e2e(args, q, torch, dev, st, pool):
+    """The same step through the host-buffer C ABI: frames copied from pinned
+    host memory, the three images copied back to pinned host memory, every
+    step; wall-clock over the run, one synchronisation at the end."""
+    HP = 256
+    host = torch.empty((HP, H, W), dtype=torch.uint16).pin_memory()
+    host.copy_(pool[:HP])
+    amp_h = torch.empty(H * W, dtype=torch.float32).pin_memory()
+    ph_h = torch.empty_like(amp_h).pin_memory()
+    pw_h = torch.empty_like(amp_h).pin_memory()
+    ctx = q.qld_create(H, W, N, q.QLD_U16)
+    for i in range(0, N, HP):
+        q.qld_push_frames_host(ctx, host, HP, st)
+
+    def step(i):
+        j = (ADV * i) % HP
+        q.qld_push_frames_host(ctx, host[j:j + ADV], ADV, st)
+        q.qld_image_host(ctx, amp_h, ph_h)
+        q.qld_fft_bin_host(ctx, K_BIN, pw_h)
+
+    for i in range(max(3, args.warmup)):
+        step(i)
+    q.qld_sync(ctx)
+    K = min(args.steps, 2000)
+    t0 = time.perf_counter()
+    for i in range(K):
+        step(i)
+    q.qld_sync(ctx)
+    dt = time.perf_counter() - t0
+    ctx.destroy()
+    return {"value": H * W * ADV * K / dt / 1e9, "unit": UNIT, "h2d_bytes_per_step": ADV * H * W * 2,
+            "d2h_bytes_per_step": 3 * H * W * 4, "steps": K, "ms_per_step": dt / K * 1e3,
+            "api": "qld_push_frames_host + qld_image_host + qld_fft_bin_host, pinned host buffers"}
+
+
+# ------------------------------------------------------ reference arm ---
+
+def run_reference(args):
+    """The CPU oracle as it stands, on the same workload: a band of rows of
+    the same scene (numpy generator), each step one window 4 frames later."""
+    from qldscene import scene_fog
+
+    nthreads = os.cpu_count() or 1
+    rows = 8
+    sc = scene_fog(OD, seed=SEED, H=H, W=W)
+    pix = __import__("numpy").arange(rows * W)
+    band = sc.frames(1, N + ADV * 64, pix=pix)
+    t_w = oracle_steps(band, rows, nthreads, max(1, args.warmup), 60.0)
+    budget = 120.0
+    t = oracle_steps(band, rows, nthreads, args.steps, budget)
+    per_step = statistics.median(t)
+    pf = rows * W * ADV
+    value = pf / per_step / 1e9
+    sample = ("%d of %d rows (%d px) per step, %d timed windows (of %d requested; capped at %.0f s), %d threads; "
+              "per window S,C,R,phase recomputed over N=%d and DFT bin k=N/4" % (rows, H, rows * W, len(t), args.steps,
+                                                                                   budget, nthreads, N))
+    return {
+        "impl": "reference",
+        "metric": METRIC,
+        "value": value,
+        "unit": UNIT,
+        "n_gpus": args.gpus,
+        "steps": len(t),
+        "warmup": len(t_w),
+        "ms_per_step": H * W * ADV / (value * 1e9) * 1e3,
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "int64 sums, f64 images",
+        "data": "synthetic (seeded scattered-light scene generator)",
+        "config": {"workload": WORKLOAD, "H": H, "W": W, "N": N, "advance": ADV, "pixfmt": "uint16 12-bit",
+                   "od": OD, "dft_bin_k": K_BIN},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": nthreads, "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+
+
+def main():
+    args = parse_args()
+    world, rank, local = dist_setup()
+    if args.impl == "reference":
+        if rank == 0:
+            print(json.dumps(run_reference(args)), flush=True)
+        return 0
+    out = run_cuda(args, world, rank, local)
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -22,10 +22,12 @@
  * Memory: all frame, image and sum pointers are DEVICE pointers unless the
  * function name ends in _host. Frames are laid out [count][H][W], row-major,
  * contiguous, uint8 (QLD_U8) or uint16 (QLD_U16, 12- or 16-bit data in the
- * low bits). Images are float32 [H][W]; sums are int32 [H][W]. Any pointer
- * alignment and any W are accepted (unaligned inputs take a slower scalar
- * path). The context owns its ring buffer, sums and scratch; the caller owns
- * every pointer it passes.
+ * low bits). Images are float32 [H][W]; sums are int32 [H][W]. Any H and W
+ * are accepted. Pointers must be aligned to their element size (uint16
+ * frames to 2 bytes, float and int32 buffers to 4), else QLD_E_INVAL; frame
+ * buffers that are not 16-byte aligned, or frames whose size is not a
+ * multiple of 16 bytes, take a slower scalar path. The context owns its ring
+ * buffer, sums and scratch; the caller owns every pointer it passes.
  *
  * Streams: qld_push_frames and its variants enqueue on the stream they are
  * given and make it the context's current stream; every other call enqueues
@@ -64,8 +66,9 @@ enum qld_status {
     QLD_E_TIMEOUT = -5    /* a bounded wait ran out */
 };
 
-/* Largest window. With |x| <= 65535, |S|, |C| <= (N/2) * 65535 < 2^31 for
- * N <= 65536, so the int32 sums are exact. */
+/* Largest window. S adds N/4 frames and subtracts N/4 others (likewise C),
+ * so with |x| <= 65535, |S|, |C| <= (N/4) * 65535 < 2^31 for N <= 65536 and
+ * the int32 sums are exact. */
 #define QLD_MAX_N 65536
 
 /* Creates a context for H x W frames of the given pixel format and a window
@@ -147,6 +150,9 @@ int qld_sync(qld_ctx* ctx);
 
 /* The context's current stream (a cudaStream_t). */
 void* qld_stream(const qld_ctx* ctx);
+
+/* Kernels this library has launched in this process (all contexts). */
+long long qld_launch_count(void);
 
 /* Status text; last status set on this thread; version string. */
 const char* qld_strerror(int status);

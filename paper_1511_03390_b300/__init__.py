@@ -19,7 +19,7 @@ __all__ = [
     "qld_push_image", "qld_image", "qld_fft_bin", "qld_push_frames_host", "qld_image_host",
     "qld_fft_bin_host", "qld_get_iq", "qld_reset", "qld_frames_pushed", "qld_sync", "qld_stream",
     "qld_strerror", "qld_last_error", "qld_version", "qld_footprint_bytes", "qld_set_mem_budget",
-    "qld_mem_in_use", "LIB_PATH", "lib",
+    "qld_mem_in_use", "qld_launch_count", "LIB_PATH", "lib",
 ]
 
 QLD_U8, QLD_U16 = 1, 2
@@ -27,8 +27,13 @@ QLD_OK, QLD_E_INVAL, QLD_E_NOMEM, QLD_E_NOT_READY, QLD_E_CUDA, QLD_E_TIMEOUT = 0
 QLD_MAX_N = 65536
 
 LIB_PATH = _build.LIB
-if not os.path.exists(LIB_PATH):
-    raise ImportError("libqld.so is not built (%s); run `python -m paper_1511_03390_b300.build`" % LIB_PATH)
+if not _build.up_to_date():
+    # Missing, or older than its sources: rebuild in-tree with nvcc.
+    try:
+        _build.build()
+    except Exception as exc:  # no nvcc, or a compile error
+        if not os.path.exists(LIB_PATH):
+            raise ImportError("libqld.so is not built (%s) and building it failed: %s" % (LIB_PATH, exc))
 
 _p = ctypes.c_void_p
 _i = ctypes.c_int
@@ -40,6 +45,7 @@ _SIGS = {
     "qld_footprint_bytes": ([_i, _i, _i, _i], _ll),
     "qld_set_mem_budget": ([_ll], None),
     "qld_mem_in_use": ([], _ll),
+    "qld_launch_count": ([], _ll),
     "qld_destroy": ([_p], None),
     "qld_push_frames": ([_p, _p, _i, _p], _i),
     "qld_push_image": ([_p, _p, _i, _p, _p, _p], _i),
@@ -163,6 +169,10 @@ def qld_set_mem_budget(nbytes):
 
 def qld_mem_in_use():
     return lib.qld_mem_in_use()
+
+
+def qld_launch_count():
+    return lib.qld_launch_count()
 
 
 def _count_of(frames, count, frame_bytes):

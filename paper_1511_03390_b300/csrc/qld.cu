@@ -44,6 +44,7 @@ namespace {
 thread_local int g_last_error = QLD_OK;
 std::atomic<long long> g_budget{0};
 std::atomic<long long> g_in_use{0};
+std::atomic<long long> g_launches{0};
 
 int set_err(int st) {
     if (st != QLD_OK) g_last_error = st;
@@ -140,6 +141,7 @@ int enqueue_push(qld_ctx* c, const uint8_t* frames, int count, bool epi, float* 
     a.out_aligned = (aligned(amp, 16) && aligned(phase, 16)) ? 1 : 0;
     const bool vec = aligned(a.frames, 16) && (frame_bytes % qldk::kVecBytes) == 0;
     a.nvec = vec ? frame_bytes / qldk::kVecBytes : c->npix;
+    g_launches.fetch_add(1);
     if (reset) {
         if (epi) launch_push_t<true, true>(c, a, vec);
         else launch_push_t<true, false>(c, a, vec);
@@ -156,17 +158,14 @@ int enqueue_image(qld_ctx* c, float* amp, float* phase) {
     if (!amp && !phase) return QLD_OK;
     const long long nthr = (c->npix + 3) / 4;
     const int oa = (aligned(amp, 16) && aligned(phase, 16)) ? 1 : 0;
+    g_launches.fetch_add(1);
     qldk::image_kernel<<<blocks_for(nthr, 256), 256, 0, c->stream>>>(c->S, c->C, c->npix, amp, phase, oa);
     return cudaGetLastError() == cudaSuccess ? QLD_OK : QLD_E_CUDA;
 }
 
 template <typename T>
 void launch_fftbin_t(const qld_ctx* c, float* out, long long nvec) {
-    // Pixel vectors per CTA: 32 (8 time slices) when there are enough pixels
-    // for two CTAs per SM, fewer (more time slices, reduced by warp shuffles)
-    // for small frames so the grid still covers the GPU.
-    int pv_log = 5;
-    while (pv_log > 2 && (nvec + (1ll << pv_log) - 1) / (1ll << pv_log) < 296) --pv_log;
+    const int pv_log = qldk::fftbin_pv_log(nvec);
     const unsigned grid = (unsigned)((nvec + (1ll << pv_log) - 1) >> pv_log);
     switch (pv_log) {
         case 5: qldk::fftbin_kernel<T, 5><<<grid, 256, 0, c->stream>>>(c->ring, c->slot_stride, c->N, c->tw, nvec, c->npix, out); break;
@@ -178,11 +177,13 @@ void launch_fftbin_t(const qld_ctx* c, float* out, long long nvec) {
 
 int enqueue_fft_bin(qld_ctx* c, int k, float* out) {
     if (c->tw_k != k) {
+        g_launches.fetch_add(1);
         qldk::twiddle_kernel<<<blocks_for(c->N, 256), 256, 0, c->stream>>>(c->tw, c->N, k);
         if (cudaGetLastError() != cudaSuccess) return QLD_E_CUDA;
         c->tw_k = k;
     }
     const long long nvec = (c->npix * c->bpp + qldk::kVecBytes - 1) / qldk::kVecBytes;
+    g_launches.fetch_add(1);
     if (c->pixfmt == QLD_U16) launch_fftbin_t<uint16_t>(c, out, nvec);
     else launch_fftbin_t<uint8_t>(c, out, nvec);
     return cudaGetLastError() == cudaSuccess ? QLD_OK : QLD_E_CUDA;
@@ -264,6 +265,8 @@ long long qld_footprint_bytes(int H, int W, int N, int pixfmt) {
 void qld_set_mem_budget(long long bytes) { g_budget.store(bytes < 0 ? 0 : bytes); }
 
 long long qld_mem_in_use(void) { return g_in_use.load(); }
+
+long long qld_launch_count(void) { return g_launches.load(); }
 
 qld_ctx* qld_create(int H, int W, int N, int pixfmt) {
     if (!valid_dims(H, W, N, pixfmt)) {

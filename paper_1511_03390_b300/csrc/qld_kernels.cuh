@@ -392,4 +392,14 @@ __global__ void __launch_bounds__(256) fftbin_kernel(const uint8_t* __restrict__
     }
 }
 
+// Launch geometry of fftbin_kernel: log2 of the pixel vectors per CTA. 32
+// vectors (8 time slices) when the grid still has two CTAs per SM; fewer
+// (more time slices, reduced with warp shuffles) for small frames so the
+// grid still covers the GPU.
+inline int fftbin_pv_log(long long nvec) {
+    int pv_log = 5;
+    while (pv_log > 2 && (nvec + (1ll << pv_log) - 1) / (1ll << pv_log) < 296) --pv_log;
+    return pv_log;
+}
+
 }  // namespace qldk
