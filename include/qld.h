@@ -151,6 +151,31 @@ int qld_sync(qld_ctx* ctx);
 /* The context's current stream (a cudaStream_t). */
 void* qld_stream(const qld_ctx* ctx);
 
+/* Largest N accepted by qld_fft_bin_frames_noalloc. */
+#define QLD_NOALLOC_MAX_N 16384
+
+/* |X_k|^2 of every pixel over a block of N caller frames (device,
+ * [N][H][W]) on `stream`, without allocating any memory. The paper has no
+ * counterpart: this exists for callers that cannot call cudaMalloc while
+ * they run -- for example a fixed-memory real-time camera loop, or code that
+ * must not trigger the device-wide synchronisation cudaMalloc / cudaFree can
+ * cause. The result equals qld_fft_bin on a fresh context into which the
+ * same N frames were pushed.
+ *
+ * Limits and sharing: N must be a multiple of 4 between 4 and
+ * QLD_NOALLOC_MAX_N (QLD_E_INVAL otherwise, as for any bad argument); frames
+ * must be 16-byte aligned and a frame (H*W*pixfmt bytes) a multiple of 16
+ * bytes; out is device float32 [H][W]. The twiddle table lives in one fixed
+ * 128 KiB device array that every GPU loading this library holds until the
+ * process exits. Each call rewrites the part it uses before reading it, so
+ * nothing needs clearing, but all calls share that array: calls that may
+ * overlap on the GPU (different streams, no ordering between them) race and
+ * can return wrong values. The first call on a device looks up the array's
+ * device address (cudaGetSymbolAddress) and caches it; make that first call
+ * before any stream capture. */
+int qld_fft_bin_frames_noalloc(const void* frames, int H, int W, int N, int pixfmt, int k, float* out,
+                               void* stream);
+
 /* Kernels this library has launched in this process (all contexts). */
 long long qld_launch_count(void);
 

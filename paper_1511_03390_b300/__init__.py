@@ -19,12 +19,13 @@ __all__ = [
     "qld_push_image", "qld_image", "qld_fft_bin", "qld_push_frames_host", "qld_image_host",
     "qld_fft_bin_host", "qld_get_iq", "qld_reset", "qld_frames_pushed", "qld_sync", "qld_stream",
     "qld_strerror", "qld_last_error", "qld_version", "qld_footprint_bytes", "qld_set_mem_budget",
-    "qld_mem_in_use", "qld_launch_count", "LIB_PATH", "lib",
+    "qld_mem_in_use", "qld_launch_count", "qld_fft_bin_frames_noalloc", "QLD_NOALLOC_MAX_N", "LIB_PATH", "lib",
 ]
 
 QLD_U8, QLD_U16 = 1, 2
 QLD_OK, QLD_E_INVAL, QLD_E_NOMEM, QLD_E_NOT_READY, QLD_E_CUDA, QLD_E_TIMEOUT = 0, -1, -2, -3, -4, -5
 QLD_MAX_N = 65536
+QLD_NOALLOC_MAX_N = 16384
 
 LIB_PATH = _build.LIB
 if not _build.up_to_date():
@@ -54,6 +55,7 @@ _SIGS = {
     "qld_push_frames_host": ([_p, _p, _i, _p], _i),
     "qld_image_host": ([_p, _p, _p], _i),
     "qld_fft_bin_host": ([_p, _i, _p], _i),
+    "qld_fft_bin_frames_noalloc": ([_p, _i, _i, _i, _i, _i, _p, _p], _i),
     "qld_get_iq": ([_p, _p, _p], _i),
     "qld_reset": ([_p], _i),
     "qld_frames_pushed": ([_p], _ll),
@@ -219,6 +221,14 @@ def qld_image_host(ctx, amp=None, phase=None):
 
 def qld_fft_bin_host(ctx, k, out):
     return _check(lib.qld_fft_bin_host(_h(ctx), int(k), _addr(out, 4 * ctx.npix, "out")), "qld_fft_bin_host")
+
+
+def qld_fft_bin_frames_noalloc(frames, H, W, N, pixfmt, k, out, stream=None):
+    """|X_k|^2 over N device frames without any allocation (see qld.h)."""
+    nb = int(H) * int(W) * int(pixfmt)
+    return _check(lib.qld_fft_bin_frames_noalloc(_addr(frames, int(N) * nb, "frames"), int(H), int(W), int(N),
+                                                 int(pixfmt), int(k), _addr(out, 4 * int(H) * int(W), "out"),
+                                                 _stream(stream)), "qld_fft_bin_frames_noalloc")
 
 
 def qld_get_iq(ctx, S=None, C=None):

@@ -13,6 +13,7 @@
 #include <cstdint>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <cuda_runtime.h>
 
 #include "qld.h"
@@ -479,3 +480,78 @@ int qld_sync(qld_ctx* c) {
 void* qld_stream(const qld_ctx* c) { return c ? (void*)c->stream : nullptr; }
 
 }  // extern "C"
+
+// ------------------------------------------------------------------------
+// Allocation-free DFT bin over caller frames.
+//
+// For callers that must not allocate device memory while they run: the
+// twiddle table this computation needs lives in a fixed file-scope device
+// array instead of a context. Host code cannot use the array's name as a
+// device address (on the host it names a stand-in object), so the device
+// address is looked up once per device with cudaGetSymbolAddress and cached.
+
+namespace {
+
+constexpr int kNoAllocMaxDevices = 64;
+static __device__ __align__(256) float2 g_noalloc_twiddles[QLD_NOALLOC_MAX_N];
+float2* g_noalloc_twiddles_addr[kNoAllocMaxDevices] = {};
+std::mutex g_noalloc_mu;
+
+// Device address of g_noalloc_twiddles on the current device (looked up on
+// the first call on that device), or nullptr on error.
+float2* noalloc_twiddles(int dev) {
+    if (dev < 0 || dev >= kNoAllocMaxDevices) return nullptr;
+    std::lock_guard<std::mutex> lock(g_noalloc_mu);
+    if (!g_noalloc_twiddles_addr[dev]) {
+        void* p = nullptr;
+        if (cudaGetSymbolAddress(&p, g_noalloc_twiddles) != cudaSuccess || !p) {
+            cudaGetLastError();
+            return nullptr;
+        }
+        g_noalloc_twiddles_addr[dev] = (float2*)p;
+    }
+    return g_noalloc_twiddles_addr[dev];
+}
+
+}  // namespace
+
+extern "C" int qld_fft_bin_frames_noalloc(const void* frames, int H, int W, int N, int pixfmt, int k, float* out,
+                                          void* stream) {
+    if (!frames || !out || H < 1 || W < 1 || (pixfmt != QLD_U8 && pixfmt != QLD_U16)) return set_err(QLD_E_INVAL);
+    if (N < 4 || (N % 4) != 0 || N > QLD_NOALLOC_MAX_N || k < 0 || k >= N) return set_err(QLD_E_INVAL);
+    const long long npix = (long long)H * W;
+    const long long frame_bytes = npix * pixfmt;
+    if (npix > (1ll << 31) - 1 || (frame_bytes % qldk::kVecBytes) != 0 || !aligned(frames, 16) || !aligned(out, 4))
+        return set_err(QLD_E_INVAL);
+    int dev = -1;
+    if (cudaGetDevice(&dev) != cudaSuccess) return set_err(QLD_E_CUDA);
+    float2* tw = noalloc_twiddles(dev);
+    if (!tw) return set_err(QLD_E_CUDA);
+    cudaStream_t st = (cudaStream_t)stream;
+    // Frame i of the block plays the part of ring slot i. Its absolute index
+    // in a fresh stream would be i + 1; that shifts every X_k by the same
+    // unit-modulus factor, so |X_k|^2 is unchanged.
+    g_launches.fetch_add(1);
+    qldk::twiddle_kernel<<<blocks_for(N, 256), 256, 0, st>>>(tw, N, k);
+    const uint8_t* base = (const uint8_t*)frames;
+    const long long nvec = frame_bytes / qldk::kVecBytes;
+    const int pv_log = qldk::fftbin_pv_log(nvec);
+    const unsigned grid = (unsigned)((nvec + (1ll << pv_log) - 1) >> pv_log);
+    g_launches.fetch_add(1);
+    if (pixfmt == QLD_U16) {
+        switch (pv_log) {
+            case 5: qldk::fftbin_kernel<uint16_t, 5><<<grid, 256, 0, st>>>(base, frame_bytes, N, tw, nvec, npix, out); break;
+            case 4: qldk::fftbin_kernel<uint16_t, 4><<<grid, 256, 0, st>>>(base, frame_bytes, N, tw, nvec, npix, out); break;
+            case 3: qldk::fftbin_kernel<uint16_t, 3><<<grid, 256, 0, st>>>(base, frame_bytes, N, tw, nvec, npix, out); break;
+            default: qldk::fftbin_kernel<uint16_t, 2><<<grid, 256, 0, st>>>(base, frame_bytes, N, tw, nvec, npix, out); break;
+        }
+    } else {
+        switch (pv_log) {
+            case 5: qldk::fftbin_kernel<uint8_t, 5><<<grid, 256, 0, st>>>(base, frame_bytes, N, tw, nvec, npix, out); break;
+            case 4: qldk::fftbin_kernel<uint8_t, 4><<<grid, 256, 0, st>>>(base, frame_bytes, N, tw, nvec, npix, out); break;
+            case 3: qldk::fftbin_kernel<uint8_t, 3><<<grid, 256, 0, st>>>(base, frame_bytes, N, tw, nvec, npix, out); break;
+            default: qldk::fftbin_kernel<uint8_t, 2><<<grid, 256, 0, st>>>(base, frame_bytes, N, tw, nvec, npix, out); break;
+        }
+    }
+    return set_err(cudaGetLastError() == cudaSuccess ? QLD_OK : QLD_E_CUDA);
+}
