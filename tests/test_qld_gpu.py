@@ -234,3 +234,44 @@ def test_memory_budget_and_accounting_on_device():
         q.qld_set_mem_budget(0)
     ctx.destroy()
     assert q.qld_mem_in_use() == base
+
+
+def _frames_for_sums(S1, C1, P):
+    """Frames whose window of N = 4P frames (s = 1..4P) has S = P*S1 and
+    C = P*C1 per pixel: per period x1 - x3 = S1 and x4 - x2 = C1."""
+    x1 = np.where(S1 > 0, S1, 0)
+    x3 = np.where(S1 < 0, -S1, 0)
+    x4 = np.where(C1 > 0, C1, 0)
+    x2 = np.where(C1 < 0, -C1, 0)
+    period = np.stack([x1, x2, x3, x4]).astype(np.uint16)
+    return np.tile(period, (P, 1))
+
+
+@pytest.mark.parametrize("P", [1, 3, 16384])
+def test_amplitude_phase_on_every_octant_axis_and_extreme(P):
+    """Chosen (S, C) pairs -- zero, both axes with both signs, the diagonals,
+    points near every octant boundary, full-scale values, random pairs --
+    through the push kernel's fused epilogue and the image kernel."""
+    rng = np.random.default_rng(P)
+    m = 65535
+    pairs = [(0, 0), (0, 5), (0, -5), (5, 0), (-5, 0), (7, 7), (-7, 7), (7, -7), (-7, -7), (m, m), (-m, m),
+             (m, -m), (-m, -m), (m, 0), (0, -m), (1, m), (m, 1), (-1, -m), (m - 1, m), (m, m - 1), (-m, m - 1),
+             (1, 0), (0, 1), (-1, 0), (0, -1)]
+    S1 = np.array([p[0] for p in pairs] + list(rng.integers(-m, m + 1, 999)), np.int64)
+    C1 = np.array([p[1] for p in pairs] + list(rng.integers(-m, m + 1, 999)), np.int64)
+    W = S1.size
+    N = 4 * P
+    x = _frames_for_sums(S1, C1, P)
+    st = Stream(1, W, N, 2)
+    amp_f, ph_f = (None, None)
+    st.push(x[:-1])
+    amp_f, ph_f = st.push(x[-1:], fused=True)
+    S, C = get_iq(st.ctx)
+    assert np.array_equal(S, P * S1) and np.array_equal(C, P * C1)
+    R, ph = oracle.amplitude_phase(S, C)
+    from qld_check import check_amp_phase
+
+    check_amp_phase(amp_f, ph_f, R, ph, "fused epilogue")
+    amp, phs = get_image(st.ctx)
+    check_amp_phase(amp, phs, R, ph, "image kernel")
+    assert phs[pairs.index((0, -5))] == np.float32(np.pi)  # S = 0, C < 0: +pi on the branch cut
