@@ -54,6 +54,7 @@ def parse_args():
     ap.add_argument("--cpu-seconds", type=float, default=12.0, help="budget of the oracle CPU baseline")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-large", action="store_true", help="skip the 4096x4096 N=2048 (68.7 GB ring) stream")
     ap.add_argument("--case", choices=["full", "small"], default="full",
                     help="small: N=256 and a 512-frame pool (1.5 GB on the device) for profiler captures")
     args = ap.parse_args()
@@ -320,6 +321,41 @@ def run_cuda(args, world, rank, local):
         lat.append((time.perf_counter() - t0) * 1e6)
     lat.sort()
 
+    # QLD alone (the sliding lock-in without the DFT-bin comparison). Eager:
+    # K2 calls back to back between one event pair; on a slow host this is
+    # bound by the per-call host cost. Graph: the same K2 calls captured in a
+    # CUDA graph and replayed, so the kernels run back to back on the device.
+    # The graph bakes in each call's frame indices; the context is not used
+    # for anything else afterwards.
+    K2 = 500
+    base = args.warmup + K + args.latency_samples
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(st)
+    for i in range(K2):
+        q.qld_push_image(ctx, frames_of(base + i), ADV, st, amp, ph)
+    e1.record(st)
+    e1.synchronize()
+    us_eager = e0.elapsed_time(e1) * 1e3 / K2
+    cap = torch.cuda.Stream(dev)
+    cap.wait_stream(st)
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph, stream=cap):
+        for i in range(K2):
+            q.qld_push_image(ctx, frames_of(base + K2 + i), ADV, cap, amp, ph)
+    graph.replay()
+    torch.cuda.synchronize(dev)
+    e0.record(st)
+    graph.replay()
+    e1.record(st)
+    e1.synchronize()
+    us = e0.elapsed_time(e1) * 1e3 / K2
+    qld_stream = {"what": "qld_push_image, %d frames per launch, %d launches replayed from a CUDA graph" % (ADV, K2),
+                  "us_per_launch": us, "gpf_s": H * W * ADV / (us * 1e-6) / 1e9,
+                  "achieved_gbs": ab["push_image"] / (us * 1e-6) / 1e9,
+                  "frac": ab["push_image"] / (us * 1e-6) / 1e9 / peak, "algorithmic_bytes": ab["push_image"],
+                  "eager_us_per_launch": us_eager}
+    del graph
+
     e2e = None
     if not args.no_e2e:
         e2e = run_e2e(args, q, torch, dev, st, pool)
@@ -331,6 +367,11 @@ def run_cuda(args, world, rank, local):
         cpu = cpu_baseline_from_band(band, rows, args.cpu_seconds)
 
     ctx.destroy()
+    del pool
+    large = None
+    if not args.no_large and args.case == "full":
+        torch.cuda.empty_cache()
+        large = run_large(q, torch, dev, st, peak)
     traffic = profiled_traffic("fftbin")
     out = {
         "metric": METRIC,
@@ -362,12 +403,56 @@ def run_cuda(args, world, rank, local):
                        "samples": len(lat),
                        "what": "host call of qld_push_image (4 frames already in HBM) to image complete"}
         if lat else None,
+        "qld_stream": qld_stream,
+        "qld_large": large,
         "gpu_launches": launches,
         "clocks": clk,
         "e2e": e2e,
         "cpu_baseline": cpu,
     }
     return out
+
+
+def run_large(q, torch, dev, st, peak, steps=200):
+    """4096x4096 uint16, N = 2048 (a 68.7 GB ring), one new frame per push with
+    the image fused: the sliding window at a size where launch overhead no
+    longer hides the streaming rate."""
+    from qldscene import DeviceScene, scene_fog
+
+    HL = WL = 4096
+    NL = 2048
+    P = 64
+    sc = scene_fog(5, seed=1005, H=HL, W=WL)
+    ds = DeviceScene(sc, dev)
+    pool = torch.empty((P, HL, WL), dtype=torch.uint16, device=dev)
+    ctx = q.qld_create(HL, WL, NL, q.QLD_U16)
+    for s0 in range(1, NL + 1, P):
+        ds.generate_into(pool, s0, P)
+        q.qld_push_frames(ctx, pool, P, st)
+    ds.generate_into(pool, NL + 1, P)
+    amp = torch.empty(HL * WL, dtype=torch.float32, device=dev)
+    ph = torch.empty_like(amp)
+    for i in range(5):
+        q.qld_push_image(ctx, pool[i:i + 1], 1, st, amp, ph)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize(dev)
+    e0.record(st)
+    for i in range(steps):
+        j = (5 + i) % P
+        q.qld_push_image(ctx, pool[j:j + 1], 1, st, amp, ph)
+    e1.record(st)
+    e1.synchronize()
+    us = e0.elapsed_time(e1) * 1e3 / steps
+    npix = HL * WL
+    nbytes = npix * (3 * 2 + 16 + 8)
+    ring_gb = q.qld_footprint_bytes(HL, WL, NL, 2) / 1e9
+    ctx.destroy()
+    del pool, amp, ph
+    torch.cuda.empty_cache()
+    return {"workload": "4096x4096 uint16, N=2048 (context %.1f GB), +1 frame per qld_push_image, %d launches "
+                        "back to back" % (ring_gb, steps),
+            "us_per_launch": us, "gpf_s": npix / (us * 1e-6) / 1e9, "algorithmic_bytes": nbytes,
+            "achieved_gbs": nbytes / (us * 1e-6) / 1e9, "frac": nbytes / (us * 1e-6) / 1e9 / peak}
 
 
 def run_e2e(args, q, torch, dev, st, pool):

@@ -164,18 +164,6 @@ int enqueue_image(qld_ctx* c, float* amp, float* phase) {
     return cudaGetLastError() == cudaSuccess ? QLD_OK : QLD_E_CUDA;
 }
 
-template <typename T>
-void launch_fftbin_t(const qld_ctx* c, float* out, long long nvec) {
-    const int pv_log = qldk::fftbin_pv_log(nvec);
-    const unsigned grid = (unsigned)((nvec + (1ll << pv_log) - 1) >> pv_log);
-    switch (pv_log) {
-        case 5: qldk::fftbin_kernel<T, 5><<<grid, 256, 0, c->stream>>>(c->ring, c->slot_stride, c->N, c->tw, nvec, c->npix, out); break;
-        case 4: qldk::fftbin_kernel<T, 4><<<grid, 256, 0, c->stream>>>(c->ring, c->slot_stride, c->N, c->tw, nvec, c->npix, out); break;
-        case 3: qldk::fftbin_kernel<T, 3><<<grid, 256, 0, c->stream>>>(c->ring, c->slot_stride, c->N, c->tw, nvec, c->npix, out); break;
-        default: qldk::fftbin_kernel<T, 2><<<grid, 256, 0, c->stream>>>(c->ring, c->slot_stride, c->N, c->tw, nvec, c->npix, out); break;
-    }
-}
-
 int enqueue_fft_bin(qld_ctx* c, int k, float* out) {
     if (c->tw_k != k) {
         g_launches.fetch_add(1);
@@ -185,8 +173,10 @@ int enqueue_fft_bin(qld_ctx* c, int k, float* out) {
     }
     const long long nvec = (c->npix * c->bpp + qldk::kVecBytes - 1) / qldk::kVecBytes;
     g_launches.fetch_add(1);
-    if (c->pixfmt == QLD_U16) launch_fftbin_t<uint16_t>(c, out, nvec);
-    else launch_fftbin_t<uint8_t>(c, out, nvec);
+    if (c->pixfmt == QLD_U16)
+        qldk::launch_fftbin<uint16_t>(c->ring, c->slot_stride, c->N, c->tw, nvec, c->npix, out, c->stream);
+    else
+        qldk::launch_fftbin<uint8_t>(c->ring, c->slot_stride, c->N, c->tw, nvec, c->npix, out, c->stream);
     return cudaGetLastError() == cudaSuccess ? QLD_OK : QLD_E_CUDA;
 }
 
@@ -535,23 +525,8 @@ extern "C" int qld_fft_bin_frames_noalloc(const void* frames, int H, int W, int 
     qldk::twiddle_kernel<<<blocks_for(N, 256), 256, 0, st>>>(tw, N, k);
     const uint8_t* base = (const uint8_t*)frames;
     const long long nvec = frame_bytes / qldk::kVecBytes;
-    const int pv_log = qldk::fftbin_pv_log(nvec);
-    const unsigned grid = (unsigned)((nvec + (1ll << pv_log) - 1) >> pv_log);
     g_launches.fetch_add(1);
-    if (pixfmt == QLD_U16) {
-        switch (pv_log) {
-            case 5: qldk::fftbin_kernel<uint16_t, 5><<<grid, 256, 0, st>>>(base, frame_bytes, N, tw, nvec, npix, out); break;
-            case 4: qldk::fftbin_kernel<uint16_t, 4><<<grid, 256, 0, st>>>(base, frame_bytes, N, tw, nvec, npix, out); break;
-            case 3: qldk::fftbin_kernel<uint16_t, 3><<<grid, 256, 0, st>>>(base, frame_bytes, N, tw, nvec, npix, out); break;
-            default: qldk::fftbin_kernel<uint16_t, 2><<<grid, 256, 0, st>>>(base, frame_bytes, N, tw, nvec, npix, out); break;
-        }
-    } else {
-        switch (pv_log) {
-            case 5: qldk::fftbin_kernel<uint8_t, 5><<<grid, 256, 0, st>>>(base, frame_bytes, N, tw, nvec, npix, out); break;
-            case 4: qldk::fftbin_kernel<uint8_t, 4><<<grid, 256, 0, st>>>(base, frame_bytes, N, tw, nvec, npix, out); break;
-            case 3: qldk::fftbin_kernel<uint8_t, 3><<<grid, 256, 0, st>>>(base, frame_bytes, N, tw, nvec, npix, out); break;
-            default: qldk::fftbin_kernel<uint8_t, 2><<<grid, 256, 0, st>>>(base, frame_bytes, N, tw, nvec, npix, out); break;
-        }
-    }
+    if (pixfmt == QLD_U16) qldk::launch_fftbin<uint16_t>(base, frame_bytes, N, tw, nvec, npix, out, st);
+    else qldk::launch_fftbin<uint8_t>(base, frame_bytes, N, tw, nvec, npix, out, st);
     return set_err(cudaGetLastError() == cudaSuccess ? QLD_OK : QLD_E_CUDA);
 }

@@ -329,22 +329,24 @@ __global__ void twiddle_kernel(float2* __restrict__ tw, int N, int k) {
     tw[j] = make_float2((float)cs, (float)(-sn));
 }
 
-// Pixel-tiled single-bin DFT over the N ring slots. A CTA of 256 threads
-// covers PV = 2^PV_LOG pixel vectors and splits the time axis into 256/PV
-// slices: thread t takes vector t mod PV and frames j = t/PV, t/PV + 256/PV,
-// ... Each thread accumulates in float32, flushing a partial every 16 frames
-// into a running sum to keep rounding small. When PV < 32 one warp holds
-// 32/PV time slices of the same pixels and they are combined with
-// warp shuffles; the 8 warps' partials are then combined in shared memory.
-template <typename T, int PV_LOG>
-__global__ void __launch_bounds__(256) fftbin_kernel(const uint8_t* __restrict__ ring, long long slot_stride, int N,
-                                                     const float2* __restrict__ tw, long long nvec, long long npix,
-                                                     float* __restrict__ out) {
+// Pixel-tiled single-bin DFT over the N ring slots. A CTA of NT threads
+// covers PV = 2^PV_LOG pixel vectors and splits the time axis into NT/PV
+// slices: thread t takes vector t mod PV and frames j = t/PV, t/PV + NT/PV,
+// ..., four loads in flight. Each thread accumulates in float32, flushing a
+// partial every 16 frames into a running sum to keep rounding small. When
+// PV < 32 one warp holds 32/PV time slices of the same pixels and they are
+// combined with warp shuffles; the warps' partials are then combined in
+// shared memory.
+template <typename T, int PV_LOG, int NT>
+__global__ void __launch_bounds__(NT) fftbin_kernel(const uint8_t* __restrict__ ring, long long slot_stride, int N,
+                                                    const float2* __restrict__ tw, long long nvec, long long npix,
+                                                    float* __restrict__ out) {
     constexpr int VP = kVecBytes / (int)sizeof(T);
     constexpr int PV = 1 << PV_LOG;
-    constexpr int TS = 256 / PV;
-    static_assert(PV >= 4 && PV <= 32, "pixel vectors per CTA must be 4..32");
-    __shared__ float2 red[8][PV * VP];
+    constexpr int TS = NT / PV;
+    constexpr int NW = NT / 32;
+    static_assert(PV >= 4 && PV <= 32 && NT % 32 == 0 && TS >= 1, "bad fftbin_kernel geometry");
+    __shared__ float2 red[NW][PV * VP];
 
     const int t = threadIdx.x;
     const int pv = t & (PV - 1);
@@ -413,10 +415,10 @@ __global__ void __launch_bounds__(256) fftbin_kernel(const uint8_t* __restrict__
     }
     __syncthreads();
     const long long pbase = (long long)blockIdx.x * PV * VP;
-    for (int e = t; e < PV * VP; e += 256) {
+    for (int e = t; e < PV * VP; e += NT) {
         float a = 0.f, b = 0.f;
 #pragma unroll
-        for (int w = 0; w < 8; ++w) {
+        for (int w = 0; w < NW; ++w) {
             const float2 r = red[w][e];
             a += r.x;
             b += r.y;
@@ -427,13 +429,28 @@ __global__ void __launch_bounds__(256) fftbin_kernel(const uint8_t* __restrict__
 }
 
 // Launch geometry of fftbin_kernel: log2 of the pixel vectors per CTA. 32
-// vectors (8 time slices) when the grid still has two CTAs per SM; fewer
-// (more time slices, reduced with warp shuffles) for small frames so the
-// grid still covers the GPU.
+// vectors in 128-thread CTAs (4 time slices) when the grid still has two
+// CTAs per SM; fewer vectors in 256-thread CTAs (more time slices, reduced
+// with warp shuffles) for small frames so the grid still covers the GPU.
 inline int fftbin_pv_log(long long nvec) {
     int pv_log = 5;
     while (pv_log > 2 && (nvec + (1ll << pv_log) - 1) / (1ll << pv_log) < 296) --pv_log;
     return pv_log;
+}
+
+// Enqueues fftbin_kernel over `N` frames (frame j at base + j * stride) of
+// nvec 16-byte vectors each, npix pixels, twiddles tw[j], power into out.
+template <typename T>
+inline void launch_fftbin(const uint8_t* base, long long stride, int N, const float2* tw, long long nvec,
+                          long long npix, float* out, cudaStream_t st) {
+    const int pv_log = fftbin_pv_log(nvec);
+    const unsigned grid = (unsigned)((nvec + (1ll << pv_log) - 1) >> pv_log);
+    switch (pv_log) {
+        case 5: fftbin_kernel<T, 5, 128><<<grid, 128, 0, st>>>(base, stride, N, tw, nvec, npix, out); break;
+        case 4: fftbin_kernel<T, 4, 256><<<grid, 256, 0, st>>>(base, stride, N, tw, nvec, npix, out); break;
+        case 3: fftbin_kernel<T, 3, 256><<<grid, 256, 0, st>>>(base, stride, N, tw, nvec, npix, out); break;
+        default: fftbin_kernel<T, 2, 256><<<grid, 256, 0, st>>>(base, stride, N, tw, nvec, npix, out); break;
+    }
 }
 
 }  // namespace qldk
