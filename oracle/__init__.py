@@ -53,6 +53,10 @@ class Oracle:
         lib.orc_amplitude_phase.restype = _int
         lib.orc_dft_bin.argtypes = [_p, _int, _i64, _i64, _int, _i64, _i64, _p, _p, _p, _int]
         lib.orc_dft_bin.restype = _int
+        lib.orc_lockin_general.argtypes = [_p, _int, _i64, _i64, _int, _i64, ctypes.c_double, _p, _p, _p, _p, _int]
+        lib.orc_lockin_general.restype = _int
+        lib.orc_cnr.argtypes = [_p, _int, _int, _int, _int, _int, _p]
+        lib.orc_cnr.restype = _int
         self.lib = lib
         self.path = lib_path
 
@@ -106,6 +110,28 @@ class Oracle:
         return re.reshape(shape), im.reshape(shape), pw.reshape(shape)
 
 
+    def lockin_general(self, x, omega_dt, s0=1, nthreads=1):
+        """FP64 (S, C, R, phase) of the lock-in at omega*dt = omega_dt rad/frame."""
+        flat, fmt, N, shape = _window(x)
+        npix = flat.shape[1]
+        out = [np.zeros(npix, np.float64) for _ in range(4)]
+        rc = self.lib.orc_lockin_general(_ptr(flat), fmt, npix, npix, N, int(s0), float(omega_dt),
+                                         *[_ptr(a) for a in out], int(nthreads))
+        if rc != 0:
+            raise ValueError("orc_lockin_general rejected its arguments")
+        return tuple(a.reshape(shape) for a in out)
+
+    def cnr(self, img, r0, c0, m):
+        """Contrast-to-noise ratio of the m x m source at (r0, c0) of img."""
+        img = np.ascontiguousarray(np.asarray(img, np.float64))
+        H, W = img.shape
+        out = np.zeros(1, np.float64)
+        rc = self.lib.orc_cnr(_ptr(img), H, W, int(r0), int(c0), int(m), _ptr(out))
+        if rc != 0:
+            raise ValueError("orc_cnr: the surround ring leaves the image")
+        return float(out[0])
+
+
 _default = None
 
 
@@ -135,3 +161,11 @@ def qld(x, s0=1, nthreads=1):
 
 def dft_bin(x, k, s0=1, nthreads=1):
     return get().dft_bin(x, k, s0, nthreads)
+
+
+def lockin_general(x, omega_dt, s0=1, nthreads=1):
+    return get().lockin_general(x, omega_dt, s0, nthreads)
+
+
+def cnr(img, r0, c0, m):
+    return get().cnr(img, r0, c0, m)

@@ -22,6 +22,9 @@
 //  * DFT bin (Methods, FFT discrimination): X_k = sum_s I(s) exp(-2 pi i k s / N)
 //    over the window, with (k * s) mod N reduced in integers before the FP64
 //    cos/sin; the map is |X_k|^2.
+//  * General-frequency lock-in (Methods, Fig. 1 frequencies): the same sums
+//    with sin/cos(omega s dt) tabulated in FP64 for any omega dt.
+//  * Contrast-to-noise ratio (Methods, CNR equation and the "surround" figure).
 //
 // Every array is a window of N frames laid out frame-major: frame i of the
 // window starts at x + i * stride (elements), and pixels 0 .. npix-1 of a
@@ -193,6 +196,73 @@ int orc_dft_bin(const void* x, int pixfmt, int64_t stride, int64_t npix, int N, 
     } else {
         return -1;
     }
+    return 0;
+}
+
+// Lock-in at an arbitrary frequency (Methods, R(j,k) with the values of
+// sin(omega_i t_s) and cos(omega_i t_s) read from pre-calculated arrays;
+// t_s = s dt). omega_dt = omega * dt in radians per frame; the window holds
+// frames s0 .. s0+N-1. S = sum I sin(omega t_s), C = sum I cos(omega t_s),
+// R = sqrt(S^2 + C^2), phase = atan2(-S, C), all FP64. Any output may be NULL.
+int orc_lockin_general(const void* x, int pixfmt, int64_t stride, int64_t npix, int N, int64_t s0,
+                       double omega_dt, double* S, double* C, double* R, double* phase, int nthreads) {
+    if (!x || N < 1 || npix < 0 || stride < npix || (pixfmt != 1 && pixfmt != 2)) return -1;
+    std::vector<double> sin_t(N), cos_t(N);
+    for (int i = 0; i < N; ++i) {
+        const double arg = omega_dt * (double)(s0 + i);
+        sin_t[i] = std::sin(arg);
+        cos_t[i] = std::cos(arg);
+    }
+    run_partitioned(npix, nthreads, [&](int64_t lo, int64_t n) {
+        for (int64_t p = lo; p < lo + n; ++p) {
+            double a = 0.0, b = 0.0;
+            for (int i = 0; i < N; ++i) {
+                const int64_t idx = (int64_t)i * stride + p;
+                const double I = pixfmt == 1 ? (double)((const uint8_t*)x)[idx] : (double)((const uint16_t*)x)[idx];
+                a += I * sin_t[i];
+                b += I * cos_t[i];
+            }
+            if (S) S[p] = a;
+            if (C) C[p] = b;
+            if (R) R[p] = std::sqrt(a * a + b * b);
+            if (phase) phase[p] = (a == 0.0 && b == 0.0) ? 0.0 : std::atan2(-a, b);
+        }
+    });
+    return 0;
+}
+
+// Contrast-to-noise ratio (Methods, "Estimation of Contrast-to-noise-ratio"):
+// the source is the m x m block with top-left corner (r0, c0) of the H x W
+// image; the surround is the m-pixel-wide square ring around it, i.e. the
+// 3m x 3m block centred on the source minus the source (8 m^2 pixels).
+// CNR = (mean_source - mean_surround) / sqrt(mean over the surround of
+// (I - mean_surround)^2). Returns -1 if the ring leaves the image.
+int orc_cnr(const double* img, int H, int W, int r0, int c0, int m, double* cnr) {
+    if (!img || !cnr || m < 1 || r0 - m < 0 || c0 - m < 0 || r0 + 2 * m > H || c0 + 2 * m > W) return -1;
+    double src = 0.0;
+    for (int r = r0; r < r0 + m; ++r)
+        for (int c = c0; c < c0 + m; ++c) src += img[(int64_t)r * W + c];
+    src /= (double)m * m;
+    double sur = 0.0;
+    int64_t count = 0;
+    for (int r = r0 - m; r < r0 + 2 * m; ++r)
+        for (int c = c0 - m; c < c0 + 2 * m; ++c) {
+            const bool in_source = r >= r0 && r < r0 + m && c >= c0 && c < c0 + m;
+            if (in_source) continue;
+            sur += img[(int64_t)r * W + c];
+            ++count;
+        }
+    sur /= (double)count;
+    double var = 0.0;
+    for (int r = r0 - m; r < r0 + 2 * m; ++r)
+        for (int c = c0 - m; c < c0 + 2 * m; ++c) {
+            const bool in_source = r >= r0 && r < r0 + m && c >= c0 && c < c0 + m;
+            if (in_source) continue;
+            const double d = img[(int64_t)r * W + c] - sur;
+            var += d * d;
+        }
+    var /= (double)count;
+    *cnr = (src - sur) / std::sqrt(var);
     return 0;
 }
 

@@ -234,6 +234,90 @@ def pin_golden_worked_example(o):
     _assert_close(o.dft_bin(x, N // 2, s0=s0)[0], g["XN2"], 0, 1e-9, "golden X_{N/2}")
 
 
+# General-frequency lock-in (Methods, Fig. 1 frequencies). At omega dt = pi/2
+# it is the four-samples-per-period QLD.
+def pin_lockin_general_quarter_rate(o):
+    rng = np.random.default_rng(21)
+    x = rng.integers(0, 4096, size=(64, 9)).astype(np.uint16)
+    S, C, R, ph = o.lockin_general(x, math.pi / 2, s0=7)
+    Si, Ci = o.quadrature_sums(x, s0=7)
+    tol = 1e-12 * float(x.astype(np.float64).sum())
+    _assert_close(S, Si, 0, tol, "general lock-in at pi/2: S")
+    _assert_close(C, Ci, 0, tol, "general lock-in at pi/2: C")
+    R_i, ph_i = o.amplitude_phase(Si, Ci)
+    _assert_close(R, R_i, 1e-12, 0, "general lock-in at pi/2: R")
+    _assert_close(ph, ph_i, 0, 1e-9, "general lock-in at pi/2: phase")
+
+
+# Tone x_s = B + A cos(w s + phi0), rounded to integers, with w = 2 pi p / N so the
+# window holds p whole periods. Over whole periods sum sin(w s) = sum cos(w s) = 0,
+# sum sin^2 = sum cos^2 = N/2 and sum sin cos = 0, so the lock-in at w gives
+# S = -(N/2) A sin(phi0), C = (N/2) A cos(phi0), R = (N/2) A; at any other
+# w' = 2 pi p' / N (p' != p, N - p, 0) S = C = 0. Rounding each sample moves S
+# and C by at most N/2.
+def pin_lockin_general_tone_and_orthogonality(o):
+    for N, p, pw, s0, phi0 in [(64, 5, 9, 1, 0.7), (82, 19, 23, 4, -2.0), (100, 23, 29, 11, 2.9)]:
+        A, B = 10000.0, 20000.0
+        s = np.arange(s0, s0 + N, dtype=np.float64)
+        w = 2 * math.pi * p / N
+        x = np.rint(B + A * np.cos(w * s + phi0)).astype(np.uint16).reshape(N, 1)
+        S, C, R, ph = o.lockin_general(x, w, s0=s0)
+        bound = N / 2 + 1e-6
+        _assert_close(S, [-(N / 2) * A * math.sin(phi0)], 0, bound, "tone S")
+        _assert_close(C, [(N / 2) * A * math.cos(phi0)], 0, bound, "tone C")
+        _assert_close(R, [(N / 2) * A], 0, bound, "tone R")
+        _assert_close(ph, [phi0], 0, 2 * bound / (N / 2 * A), "tone phase")
+        So, Co, Ro, _ = o.lockin_general(x, 2 * math.pi * pw / N, s0=s0)
+        _assert_close(Ro, [0.0], 0, math.sqrt(2) * bound, "off-frequency tone gives zero")
+
+
+# At w = 2 pi k / N the lock-in is the DFT bin: C - iS = X_k (numpy's FFT of the
+# window times exp(-2 pi i k s0 / N) for the absolute frame index).
+def pin_lockin_general_is_dft_bin(o):
+    rng = np.random.default_rng(22)
+    for N, s0 in [(12, 1), (41, 5), (82, 2)]:
+        x = rng.integers(0, 256, size=(N, 4)).astype(np.uint8)
+        Y = np.fft.fft(x.astype(np.float64), axis=0)
+        for k in [0, 1, N // 3, N - 1]:
+            S, C, R, ph = o.lockin_general(x, 2 * math.pi * k / N, s0=s0)
+            X = Y[k] * np.exp(-2j * np.pi * k * s0 / N)
+            scale = float(x.astype(np.float64).sum())
+            _assert_close(C, X.real, 0, 1e-11 * scale, "lock-in = DFT real part")
+            _assert_close(-S, X.imag, 0, 1e-11 * scale, "lock-in = DFT imaginary part")
+
+
+def _load_cnr_golden():
+    vals = {}
+    with open(os.path.join(GOLDEN, "cnr_surround_example.txt")) as f:
+        for line in f:
+            line = line.split("#", 1)[0].strip()
+            if line:
+                k, v = line.split(":", 1)
+                vals[k.strip()] = [int(t) for t in v.split()]
+    H, W = vals["H"][0], vals["W"][0]
+    A = np.array([vals["A_row%02d" % r] for r in range(H)], np.float64)
+    B = np.array([vals["B_row%02d" % r] for r in range(H)], np.float64)
+    return vals, A, B
+
+
+def pin_cnr_worked_example(o):
+    vals, A, B = _load_cnr_golden()
+    r0, c0, m = vals["r0"][0], vals["c0"][0], vals["m"][0]
+    _assert_close([o.cnr(A, r0, c0, m) ** 2], vals["A_cnr_sq"], 1e-12, 0, "CNR case A")
+    _assert_close([o.cnr(B, r0, c0, m) ** 2], vals["B_cnr_sq"], 1e-12, 0, "CNR case B")
+    # CNR is unchanged by an offset, a positive scale, or pixels outside the ring
+    A2 = 3.5 * A + 17.0
+    A2[0, :] = -1e6
+    A2[:, -1] = 1e6
+    _assert_close([o.cnr(A2, r0, c0, m)], [8.0], 1e-12, 0, "CNR invariances")
+    try:
+        o.cnr(A, 1, 1, 4)
+    except ValueError:
+        pass
+    else:
+        raise AssertionError("a ring leaving the image must be rejected")
+
+
 ALL_PINS = [
     pin_reference_tables,
     pin_square_wave,
@@ -246,4 +330,8 @@ ALL_PINS = [
     pin_amplitude_phase_cases,
     pin_threads_agree,
     pin_golden_worked_example,
+    pin_lockin_general_quarter_rate,
+    pin_lockin_general_tone_and_orthogonality,
+    pin_lockin_general_is_dft_bin,
+    pin_cnr_worked_example,
 ]

@@ -37,6 +37,16 @@ MUTANTS = [
     ("dft_power_term", "power[p] = a * a + b * b;", "power[p] = a * a + b;"),
     ("dft_half_angle", "const double theta = 2.0 * M_PI * (double)m / (double)N;",
      "const double theta = M_PI * (double)m / (double)N;"),
+    ("lockin_sin_cos_swapped", "a += I * sin_t[i];\n                b += I * cos_t[i];",
+     "a += I * cos_t[i];\n                b += I * sin_t[i];"),
+    ("lockin_zero_based_time", "const double arg = omega_dt * (double)(s0 + i);",
+     "const double arg = omega_dt * (double)(s0 + i - 1);"),
+    ("cnr_ring_includes_source", "            if (in_source) continue;\n            sur += img",
+     "            sur += img"),
+    ("cnr_deviation_about_source_mean", "const double d = img[(int64_t)r * W + c] - sur;",
+     "const double d = img[(int64_t)r * W + c] - src;"),
+    ("cnr_ring_one_pixel_short", "for (int r = r0 - m; r < r0 + 2 * m; ++r)\n        for (int c = c0 - m; c < c0 + 2 * m; ++c) {\n            const bool in_source = r >= r0 && r < r0 + m && c >= c0 && c < c0 + m;\n            if (in_source) continue;\n            sur",
+     "for (int r = r0 - m; r < r0 + 2 * m; ++r)\n        for (int c = c0 - m; c < c0 + 2 * m - 1; ++c) {\n            const bool in_source = r >= r0 && r < r0 + m && c >= c0 && c < c0 + m;\n            if (in_source) continue;\n            sur"),
     ("threads_last_range_lost", "for (int t = 0; t < nthreads; ++t) {", "for (int t = 0; t < nthreads - 1; ++t) {"),
 ]
 
