@@ -20,6 +20,7 @@ every window from scratch) on the host cores on a bounded band of rows.
 import argparse
 import hashlib
 import json
+import math
 import os
 import statistics
 import subprocess
@@ -356,6 +357,26 @@ def run_cuda(args, world, rank, local):
                   "eager_us_per_launch": us_eager}
     del graph
 
+    # General-frequency lock-in (block mode over caller frames, Fig. 1 style):
+    # N frames of the pool at 23 Hz sampled at 102 frames/s, amplitude and phase
+    lk_table = torch.empty(2 * N, dtype=torch.float32, device=dev)
+    q.qld_lockin_table(2 * math.pi * 23.0 / 102.0, 1, N, lk_table, st)
+    lk_frames = pool[:N]
+    for _ in range(3):
+        q.qld_lockin_frames(lk_frames, H, W, N, q.QLD_U16, lk_table, amp, ph, st)
+    LK = 20
+    e0.record(st)
+    for _ in range(LK):
+        q.qld_lockin_frames(lk_frames, H, W, N, q.QLD_U16, lk_table, amp, ph, st)
+    e1.record(st)
+    e1.synchronize()
+    us_lk = e0.elapsed_time(e1) * 1e3 / LK
+    lk_bytes = N * H * W * 2 + H * W * 8
+    lockin = {"what": "qld_lockin_frames over %d caller frames of 1024x1024 uint16 at 23 Hz / 102 frames/s, "
+                      "amplitude + phase, %d launches" % (N, LK),
+              "us_per_launch": us_lk, "algorithmic_bytes": lk_bytes, "achieved_gbs": lk_bytes / (us_lk * 1e-6) / 1e9,
+              "frac": lk_bytes / (us_lk * 1e-6) / 1e9 / peak}
+
     e2e = None
     if not args.no_e2e:
         e2e = run_e2e(args, q, torch, dev, st, pool)
@@ -372,7 +393,7 @@ def run_cuda(args, world, rank, local):
     if not args.no_large and args.case == "full":
         torch.cuda.empty_cache()
         large = run_large(q, torch, dev, st, peak)
-    traffic = profiled_traffic("fftbin")
+    traffic = profiled_traffic("bin_power")
     out = {
         "metric": METRIC,
         "value": value,
@@ -389,7 +410,7 @@ def run_cuda(args, world, rank, local):
         "config": {"workload": WORKLOAD, "H": H, "W": W, "N": N, "advance": ADV, "pixfmt": "uint16 12-bit",
                    "od": OD, "dft_bin_k": K_BIN, "parallelism": "one camera stream per GPU" if world > 1 else "1 GPU",
                    "l2": "inputs larger than L2: 4 GiB frame pool cycled + 2 GiB window read by the DFT bin each step"},
-        "roofline": {"bound": "hbm", "kernel": "fftbin_kernel (qld_fft_bin)", "achieved": fft_gbs, "peak": peak,
+        "roofline": {"bound": "hbm", "kernel": "bin_kernel<uint16_t,5,128,power> (qld_fft_bin)", "achieved": fft_gbs, "peak": peak,
                      "unit": "GB/s", "frac": fft_gbs / peak, "peak_kind": peak_kind,
                      "algorithmic_bytes_per_launch": ab["fft_bin"], "traffic": traffic},
         "kernels": {
@@ -405,6 +426,7 @@ def run_cuda(args, world, rank, local):
         if lat else None,
         "qld_stream": qld_stream,
         "qld_large": large,
+        "lockin_general": lockin,
         "gpu_launches": launches,
         "clocks": clk,
         "e2e": e2e,

@@ -151,6 +151,28 @@ int qld_sync(qld_ctx* ctx);
 /* The context's current stream (a cudaStream_t). */
 void* qld_stream(const qld_ctx* ctx);
 
+/* General-frequency lock-in (Methods, "Numerical simulations": the sums of
+ * I(t_s) sin(omega_i t_s) and I(t_s) cos(omega_i t_s) with the sine and
+ * cosine read from pre-calculated arrays; Fig. 1 uses 20-29 Hz sources and
+ * N = 82 or 41 frames, not four samples per period).
+ *
+ * qld_lockin_table fills table (device float32 [N][2], caller-owned, 8-byte
+ * aligned) with (cos, -sin) of omega_dt * s for s = s0 .. s0+N-1, omega_dt =
+ * omega * dt in radians per frame, evaluated in FP64 and rounded to float
+ * (SI item 1: the set-up thread builds the tables). With omega_dt = 2 pi k / N
+ * the table holds the DFT twiddles of bin k.
+ *
+ * qld_lockin_frames computes, for every pixel of a block of N frames (device
+ * [N][H][W], 16-byte aligned, H*W*pixfmt a multiple of 16 bytes; N >= 1, not
+ * restricted to multiples of 4), X = sum_j x_j * table[j] accumulated in
+ * float32, and writes the amplitude R = |X| = sqrt(S^2 + C^2) into amp and the
+ * phase atan2(-S, C) into phase (device float32 [H][W]; either may be NULL).
+ * Frame j of the block is the frame of index s0 + j the table was built for.
+ * Both enqueue on `stream` and return QLD_E_INVAL for bad arguments. */
+int qld_lockin_table(double omega_dt, long long s0, int N, float* table, void* stream);
+int qld_lockin_frames(const void* frames, int H, int W, int N, int pixfmt, const float* table, float* amp,
+                      float* phase, void* stream);
+
 /* Largest N accepted by qld_fft_bin_frames_noalloc. */
 #define QLD_NOALLOC_MAX_N 16384
 

@@ -19,7 +19,8 @@ __all__ = [
     "qld_push_image", "qld_image", "qld_fft_bin", "qld_push_frames_host", "qld_image_host",
     "qld_fft_bin_host", "qld_get_iq", "qld_reset", "qld_frames_pushed", "qld_sync", "qld_stream",
     "qld_strerror", "qld_last_error", "qld_version", "qld_footprint_bytes", "qld_set_mem_budget",
-    "qld_mem_in_use", "qld_launch_count", "qld_fft_bin_frames_noalloc", "QLD_NOALLOC_MAX_N", "LIB_PATH", "lib",
+    "qld_mem_in_use", "qld_launch_count", "qld_fft_bin_frames_noalloc", "QLD_NOALLOC_MAX_N",
+    "qld_lockin_table", "qld_lockin_frames", "LIB_PATH", "lib",
 ]
 
 QLD_U8, QLD_U16 = 1, 2
@@ -56,6 +57,8 @@ _SIGS = {
     "qld_image_host": ([_p, _p, _p], _i),
     "qld_fft_bin_host": ([_p, _i, _p], _i),
     "qld_fft_bin_frames_noalloc": ([_p, _i, _i, _i, _i, _i, _p, _p], _i),
+    "qld_lockin_table": ([ctypes.c_double, _ll, _i, _p, _p], _i),
+    "qld_lockin_frames": ([_p, _i, _i, _i, _i, _p, _p, _p, _p], _i),
     "qld_get_iq": ([_p, _p, _p], _i),
     "qld_reset": ([_p], _i),
     "qld_frames_pushed": ([_p], _ll),
@@ -229,6 +232,20 @@ def qld_fft_bin_frames_noalloc(frames, H, W, N, pixfmt, k, out, stream=None):
     return _check(lib.qld_fft_bin_frames_noalloc(_addr(frames, int(N) * nb, "frames"), int(H), int(W), int(N),
                                                  int(pixfmt), int(k), _addr(out, 4 * int(H) * int(W), "out"),
                                                  _stream(stream)), "qld_fft_bin_frames_noalloc")
+
+
+def qld_lockin_table(omega_dt, s0, N, table, stream=None):
+    """Fills the device float32 [N][2] table with (cos, -sin)(omega_dt * s), s = s0 .. s0+N-1."""
+    return _check(lib.qld_lockin_table(float(omega_dt), int(s0), int(N), _addr(table, 8 * int(N), "table"),
+                                       _stream(stream)), "qld_lockin_table")
+
+
+def qld_lockin_frames(frames, H, W, N, pixfmt, table, amp=None, phase=None, stream=None):
+    """Amplitude and phase of the lock-in with `table` over N device frames."""
+    npix = int(H) * int(W)
+    return _check(lib.qld_lockin_frames(_addr(frames, int(N) * npix * int(pixfmt), "frames"), int(H), int(W), int(N),
+                                        int(pixfmt), _addr(table, 8 * int(N), "table"), _addr(amp, 4 * npix, "amp"),
+                                        _addr(phase, 4 * npix, "phase"), _stream(stream)), "qld_lockin_frames")
 
 
 def qld_get_iq(ctx, S=None, C=None):

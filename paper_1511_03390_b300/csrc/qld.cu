@@ -174,9 +174,11 @@ int enqueue_fft_bin(qld_ctx* c, int k, float* out) {
     const long long nvec = (c->npix * c->bpp + qldk::kVecBytes - 1) / qldk::kVecBytes;
     g_launches.fetch_add(1);
     if (c->pixfmt == QLD_U16)
-        qldk::launch_fftbin<uint16_t>(c->ring, c->slot_stride, c->N, c->tw, nvec, c->npix, out, c->stream);
+        qldk::launch_bin<uint16_t, qldk::kBinPower>(c->ring, c->slot_stride, c->N, c->tw, nvec, c->npix, out, nullptr,
+                                                   c->stream);
     else
-        qldk::launch_fftbin<uint8_t>(c->ring, c->slot_stride, c->N, c->tw, nvec, c->npix, out, c->stream);
+        qldk::launch_bin<uint8_t, qldk::kBinPower>(c->ring, c->slot_stride, c->N, c->tw, nvec, c->npix, out, nullptr,
+                                                  c->stream);
     return cudaGetLastError() == cudaSuccess ? QLD_OK : QLD_E_CUDA;
 }
 
@@ -526,7 +528,41 @@ extern "C" int qld_fft_bin_frames_noalloc(const void* frames, int H, int W, int 
     const uint8_t* base = (const uint8_t*)frames;
     const long long nvec = frame_bytes / qldk::kVecBytes;
     g_launches.fetch_add(1);
-    if (pixfmt == QLD_U16) qldk::launch_fftbin<uint16_t>(base, frame_bytes, N, tw, nvec, npix, out, st);
-    else qldk::launch_fftbin<uint8_t>(base, frame_bytes, N, tw, nvec, npix, out, st);
+    if (pixfmt == QLD_U16) qldk::launch_bin<uint16_t, qldk::kBinPower>(base, frame_bytes, N, tw, nvec, npix, out, nullptr, st);
+    else qldk::launch_bin<uint8_t, qldk::kBinPower>(base, frame_bytes, N, tw, nvec, npix, out, nullptr, st);
+    return set_err(cudaGetLastError() == cudaSuccess ? QLD_OK : QLD_E_CUDA);
+}
+
+// ------------------------------------------------------------------------
+// Lock-in at an arbitrary frequency over caller frames (block mode).
+
+extern "C" int qld_lockin_table(double omega_dt, long long s0, int N, float* table, void* stream) {
+    if (!table || !aligned(table, 8) || N < 1 || N > (1 << 30)) return set_err(QLD_E_INVAL);
+    if (pending_error() != QLD_OK) return set_err(QLD_E_CUDA);
+    g_launches.fetch_add(1);
+    qldk::lockin_table_kernel<<<blocks_for(N, 256), 256, 0, (cudaStream_t)stream>>>((float2*)table, N, omega_dt, s0);
+    return set_err(cudaGetLastError() == cudaSuccess ? QLD_OK : QLD_E_CUDA);
+}
+
+extern "C" int qld_lockin_frames(const void* frames, int H, int W, int N, int pixfmt, const float* table, float* amp,
+                                 float* phase, void* stream) {
+    if (!frames || !table || (!amp && !phase) || H < 1 || W < 1 || N < 1 || (pixfmt != QLD_U8 && pixfmt != QLD_U16))
+        return set_err(QLD_E_INVAL);
+    const long long npix = (long long)H * W;
+    const long long frame_bytes = npix * pixfmt;
+    if (npix > (1ll << 31) - 1 || (frame_bytes % qldk::kVecBytes) != 0 || !aligned(frames, 16) ||
+        !aligned(table, 8) || !aligned(amp, 4) || !aligned(phase, 4))
+        return set_err(QLD_E_INVAL);
+    if (pending_error() != QLD_OK) return set_err(QLD_E_CUDA);
+    const uint8_t* base = (const uint8_t*)frames;
+    const long long nvec = frame_bytes / qldk::kVecBytes;
+    cudaStream_t st = (cudaStream_t)stream;
+    g_launches.fetch_add(1);
+    if (pixfmt == QLD_U16)
+        qldk::launch_bin<uint16_t, qldk::kBinAmpPhase>(base, frame_bytes, N, (const float2*)table, nvec, npix, amp,
+                                                       phase, st);
+    else
+        qldk::launch_bin<uint8_t, qldk::kBinAmpPhase>(base, frame_bytes, N, (const float2*)table, nvec, npix, amp,
+                                                      phase, st);
     return set_err(cudaGetLastError() == cudaSuccess ? QLD_OK : QLD_E_CUDA);
 }

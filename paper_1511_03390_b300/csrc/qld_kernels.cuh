@@ -120,14 +120,12 @@ __device__ __forceinline__ float atan_unit(float x) {
     return x * p;
 }
 
-// phase = atan2(-S, C) in (-pi, pi]: the ratio of the smaller to the larger
+// atan2(y, x) in (-pi, pi]: the ratio of the smaller to the larger
 // magnitude goes through atan_unit, then the octant is restored (pi/2 - r
-// above the diagonal, pi - r for C < 0, sign of -S last). The negation is
-// done on the integer, so S = 0 gives y = +0 and C < 0 gives +pi; S = C = 0
-// gives 0. Error about 4e-7 rad (float32 rounding of the reduction and of pi).
-__device__ __forceinline__ float phase_of(int32_t s, int32_t c) {
-    const float y = (float)(-s);
-    const float x = (float)c;
+// above the diagonal, pi - r for x < 0, the sign of y last), so y = +0 with
+// x < 0 gives +pi and x = y = 0 gives 0. Error about 4e-7 rad (float32
+// rounding of the reduction and of pi).
+__device__ __forceinline__ float atan2_unit_poly(float y, float x) {
     const float ay = fabsf(y), ax = fabsf(x);
     const float mx = fmaxf(ay, ax), mn = fminf(ay, ax);
     const float a = mx > 0.f ? __fdividef(mn, mx) : 0.f;
@@ -135,6 +133,12 @@ __device__ __forceinline__ float phase_of(int32_t s, int32_t c) {
     if (ay > ax) r = 1.57079632679489662f - r;
     if (x < 0.f) r = 3.14159265358979324f - r;
     return (y < 0.f) ? -r : r;
+}
+
+// phase = atan2(-S, C), with the negation done on the integer so S = 0 gives
+// y = +0 (C < 0 then gives +pi).
+__device__ __forceinline__ float phase_of(int32_t s, int32_t c) {
+    return atan2_unit_poly((float)(-s), (float)c);
 }
 
 // ------------------------------------------------------------------- push --
@@ -329,6 +333,11 @@ __global__ void twiddle_kernel(float2* __restrict__ tw, int N, int k) {
     tw[j] = make_float2((float)cs, (float)(-sn));
 }
 
+// Output of bin_kernel: the power |X|^2, or the amplitude |X| and phase
+// arg X (the general-frequency lock-in R and atan2(-S, C), since with
+// twiddles (cos, -sin) the real part is C and the imaginary part -S).
+enum BinOut { kBinPower = 0, kBinAmpPhase = 1 };
+
 // Pixel-tiled single-bin DFT over the N ring slots. A CTA of NT threads
 // covers PV = 2^PV_LOG pixel vectors and splits the time axis into NT/PV
 // slices: thread t takes vector t mod PV and frames j = t/PV, t/PV + NT/PV,
@@ -337,15 +346,15 @@ __global__ void twiddle_kernel(float2* __restrict__ tw, int N, int k) {
 // PV < 32 one warp holds 32/PV time slices of the same pixels and they are
 // combined with warp shuffles; the warps' partials are then combined in
 // shared memory.
-template <typename T, int PV_LOG, int NT>
-__global__ void __launch_bounds__(NT) fftbin_kernel(const uint8_t* __restrict__ ring, long long slot_stride, int N,
-                                                    const float2* __restrict__ tw, long long nvec, long long npix,
-                                                    float* __restrict__ out) {
+template <typename T, int PV_LOG, int NT, int OUT>
+__global__ void __launch_bounds__(NT) bin_kernel(const uint8_t* __restrict__ ring, long long slot_stride, int N,
+                                                 const float2* __restrict__ tw, long long nvec, long long npix,
+                                                 float* __restrict__ out, float* __restrict__ out2) {
     constexpr int VP = kVecBytes / (int)sizeof(T);
     constexpr int PV = 1 << PV_LOG;
     constexpr int TS = NT / PV;
     constexpr int NW = NT / 32;
-    static_assert(PV >= 4 && PV <= 32 && NT % 32 == 0 && TS >= 1, "bad fftbin_kernel geometry");
+    static_assert(PV >= 4 && PV <= 32 && NT % 32 == 0 && TS >= 1, "bad bin_kernel geometry");
     __shared__ float2 red[NW][PV * VP];
 
     const int t = threadIdx.x;
@@ -424,11 +433,18 @@ __global__ void __launch_bounds__(NT) fftbin_kernel(const uint8_t* __restrict__ 
             b += r.y;
         }
         const long long p = pbase + e;
-        if (p < npix) out[p] = a * a + b * b;
+        if (p < npix) {
+            if (OUT == kBinPower) {
+                out[p] = a * a + b * b;
+            } else {
+                if (out) out[p] = sqrtf(fmaf(a, a, b * b));
+                if (out2) out2[p] = atan2_unit_poly(b, a);
+            }
+        }
     }
 }
 
-// Launch geometry of fftbin_kernel: log2 of the pixel vectors per CTA. 32
+// Launch geometry of bin_kernel: log2 of the pixel vectors per CTA. 32
 // vectors in 128-thread CTAs (4 time slices) when the grid still has two
 // CTAs per SM; fewer vectors in 256-thread CTAs (more time slices, reduced
 // with warp shuffles) for small frames so the grid still covers the GPU.
@@ -438,19 +454,32 @@ inline int fftbin_pv_log(long long nvec) {
     return pv_log;
 }
 
-// Enqueues fftbin_kernel over `N` frames (frame j at base + j * stride) of
-// nvec 16-byte vectors each, npix pixels, twiddles tw[j], power into out.
-template <typename T>
-inline void launch_fftbin(const uint8_t* base, long long stride, int N, const float2* tw, long long nvec,
-                          long long npix, float* out, cudaStream_t st) {
+// Enqueues bin_kernel over `N` frames (frame j at base + j * stride) of
+// nvec 16-byte vectors each, npix pixels, twiddles tw[j]; writes the power
+// into out (OUT = kBinPower) or the amplitude into out and the phase into
+// out2 (OUT = kBinAmpPhase; either may be NULL).
+template <typename T, int OUT>
+inline void launch_bin(const uint8_t* base, long long stride, int N, const float2* tw, long long nvec,
+                       long long npix, float* out, float* out2, cudaStream_t st) {
     const int pv_log = fftbin_pv_log(nvec);
     const unsigned grid = (unsigned)((nvec + (1ll << pv_log) - 1) >> pv_log);
     switch (pv_log) {
-        case 5: fftbin_kernel<T, 5, 128><<<grid, 128, 0, st>>>(base, stride, N, tw, nvec, npix, out); break;
-        case 4: fftbin_kernel<T, 4, 256><<<grid, 256, 0, st>>>(base, stride, N, tw, nvec, npix, out); break;
-        case 3: fftbin_kernel<T, 3, 256><<<grid, 256, 0, st>>>(base, stride, N, tw, nvec, npix, out); break;
-        default: fftbin_kernel<T, 2, 256><<<grid, 256, 0, st>>>(base, stride, N, tw, nvec, npix, out); break;
+        case 5: bin_kernel<T, 5, 128, OUT><<<grid, 128, 0, st>>>(base, stride, N, tw, nvec, npix, out, out2); break;
+        case 4: bin_kernel<T, 4, 256, OUT><<<grid, 256, 0, st>>>(base, stride, N, tw, nvec, npix, out, out2); break;
+        case 3: bin_kernel<T, 3, 256, OUT><<<grid, 256, 0, st>>>(base, stride, N, tw, nvec, npix, out, out2); break;
+        default: bin_kernel<T, 2, 256, OUT><<<grid, 256, 0, st>>>(base, stride, N, tw, nvec, npix, out, out2); break;
     }
+}
+
+// Twiddles of a lock-in at omega * dt = omega_dt radians per frame for the
+// frames with absolute indices s0 .. s0+N-1: tw[j] = (cos, -sin) of
+// omega_dt * (s0 + j), evaluated in FP64 and rounded to float.
+__global__ void lockin_table_kernel(float2* __restrict__ tw, int N, double omega_dt, long long s0) {
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= N) return;
+    double sn, cs;
+    sincos(omega_dt * (double)(s0 + j), &sn, &cs);
+    tw[j] = make_float2((float)cs, (float)(-sn));
 }
 
 }  // namespace qldk

@@ -90,6 +90,26 @@ def check_power(p_g, p_r, sumx, what=""):
                                                                        (err / np.maximum(tol, 1e-300)).max())
 
 
+def check_lockin(amp_g, ph_g, R, ph, sumx, what=""):
+    """General-frequency lock-in against the FP64 oracle: the DFT-bin
+    tolerance on the amplitude (|X| within 5e-5 relative plus a floor of
+    1e-6 of the pixel's summed counts), and the phase where the amplitude
+    clears that floor, within the angle the same error subtends."""
+    amp_g = amp_g.astype(np.float64)
+    e = POW_FLOOR * sumx.astype(np.float64)
+    tol = 0.5 * POW_RTOL * R + e
+    err = np.abs(amp_g - R)
+    ok = err <= tol
+    assert ok.all(), "%s lock-in amplitude: %d bad of %d, worst err/tol %g" % (what, (~ok).sum(), ok.size,
+                                                                               (err / tol).max())
+    if ph_g is not None:
+        sel = R > 100 * tol
+        d = np.abs(np.angle(np.exp(1j * (ph_g.astype(np.float64) - ph))))
+        lim = 2 * tol / np.maximum(R, 1e-300) + 1e-6
+        okp = (d <= lim) | ~sel
+        assert okp.all(), "%s lock-in phase: %d bad" % (what, (~okp).sum())
+
+
 class Stream:
     """A context plus a host record of every frame pushed, checked against the
     oracle recomputing each window from scratch."""
