@@ -127,10 +127,16 @@ int qld_push_image(qld_ctx* ctx, const void* frames, int count, void* stream, fl
 int qld_fft_bin(qld_ctx* ctx, int k, float* out);
 
 /* Host-buffer variants: frames are read from, and images written to, HOST
- * memory (pinned memory makes the copies asynchronous). The copies and the
- * kernels are stream-ordered on the context's stream; results in host memory
- * are valid after qld_sync. The context allocates a device staging area on
- * first use (not counted in qld_footprint_bytes). */
+ * memory (SI "Timing sequence" item 3: frames cross the PCI express bus to
+ * the GPU). The context keeps device staging (two input stages of up to
+ * 64 MiB, four output images; created on first use, not counted in
+ * qld_footprint_bytes) and two private copy streams: host-to-device copies,
+ * kernels on the context's stream and device-to-host copies are ordered by
+ * events, so copies of one call overlap the kernels of neighbouring calls.
+ * Pinned host memory makes the copies asynchronous (pageable memory works,
+ * with synchronous copies). Host results are valid after qld_sync, which
+ * also waits for the copy streams; a host frame buffer may be reused after
+ * qld_sync. */
 int qld_push_frames_host(qld_ctx* ctx, const void* host_frames, int count, void* stream);
 int qld_image_host(qld_ctx* ctx, float* amp_host, float* phase_host);
 int qld_fft_bin_host(qld_ctx* ctx, int k, float* out_host);

@@ -33,11 +33,26 @@ struct qld_ctx {
     long long pushed;
     cudaStream_t stream;
     long long footprint;
-    // host-buffer variants
-    uint8_t* stage;
+    // host-buffer variants (created on first use)
+    struct HostPipe* pipe;
+};
+
+// Device staging for the host-buffer calls. Frames go host -> stage[i] on
+// the copy-in stream, the push reads stage[i] on the context's stream;
+// images go to out[o] on the context's stream and out[o] -> host on the
+// copy-out stream. Two input stages and four output buffers, each guarded by
+// a ready / free event pair, let the copies of one step overlap the kernels
+// of the next and previous steps.
+struct HostPipe {
+    static constexpr int kIn = 2, kOut = 4;
+    cudaStream_t cin, cout;
+    uint8_t* stage[kIn];
     long long stage_bytes;
-    float* out_dev;
+    cudaEvent_t in_ready[kIn], in_free[kIn];
+    float* out[kOut];
     long long out_elems;
+    cudaEvent_t out_ready[kOut], out_free[kOut];
+    int in_idx, out_idx;
 };
 
 namespace {
@@ -182,52 +197,91 @@ int enqueue_fft_bin(qld_ctx* c, int k, float* out) {
     return cudaGetLastError() == cudaSuccess ? QLD_OK : QLD_E_CUDA;
 }
 
+void free_pipe(HostPipe* hp) {
+    if (!hp) return;
+    if (hp->cin) cudaStreamSynchronize(hp->cin);
+    if (hp->cout) cudaStreamSynchronize(hp->cout);
+    for (int i = 0; i < HostPipe::kIn; ++i) {
+        if (hp->stage[i]) cudaFree(hp->stage[i]);
+        if (hp->in_ready[i]) cudaEventDestroy(hp->in_ready[i]);
+        if (hp->in_free[i]) cudaEventDestroy(hp->in_free[i]);
+    }
+    for (int o = 0; o < HostPipe::kOut; ++o) {
+        if (hp->out[o]) cudaFree(hp->out[o]);
+        if (hp->out_ready[o]) cudaEventDestroy(hp->out_ready[o]);
+        if (hp->out_free[o]) cudaEventDestroy(hp->out_free[o]);
+    }
+    if (hp->cin) cudaStreamDestroy(hp->cin);
+    if (hp->cout) cudaStreamDestroy(hp->cout);
+    delete hp;
+}
+
 void free_ctx_memory(qld_ctx* c) {
     if (c->ring) cudaFree(c->ring);
     if (c->S) cudaFree(c->S);
     if (c->C) cudaFree(c->C);
     if (c->tw) cudaFree(c->tw);
-    if (c->stage) cudaFree(c->stage);
-    if (c->out_dev) cudaFree(c->out_dev);
+    free_pipe(c->pipe);
     c->ring = nullptr;
     c->S = c->C = nullptr;
     c->tw = nullptr;
-    c->stage = nullptr;
-    c->out_dev = nullptr;
+    c->pipe = nullptr;
 }
 
-int ensure_stage(qld_ctx* c, long long bytes) {
-    if (c->stage_bytes >= bytes) return QLD_OK;
-    if (c->stage) {
+// Creates the host pipeline with input stages of at least `stage_bytes`
+// (staging up to 64 MiB per chunk) and output buffers of two images.
+int ensure_pipe(qld_ctx* c, long long stage_bytes) {
+    if (c->pipe && c->pipe->stage_bytes >= stage_bytes) return QLD_OK;
+    if (c->pipe) {  // grow: wait for everything in flight, then rebuild
         cudaStreamSynchronize(c->stream);
-        cudaFree(c->stage);
-        c->stage = nullptr;
-        c->stage_bytes = 0;
+        free_pipe(c->pipe);
+        c->pipe = nullptr;
     }
-    if (cudaMalloc(&c->stage, (size_t)bytes) != cudaSuccess) {
+    HostPipe* hp = new HostPipe();
+    std::memset(hp, 0, sizeof(*hp));
+    bool ok = cudaStreamCreateWithFlags(&hp->cin, cudaStreamNonBlocking) == cudaSuccess &&
+              cudaStreamCreateWithFlags(&hp->cout, cudaStreamNonBlocking) == cudaSuccess;
+    hp->stage_bytes = stage_bytes;
+    hp->out_elems = 2 * c->npad;
+    for (int i = 0; ok && i < HostPipe::kIn; ++i)
+        ok = cudaMalloc(&hp->stage[i], (size_t)stage_bytes) == cudaSuccess &&
+             cudaEventCreateWithFlags(&hp->in_ready[i], cudaEventDisableTiming) == cudaSuccess &&
+             cudaEventCreateWithFlags(&hp->in_free[i], cudaEventDisableTiming) == cudaSuccess;
+    for (int o = 0; ok && o < HostPipe::kOut; ++o)
+        ok = cudaMalloc(&hp->out[o], (size_t)hp->out_elems * sizeof(float)) == cudaSuccess &&
+             cudaEventCreateWithFlags(&hp->out_ready[o], cudaEventDisableTiming) == cudaSuccess &&
+             cudaEventCreateWithFlags(&hp->out_free[o], cudaEventDisableTiming) == cudaSuccess;
+    if (!ok) {
         cudaGetLastError();
-        c->stage = nullptr;
+        free_pipe(hp);
         return QLD_E_NOMEM;
     }
-    c->stage_bytes = bytes;
+    c->pipe = hp;
     return QLD_OK;
 }
 
-int ensure_out(qld_ctx* c, long long elems) {
-    if (c->out_elems >= elems) return QLD_OK;
-    if (c->out_dev) {
-        cudaStreamSynchronize(c->stream);
-        cudaFree(c->out_dev);
-        c->out_dev = nullptr;
-        c->out_elems = 0;
-    }
-    if (cudaMalloc(&c->out_dev, (size_t)elems * sizeof(float)) != cudaSuccess) {
-        cudaGetLastError();
-        c->out_dev = nullptr;
-        return QLD_E_NOMEM;
-    }
-    c->out_elems = elems;
-    return QLD_OK;
+// Next output buffer: the context's stream waits until its previous
+// device-to-host copy has finished.
+float* acquire_out(qld_ctx* c, int* slot) {
+    HostPipe* hp = c->pipe;
+    const int o = hp->out_idx;
+    hp->out_idx = (o + 1) % HostPipe::kOut;
+    cudaStreamWaitEvent(c->stream, hp->out_free[o], 0);
+    *slot = o;
+    return hp->out[o];
+}
+
+// Copies n floats of buffer `slot` (after its producer on the context's
+// stream) to each non-NULL host pointer, on the copy-out stream.
+int release_out(qld_ctx* c, int slot, const float* d0, float* h0, const float* d1, float* h1) {
+    HostPipe* hp = c->pipe;
+    const size_t bytes = (size_t)c->npix * sizeof(float);
+    if (cudaEventRecord(hp->out_ready[slot], c->stream) != cudaSuccess ||
+        cudaStreamWaitEvent(hp->cout, hp->out_ready[slot], 0) != cudaSuccess)
+        return QLD_E_CUDA;
+    if (h0 && cudaMemcpyAsync(h0, d0, bytes, cudaMemcpyDeviceToHost, hp->cout) != cudaSuccess) return QLD_E_CUDA;
+    if (h1 && cudaMemcpyAsync(h1, d1, bytes, cudaMemcpyDeviceToHost, hp->cout) != cudaSuccess) return QLD_E_CUDA;
+    return cudaEventRecord(hp->out_free[slot], hp->cout) == cudaSuccess ? QLD_OK : QLD_E_CUDA;
 }
 
 }  // namespace
@@ -373,21 +427,28 @@ int qld_push_frames_host(qld_ctx* c, const void* host_frames, int count, void* s
     c->stream = (cudaStream_t)stream;
     if (count == 0) return QLD_OK;
     const long long frame_bytes = c->npix * c->bpp;
-    // Stage at most 256 MiB (and at least one frame) per copy; larger pushes
-    // run as consecutive chunks, which is the same as one push.
-    long long chunk = (256ll << 20) / frame_bytes;
+    // Chunks of at most 64 MiB (and at least one frame); consecutive chunks
+    // are the same as one push.
+    long long chunk = (64ll << 20) / frame_bytes;
     if (chunk < 1) chunk = 1;
     if (chunk > count) chunk = count;
-    int st = ensure_stage(c, round_up(chunk * frame_bytes, 256));
+    int st = ensure_pipe(c, round_up(chunk * frame_bytes, 256));
     if (st != QLD_OK) return set_err(st);
+    HostPipe* hp = c->pipe;
     const uint8_t* src = (const uint8_t*)host_frames;
     for (long long done = 0; done < count; done += chunk) {
         const long long n = (count - done < chunk) ? count - done : chunk;
-        if (cudaMemcpyAsync(c->stage, src + done * frame_bytes, (size_t)(n * frame_bytes), cudaMemcpyHostToDevice,
-                            c->stream) != cudaSuccess)
+        const int i = hp->in_idx;
+        hp->in_idx = (i + 1) % HostPipe::kIn;
+        if (cudaStreamWaitEvent(hp->cin, hp->in_free[i], 0) != cudaSuccess ||
+            cudaMemcpyAsync(hp->stage[i], src + done * frame_bytes, (size_t)(n * frame_bytes), cudaMemcpyHostToDevice,
+                            hp->cin) != cudaSuccess ||
+            cudaEventRecord(hp->in_ready[i], hp->cin) != cudaSuccess ||
+            cudaStreamWaitEvent(c->stream, hp->in_ready[i], 0) != cudaSuccess)
             return set_err(QLD_E_CUDA);
-        st = enqueue_push(c, c->stage, (int)n, false, nullptr, nullptr);
+        st = enqueue_push(c, hp->stage[i], (int)n, false, nullptr, nullptr);
         if (st != QLD_OK) return set_err(st);
+        if (cudaEventRecord(hp->in_free[i], c->stream) != cudaSuccess) return set_err(QLD_E_CUDA);
     }
     return QLD_OK;
 }
@@ -399,19 +460,15 @@ int qld_image_host(qld_ctx* c, float* amp_host, float* phase_host) {
     DeviceGuard g(c->device);
     if (!g.ok) return set_err(QLD_E_CUDA);
     if (pending_error() != QLD_OK) return set_err(QLD_E_CUDA);
-    const long long n = c->npad;
-    int st = ensure_out(c, 2 * n);
+    int st = ensure_pipe(c, c->pipe ? c->pipe->stage_bytes : round_up(c->npix * c->bpp, 256));
     if (st != QLD_OK) return set_err(st);
-    float* da = amp_host ? c->out_dev : nullptr;
-    float* dp = phase_host ? c->out_dev + n : nullptr;
+    int slot = 0;
+    float* buf = acquire_out(c, &slot);
+    float* da = amp_host ? buf : nullptr;
+    float* dp = phase_host ? buf + c->npad : nullptr;
     st = enqueue_image(c, da, dp);
     if (st != QLD_OK) return set_err(st);
-    const size_t bytes = (size_t)c->npix * sizeof(float);
-    if (amp_host && cudaMemcpyAsync(amp_host, da, bytes, cudaMemcpyDeviceToHost, c->stream) != cudaSuccess)
-        return set_err(QLD_E_CUDA);
-    if (phase_host && cudaMemcpyAsync(phase_host, dp, bytes, cudaMemcpyDeviceToHost, c->stream) != cudaSuccess)
-        return set_err(QLD_E_CUDA);
-    return QLD_OK;
+    return set_err(release_out(c, slot, da, amp_host, dp, phase_host));
 }
 
 int qld_fft_bin_host(qld_ctx* c, int k, float* out_host) {
@@ -420,14 +477,13 @@ int qld_fft_bin_host(qld_ctx* c, int k, float* out_host) {
     DeviceGuard g(c->device);
     if (!g.ok) return set_err(QLD_E_CUDA);
     if (pending_error() != QLD_OK) return set_err(QLD_E_CUDA);
-    int st = ensure_out(c, 2 * c->npad);
+    int st = ensure_pipe(c, c->pipe ? c->pipe->stage_bytes : round_up(c->npix * c->bpp, 256));
     if (st != QLD_OK) return set_err(st);
-    st = enqueue_fft_bin(c, k, c->out_dev);
+    int slot = 0;
+    float* buf = acquire_out(c, &slot);
+    st = enqueue_fft_bin(c, k, buf);
     if (st != QLD_OK) return set_err(st);
-    if (cudaMemcpyAsync(out_host, c->out_dev, (size_t)c->npix * sizeof(float), cudaMemcpyDeviceToHost,
-                        c->stream) != cudaSuccess)
-        return set_err(QLD_E_CUDA);
-    return QLD_OK;
+    return set_err(release_out(c, slot, buf, out_host, nullptr, nullptr));
 }
 
 int qld_get_iq(qld_ctx* c, int32_t* S, int32_t* C) {
@@ -462,7 +518,12 @@ int qld_sync(qld_ctx* c) {
     if (!c) return set_err(QLD_E_INVAL);
     DeviceGuard g(c->device);
     if (!g.ok) return set_err(QLD_E_CUDA);
-    if (cudaStreamSynchronize(c->stream) != cudaSuccess) {
+    bool ok = cudaStreamSynchronize(c->stream) == cudaSuccess;
+    if (c->pipe) {
+        ok = cudaStreamSynchronize(c->pipe->cin) == cudaSuccess && ok;
+        ok = cudaStreamSynchronize(c->pipe->cout) == cudaSuccess && ok;
+    }
+    if (!ok) {
         cudaGetLastError();
         return set_err(QLD_E_CUDA);
     }

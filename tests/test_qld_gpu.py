@@ -275,3 +275,29 @@ def test_amplitude_phase_on_every_octant_axis_and_extreme(P):
     amp, phs = get_image(st.ctx)
     check_amp_phase(amp, phs, R, ph, "image kernel")
     assert phs[pairs.index((0, -5))] == np.float32(np.pi)  # S = 0, C < 0: +pi on the branch cut
+
+
+def test_pipelined_host_path_many_steps_without_sync():
+    """Twelve steps of host push + image + DFT bin queued without any sync:
+    the staging and the four output buffers are reused while copies overlap
+    kernels, and every step's host results must equal the device path's."""
+    rng = np.random.default_rng(12)
+    H, W, N, steps = 128, 96, 16, 12
+    x = rand_frames(rng, N + 4 * steps, H, W, 2)
+    host = torch.from_numpy(x.copy()).pin_memory()
+    ctx = q.qld_create(H, W, N, 2)
+    q.qld_push_frames_host(ctx, host[:N], N)
+    outs = [tuple(torch.empty(H * W, dtype=torch.float32).pin_memory() for _ in range(3)) for _ in range(steps)]
+    for i in range(steps):
+        q.qld_push_frames_host(ctx, host[N + 4 * i:N + 4 * i + 4], 4)
+        q.qld_image_host(ctx, outs[i][0], outs[i][1])
+        q.qld_fft_bin_host(ctx, 3, outs[i][2])
+    q.qld_sync(ctx)
+    ref = Stream(H, W, N, 2)
+    ref.push(x[:N])
+    for i in range(steps):
+        ref.push(x[N + 4 * i:N + 4 * i + 4])
+        amp, ph = get_image(ref.ctx)
+        assert np.array_equal(outs[i][0].numpy(), amp) and np.array_equal(outs[i][1].numpy(), ph), i
+        assert np.array_equal(outs[i][2].numpy(), get_bin(ref.ctx, 3)), i
+    ctx.destroy()
