@@ -21,12 +21,12 @@
  *
  * Memory: all frame, image and sum pointers are DEVICE pointers unless the
  * function name ends in _host. Frames are laid out [count][H][W], row-major,
- * contiguous, uint8 (QLD_U8) or uint16 (QLD_U16, 12- or 16-bit data in the
- * low bits). Images are float32 [H][W]; sums are int32 [H][W]. Any H and W
+ * contiguous, uint8 (QLD_U8), uint16 (QLD_U16, 12- or 16-bit data in the
+ * low bits) or packed 12-bit (QLD_P12). Images are float32 [H][W]; sums are int32 [H][W]. Any H and W
  * are accepted. Pointers must be aligned to their element size (uint16
  * frames to 2 bytes, float and int32 buffers to 4), else QLD_E_INVAL; frame
- * buffers that are not 16-byte aligned, or frames whose size is not a
- * multiple of 16 bytes, take a slower scalar path. The context owns its ring
+ * buffers that are not 16-byte aligned (8 for QLD_P12), or frames whose size
+ * is not a multiple of 16 bytes (24 for QLD_P12), take a slower scalar path. The context owns its ring
  * buffer, sums and scratch; the caller owns every pointer it passes.
  *
  * Streams: qld_push_frames and its variants enqueue on the stream they are
@@ -55,7 +55,11 @@ extern "C" {
 
 typedef struct qld_ctx qld_ctx;
 
-enum qld_pixfmt { QLD_U8 = 1, QLD_U16 = 2 };
+/* QLD_P12: 12-bit pixels packed two in three bytes, least significant bits
+ * first (GenICam Mono12p: pixel 2i = b0 | (b1 & 0xF) << 8, pixel 2i+1 =
+ * (b1 >> 4) | b2 << 4); H*W must be even. The window ring stores frames in
+ * the input format, so packed data moves 25 % fewer bytes than uint16. */
+enum qld_pixfmt { QLD_U8 = 1, QLD_U16 = 2, QLD_P12 = 3 };
 
 enum qld_status {
     QLD_OK = 0,

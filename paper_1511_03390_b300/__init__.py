@@ -14,7 +14,7 @@ import os
 from . import build as _build
 
 __all__ = [
-    "QLD_U8", "QLD_U16", "QLD_OK", "QLD_E_INVAL", "QLD_E_NOMEM", "QLD_E_NOT_READY", "QLD_E_CUDA",
+    "QLD_U8", "QLD_U16", "QLD_P12", "QLD_OK", "QLD_E_INVAL", "QLD_E_NOMEM", "QLD_E_NOT_READY", "QLD_E_CUDA",
     "QLD_E_TIMEOUT", "QLD_MAX_N", "QLDError", "Context", "qld_create", "qld_destroy", "qld_push_frames",
     "qld_push_image", "qld_image", "qld_fft_bin", "qld_push_frames_host", "qld_image_host",
     "qld_fft_bin_host", "qld_get_iq", "qld_reset", "qld_frames_pushed", "qld_sync", "qld_stream",
@@ -23,7 +23,7 @@ __all__ = [
     "qld_lockin_table", "qld_lockin_frames", "LIB_PATH", "lib",
 ]
 
-QLD_U8, QLD_U16 = 1, 2
+QLD_U8, QLD_U16, QLD_P12 = 1, 2, 3
 QLD_OK, QLD_E_INVAL, QLD_E_NOMEM, QLD_E_NOT_READY, QLD_E_CUDA, QLD_E_TIMEOUT = 0, -1, -2, -3, -4, -5
 QLD_MAX_N = 65536
 QLD_NOALLOC_MAX_N = 16384
@@ -125,7 +125,7 @@ class Context:
         self.handle = handle
         self.H, self.W, self.N, self.pixfmt = H, W, N, pixfmt
         self.npix = H * W
-        self.frame_bytes = self.npix * pixfmt
+        self.frame_bytes = self.npix // 2 * 3 if pixfmt == QLD_P12 else self.npix * pixfmt
 
     def __del__(self):
         if getattr(self, "handle", None):

@@ -20,7 +20,8 @@
 #include "qld_kernels.cuh"
 
 struct qld_ctx {
-    int H, W, N, pixfmt, bpp;
+    int H, W, N, pixfmt;
+    long long frame_bytes;  // bytes of one frame in the input format
     long long npix;
     long long npad;         // padded pixel count of S and C
     long long slot_stride;  // bytes
@@ -71,10 +72,16 @@ long long round_up(long long x, long long m) { return (x + m - 1) / m * m; }
 
 bool valid_dims(int H, int W, int N, int pixfmt) {
     if (H < 1 || W < 1 || N < 4 || N > QLD_MAX_N || (N % 4) != 0) return false;
-    if (pixfmt != QLD_U8 && pixfmt != QLD_U16) return false;
+    if (pixfmt != QLD_U8 && pixfmt != QLD_U16 && pixfmt != QLD_P12) return false;
     const long long npix = (long long)H * W;
+    if (pixfmt == QLD_P12 && (npix % 2) != 0) return false;  // pixel pairs must not straddle frames
     return npix <= (1ll << 31) - 1;
 }
+
+// Bytes of one frame, and of one kernel vector, per pixel format.
+long long frame_bytes_of(long long npix, int pixfmt) { return pixfmt == QLD_P12 ? npix / 2 * 3 : npix * pixfmt; }
+int vec_bytes_of(int pixfmt) { return pixfmt == QLD_P12 ? qldk::Fmt<qldk::p12_t>::VB : qldk::kVecBytes; }
+unsigned vec_align_of(int pixfmt) { return pixfmt == QLD_P12 ? qldk::Fmt<qldk::p12_t>::ALIGN : 16u; }
 
 struct Layout {
     long long npix, npad, slot_stride, ring_bytes, sums_bytes, tw_bytes, total;
@@ -84,7 +91,8 @@ Layout layout_of(int H, int W, int N, int pixfmt) {
     Layout L;
     L.npix = (long long)H * W;
     L.npad = round_up(L.npix, 64);
-    L.slot_stride = round_up(L.npix * pixfmt, 256);
+    // a whole number of kernel vectors, and 256-byte aligned slots
+    L.slot_stride = round_up(round_up(frame_bytes_of(L.npix, pixfmt), vec_bytes_of(pixfmt)), 256);
     L.ring_bytes = L.slot_stride * N;
     L.sums_bytes = L.npad * (long long)sizeof(int32_t);
     L.tw_bytes = round_up((long long)N * (long long)sizeof(float2), 256);
@@ -121,6 +129,13 @@ unsigned blocks_for(long long n, int threads) { return (unsigned)((n + threads -
 
 template <bool RESET, bool EPI>
 void launch_push_t(const qld_ctx* c, const qldk::PushArgs& a, bool vec) {
+    if (c->pixfmt == QLD_P12) {
+        if (vec)
+            qldk::push_vec_kernel<qldk::p12_t, RESET, EPI><<<blocks_for(a.nvec, 128), 128, 0, c->stream>>>(a);
+        else
+            qldk::push_scalar_p12_kernel<RESET, EPI><<<blocks_for(a.npix / 2, 256), 256, 0, c->stream>>>(a);
+        return;
+    }
     if (vec) {
         if (c->pixfmt == QLD_U16)
             qldk::push_vec_kernel<uint16_t, RESET, EPI><<<blocks_for(a.nvec, 128), 128, 0, c->stream>>>(a);
@@ -138,7 +153,7 @@ void launch_push_t(const qld_ctx* c, const qldk::PushArgs& a, bool vec) {
 // c->stream. Arguments are already validated.
 int enqueue_push(qld_ctx* c, const uint8_t* frames, int count, bool epi, float* amp, float* phase) {
     if (count == 0) return QLD_OK;
-    const long long frame_bytes = c->npix * c->bpp;
+    const long long frame_bytes = c->frame_bytes;
     const bool reset = count >= c->N;
     const int first = reset ? count - c->N : 0;
     qldk::PushArgs a;
@@ -155,8 +170,9 @@ int enqueue_push(qld_ctx* c, const uint8_t* frames, int count, bool epi, float* 
     a.amp = amp;
     a.phase = phase;
     a.out_aligned = (aligned(amp, 16) && aligned(phase, 16)) ? 1 : 0;
-    const bool vec = aligned(a.frames, 16) && (frame_bytes % qldk::kVecBytes) == 0;
-    a.nvec = vec ? frame_bytes / qldk::kVecBytes : c->npix;
+    const int vb = vec_bytes_of(c->pixfmt);
+    const bool vec = aligned(a.frames, vec_align_of(c->pixfmt)) && (frame_bytes % vb) == 0;
+    a.nvec = vec ? frame_bytes / vb : c->npix;
     g_launches.fetch_add(1);
     if (reset) {
         if (epi) launch_push_t<true, true>(c, a, vec);
@@ -186,9 +202,13 @@ int enqueue_fft_bin(qld_ctx* c, int k, float* out) {
         if (cudaGetLastError() != cudaSuccess) return QLD_E_CUDA;
         c->tw_k = k;
     }
-    const long long nvec = (c->npix * c->bpp + qldk::kVecBytes - 1) / qldk::kVecBytes;
+    const int vb = vec_bytes_of(c->pixfmt);
+    const long long nvec = (c->frame_bytes + vb - 1) / vb;
     g_launches.fetch_add(1);
-    if (c->pixfmt == QLD_U16)
+    if (c->pixfmt == QLD_P12)
+        qldk::launch_bin<qldk::p12_t, qldk::kBinPower>(c->ring, c->slot_stride, c->N, c->tw, nvec, c->npix, out,
+                                                       nullptr, c->stream);
+    else if (c->pixfmt == QLD_U16)
         qldk::launch_bin<uint16_t, qldk::kBinPower>(c->ring, c->slot_stride, c->N, c->tw, nvec, c->npix, out, nullptr,
                                                    c->stream);
     else
@@ -335,7 +355,7 @@ qld_ctx* qld_create(int H, int W, int N, int pixfmt) {
     c->W = W;
     c->N = N;
     c->pixfmt = pixfmt;
-    c->bpp = pixfmt;
+    c->frame_bytes = frame_bytes_of(L.npix, pixfmt);
     c->npix = L.npix;
     c->npad = L.npad;
     c->slot_stride = L.slot_stride;
@@ -426,7 +446,7 @@ int qld_push_frames_host(qld_ctx* c, const void* host_frames, int count, void* s
     if (pending_error() != QLD_OK) return set_err(QLD_E_CUDA);
     c->stream = (cudaStream_t)stream;
     if (count == 0) return QLD_OK;
-    const long long frame_bytes = c->npix * c->bpp;
+    const long long frame_bytes = c->frame_bytes;
     // Chunks of at most 64 MiB (and at least one frame); consecutive chunks
     // are the same as one push.
     long long chunk = (64ll << 20) / frame_bytes;
@@ -460,7 +480,7 @@ int qld_image_host(qld_ctx* c, float* amp_host, float* phase_host) {
     DeviceGuard g(c->device);
     if (!g.ok) return set_err(QLD_E_CUDA);
     if (pending_error() != QLD_OK) return set_err(QLD_E_CUDA);
-    int st = ensure_pipe(c, c->pipe ? c->pipe->stage_bytes : round_up(c->npix * c->bpp, 256));
+    int st = ensure_pipe(c, c->pipe ? c->pipe->stage_bytes : round_up(c->frame_bytes, 256));
     if (st != QLD_OK) return set_err(st);
     int slot = 0;
     float* buf = acquire_out(c, &slot);
@@ -477,7 +497,7 @@ int qld_fft_bin_host(qld_ctx* c, int k, float* out_host) {
     DeviceGuard g(c->device);
     if (!g.ok) return set_err(QLD_E_CUDA);
     if (pending_error() != QLD_OK) return set_err(QLD_E_CUDA);
-    int st = ensure_pipe(c, c->pipe ? c->pipe->stage_bytes : round_up(c->npix * c->bpp, 256));
+    int st = ensure_pipe(c, c->pipe ? c->pipe->stage_bytes : round_up(c->frame_bytes, 256));
     if (st != QLD_OK) return set_err(st);
     int slot = 0;
     float* buf = acquire_out(c, &slot);

@@ -10,8 +10,9 @@
 // buffer of N frames.)
 //
 // All three are HBM-streaming kernels: pixels are independent, frames are
-// contiguous rows, and every thread owns a 16-byte vector of pixels (8 uint16
-// or 16 uint8) so loads and stores are 128-bit and fully coalesced.
+// contiguous rows, and every thread owns one vector of pixels -- 16 bytes
+// (8 uint16 or 16 uint8 pixels) or, for packed 12-bit data, 24 bytes (16
+// pixels) -- so loads and stores are wide and fully coalesced.
 
 #pragma once
 
@@ -22,36 +23,91 @@ namespace qldk {
 
 constexpr int kVecBytes = 16;
 
+// Tag type of the packed 12-bit pixel format: two pixels in three bytes,
+// least significant bits first (GenICam Mono12p), so pixel i of a run is
+// bits [12 i, 12 i + 12) of the little-endian byte string.
+struct p12_t {};
+
+// 24 bytes = 16 packed 12-bit pixels.
+struct P12Vec {
+    uint32_t w[6];
+};
+
+// Per-format vector traits: Vec, bytes per vector VB, pixels per vector VP,
+// and streaming load / store of one vector (cache-streaming hints: every
+// frame byte is touched once per kernel).
+template <typename T>
+struct Fmt;
+
+template <>
+struct Fmt<uint8_t> {
+    using Vec = uint4;
+    static constexpr int VB = 16, VP = 16, ALIGN = 16;
+    static __device__ __forceinline__ Vec load(const uint8_t* p) { return __ldcs(reinterpret_cast<const uint4*>(p)); }
+    static __device__ __forceinline__ void store(uint8_t* p, const Vec& v) { __stcs(reinterpret_cast<uint4*>(p), v); }
+    static __device__ __forceinline__ Vec zero() { return make_uint4(0, 0, 0, 0); }
+};
+
+template <>
+struct Fmt<uint16_t> {
+    using Vec = uint4;
+    static constexpr int VB = 16, VP = 8, ALIGN = 16;
+    static __device__ __forceinline__ Vec load(const uint8_t* p) { return __ldcs(reinterpret_cast<const uint4*>(p)); }
+    static __device__ __forceinline__ void store(uint8_t* p, const Vec& v) { __stcs(reinterpret_cast<uint4*>(p), v); }
+    static __device__ __forceinline__ Vec zero() { return make_uint4(0, 0, 0, 0); }
+};
+
+template <>
+struct Fmt<p12_t> {
+    using Vec = P12Vec;
+    static constexpr int VB = 24, VP = 16, ALIGN = 8;
+    static __device__ __forceinline__ Vec load(const uint8_t* p) {
+        const uint2* q = reinterpret_cast<const uint2*>(p);
+        const uint2 a = __ldcs(q), b = __ldcs(q + 1), c = __ldcs(q + 2);
+        return P12Vec{{a.x, a.y, b.x, b.y, c.x, c.y}};
+    }
+    static __device__ __forceinline__ void store(uint8_t* p, const Vec& v) {
+        uint2* q = reinterpret_cast<uint2*>(p);
+        __stcs(q, make_uint2(v.w[0], v.w[1]));
+        __stcs(q + 1, make_uint2(v.w[2], v.w[3]));
+        __stcs(q + 2, make_uint2(v.w[4], v.w[5]));
+    }
+    static __device__ __forceinline__ Vec zero() { return P12Vec{{0, 0, 0, 0, 0, 0}}; }
+};
+
 // ---------------------------------------------------------------- helpers --
 
-__device__ __forceinline__ uint4 ld_stream(const void* p) {
-    return __ldcs(reinterpret_cast<const uint4*>(p));
-}
-__device__ __forceinline__ void st_stream(void* p, uint4 v) {
-    __stcs(reinterpret_cast<uint4*>(p), v);
-}
-
-// Pixel q (0-based) of a 16-byte vector as an int.
-template <typename T>
-__device__ __forceinline__ int pix(const uint4& v, int q);
-
-template <>
-__device__ __forceinline__ int pix<uint16_t>(const uint4& v, int q) {
+// Raw bits of pixel q of a vector (q is a compile-time constant after
+// unrolling, so the word selection and shifts fold away).
+__device__ __forceinline__ uint32_t raw_pix(const uint4& v, int q, uint16_t*) {
     const uint32_t w = (q < 2) ? v.x : (q < 4) ? v.y : (q < 6) ? v.z : v.w;
-    return (q & 1) ? (int)(w >> 16) : (int)(w & 0xFFFFu);
+    return (q & 1) ? (w >> 16) : (w & 0xFFFFu);
 }
-template <>
-__device__ __forceinline__ int pix<uint8_t>(const uint4& v, int q) {
+__device__ __forceinline__ uint32_t raw_pix(const uint4& v, int q, uint8_t*) {
     const uint32_t w = (q < 4) ? v.x : (q < 8) ? v.y : (q < 12) ? v.z : v.w;
-    return (int)((w >> (8 * (q & 3))) & 0xFFu);
+    return (w >> (8 * (q & 3))) & 0xFFu;
+}
+__device__ __forceinline__ uint32_t raw_pix(const P12Vec& v, int q, p12_t*) {
+    const int o = 12 * q;  // bit offset of pixel q in the 192-bit vector
+    const int wi = o >> 5;
+    const uint32_t lo = v.w[wi];
+    const uint32_t hi = (wi + 1 < 6) ? v.w[wi + 1] : 0u;
+    return __funnelshift_r(lo, hi, o & 31) & 0xFFFu;
 }
 
-// Pixel q of a 16-byte vector as an exact float: the integer bits are placed
-// in the mantissa of 2^23 by one byte permute, and 2^23 is subtracted (exact
-// for values below 2^23).
+// Pixel q of a vector as an int.
 template <typename T>
-__device__ __forceinline__ float pixf(const uint4& v, int q);
+__device__ __forceinline__ int pix(const typename Fmt<T>::Vec& v, int q) {
+    return (int)raw_pix(v, q, (T*)nullptr);
+}
 
+// Pixel q of a vector as an exact float: the integer bits are placed in the
+// mantissa of 2^23 and 2^23 is subtracted (exact for values below 2^23); for
+// uint8 / uint16 one byte permute builds the float bits.
+template <typename T>
+__device__ __forceinline__ float pixf(const typename Fmt<T>::Vec& v, int q) {
+    return __uint_as_float(raw_pix(v, q, (T*)nullptr) | 0x4B000000u) - 8388608.0f;
+}
 template <>
 __device__ __forceinline__ float pixf<uint16_t>(const uint4& v, int q) {
     const uint32_t w = (q < 2) ? v.x : (q < 4) ? v.y : (q < 6) ? v.z : v.w;
@@ -70,8 +126,9 @@ __device__ __forceinline__ float pixf<uint8_t>(const uint4& v, int q) {
 // 0, 1 for r = 1, 2, 3, 0, so exactly one of S, C changes. r is the same for
 // every thread of a launch, so the switch does not diverge.
 template <typename T, bool HAS_OLD>
-__device__ __forceinline__ void accumulate(int32_t* sacc, int32_t* cacc, const uint4& xn, const uint4& xo, int r) {
-    constexpr int VP = kVecBytes / (int)sizeof(T);
+__device__ __forceinline__ void accumulate(int32_t* sacc, int32_t* cacc, const typename Fmt<T>::Vec& xn,
+                                           const typename Fmt<T>::Vec& xo, int r) {
+    constexpr int VP = Fmt<T>::VP;
     switch (r) {
         case 1:
 #pragma unroll
@@ -166,10 +223,12 @@ struct PushArgs {
 // read. EPI: also write the amplitude / phase image.
 template <typename T, bool RESET, bool EPI>
 __global__ void __launch_bounds__(128) push_vec_kernel(const PushArgs a) {
-    constexpr int VP = kVecBytes / (int)sizeof(T);
+    using F = Fmt<T>;
+    using Vec = typename F::Vec;
+    constexpr int VP = F::VP;
     const long long v = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (v >= a.nvec) return;
-    const long long off = v * kVecBytes;
+    const long long off = v * F::VB;
     const long long p0 = v * VP;
 
     int32_t sacc[VP], cacc[VP];
@@ -192,20 +251,22 @@ __global__ void __launch_bounds__(128) push_vec_kernel(const PushArgs a) {
     // Groups of four frames: all loads are issued before any store so eight
     // 128-bit loads per thread are in flight.
     for (; f + 4 <= a.nf; f += 4) {
-        uint4 xn[4], xo[4];
+        Vec xn[4], xo[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) xo[u] = F::zero();
         long long slot[4];
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
             const long long s = a.s_first + f + u;
             slot[u] = s % a.N;
-            xn[u] = ld_stream(src + (long long)(f + u) * a.frame_stride);
+            xn[u] = F::load(src + (long long)(f + u) * a.frame_stride);
         }
         if (!RESET) {
 #pragma unroll
-            for (int u = 0; u < 4; ++u) xo[u] = ld_stream(ring + slot[u] * a.slot_stride);
+            for (int u = 0; u < 4; ++u) xo[u] = F::load(ring + slot[u] * a.slot_stride);
         }
 #pragma unroll
-        for (int u = 0; u < 4; ++u) st_stream(ring + slot[u] * a.slot_stride, xn[u]);
+        for (int u = 0; u < 4; ++u) F::store(ring + slot[u] * a.slot_stride, xn[u]);
 #pragma unroll
         for (int u = 0; u < 4; ++u)
             accumulate<T, !RESET>(sacc, cacc, xn[u], xo[u], (int)((a.s_first + f + u) & 3));
@@ -213,10 +274,10 @@ __global__ void __launch_bounds__(128) push_vec_kernel(const PushArgs a) {
     for (; f < a.nf; ++f) {
         const long long s = a.s_first + f;
         const long long slot = s % a.N;
-        const uint4 xn = ld_stream(src + (long long)f * a.frame_stride);
-        uint4 xo = make_uint4(0, 0, 0, 0);
-        if (!RESET) xo = ld_stream(ring + slot * a.slot_stride);
-        st_stream(ring + slot * a.slot_stride, xn);
+        const Vec xn = F::load(src + (long long)f * a.frame_stride);
+        Vec xo = F::zero();
+        if (!RESET) xo = F::load(ring + slot * a.slot_stride);
+        F::store(ring + slot * a.slot_stride, xn);
         accumulate<T, !RESET>(sacc, cacc, xn, xo, (int)(s & 3));
     }
 
@@ -286,6 +347,55 @@ __global__ void __launch_bounds__(256) push_scalar_kernel(const PushArgs a) {
     }
 }
 
+// Scalar path for packed 12-bit frames that are not 8-byte aligned or whose
+// size is not a multiple of 24 bytes: one pixel pair (3 bytes) per thread,
+// so no two threads write the same byte of a ring slot.
+template <bool RESET, bool EPI>
+__global__ void __launch_bounds__(256) push_scalar_p12_kernel(const PushArgs a) {
+    const long long pr = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (2 * pr >= a.npix) return;
+    const long long p = 2 * pr;
+    int32_t s0 = RESET ? 0 : a.S[p], s1 = RESET ? 0 : a.S[p + 1];
+    int32_t c0 = RESET ? 0 : a.C[p], c1 = RESET ? 0 : a.C[p + 1];
+    for (int f = 0; f < a.nf; ++f) {
+        const long long s = a.s_first + f;
+        const uint8_t* src = a.frames + (long long)f * a.frame_stride + 3 * pr;
+        uint8_t* slotp = a.ring + (s % a.N) * a.slot_stride + 3 * pr;
+        const uint32_t b0 = src[0], b1 = src[1], b2 = src[2];
+        const int n0 = (int)(b0 | ((b1 & 0xFu) << 8)), n1 = (int)((b1 >> 4) | (b2 << 4));
+        int o0 = 0, o1 = 0;
+        if (!RESET) {
+            const uint32_t q0 = slotp[0], q1 = slotp[1], q2 = slotp[2];
+            o0 = (int)(q0 | ((q1 & 0xFu) << 8));
+            o1 = (int)((q1 >> 4) | (q2 << 4));
+        }
+        slotp[0] = (uint8_t)b0;
+        slotp[1] = (uint8_t)b1;
+        slotp[2] = (uint8_t)b2;
+        const int d0 = n0 - o0, d1 = n1 - o1;
+        switch ((int)(s & 3)) {
+            case 1: s0 += d0; s1 += d1; break;
+            case 2: c0 -= d0; c1 -= d1; break;
+            case 3: s0 -= d0; s1 -= d1; break;
+            default: c0 += d0; c1 += d1; break;
+        }
+    }
+    a.S[p] = s0;
+    a.S[p + 1] = s1;
+    a.C[p] = c0;
+    a.C[p + 1] = c1;
+    if (EPI) {
+        if (a.amp) {
+            a.amp[p] = amplitude(s0, c0);
+            a.amp[p + 1] = amplitude(s1, c1);
+        }
+        if (a.phase) {
+            a.phase[p] = phase_of(s0, c0);
+            a.phase[p + 1] = phase_of(s1, c1);
+        }
+    }
+}
+
 // ------------------------------------------------------------------ image --
 
 // Four pixels per thread; S and C are padded so the int4 loads stay in bounds.
@@ -350,7 +460,8 @@ template <typename T, int PV_LOG, int NT, int OUT>
 __global__ void __launch_bounds__(NT) bin_kernel(const uint8_t* __restrict__ ring, long long slot_stride, int N,
                                                  const float2* __restrict__ tw, long long nvec, long long npix,
                                                  float* __restrict__ out, float* __restrict__ out2) {
-    constexpr int VP = kVecBytes / (int)sizeof(T);
+    using F = Fmt<T>;
+    constexpr int VP = F::VP;
     constexpr int PV = 1 << PV_LOG;
     constexpr int TS = NT / PV;
     constexpr int NW = NT / 32;
@@ -367,7 +478,7 @@ __global__ void __launch_bounds__(NT) bin_kernel(const uint8_t* __restrict__ rin
     for (int q = 0; q < VP; ++q) re[q] = im[q] = 0.f;
 
     if (v < nvec) {
-        const uint8_t* base = ring + v * kVecBytes;
+        const uint8_t* base = ring + v * F::VB;
         int j = ts;
         while (j < N) {
             float pr[VP], pi[VP];
@@ -375,16 +486,16 @@ __global__ void __launch_bounds__(NT) bin_kernel(const uint8_t* __restrict__ rin
             for (int q = 0; q < VP; ++q) pr[q] = pi[q] = 0.f;
             // Up to 16 frames (4 groups of 4) into the partial.
             for (int g = 0; g < 4 && j < N; ++g, j += 4 * TS) {
-                uint4 x[4];
+                typename F::Vec x[4];
                 float2 w[4];
 #pragma unroll
                 for (int u = 0; u < 4; ++u) {
                     const int jj = j + u * TS;
                     if (jj < N) {
-                        x[u] = ld_stream(base + (long long)jj * slot_stride);
+                        x[u] = F::load(base + (long long)jj * slot_stride);
                         w[u] = __ldg(tw + jj);
                     } else {
-                        x[u] = make_uint4(0, 0, 0, 0);
+                        x[u] = F::zero();
                         w[u] = make_float2(0.f, 0.f);
                     }
                 }

@@ -110,9 +110,24 @@ def check_lockin(amp_g, ph_g, R, ph, sumx, what=""):
         assert okp.all(), "%s lock-in phase: %d bad" % (what, (~okp).sum())
 
 
+def pack12(x):
+    """Packs 12-bit values (uint16 array, last axis even) two per three bytes,
+    least significant bits first (GenICam Mono12p)."""
+    x = np.asarray(x, np.uint16)
+    assert x.max(initial=0) <= 4095 and x.shape[-1] % 2 == 0
+    a = x[..., 0::2].astype(np.uint16)
+    b = x[..., 1::2].astype(np.uint16)
+    out = np.empty(x.shape[:-1] + (a.shape[-1], 3), np.uint8)
+    out[..., 0] = a & 0xFF
+    out[..., 1] = (a >> 8) | ((b & 0xF) << 4)
+    out[..., 2] = b >> 4
+    return out.reshape(x.shape[:-1] + (x.shape[-1] // 2 * 3,))
+
+
 class Stream:
     """A context plus a host record of every frame pushed, checked against the
-    oracle recomputing each window from scratch."""
+    oracle recomputing each window from scratch. For the packed 12-bit format
+    the record holds the unpacked values and the pushes send packed bytes."""
 
     def __init__(self, H, W, N, fmt):
         self.ctx = q.qld_create(H, W, N, fmt)
@@ -122,7 +137,7 @@ class Stream:
 
     def push(self, x, offset=0, fused=False):
         x = np.asarray(x, self.dtype).reshape(-1, self.H * self.W)
-        buf, addr = dev_bytes(x, offset)
+        buf, addr = dev_bytes(pack12(x) if self.fmt == 3 else x, offset)
         if fused:
             amp = torch.empty(self.H * self.W, dtype=torch.float32, device="cuda")
             ph = torch.empty_like(amp)

@@ -47,7 +47,8 @@ def test_library_is_built_for_sm_103a():
 
 
 @pytest.mark.parametrize("H,W,N,fmt", [(0, 4, 8, 1), (4, 0, 8, 1), (4, 4, 6, 1), (4, 4, 0, 1), (4, 4, -4, 2),
-                                       (4, 4, 8, 3), (4, 4, 65540, 2), (65536, 65536, 4, 1)])
+                                       (4, 4, 8, 4), (4, 4, 8, 0), (3, 5, 8, 3), (4, 4, 65540, 2),
+                                       (65536, 65536, 4, 1)])
 def test_create_rejects_bad_arguments(H, W, N, fmt):
     assert q.lib.qld_create(H, W, N, fmt) is None
     assert q.qld_last_error() == q.QLD_E_INVAL
@@ -60,6 +61,10 @@ def test_footprint():
     assert q.qld_footprint_bytes(128, 128, 64, 1) == 64 * 16384 + 2 * 4 * 16384 + 512
     assert q.qld_footprint_bytes(1024, 1024, 1024, 2) == 1024 * 2 ** 21 + 2 * 4 * 2 ** 20 + 8192
     assert q.qld_footprint_bytes(1, 17, 4, 1) == 4 * 256 + 2 * 4 * 64 + 256
+    # packed 12-bit: 1.5 bytes per pixel, slots a whole number of 24-byte vectors
+    assert q.qld_footprint_bytes(1024, 1024, 1024, 3) == 1024 * 3 * 2 ** 19 + 2 * 4 * 2 ** 20 + 8192
+    # a 255-byte frame rounds up to 264 (11 vectors of 24 B), then to a 512-byte slot
+    assert q.qld_footprint_bytes(1, 170, 4, 3) == 4 * 512 + 2 * 4 * 192 + 256
     big = q.qld_footprint_bytes(4096, 4096, 2048, 2)
     assert big == 2048 * 32 * 2 ** 20 + 2 * 4 * 2 ** 24 + 16384
     assert big > 68.7e9
