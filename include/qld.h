@@ -208,6 +208,53 @@ int qld_lockin_frames(const void* frames, int H, int W, int N, int pixfmt, const
 int qld_fft_bin_frames_noalloc(const void* frames, int H, int W, int N, int pixfmt, int k, float* out,
                                void* stream);
 
+/* ---- Serving several camera streams (continuous batching) ---------------
+ *
+ * The paper runs one camera through a real-time loop in which acquisition,
+ * transfer and processing overlap and each new frame yields an image (SI,
+ * "Timing sequence for hybrid parallelisation"). A server runs that loop for
+ * up to QLD_SERVER_MAX_STREAMS streams of different sizes, windows and pixel
+ * formats on the current device:
+ *  - qld_server_request asks for a stream (H, W, N, pixfmt as for
+ *    qld_create; H*W*pixel bytes must be a whole number of 16-byte vectors,
+ *    24 for QLD_P12) and returns its ticket. It is admitted at once if its
+ *    footprint (qld_footprint_bytes + two float images) fits the server's
+ *    HBM budget and a slot is free; otherwise it waits, and waiting requests
+ *    are admitted in arrival order whenever a close frees room. A request
+ *    larger than the whole budget fails with QLD_E_NOMEM.
+ *  - qld_server_submit hands over the next frames of an admitted stream
+ *    (device memory, aligned to 16 bytes, 8 for QLD_P12; at most one submission
+ *    per stream per tick; QLD_E_NOT_READY while the request waits). The frames
+ *    must stay valid until the tick that consumes them has completed.
+ *  - qld_server_tick runs every submitted push, with its amplitude/phase image
+ *    once the stream's window is full, in ONE persistent kernel launch replayed
+ *    from a CUDA graph, on `stream`; it returns the number of streams served.
+ *    Streams admitted while earlier ticks are still running join the next tick.
+ *  - qld_server_image gives the device pointers of a stream's latest images
+ *    (owned by the server; read them after the tick, in stream order).
+ *  - qld_server_autotune times the batched kernel's candidate launch shapes
+ *    on small-window replicas of the active streams (same bytes per pushed
+ *    frame; temporary memory outside the budget), keeps the fastest and
+ *    returns its index (best time per tick in *best_us).
+ * One host thread must drive a server at a time. */
+#define QLD_SERVER_MAX_STREAMS 64
+typedef struct qld_server qld_server;
+qld_server* qld_server_create(long long hbm_budget_bytes, int max_streams);
+void qld_server_destroy(qld_server* srv);
+int qld_server_request(qld_server* srv, int H, int W, int N, int pixfmt);
+/* 1 = waiting, 0 = admitted, -1 = closed or failed, QLD_E_INVAL = no such ticket */
+int qld_server_state(qld_server* srv, int ticket);
+int qld_server_close(qld_server* srv, int ticket);
+int qld_server_submit(qld_server* srv, int ticket, const void* frames, int count);
+int qld_server_tick(qld_server* srv, void* stream);
+int qld_server_image(qld_server* srv, int ticket, float** amp, float** phase);
+int qld_server_iq(qld_server* srv, int ticket, int32_t* S, int32_t* C);
+long long qld_server_frames_pushed(qld_server* srv, int ticket);
+long long qld_server_mem_in_use(const qld_server* srv);
+int qld_server_sync(qld_server* srv);
+int qld_server_autotune(qld_server* srv, void* stream, float* best_us);
+int qld_server_shape(const qld_server* srv, int* threads, int* vectors_per_thread, int* ctas_per_sm);
+
 /* Kernels this library has launched in this process (all contexts). */
 long long qld_launch_count(void);
 

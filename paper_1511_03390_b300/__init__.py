@@ -20,13 +20,17 @@ __all__ = [
     "qld_fft_bin_host", "qld_get_iq", "qld_reset", "qld_frames_pushed", "qld_sync", "qld_stream",
     "qld_strerror", "qld_last_error", "qld_version", "qld_footprint_bytes", "qld_set_mem_budget",
     "qld_mem_in_use", "qld_launch_count", "qld_fft_bin_frames_noalloc", "QLD_NOALLOC_MAX_N",
-    "qld_lockin_table", "qld_lockin_frames", "LIB_PATH", "lib",
+    "qld_lockin_table", "qld_lockin_frames", "Server", "QLD_SERVER_MAX_STREAMS", "qld_server_create",
+    "qld_server_destroy", "qld_server_request", "qld_server_state", "qld_server_close", "qld_server_submit",
+    "qld_server_tick", "qld_server_image", "qld_server_iq", "qld_server_frames_pushed", "qld_server_mem_in_use",
+    "qld_server_sync", "qld_server_autotune", "qld_server_shape", "LIB_PATH", "lib",
 ]
 
 QLD_U8, QLD_U16, QLD_P12 = 1, 2, 3
 QLD_OK, QLD_E_INVAL, QLD_E_NOMEM, QLD_E_NOT_READY, QLD_E_CUDA, QLD_E_TIMEOUT = 0, -1, -2, -3, -4, -5
 QLD_MAX_N = 65536
 QLD_NOALLOC_MAX_N = 16384
+QLD_SERVER_MAX_STREAMS = 64
 
 LIB_PATH = _build.LIB
 if not _build.up_to_date():
@@ -58,6 +62,20 @@ _SIGS = {
     "qld_fft_bin_host": ([_p, _i, _p], _i),
     "qld_fft_bin_frames_noalloc": ([_p, _i, _i, _i, _i, _i, _p, _p], _i),
     "qld_lockin_table": ([ctypes.c_double, _ll, _i, _p, _p], _i),
+    "qld_server_create": ([_ll, _i], _p),
+    "qld_server_destroy": ([_p], None),
+    "qld_server_request": ([_p, _i, _i, _i, _i], _i),
+    "qld_server_state": ([_p, _i], _i),
+    "qld_server_close": ([_p, _i], _i),
+    "qld_server_submit": ([_p, _i, _p, _i], _i),
+    "qld_server_tick": ([_p, _p], _i),
+    "qld_server_image": ([_p, _i, ctypes.POINTER(_p), ctypes.POINTER(_p)], _i),
+    "qld_server_iq": ([_p, _i, _p, _p], _i),
+    "qld_server_frames_pushed": ([_p, _i], _ll),
+    "qld_server_mem_in_use": ([_p], _ll),
+    "qld_server_sync": ([_p], _i),
+    "qld_server_autotune": ([_p, _p, ctypes.POINTER(ctypes.c_float)], _i),
+    "qld_server_shape": ([_p, ctypes.POINTER(_i), ctypes.POINTER(_i), ctypes.POINTER(_i)], _i),
     "qld_lockin_frames": ([_p, _i, _i, _i, _i, _p, _p, _p, _p], _i),
     "qld_get_iq": ([_p, _p, _p], _i),
     "qld_reset": ([_p], _i),
@@ -278,3 +296,112 @@ def qld_last_error():
 
 def qld_version():
     return lib.qld_version().decode()
+
+
+# ---- serving ---------------------------------------------------------------
+
+class Server:
+    """A qld_server handle (see qld.h: continuous batching of camera streams)."""
+
+    def __init__(self, handle):
+        self.handle = handle
+        self.shapes = {}  # ticket -> (H, W, N, pixfmt)
+
+    def destroy(self):
+        if self.handle:
+            lib.qld_server_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.destroy()
+        except Exception:
+            pass
+
+
+def _sh(srv):
+    if srv is None or not srv.handle:
+        raise ValueError("invalid (destroyed) server")
+    return srv.handle
+
+
+def qld_server_create(hbm_budget_bytes, max_streams=QLD_SERVER_MAX_STREAMS):
+    h = lib.qld_server_create(int(hbm_budget_bytes), int(max_streams))
+    if not h:
+        raise QLDError(lib.qld_last_error(), "qld_server_create")
+    return Server(h)
+
+
+def qld_server_destroy(srv):
+    srv.destroy()
+
+
+def qld_server_request(srv, H, W, N, pixfmt):
+    t = lib.qld_server_request(_sh(srv), int(H), int(W), int(N), int(pixfmt))
+    if t < 0:
+        raise QLDError(t, "qld_server_request")
+    srv.shapes[t] = (int(H), int(W), int(N), int(pixfmt))
+    return t
+
+
+def qld_server_state(srv, ticket):
+    return lib.qld_server_state(_sh(srv), int(ticket))
+
+
+def qld_server_close(srv, ticket):
+    return _check(lib.qld_server_close(_sh(srv), int(ticket)), "qld_server_close")
+
+
+def qld_server_submit(srv, ticket, frames, count=None):
+    H, W, N, fmt = srv.shapes[ticket]
+    fb = H * W // 2 * 3 if fmt == QLD_P12 else H * W * fmt
+    n = _count_of(frames, count, fb)
+    return _check(lib.qld_server_submit(_sh(srv), int(ticket), _addr(frames, n * fb, "frames"), n),
+                  "qld_server_submit")
+
+
+def qld_server_tick(srv, stream=None):
+    n = lib.qld_server_tick(_sh(srv), _stream(stream))
+    if n < 0:
+        raise QLDError(n, "qld_server_tick")
+    return n
+
+
+def qld_server_image(srv, ticket):
+    """(amp, phase) device addresses of the stream's latest images."""
+    a, p = ctypes.c_void_p(), ctypes.c_void_p()
+    _check(lib.qld_server_image(_sh(srv), int(ticket), ctypes.byref(a), ctypes.byref(p)), "qld_server_image")
+    return a.value, p.value
+
+
+def qld_server_iq(srv, ticket, S=None, C=None):
+    H, W, _, _ = srv.shapes[ticket]
+    return _check(lib.qld_server_iq(_sh(srv), int(ticket), _addr(S, 4 * H * W, "S"), _addr(C, 4 * H * W, "C")),
+                  "qld_server_iq")
+
+
+def qld_server_frames_pushed(srv, ticket):
+    return lib.qld_server_frames_pushed(_sh(srv), int(ticket))
+
+
+def qld_server_mem_in_use(srv):
+    return lib.qld_server_mem_in_use(_sh(srv))
+
+
+def qld_server_sync(srv):
+    return _check(lib.qld_server_sync(_sh(srv)), "qld_server_sync")
+
+
+def qld_server_autotune(srv, stream=None):
+    """Index of the fastest launch shape on the active streams, and its time (us)."""
+    us = ctypes.c_float()
+    k = lib.qld_server_autotune(_sh(srv), _stream(stream), ctypes.byref(us))
+    if k < 0:
+        raise QLDError(k, "qld_server_autotune")
+    return k, us.value
+
+
+def qld_server_shape(srv):
+    t, v, c = _i(), _i(), _i()
+    _check(lib.qld_server_shape(_sh(srv), ctypes.byref(t), ctypes.byref(v), ctypes.byref(c)), "qld_server_shape")
+    return t.value, v.value, c.value

@@ -19,54 +19,29 @@
 #include "qld.h"
 #include "qld_kernels.cuh"
 
-struct qld_ctx {
-    int H, W, N, pixfmt;
-    long long frame_bytes;  // bytes of one frame in the input format
-    long long npix;
-    long long npad;         // padded pixel count of S and C
-    long long slot_stride;  // bytes
-    int device;
-    uint8_t* ring;
-    int32_t* S;
-    int32_t* C;
-    float2* tw;
-    int tw_k;               // bin whose twiddles are in tw, -1 if none
-    long long pushed;
-    cudaStream_t stream;
-    long long footprint;
-    // host-buffer variants (created on first use)
-    struct HostPipe* pipe;
-};
+#include "qld_internal.h"
 
-// Device staging for the host-buffer calls. Frames go host -> stage[i] on
-// the copy-in stream, the push reads stage[i] on the context's stream;
-// images go to out[o] on the context's stream and out[o] -> host on the
-// copy-out stream. Two input stages and four output buffers, each guarded by
-// a ready / free event pair, let the copies of one step overlap the kernels
-// of the next and previous steps.
-struct HostPipe {
-    static constexpr int kIn = 2, kOut = 4;
-    cudaStream_t cin, cout;
-    uint8_t* stage[kIn];
-    long long stage_bytes;
-    cudaEvent_t in_ready[kIn], in_free[kIn];
-    float* out[kOut];
-    long long out_elems;
-    cudaEvent_t out_ready[kOut], out_free[kOut];
-    int in_idx, out_idx;
-};
-
-namespace {
+namespace qldi {
 
 thread_local int g_last_error = QLD_OK;
-std::atomic<long long> g_budget{0};
-std::atomic<long long> g_in_use{0};
 std::atomic<long long> g_launches{0};
 
 int set_err(int st) {
     if (st != QLD_OK) g_last_error = st;
     return st;
 }
+
+void count_launches(int n) { g_launches.fetch_add(n); }
+
+}  // namespace qldi
+
+using qldi::g_launches;
+using qldi::set_err;
+
+namespace {
+
+std::atomic<long long> g_budget{0};
+std::atomic<long long> g_in_use{0};
 
 long long round_up(long long x, long long m) { return (x + m - 1) / m * m; }
 
@@ -78,10 +53,19 @@ bool valid_dims(int H, int W, int N, int pixfmt) {
     return npix <= (1ll << 31) - 1;
 }
 
-// Bytes of one frame, and of one kernel vector, per pixel format.
+}  // namespace
+
+namespace qldi {
 long long frame_bytes_of(long long npix, int pixfmt) { return pixfmt == QLD_P12 ? npix / 2 * 3 : npix * pixfmt; }
 int vec_bytes_of(int pixfmt) { return pixfmt == QLD_P12 ? qldk::Fmt<qldk::p12_t>::VB : qldk::kVecBytes; }
 unsigned vec_align_of(int pixfmt) { return pixfmt == QLD_P12 ? qldk::Fmt<qldk::p12_t>::ALIGN : 16u; }
+}  // namespace qldi
+
+using qldi::frame_bytes_of;
+using qldi::vec_align_of;
+using qldi::vec_bytes_of;
+
+namespace {
 
 struct Layout {
     long long npix, npad, slot_stride, ring_bytes, sums_bytes, tw_bytes, total;
@@ -322,7 +306,7 @@ const char* qld_strerror(int st) {
     }
 }
 
-int qld_last_error(void) { return g_last_error; }
+int qld_last_error(void) { return qldi::g_last_error; }
 
 long long qld_footprint_bytes(int H, int W, int N, int pixfmt) {
     if (!valid_dims(H, W, N, pixfmt)) return QLD_E_INVAL;

@@ -1,0 +1,95 @@
+// qld_batch.cuh -- one persistent launch that pushes frames into many
+// streams of different sizes, windows and pixel formats.
+//
+// The paper's real-time loop acquires and processes frames of one camera as
+// they arrive (SI, "Timing sequence for hybrid parallelisation"). Serving
+// several cameras at once, each stream's push (ring update, exact int32 sums,
+// amplitude/phase image) is the per-vector work of push_vec_kernel; here the
+// vectors of every stream with pending frames form one list of tiles that a
+// persistent grid walks, so uneven streams share one launch.
+
+#pragma once
+
+#include "qld_kernels.cuh"
+
+namespace qldk {
+
+// One stream's share of a batch.
+struct BatchItem {
+    PushArgs a;       // nvec counts Fmt<T>::VB-byte vectors (vector path only)
+    int fmt;          // 1 = uint8, 2 = uint16, 3 = packed 12-bit
+    int reset;        // the push holds at least N frames: rebuild the window
+    int epi;          // write the amplitude / phase image after the push
+    long long tile0;  // first tile of this item in the batch
+};
+
+struct BatchHeader {
+    int nitems;
+    long long ntiles;  // sum over items of ceil(nvec / tile vectors)
+};
+
+template <typename T>
+__device__ __forceinline__ void push_vector_mode(const PushArgs& a, int reset, int epi, long long v) {
+    if (reset) {
+        if (epi) push_vector<T, true, true>(a, v);
+        else push_vector<T, true, false>(a, v);
+    } else {
+        if (epi) push_vector<T, false, true>(a, v);
+        else push_vector<T, false, false>(a, v);
+    }
+}
+
+// Tile = NT * VPT consecutive vectors of one item; CTA b takes tiles b,
+// b + gridDim.x, ... The item of a tile is found by binary search over the
+// items' tile0 (the same for every thread of the CTA, so no divergence).
+template <int NT, int VPT>
+__global__ void __launch_bounds__(NT) batch_push_kernel(const BatchHeader* __restrict__ hdr,
+                                                        const BatchItem* __restrict__ items) {
+    const int n = hdr->nitems;
+    const long long ntiles = hdr->ntiles;
+    for (long long tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+        int lo = 0, hi = n - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (items[mid].tile0 <= tile) lo = mid;
+            else hi = mid - 1;
+        }
+        const BatchItem& it = items[lo];
+        const PushArgs a = it.a;
+        const int fmt = it.fmt, reset = it.reset, epi = it.epi;
+        const long long vbase = (tile - it.tile0) * (long long)(NT * VPT);
+#pragma unroll 1
+        for (int k = 0; k < VPT; ++k) {
+            const long long v = vbase + (long long)k * NT + threadIdx.x;
+            if (v >= a.nvec) break;
+            if (fmt == 2) push_vector_mode<uint16_t>(a, reset, epi, v);
+            else if (fmt == 1) push_vector_mode<uint8_t>(a, reset, epi, v);
+            else push_vector_mode<p12_t>(a, reset, epi, v);
+        }
+    }
+}
+
+// Launch shapes the autotuner chooses from: threads per CTA, vectors per
+// thread per tile, resident CTAs per SM of the persistent grid.
+struct BatchShape {
+    int threads, vpt, ctas_per_sm;
+};
+
+constexpr BatchShape kBatchShapes[] = {{128, 1, 4}, {128, 2, 4}, {128, 4, 4}, {256, 1, 2},
+                                       {256, 2, 2}, {256, 1, 4}, {128, 1, 8}, {64, 2, 8}};
+constexpr int kNumBatchShapes = (int)(sizeof(kBatchShapes) / sizeof(kBatchShapes[0]));
+
+inline long long batch_tile_vectors(const BatchShape& s) { return (long long)s.threads * s.vpt; }
+
+inline void launch_batch(const BatchShape& s, int num_sms, const BatchHeader* hdr, const BatchItem* items,
+                         cudaStream_t st) {
+    const unsigned grid = (unsigned)(num_sms * s.ctas_per_sm);
+    if (s.threads == 128 && s.vpt == 1) batch_push_kernel<128, 1><<<grid, 128, 0, st>>>(hdr, items);
+    else if (s.threads == 128 && s.vpt == 2) batch_push_kernel<128, 2><<<grid, 128, 0, st>>>(hdr, items);
+    else if (s.threads == 128 && s.vpt == 4) batch_push_kernel<128, 4><<<grid, 128, 0, st>>>(hdr, items);
+    else if (s.threads == 256 && s.vpt == 1) batch_push_kernel<256, 1><<<grid, 256, 0, st>>>(hdr, items);
+    else if (s.threads == 256 && s.vpt == 2) batch_push_kernel<256, 2><<<grid, 256, 0, st>>>(hdr, items);
+    else batch_push_kernel<64, 2><<<grid, 64, 0, st>>>(hdr, items);
+}
+
+}  // namespace qldk

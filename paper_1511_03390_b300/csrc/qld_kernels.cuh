@@ -217,17 +217,16 @@ struct PushArgs {
     int out_aligned;        // amp and phase are 16-byte aligned (or NULL)
 };
 
-// Vector path: frames 16-byte aligned and frame_stride a multiple of 16.
-// RESET: the window is rebuilt from the applied frames alone (a push of at
-// least N frames), so the sums start at zero and the expiring slots are not
-// read. EPI: also write the amplitude / phase image.
+// Push of the vector v of every applied frame (vector path: frames aligned to
+// Fmt<T>::ALIGN and frame_stride a multiple of Fmt<T>::VB). RESET: the
+// window is rebuilt from the applied frames alone (a push of at least N
+// frames), so the sums start at zero and the expiring slots are not read.
+// EPI: also write the amplitude / phase image.
 template <typename T, bool RESET, bool EPI>
-__global__ void __launch_bounds__(128) push_vec_kernel(const PushArgs a) {
+__device__ __forceinline__ void push_vector(const PushArgs& a, long long v) {
     using F = Fmt<T>;
     using Vec = typename F::Vec;
     constexpr int VP = F::VP;
-    const long long v = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (v >= a.nvec) return;
     const long long off = v * F::VB;
     const long long p0 = v * VP;
 
@@ -315,6 +314,12 @@ __global__ void __launch_bounds__(128) push_vec_kernel(const PushArgs a) {
     }
 }
 
+template <typename T, bool RESET, bool EPI>
+__global__ void __launch_bounds__(128) push_vec_kernel(const PushArgs a) {
+    const long long v = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (v < a.nvec) push_vector<T, RESET, EPI>(a, v);
+}
+
 // Scalar path for inputs that are not 16-byte aligned or whose frame size is
 // not a multiple of 16 bytes: one pixel per thread.
 template <typename T, bool RESET, bool EPI>
@@ -399,7 +404,7 @@ __global__ void __launch_bounds__(256) push_scalar_p12_kernel(const PushArgs a) 
 // ------------------------------------------------------------------ image --
 
 // Four pixels per thread; S and C are padded so the int4 loads stay in bounds.
-__global__ void __launch_bounds__(256) image_kernel(const int32_t* __restrict__ S, const int32_t* __restrict__ C,
+static __global__ void __launch_bounds__(256) image_kernel(const int32_t* __restrict__ S, const int32_t* __restrict__ C,
                                                     long long npix, float* __restrict__ amp,
                                                     float* __restrict__ phase, int out_aligned) {
     const long long p0 = ((long long)blockIdx.x * blockDim.x + threadIdx.x) * 4;
@@ -434,7 +439,7 @@ __global__ void __launch_bounds__(256) image_kernel(const int32_t* __restrict__ 
 // the frame whose absolute index s satisfies s = j (mod N), and
 // exp(-2 pi i k s / N) depends only on (k s) mod N, so slot order needs no
 // window rotation.
-__global__ void twiddle_kernel(float2* __restrict__ tw, int N, int k) {
+static __global__ void twiddle_kernel(float2* __restrict__ tw, int N, int k) {
     const int j = blockIdx.x * blockDim.x + threadIdx.x;
     if (j >= N) return;
     const long long m = ((long long)k * j) % N;
@@ -585,7 +590,7 @@ inline void launch_bin(const uint8_t* base, long long stride, int N, const float
 // Twiddles of a lock-in at omega * dt = omega_dt radians per frame for the
 // frames with absolute indices s0 .. s0+N-1: tw[j] = (cos, -sin) of
 // omega_dt * (s0 + j), evaluated in FP64 and rounded to float.
-__global__ void lockin_table_kernel(float2* __restrict__ tw, int N, double omega_dt, long long s0) {
+static __global__ void lockin_table_kernel(float2* __restrict__ tw, int N, double omega_dt, long long s0) {
     const int j = blockIdx.x * blockDim.x + threadIdx.x;
     if (j >= N) return;
     double sn, cs;

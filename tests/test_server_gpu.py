@@ -1,0 +1,180 @@
+"""Serving several streams with continuous batching: each stream's results in
+the mix equal its results alone (and the oracle's), admission follows the HBM
+budget in arrival order, streams join while earlier ticks run, and the
+autotuner's choice leaves results unchanged."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import paper_1511_03390_b300 as q
+from qld_check import pack12
+
+pytestmark = pytest.mark.gpu
+
+# (H, W, N, pixfmt): uneven sizes, windows and formats
+MIX = [(48, 64, 16, q.QLD_U8), (64, 80, 32, q.QLD_U16), (32, 48, 8, q.QLD_P12), (96, 128, 64, q.QLD_U16),
+       (40, 64, 12, q.QLD_U8)]
+
+
+@pytest.fixture(autouse=True)
+def _need_gpu():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+
+
+def frames_for(rng, H, W, fmt, n):
+    hi = 256 if fmt == q.QLD_U8 else 4096
+    x = rng.integers(0, hi, size=(n, H * W)).astype(np.uint8 if fmt == q.QLD_U8 else np.uint16)
+    raw = pack12(x) if fmt == q.QLD_P12 else x
+    dev = torch.from_numpy(np.ascontiguousarray(raw).view(np.uint8).reshape(n, -1)).cuda()
+    return x, dev
+
+
+class _DevArray:
+    """A zero-copy view of library-owned device memory for torch."""
+
+    def __init__(self, addr, n, typestr):
+        self.__cuda_array_interface__ = {"shape": (n,), "typestr": typestr, "data": (addr, False), "version": 3}
+
+
+def server_images(srv, ticket, npix):
+    a, p = q.qld_server_image(srv, ticket)
+    torch.cuda.synchronize()
+    amp = torch.as_tensor(_DevArray(a, npix, "<f4"), device="cuda").cpu().numpy()
+    ph = torch.as_tensor(_DevArray(p, npix, "<f4"), device="cuda").cpu().numpy()
+    return amp, ph
+
+
+def server_iq(srv, ticket, npix):
+    S = torch.empty(npix, dtype=torch.int32, device="cuda")
+    C = torch.empty_like(S)
+    q.qld_server_iq(srv, ticket, S, C)
+    torch.cuda.synchronize()
+    return S.cpu().numpy(), C.cpu().numpy()
+
+
+def ctx_state(ctx):
+    S = torch.empty(ctx.npix, dtype=torch.int32, device="cuda")
+    C = torch.empty_like(S)
+    amp = torch.empty(ctx.npix, dtype=torch.float32, device="cuda")
+    ph = torch.empty_like(amp)
+    q.qld_get_iq(ctx, S, C)
+    q.qld_image(ctx, amp, ph)
+    q.qld_sync(ctx)
+    return S.cpu().numpy(), C.cpu().numpy(), amp.cpu().numpy(), ph.cpu().numpy()
+
+
+def run_mix(autotune=False, ticks=10, seed=0):
+    rng = np.random.default_rng(seed)
+    srv = q.qld_server_create(1 << 36)
+    tickets = [q.qld_server_request(srv, *m) for m in MIX]
+    assert all(q.qld_server_state(srv, t) == 0 for t in tickets)
+    alone = [q.qld_create(*m) for m in MIX]
+    history = [np.zeros((0, m[0] * m[1]), np.uint8 if m[3] == q.QLD_U8 else np.uint16) for m in MIX]
+    keep = []
+    for tick in range(ticks):
+        for i, (t, m) in enumerate(zip(tickets, MIX)):
+            H, W, N, fmt = m
+            pattern = [1, 2, 0, 3, 1, N + 1, 1, 4, 0, 2]
+            count = pattern[(tick + i) % len(pattern)] if tick < ticks - 1 else 1
+            if count == 0:
+                continue
+            x, dev = frames_for(rng, H, W, fmt, count)
+            keep.append(dev)
+            q.qld_server_submit(srv, t, dev, count)
+            q.qld_push_frames(alone[i], dev, count)
+            history[i] = np.concatenate([history[i], x])
+        assert q.qld_server_tick(srv) >= 1
+        if autotune and tick == 2:
+            k, us = q.qld_server_autotune(srv)
+            assert 0 <= k and us > 0
+    q.qld_server_sync(srv)
+    for i, (t, m) in enumerate(zip(tickets, MIX)):
+        H, W, N, fmt = m
+        npix = H * W
+        assert q.qld_server_frames_pushed(srv, t) == history[i].shape[0]
+        S, C = server_iq(srv, t, npix)
+        amp, ph = server_images(srv, t, npix)
+        Sa, Ca, ampa, pha = ctx_state(alone[i])
+        assert np.array_equal(S, Sa) and np.array_equal(C, Ca), "sums differ in the mix for stream %d" % i
+        assert np.array_equal(amp, ampa) and np.array_equal(ph, pha), "images differ in the mix for stream %d" % i
+        win = history[i][-N:]
+        S_r, C_r = oracle.quadrature_sums(win, s0=history[i].shape[0] - N + 1)
+        assert np.array_equal(S, S_r) and np.array_equal(C, C_r)
+        alone[i].destroy()
+    srv.destroy()
+
+
+def test_each_stream_in_the_mix_equals_it_alone():
+    run_mix()
+
+
+def test_autotuned_shape_gives_the_same_results():
+    run_mix(autotune=True, seed=1)
+
+
+def test_admission_by_budget_in_arrival_order():
+    fa = q.qld_footprint_bytes(64, 64, 64, q.QLD_U16) + 2 * 64 * 64 * 4
+    fb = q.qld_footprint_bytes(32, 32, 16, q.QLD_U8) + 2 * 32 * 32 * 4
+    srv = q.qld_server_create(2 * fa + fb // 2)
+    a = q.qld_server_request(srv, 64, 64, 64, q.QLD_U16)
+    b = q.qld_server_request(srv, 64, 64, 64, q.QLD_U16)
+    c = q.qld_server_request(srv, 64, 64, 64, q.QLD_U16)  # does not fit: waits
+    d = q.qld_server_request(srv, 32, 32, 16, q.QLD_U8)   # would fit, but arrived after c: waits too
+    assert [q.qld_server_state(srv, t) for t in (a, b, c, d)] == [0, 0, 1, 1]
+    assert q.qld_server_mem_in_use(srv) == 2 * fa
+    rng = np.random.default_rng(4)
+    x, dev = frames_for(rng, 64, 64, q.QLD_U16, 2)
+    with pytest.raises(q.QLDError) as e:
+        q.qld_server_submit(srv, c, dev, 2)
+    assert e.value.status == q.QLD_E_NOT_READY
+    with pytest.raises(q.QLDError) as e:
+        q.qld_server_request(srv, 1024, 1024, 4096, q.QLD_U16)  # larger than the whole budget
+    assert e.value.status == q.QLD_E_NOMEM
+    q.qld_server_submit(srv, a, dev, 2)
+    q.qld_server_tick(srv)
+    q.qld_server_close(srv, a)  # frees room: c is admitted, then d does not fit behind it
+    assert [q.qld_server_state(srv, t) for t in (a, b, c, d)] == [-1, 0, 0, 1]
+    q.qld_server_close(srv, b)
+    assert q.qld_server_state(srv, d) == 0
+    assert q.qld_server_mem_in_use(srv) == fa + fb
+    srv.destroy()
+
+
+def test_stream_admitted_while_ticks_run_joins_the_next_tick():
+    rng = np.random.default_rng(5)
+    srv = q.qld_server_create(1 << 34)
+    a = q.qld_server_request(srv, 64, 96, 8, q.QLD_U16)
+    xa, da = frames_for(rng, 64, 96, q.QLD_U16, 8)
+    q.qld_server_submit(srv, a, da, 8)
+    q.qld_server_tick(srv)                      # no sync: still on the GPU
+    b = q.qld_server_request(srv, 48, 32, 4, q.QLD_U8)
+    assert q.qld_server_state(srv, b) == 0
+    xb, db = frames_for(rng, 48, 32, q.QLD_U8, 5)
+    xa2, da2 = frames_for(rng, 64, 96, q.QLD_U16, 1)
+    q.qld_server_submit(srv, b, db, 5)
+    q.qld_server_submit(srv, a, da2, 1)
+    assert q.qld_server_tick(srv) == 2         # both streams in one launch
+    q.qld_server_sync(srv)
+    for t, hist, H, W, N in [(a, np.concatenate([xa, xa2]), 64, 96, 8), (b, xb, 48, 32, 4)]:
+        S, C = server_iq(srv, t, H * W)
+        S_r, C_r = oracle.quadrature_sums(hist[-N:], s0=hist.shape[0] - N + 1)
+        assert np.array_equal(S, S_r) and np.array_equal(C, C_r)
+        amp, ph = server_images(srv, t, H * W)
+        R, phr = oracle.amplitude_phase(S_r, C_r)
+        assert np.all(np.abs(amp - R) <= 1e-6 * R)
+    srv.destroy()
+
+
+def test_server_rejects_unbatchable_or_bad_requests():
+    srv = q.qld_server_create(1 << 30)
+    for args in [(3, 5, 8, q.QLD_U8), (4, 4, 6, q.QLD_U16), (2, 10, 8, q.QLD_P12)]:  # 15 B frames; N; 30 B
+        with pytest.raises(q.QLDError) as e:
+            q.qld_server_request(srv, *args)
+        assert e.value.status == q.QLD_E_INVAL
+    t = q.qld_server_request(srv, 16, 16, 8, q.QLD_U16)
+    buf = torch.zeros(16 * 16 * 2 * 2 + 16, dtype=torch.uint8, device="cuda")
+    assert q.lib.qld_server_submit(srv.handle, t, buf.data_ptr() + 4, 1) == q.QLD_E_INVAL  # misaligned
+    assert q.qld_server_tick(srv) == 0  # nothing submitted: no launch
+    srv.destroy()
