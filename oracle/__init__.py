@@ -57,6 +57,10 @@ class Oracle:
         lib.orc_lockin_general.restype = _int
         lib.orc_cnr.argtypes = [_p, _int, _int, _int, _int, _int, _p]
         lib.orc_cnr.restype = _int
+        lib.orc_conv3x3_fwd.argtypes = [_p, _p, _p, _int, _int, _int, _int, _int, _p]
+        lib.orc_conv3x3_fwd.restype = _int
+        lib.orc_conv3x3_bwd.argtypes = [_p, _p, _p, _int, _int, _int, _int, _int, _p, _p, _p]
+        lib.orc_conv3x3_bwd.restype = _int
         self.lib = lib
         self.path = lib_path
 
@@ -131,6 +135,35 @@ class Oracle:
             raise ValueError("orc_cnr: the surround ring leaves the image")
         return float(out[0])
 
+    def conv3x3(self, x, w, bias=None):
+        """FP64 3x3 convolution, zero padding 1: x [B,H,W,Cin], w [3,3,Cin,Cout]."""
+        x = np.ascontiguousarray(x, np.float64)
+        w = np.ascontiguousarray(w, np.float64)
+        B, H, W, Cin = x.shape
+        Cout = w.shape[3]
+        assert w.shape == (3, 3, Cin, Cout)
+        b = None if bias is None else np.ascontiguousarray(bias, np.float64)
+        out = np.zeros((B, H, W, Cout), np.float64)
+        rc = self.lib.orc_conv3x3_fwd(_ptr(x), _ptr(w), _ptr(b), B, H, W, Cin, Cout, _ptr(out))
+        if rc != 0:
+            raise ValueError("orc_conv3x3_fwd rejected its arguments")
+        return out
+
+    def conv3x3_backward(self, x, w, g):
+        """FP64 (dx, dw, dbias) of a 3x3 convolution for the output gradient g."""
+        x = np.ascontiguousarray(x, np.float64)
+        w = np.ascontiguousarray(w, np.float64)
+        g = np.ascontiguousarray(g, np.float64)
+        B, H, W, Cin = x.shape
+        Cout = w.shape[3]
+        dx = np.zeros_like(x)
+        dw = np.zeros_like(w)
+        db = np.zeros(Cout, np.float64)
+        rc = self.lib.orc_conv3x3_bwd(_ptr(x), _ptr(w), _ptr(g), B, H, W, Cin, Cout, _ptr(dx), _ptr(dw), _ptr(db))
+        if rc != 0:
+            raise ValueError("orc_conv3x3_bwd rejected its arguments")
+        return dx, dw, db
+
 
 _default = None
 
@@ -169,3 +202,11 @@ def lockin_general(x, omega_dt, s0=1, nthreads=1):
 
 def cnr(img, r0, c0, m):
     return get().cnr(img, r0, c0, m)
+
+
+def conv3x3(x, w, bias=None):
+    return get().conv3x3(x, w, bias)
+
+
+def conv3x3_backward(x, w, g):
+    return get().conv3x3_backward(x, w, g)

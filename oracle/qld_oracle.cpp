@@ -266,4 +266,82 @@ int orc_cnr(const double* img, int H, int W, int r0, int c0, int m, double* cnr)
     return 0;
 }
 
+// ---- 3x3 convolution (the learned short-window network) ------------------
+// Not in the paper: the network maps short-window I/Q maps to the long-window
+// amplitude. Cross-correlation with zero padding 1, NHWC activations and
+// weights w[ky][kx][ci][co]:
+//   out[b][y][x][co] = bias[co] + sum_{ky,kx,ci} in[b][y+ky-1][x+kx-1][ci] w[ky][kx][ci][co]
+// Backward of a loss L with g = dL/dout:
+//   din[b][y][x][ci]  = sum_{ky,kx,co} g[b][y-ky+1][x-kx+1][co] w[ky][kx][ci][co]
+//   dw[ky][kx][ci][co] = sum_{b,y,x} in[b][y+ky-1][x+kx-1][ci] g[b][y][x][co]
+//   dbias[co]          = sum_{b,y,x} g[b][y][x][co]
+// All FP64, plain loops in that order; out-of-range taps are zero.
+int orc_conv3x3_fwd(const double* in, const double* w, const double* bias, int B, int H, int W, int Cin, int Cout,
+                    double* out) {
+    if (!in || !w || !out || B < 1 || H < 1 || W < 1 || Cin < 1 || Cout < 1) return -1;
+    for (int b = 0; b < B; ++b)
+        for (int y = 0; y < H; ++y)
+            for (int x = 0; x < W; ++x)
+                for (int co = 0; co < Cout; ++co) {
+                    double acc = bias ? bias[co] : 0.0;
+                    for (int ky = 0; ky < 3; ++ky)
+                        for (int kx = 0; kx < 3; ++kx) {
+                            const int yy = y + ky - 1, xx = x + kx - 1;
+                            if (yy < 0 || yy >= H || xx < 0 || xx >= W) continue;
+                            for (int ci = 0; ci < Cin; ++ci)
+                                acc += in[(((int64_t)b * H + yy) * W + xx) * Cin + ci] *
+                                       w[((int64_t)(ky * 3 + kx) * Cin + ci) * Cout + co];
+                        }
+                    out[(((int64_t)b * H + y) * W + x) * Cout + co] = acc;
+                }
+    return 0;
+}
+
+int orc_conv3x3_bwd(const double* in, const double* w, const double* g, int B, int H, int W, int Cin, int Cout,
+                    double* din, double* dw, double* dbias) {
+    if (!in || !w || !g || B < 1 || H < 1 || W < 1 || Cin < 1 || Cout < 1) return -1;
+    if (din) {
+        for (int b = 0; b < B; ++b)
+            for (int y = 0; y < H; ++y)
+                for (int x = 0; x < W; ++x)
+                    for (int ci = 0; ci < Cin; ++ci) {
+                        double acc = 0.0;
+                        for (int ky = 0; ky < 3; ++ky)
+                            for (int kx = 0; kx < 3; ++kx) {
+                                const int yy = y - ky + 1, xx = x - kx + 1;
+                                if (yy < 0 || yy >= H || xx < 0 || xx >= W) continue;
+                                for (int co = 0; co < Cout; ++co)
+                                    acc += g[(((int64_t)b * H + yy) * W + xx) * Cout + co] *
+                                           w[((int64_t)(ky * 3 + kx) * Cin + ci) * Cout + co];
+                            }
+                        din[(((int64_t)b * H + y) * W + x) * Cin + ci] = acc;
+                    }
+    }
+    if (dw) {
+        for (int ky = 0; ky < 3; ++ky)
+            for (int kx = 0; kx < 3; ++kx)
+                for (int ci = 0; ci < Cin; ++ci)
+                    for (int co = 0; co < Cout; ++co) {
+                        double acc = 0.0;
+                        for (int b = 0; b < B; ++b)
+                            for (int y = 0; y < H; ++y)
+                                for (int x = 0; x < W; ++x) {
+                                    const int yy = y + ky - 1, xx = x + kx - 1;
+                                    if (yy < 0 || yy >= H || xx < 0 || xx >= W) continue;
+                                    acc += in[(((int64_t)b * H + yy) * W + xx) * Cin + ci] *
+                                           g[(((int64_t)b * H + y) * W + x) * Cout + co];
+                                }
+                        dw[((int64_t)(ky * 3 + kx) * Cin + ci) * Cout + co] = acc;
+                    }
+    }
+    if (dbias) {
+        for (int co = 0; co < Cout; ++co) {
+            double acc = 0.0;
+            for (int64_t p = 0; p < (int64_t)B * H * W; ++p) acc += g[p * Cout + co];
+            dbias[co] = acc;
+        }
+    }
+    return 0;
+}
+
 }  // extern "C"

@@ -318,6 +318,52 @@ def pin_cnr_worked_example(o):
         raise AssertionError("a ring leaving the image must be rejected")
 
 
+# 3x3 convolution (learned short-window network). The backward-data map is
+# the adjoint of the forward map: <conv(x), g> = <x, conv_bwd_data(g)>; the
+# weight gradient follows from linearity in w: <dw(x, g), v> = <conv(x; v), g>
+# (bias-free); the bias gradient is the sum of g.
+def pin_conv_adjoint_and_linearity(o):
+    rng = np.random.default_rng(31)
+    for B, H, W, Cin, Cout in [(1, 5, 7, 2, 3), (2, 4, 4, 3, 1), (1, 1, 6, 1, 2)]:
+        x = rng.standard_normal((B, H, W, Cin))
+        w = rng.standard_normal((3, 3, Cin, Cout))
+        g = rng.standard_normal((B, H, W, Cout))
+        v = rng.standard_normal((3, 3, Cin, Cout))
+        y = o.conv3x3(x, w)
+        dx, dw, db = o.conv3x3_backward(x, w, g)
+        _assert_close([np.sum(y * g)], [np.sum(x * dx)], 1e-12, 1e-12, "conv adjoint")
+        _assert_close([np.sum(dw * v)], [np.sum(o.conv3x3(x, v) * g)], 1e-12, 1e-12, "weight-gradient linearity")
+        _assert_close(db, g.sum(axis=(0, 1, 2)), 1e-12, 1e-12, "bias gradient")
+        bias = rng.standard_normal(Cout)
+        _assert_close(o.conv3x3(x, w, bias), y + bias, 1e-12, 1e-12, "bias added")
+
+
+# Closed forms: the delta kernel (w[1][1] = identity) copies the input; an
+# all-ones kernel on a constant c image of Cin channels gives 9 Cin c inside,
+# 6 Cin c on edges and 4 Cin c at corners (zero padding); against scipy's
+# correlate2d (a library routine) for one channel pair.
+def pin_conv_closed_forms(o):
+    rng = np.random.default_rng(32)
+    x = rng.standard_normal((2, 6, 5, 3))
+    w = np.zeros((3, 3, 3, 3))
+    for c in range(3):
+        w[1, 1, c, c] = 1.0
+    _assert_close(o.conv3x3(x, w), x, 0, 1e-15, "delta kernel")
+    c = 2.5
+    y = o.conv3x3(np.full((1, 5, 6, 4), c), np.ones((3, 3, 4, 1)))[0, :, :, 0]
+    exp = np.full((5, 6), 9 * 4 * c)
+    exp[0, :] = exp[-1, :] = 6 * 4 * c
+    exp[:, 0] = exp[:, -1] = 6 * 4 * c
+    exp[0, 0] = exp[0, -1] = exp[-1, 0] = exp[-1, -1] = 4 * 4 * c
+    _assert_close(y, exp, 1e-14, 0, "constant image, all-ones kernel")
+    from scipy.signal import correlate2d
+
+    x1 = rng.standard_normal((1, 7, 9, 1))
+    w1 = rng.standard_normal((3, 3, 1, 1))
+    _assert_close(o.conv3x3(x1, w1)[0, :, :, 0], correlate2d(x1[0, :, :, 0], w1[:, :, 0, 0], mode="same"), 1e-12,
+                  1e-12, "scipy correlate2d")
+
+
 ALL_PINS = [
     pin_reference_tables,
     pin_square_wave,
@@ -334,4 +380,6 @@ ALL_PINS = [
     pin_lockin_general_tone_and_orthogonality,
     pin_lockin_general_is_dft_bin,
     pin_cnr_worked_example,
+    pin_conv_adjoint_and_linearity,
+    pin_conv_closed_forms,
 ]

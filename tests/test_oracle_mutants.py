@@ -47,6 +47,12 @@ MUTANTS = [
      "const double d = img[(int64_t)r * W + c] - src;"),
     ("cnr_ring_one_pixel_short", "for (int r = r0 - m; r < r0 + 2 * m; ++r)\n        for (int c = c0 - m; c < c0 + 2 * m; ++c) {\n            const bool in_source = r >= r0 && r < r0 + m && c >= c0 && c < c0 + m;\n            if (in_source) continue;\n            sur",
      "for (int r = r0 - m; r < r0 + 2 * m; ++r)\n        for (int c = c0 - m; c < c0 + 2 * m - 1; ++c) {\n            const bool in_source = r >= r0 && r < r0 + m && c >= c0 && c < c0 + m;\n            if (in_source) continue;\n            sur"),
+    ("conv_flipped_taps", "const int yy = y + ky - 1, xx = x + kx - 1;\n                            if (yy < 0 || yy >= H || xx < 0 || xx >= W) continue;\n                            for (int ci = 0; ci < Cin; ++ci)\n                                acc += in",
+     "const int yy = y - ky + 1, xx = x - kx + 1;\n                            if (yy < 0 || yy >= H || xx < 0 || xx >= W) continue;\n                            for (int ci = 0; ci < Cin; ++ci)\n                                acc += in"),
+    ("conv_bwd_data_unflipped", "const int yy = y - ky + 1, xx = x - kx + 1;", "const int yy = y + ky - 1, xx = x + kx - 1;"),
+    ("conv_wgrad_transposed_channels", "dw[((int64_t)(ky * 3 + kx) * Cin + ci) * Cout + co] = acc;",
+     "dw[((int64_t)(ky * 3 + kx) * Cin + (ci + 1) % Cin) * Cout + co] = acc;"),
+    ("conv_bias_dropped", "double acc = bias ? bias[co] : 0.0;", "double acc = 0.0;"),
     ("threads_last_range_lost", "for (int t = 0; t < nthreads; ++t) {", "for (int t = 0; t < nthreads - 1; ++t) {"),
 ]
 
