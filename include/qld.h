@@ -255,6 +255,55 @@ int qld_server_sync(qld_server* srv);
 int qld_server_autotune(qld_server* srv, void* stream, float* best_us);
 int qld_server_shape(const qld_server* srv, int* threads, int* vectors_per_thread, int* ctas_per_sm);
 
+/* ---- Learned short-window QLD: network kernels --------------------------
+ *
+ * No counterpart in the paper (which motivates shorter time series for lower
+ * latency, SI "Timing sequence" and the tree/cow experiment): a small U-Net
+ * maps the I/Q maps of a short window to the amplitude plain QLD reaches with
+ * a long window. Its building blocks, all on `stream`, all device pointers:
+ *  - qldnn_conv3x3_fwd: out = relu?(conv3x3(in, w) + bias), zero padding 1,
+ *    BF16 tensor-core implicit GEMM with FP32 accumulation. in [B][H][W][Cin]
+ *    bf16 (Cin % 16 == 0, 16-byte aligned), w [9][Cin][Cout] bf16 (tap =
+ *    3 ky + kx; Cout % 32 == 0), bias [Cout] f32 or NULL; out_bf16 and/or
+ *    out_f32 [B][H][W][Cout].
+ *  - qldnn_conv3x3_dgrad: din = data gradient of that convolution for the
+ *    output gradient g [B][H][W][Cout] bf16 (Cin % 32 == 0); wt_scratch holds
+ *    9 Cin Cout bf16 (the flipped, transposed weights).
+ *  - qldnn_conv3x3_wgrad: dw [9][Cin][Cout] f32 += weight gradient (the
+ *    caller zeroes dw); tensor-core GEMM over pixels, split across CTAs.
+ *  - qldnn_bias_grad (db [C] += sum of g; C <= 256), qldnn_relu_bwd
+ *    (out = bf16(g * (act > 0))), qldnn_avgpool2 / _bwd, qldnn_upsample2
+ *    (nearest) / _bwd, qldnn_concat / qldnn_split (channels), qldnn_head /
+ *    _bwd (1x1 convolution to one f32 channel), qldnn_mse (loss += mean
+ *    square error, grad = its gradient), qldnn_adam (Adam on f32 master
+ *    weights, refreshing an optional bf16 copy), qldnn_cast_bf16, qldnn_add,
+ *    qldnn_pack_input (network input: S, C, sqrt(S^2 + C^2) times `scale`,
+ *    zero-padded to 16 channels).
+ * All return QLD_OK or QLD_E_INVAL / QLD_E_CUDA. */
+int qldnn_conv3x3_fwd(const void* in, const void* w, const float* bias, int B, int H, int W, int Cin, int Cout,
+                      int relu, void* out_bf16, float* out_f32, void* stream);
+int qldnn_conv3x3_dgrad(const void* g, const void* w, int B, int H, int W, int Cin, int Cout, void* wt_scratch,
+                        void* din_bf16, float* din_f32, void* stream);
+int qldnn_conv3x3_wgrad(const void* in, const void* g, int B, int H, int W, int Cin, int Cout, float* dw,
+                        void* stream);
+int qldnn_bias_grad(const void* g, long long P, int C, float* db, void* stream);
+int qldnn_relu_bwd(const float* g, const void* act, long long n, void* out_bf16, void* stream);
+int qldnn_avgpool2(const void* in, int B, int H, int W, int C, void* out, void* stream);
+int qldnn_avgpool2_bwd(const float* g, int B, int H, int W, int C, float* out, int accumulate, void* stream);
+int qldnn_upsample2(const void* in, int B, int h, int w, int C, void* out, void* stream);
+int qldnn_upsample2_bwd(const float* g, int B, int h, int w, int C, float* out, void* stream);
+int qldnn_concat(const void* a, int Ca, const void* b, int Cb, long long P, void* out, void* stream);
+int qldnn_split(const float* g, long long P, int Ca, int Cb, float* ga, float* gb, int accumulate_b, void* stream);
+int qldnn_head(const void* in, const float* w, float b, long long P, int C, float* out, void* stream);
+int qldnn_head_bwd(const void* in, const float* g, const float* w, long long P, int C, float* din, float* dw,
+                   float* db, void* stream);
+int qldnn_mse(const float* pred, const float* target, long long n, float* grad, float* loss, void* stream);
+int qldnn_adam(float* p, const float* g, float* m, float* v, long long n, float lr, float b1, float b2, float eps,
+               int t, void* p_bf16, void* stream);
+int qldnn_cast_bf16(const float* x, long long n, void* y, void* stream);
+int qldnn_add(float* y, const float* x, long long n, void* stream);
+int qldnn_pack_input(const int32_t* S, const int32_t* C, long long npix, float scale, void* out, void* stream);
+
 /* Kernels this library has launched in this process (all contexts). */
 long long qld_launch_count(void);
 

@@ -23,7 +23,7 @@ __all__ = [
     "qld_lockin_table", "qld_lockin_frames", "Server", "QLD_SERVER_MAX_STREAMS", "qld_server_create",
     "qld_server_destroy", "qld_server_request", "qld_server_state", "qld_server_close", "qld_server_submit",
     "qld_server_tick", "qld_server_image", "qld_server_iq", "qld_server_frames_pushed", "qld_server_mem_in_use",
-    "qld_server_sync", "qld_server_autotune", "qld_server_shape", "LIB_PATH", "lib",
+    "qld_server_sync", "qld_server_autotune", "qld_server_shape", "nn", "LIB_PATH", "lib",
 ]
 
 QLD_U8, QLD_U16, QLD_P12 = 1, 2, 3
@@ -62,6 +62,25 @@ _SIGS = {
     "qld_fft_bin_host": ([_p, _i, _p], _i),
     "qld_fft_bin_frames_noalloc": ([_p, _i, _i, _i, _i, _i, _p, _p], _i),
     "qld_lockin_table": ([ctypes.c_double, _ll, _i, _p, _p], _i),
+    "qldnn_conv3x3_fwd": ([_p, _p, _p, _i, _i, _i, _i, _i, _i, _p, _p, _p], _i),
+    "qldnn_conv3x3_dgrad": ([_p, _p, _i, _i, _i, _i, _i, _p, _p, _p, _p], _i),
+    "qldnn_conv3x3_wgrad": ([_p, _p, _i, _i, _i, _i, _i, _p, _p], _i),
+    "qldnn_bias_grad": ([_p, _ll, _i, _p, _p], _i),
+    "qldnn_relu_bwd": ([_p, _p, _ll, _p, _p], _i),
+    "qldnn_avgpool2": ([_p, _i, _i, _i, _i, _p, _p], _i),
+    "qldnn_avgpool2_bwd": ([_p, _i, _i, _i, _i, _p, _i, _p], _i),
+    "qldnn_upsample2": ([_p, _i, _i, _i, _i, _p, _p], _i),
+    "qldnn_upsample2_bwd": ([_p, _i, _i, _i, _i, _p, _p], _i),
+    "qldnn_concat": ([_p, _i, _p, _i, _ll, _p, _p], _i),
+    "qldnn_split": ([_p, _ll, _i, _i, _p, _p, _i, _p], _i),
+    "qldnn_head": ([_p, _p, ctypes.c_float, _ll, _i, _p, _p], _i),
+    "qldnn_head_bwd": ([_p, _p, _p, _ll, _i, _p, _p, _p, _p], _i),
+    "qldnn_mse": ([_p, _p, _ll, _p, _p, _p], _i),
+    "qldnn_adam": ([_p, _p, _p, _p, _ll, ctypes.c_float, ctypes.c_float, ctypes.c_float, ctypes.c_float, _i, _p,
+                    _p], _i),
+    "qldnn_cast_bf16": ([_p, _ll, _p, _p], _i),
+    "qldnn_add": ([_p, _p, _ll, _p], _i),
+    "qldnn_pack_input": ([_p, _p, _ll, ctypes.c_float, _p, _p], _i),
     "qld_server_create": ([_ll, _i], _p),
     "qld_server_destroy": ([_p], None),
     "qld_server_request": ([_p, _i, _i, _i, _i], _i),
@@ -405,3 +424,21 @@ def qld_server_shape(srv):
     t, v, c = _i(), _i(), _i()
     _check(lib.qld_server_shape(_sh(srv), ctypes.byref(t), ctypes.byref(v), ctypes.byref(c)), "qld_server_shape")
     return t.value, v.value, c.value
+
+
+class _NN:
+    """The network kernels (qldnn_* in qld.h) with tensors or raw addresses as
+    pointers; every call enqueues on torch's current stream unless `stream`
+    is given, and raises QLDError on a non-OK status."""
+
+    def __getattr__(self, name):
+        f = getattr(lib, "qldnn_" + name)
+
+        def call(*args, stream=None):
+            conv = [_addr(a) if (a is None or hasattr(a, "data_ptr")) else a for a in args]
+            return _check(f(*conv, _stream(stream)), "qldnn_" + name)
+
+        return call
+
+
+nn = _NN()

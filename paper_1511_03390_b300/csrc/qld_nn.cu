@@ -1,0 +1,400 @@
+// qld_nn.cu -- C ABI of the learned short-window network's kernels
+// (declared in include/qld.h, section "Learned short-window QLD").
+//
+// Activations: NHWC, bf16, channels a multiple of 16. Gradients: f32 until
+// they become the operand of a tensor-core GEMM, then bf16. Weights: f32
+// master copies (Adam) and bf16 compute copies [9][Cin][Cout].
+
+#include <cstdint>
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+#include "qld.h"
+#include "qld_internal.h"
+#include "qld_nn.cuh"
+
+using qldi::set_err;
+
+namespace {
+
+unsigned nblk(long long n, int t) { return (unsigned)((n + t - 1) / t); }
+bool al(const void* p, unsigned a) { return ((uintptr_t)p % a) == 0; }
+int launched(int n) {
+    qldi::count_launches(n);
+    return cudaGetLastError() == cudaSuccess ? QLD_OK : set_err(QLD_E_CUDA);
+}
+
+// w [9][Cin][Cout] -> wt [9][Cout][Cin] with the tap order reversed, so that
+// conv(g; wt) is the data gradient of conv(x; w).
+__global__ void flip_transpose_kernel(const __nv_bfloat16* __restrict__ w, int Cin, int Cout,
+                                      __nv_bfloat16* __restrict__ wt) {
+    const long long n = 9ll * Cin * Cout;
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x) {
+        const int tap = (int)(e / ((long long)Cin * Cout));
+        const long long r = e - (long long)tap * Cin * Cout;
+        const int ci = (int)(r / Cout), co = (int)(r % Cout);
+        wt[((long long)(8 - tap) * Cout + co) * Cin + ci] = w[e];
+    }
+}
+
+__global__ void bias_grad_kernel(const __nv_bfloat16* __restrict__ g, long long P, int C, float* __restrict__ db) {
+    // thread block = 256 = `lanes` groups of C threads (plus idle ones); each
+    // thread sums one channel over a strided range of pixels
+    const int lanes = 256 / C;  // C <= 256
+    if ((int)threadIdx.x >= lanes * C) return;
+    const int c = threadIdx.x % C;
+    const int l = threadIdx.x / C;
+    float acc = 0.f;
+    for (long long p = (long long)blockIdx.x * lanes + l; p < P; p += (long long)gridDim.x * lanes)
+        acc += __bfloat162float(g[p * C + c]);
+    atomicAdd(&db[c], acc);
+}
+
+__global__ void relu_bwd_kernel(const float* __restrict__ g, const __nv_bfloat16* __restrict__ act, long long n,
+                                __nv_bfloat16* __restrict__ out) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        out[i] = __float2bfloat16_rn(__bfloat162float(act[i]) > 0.f ? g[i] : 0.f);
+}
+
+__global__ void avgpool2_fwd_kernel(const __nv_bfloat16* __restrict__ in, int B, int H, int W, int C,
+                                    __nv_bfloat16* __restrict__ out) {
+    const int h = H / 2, w = W / 2;
+    const long long n = (long long)B * h * w * C;
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x) {
+        const int c = (int)(e % C);
+        long long r = e / C;
+        const int x = (int)(r % w);
+        r /= w;
+        const int y = (int)(r % h);
+        const long long b = r / h;
+        const long long base = ((b * H + 2 * y) * W + 2 * x) * C + c;
+        const float s = __bfloat162float(in[base]) + __bfloat162float(in[base + C]) +
+                        __bfloat162float(in[base + (long long)W * C]) + __bfloat162float(in[base + (long long)W * C + C]);
+        out[e] = __float2bfloat16_rn(0.25f * s);
+    }
+}
+
+__global__ void avgpool2_bwd_kernel(const float* __restrict__ g, int B, int H, int W, int C, float* __restrict__ out,
+                                    int accumulate) {
+    const long long n = (long long)B * H * W * C;
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x) {
+        const int c = (int)(e % C);
+        long long r = e / C;
+        const int x = (int)(r % W);
+        r /= W;
+        const int y = (int)(r % H);
+        const long long b = r / H;
+        const float v = 0.25f * g[((b * (H / 2) + y / 2) * (W / 2) + x / 2) * C + c];
+        out[e] = accumulate ? out[e] + v : v;
+    }
+}
+
+__global__ void upsample2_fwd_kernel(const __nv_bfloat16* __restrict__ in, int B, int h, int w, int C,
+                                     __nv_bfloat16* __restrict__ out) {
+    const long long n = (long long)B * 2 * h * 2 * w * C;
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x) {
+        const int c = (int)(e % C);
+        long long r = e / C;
+        const int x = (int)(r % (2 * w));
+        r /= 2 * w;
+        const int y = (int)(r % (2 * h));
+        const long long b = r / (2 * h);
+        out[e] = in[((b * h + y / 2) * w + x / 2) * C + c];
+    }
+}
+
+__global__ void upsample2_bwd_kernel(const float* __restrict__ g, int B, int h, int w, int C, float* __restrict__ out) {
+    const long long n = (long long)B * h * w * C;
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x) {
+        const int c = (int)(e % C);
+        long long r = e / C;
+        const int x = (int)(r % w);
+        r /= w;
+        const int y = (int)(r % h);
+        const long long b = r / h;
+        const long long base = ((b * 2 * h + 2 * y) * (2 * w) + 2 * x) * C + c;
+        const long long row = (long long)2 * w * C;
+        out[e] = g[base] + g[base + C] + g[base + row] + g[base + row + C];
+    }
+}
+
+__global__ void concat_kernel(const __nv_bfloat16* __restrict__ a, int Ca, const __nv_bfloat16* __restrict__ b,
+                              int Cb, long long P, __nv_bfloat16* __restrict__ out) {
+    const int C = Ca + Cb;
+    const long long n = P * C;
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x) {
+        const long long p = e / C;
+        const int c = (int)(e - p * C);
+        out[e] = c < Ca ? a[p * Ca + c] : b[p * Cb + (c - Ca)];
+    }
+}
+
+__global__ void split_kernel(const float* __restrict__ g, long long P, int Ca, int Cb, float* __restrict__ ga,
+                             float* __restrict__ gb, int accumulate_b) {
+    const int C = Ca + Cb;
+    const long long n = P * C;
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x) {
+        const long long p = e / C;
+        const int c = (int)(e - p * C);
+        if (c < Ca) {
+            ga[p * Ca + c] = g[e];
+        } else {
+            float* d = gb + p * Cb + (c - Ca);
+            *d = accumulate_b ? *d + g[e] : g[e];
+        }
+    }
+}
+
+// 1x1 output head: out[p] = b + sum_c in[p][c] w[c] (f32 accumulate).
+__global__ void head_fwd_kernel(const __nv_bfloat16* __restrict__ in, const float* __restrict__ w, float b, long long P,
+                                int C, float* __restrict__ out) {
+    for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < P; p += (long long)gridDim.x * blockDim.x) {
+        float acc = b;
+        for (int c = 0; c < C; ++c) acc = fmaf(__bfloat162float(in[p * C + c]), w[c], acc);
+        out[p] = acc;
+    }
+}
+
+// head backward: din[p][c] = g[p] w[c]; dw[c] += sum_p in[p][c] g[p]; db += sum_p g[p]
+__global__ void head_bwd_kernel(const __nv_bfloat16* __restrict__ in, const float* __restrict__ g,
+                                const float* __restrict__ w, long long P, int C, float* __restrict__ din,
+                                float* __restrict__ dw, float* __restrict__ db) {
+    __shared__ float sdw[256];
+    __shared__ float sdb;
+    for (int c = threadIdx.x; c < C; c += blockDim.x) sdw[c] = 0.f;
+    if (threadIdx.x == 0) sdb = 0.f;
+    __syncthreads();
+    float pdb = 0.f;
+    for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < P; p += (long long)gridDim.x * blockDim.x) {
+        const float gp = g[p];
+        pdb += gp;
+        for (int c = 0; c < C; ++c) {
+            din[p * C + c] = gp * w[c];
+            atomicAdd(&sdw[c], __bfloat162float(in[p * C + c]) * gp);
+        }
+    }
+    atomicAdd(&sdb, pdb);
+    __syncthreads();
+    for (int c = threadIdx.x; c < C; c += blockDim.x) atomicAdd(&dw[c], sdw[c]);
+    if (threadIdx.x == 0) atomicAdd(db, sdb);
+}
+
+// mean squared error over n values: loss += sum (pred - t)^2 / n, grad = 2 (pred - t) / n
+__global__ void mse_kernel(const float* __restrict__ pred, const float* __restrict__ t, long long n,
+                           float* __restrict__ grad, float* __restrict__ loss) {
+    float acc = 0.f;
+    const float inv = 1.f / (float)n;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        const float d = pred[i] - t[i];
+        grad[i] = 2.f * d * inv;
+        acc += d * d * inv;
+    }
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xFFFFFFFFu, acc, o);
+    if ((threadIdx.x & 31) == 0) atomicAdd(loss, acc);
+}
+
+// Adam (Kingma & Ba 2015) on f32 master weights; refreshes the bf16 copy.
+__global__ void adam_kernel(float* __restrict__ p, const float* __restrict__ g, float* __restrict__ m,
+                            float* __restrict__ v, long long n, float lr, float b1, float b2, float eps, float c1,
+                            float c2, __nv_bfloat16* __restrict__ p_bf) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        const float gi = g[i];
+        const float mi = b1 * m[i] + (1.f - b1) * gi;
+        const float vi = b2 * v[i] + (1.f - b2) * gi * gi;
+        m[i] = mi;
+        v[i] = vi;
+        const float pi = p[i] - lr * (mi / c1) / (sqrtf(vi / c2) + eps);
+        p[i] = pi;
+        if (p_bf) p_bf[i] = __float2bfloat16_rn(pi);
+    }
+}
+
+__global__ void cast_bf16_kernel(const float* __restrict__ x, long long n, __nv_bfloat16* __restrict__ y) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        y[i] = __float2bfloat16_rn(x[i]);
+}
+
+__global__ void add_kernel(float* __restrict__ y, const float* __restrict__ x, long long n) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        y[i] += x[i];
+}
+
+// Network input from the short-window sums: channels (S, C, R) * scale, then
+// zeros up to 16 channels. R = sqrt(S^2 + C^2).
+__global__ void pack_input_kernel(const int32_t* __restrict__ S, const int32_t* __restrict__ C, long long n,
+                                  float scale, __nv_bfloat16* __restrict__ out) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        const float s = (float)S[i], c = (float)C[i];
+        __nv_bfloat16* o = out + i * 16;
+        o[0] = __float2bfloat16_rn(s * scale);
+        o[1] = __float2bfloat16_rn(c * scale);
+        o[2] = __float2bfloat16_rn(sqrtf(s * s + c * c) * scale);
+#pragma unroll
+        for (int k = 3; k < 16; ++k) o[k] = __float2bfloat16_rn(0.f);
+    }
+}
+
+unsigned grid_for(long long n) {
+    long long b = (n + 255) / 256;
+    if (b > 148ll * 32) b = 148ll * 32;
+    return (unsigned)(b < 1 ? 1 : b);
+}
+
+}  // namespace
+
+extern "C" {
+
+int qldnn_conv3x3_fwd(const void* in, const void* w, const float* bias, int B, int H, int W, int Cin, int Cout,
+                      int relu, void* out_bf16, float* out_f32, void* stream) {
+    if (!in || !w || (!out_bf16 && !out_f32) || B < 1 || H < 1 || W < 1 || Cin < 16 || Cin % 16 || Cout < 32 ||
+        Cout % 32 || !al(in, 16) || !al(w, 16) || !al(out_bf16, 4) || !al(out_f32, 8))
+        return set_err(QLD_E_INVAL);
+    const long long P = (long long)B * H * W;
+    const cudaStream_t st = (cudaStream_t)stream;
+    const __nv_bfloat16* x = (const __nv_bfloat16*)in;
+    const __nv_bfloat16* k = (const __nv_bfloat16*)w;
+    if (Cout % 64 == 0)
+        qldnn::conv3x3_fwd_kernel<64><<<dim3(nblk(P, 128), Cout / 64), 128, 0, st>>>(
+            x, k, bias, B, H, W, Cin, Cout, relu, (__nv_bfloat16*)out_bf16, out_f32);
+    else
+        qldnn::conv3x3_fwd_kernel<32><<<dim3(nblk(P, 128), Cout / 32), 128, 0, st>>>(
+            x, k, bias, B, H, W, Cin, Cout, relu, (__nv_bfloat16*)out_bf16, out_f32);
+    return launched(1);
+}
+
+int qldnn_conv3x3_wgrad(const void* in, const void* g, int B, int H, int W, int Cin, int Cout, float* dw,
+                        void* stream) {
+    if (!in || !g || !dw || B < 1 || H < 1 || W < 1 || Cin < 16 || Cin % 16 || Cout < 32 || Cout % 32 ||
+        !al(in, 16) || !al(g, 16))
+        return set_err(QLD_E_INVAL);
+    const long long P = (long long)B * H * W;
+    const cudaStream_t st = (cudaStream_t)stream;
+    const __nv_bfloat16* x = (const __nv_bfloat16*)in;
+    const __nv_bfloat16* y = (const __nv_bfloat16*)g;
+    const int MT = Cin % 32 == 0 ? 2 : 1;
+    const int BN = Cout % 64 == 0 ? 64 : 32;
+    const int tiles = (Cin / (16 * MT)) * (Cout / BN);
+    // pixel chunk per CTA: enough CTAs to fill the GPU twice over
+    long long chunk = (P * 9 * tiles) / (148ll * 8);
+    chunk = chunk < 256 ? 256 : (chunk > 16384 ? 16384 : chunk);
+    chunk = (chunk + 63) / 64 * 64;
+    const dim3 grid(nblk(P, (int)chunk), 9, tiles);
+    if (MT == 2 && BN == 64) qldnn::conv3x3_wgrad_kernel<2, 64><<<grid, 128, 0, st>>>(x, y, B, H, W, Cin, Cout, (int)chunk, dw);
+    else if (MT == 2) qldnn::conv3x3_wgrad_kernel<2, 32><<<grid, 128, 0, st>>>(x, y, B, H, W, Cin, Cout, (int)chunk, dw);
+    else if (BN == 64) qldnn::conv3x3_wgrad_kernel<1, 64><<<grid, 128, 0, st>>>(x, y, B, H, W, Cin, Cout, (int)chunk, dw);
+    else qldnn::conv3x3_wgrad_kernel<1, 32><<<grid, 128, 0, st>>>(x, y, B, H, W, Cin, Cout, (int)chunk, dw);
+    return launched(1);
+}
+
+int qldnn_conv3x3_dgrad(const void* g, const void* w, int B, int H, int W, int Cin, int Cout, void* wt_scratch,
+                        void* din_bf16, float* din_f32, void* stream) {
+    // the layer maps Cin -> Cout; its data gradient maps Cout -> Cin
+    if (!g || !w || !wt_scratch || Cout % 16 || Cin % 32 || Cin < 32) return set_err(QLD_E_INVAL);
+    const cudaStream_t st = (cudaStream_t)stream;
+    const long long n = 9ll * Cin * Cout;
+    flip_transpose_kernel<<<grid_for(n), 256, 0, st>>>((const __nv_bfloat16*)w, Cin, Cout,
+                                                        (__nv_bfloat16*)wt_scratch);
+    if (launched(1) != QLD_OK) return QLD_E_CUDA;
+    return qldnn_conv3x3_fwd(g, wt_scratch, nullptr, B, H, W, Cout, Cin, 0, din_bf16, din_f32, stream);
+}
+
+int qldnn_bias_grad(const void* g, long long P, int C, float* db, void* stream) {
+    if (!g || !db || C < 1 || C > 256) return set_err(QLD_E_INVAL);
+    bias_grad_kernel<<<grid_for(P / (256 / C) + 1), 256, 0, (cudaStream_t)stream>>>((const __nv_bfloat16*)g, P, C, db);
+    return launched(1);
+}
+
+int qldnn_relu_bwd(const float* g, const void* act, long long n, void* out_bf16, void* stream) {
+    if (!g || !act || !out_bf16 || n < 0) return set_err(QLD_E_INVAL);
+    relu_bwd_kernel<<<grid_for(n), 256, 0, (cudaStream_t)stream>>>(g, (const __nv_bfloat16*)act, n,
+                                                                     (__nv_bfloat16*)out_bf16);
+    return launched(1);
+}
+
+int qldnn_avgpool2(const void* in, int B, int H, int W, int C, void* out, void* stream) {
+    if (!in || !out || H % 2 || W % 2) return set_err(QLD_E_INVAL);
+    avgpool2_fwd_kernel<<<grid_for((long long)B * H * W * C / 4), 256, 0, (cudaStream_t)stream>>>(
+        (const __nv_bfloat16*)in, B, H, W, C, (__nv_bfloat16*)out);
+    return launched(1);
+}
+
+int qldnn_avgpool2_bwd(const float* g, int B, int H, int W, int C, float* out, int accumulate, void* stream) {
+    if (!g || !out || H % 2 || W % 2) return set_err(QLD_E_INVAL);
+    avgpool2_bwd_kernel<<<grid_for((long long)B * H * W * C), 256, 0, (cudaStream_t)stream>>>(g, B, H, W, C, out,
+                                                                                               accumulate);
+    return launched(1);
+}
+
+int qldnn_upsample2(const void* in, int B, int h, int w, int C, void* out, void* stream) {
+    if (!in || !out) return set_err(QLD_E_INVAL);
+    upsample2_fwd_kernel<<<grid_for(4ll * B * h * w * C), 256, 0, (cudaStream_t)stream>>>(
+        (const __nv_bfloat16*)in, B, h, w, C, (__nv_bfloat16*)out);
+    return launched(1);
+}
+
+int qldnn_upsample2_bwd(const float* g, int B, int h, int w, int C, float* out, void* stream) {
+    if (!g || !out) return set_err(QLD_E_INVAL);
+    upsample2_bwd_kernel<<<grid_for((long long)B * h * w * C), 256, 0, (cudaStream_t)stream>>>(g, B, h, w, C, out);
+    return launched(1);
+}
+
+int qldnn_concat(const void* a, int Ca, const void* b, int Cb, long long P, void* out, void* stream) {
+    if (!a || !b || !out) return set_err(QLD_E_INVAL);
+    concat_kernel<<<grid_for(P * (Ca + Cb)), 256, 0, (cudaStream_t)stream>>>(
+        (const __nv_bfloat16*)a, Ca, (const __nv_bfloat16*)b, Cb, P, (__nv_bfloat16*)out);
+    return launched(1);
+}
+
+int qldnn_split(const float* g, long long P, int Ca, int Cb, float* ga, float* gb, int accumulate_b, void* stream) {
+    if (!g || !ga || !gb) return set_err(QLD_E_INVAL);
+    split_kernel<<<grid_for(P * (Ca + Cb)), 256, 0, (cudaStream_t)stream>>>(g, P, Ca, Cb, ga, gb, accumulate_b);
+    return launched(1);
+}
+
+int qldnn_head(const void* in, const float* w, float b, long long P, int C, float* out, void* stream) {
+    if (!in || !w || !out || C > 256) return set_err(QLD_E_INVAL);
+    head_fwd_kernel<<<grid_for(P), 256, 0, (cudaStream_t)stream>>>((const __nv_bfloat16*)in, w, b, P, C, out);
+    return launched(1);
+}
+
+int qldnn_head_bwd(const void* in, const float* g, const float* w, long long P, int C, float* din, float* dw,
+                   float* db, void* stream) {
+    if (!in || !g || !w || !din || !dw || !db || C > 256) return set_err(QLD_E_INVAL);
+    head_bwd_kernel<<<grid_for(P), 256, 0, (cudaStream_t)stream>>>((const __nv_bfloat16*)in, g, w, P, C, din, dw, db);
+    return launched(1);
+}
+
+int qldnn_mse(const float* pred, const float* target, long long n, float* grad, float* loss, void* stream) {
+    if (!pred || !target || !grad || !loss || n < 1) return set_err(QLD_E_INVAL);
+    mse_kernel<<<grid_for(n), 256, 0, (cudaStream_t)stream>>>(pred, target, n, grad, loss);
+    return launched(1);
+}
+
+int qldnn_adam(float* p, const float* g, float* m, float* v, long long n, float lr, float b1, float b2, float eps,
+               int t, void* p_bf16, void* stream) {
+    if (!p || !g || !m || !v || n < 0 || t < 1) return set_err(QLD_E_INVAL);
+    const float c1 = 1.f - powf(b1, (float)t), c2 = 1.f - powf(b2, (float)t);
+    adam_kernel<<<grid_for(n), 256, 0, (cudaStream_t)stream>>>(p, g, m, v, n, lr, b1, b2, eps, c1, c2,
+                                                                (__nv_bfloat16*)p_bf16);
+    return launched(1);
+}
+
+int qldnn_cast_bf16(const float* x, long long n, void* y, void* stream) {
+    if (!x || !y || n < 0) return set_err(QLD_E_INVAL);
+    cast_bf16_kernel<<<grid_for(n), 256, 0, (cudaStream_t)stream>>>(x, n, (__nv_bfloat16*)y);
+    return launched(1);
+}
+
+int qldnn_add(float* y, const float* x, long long n, void* stream) {
+    if (!x || !y || n < 0) return set_err(QLD_E_INVAL);
+    add_kernel<<<grid_for(n), 256, 0, (cudaStream_t)stream>>>(y, x, n);
+    return launched(1);
+}
+
+int qldnn_pack_input(const int32_t* S, const int32_t* C, long long npix, float scale, void* out, void* stream) {
+    if (!S || !C || !out || npix < 0) return set_err(QLD_E_INVAL);
+    pack_input_kernel<<<grid_for(npix), 256, 0, (cudaStream_t)stream>>>(S, C, npix, scale, (__nv_bfloat16*)out);
+    return launched(1);
+}
+
+}  // extern "C"
