@@ -278,7 +278,8 @@ int qld_server_shape(const qld_server* srv, int* threads, int* vectors_per_threa
  *    square error, grad = its gradient), qldnn_adam (Adam on f32 master
  *    weights, refreshing an optional bf16 copy), qldnn_cast_bf16, qldnn_add,
  *    qldnn_pack_input (network input: S, C, sqrt(S^2 + C^2) times `scale`,
- *    zero-padded to 16 channels).
+ *    zero-padded to 16 channels; optionally the scaled amplitude in f32 as
+ *    `baseline`), qldnn_zero (clears a device buffer).
  * All return QLD_OK or QLD_E_INVAL / QLD_E_CUDA. */
 int qldnn_conv3x3_fwd(const void* in, const void* w, const float* bias, int B, int H, int W, int Cin, int Cout,
                       int relu, void* out_bf16, float* out_f32, void* stream);
@@ -294,7 +295,7 @@ int qldnn_upsample2(const void* in, int B, int h, int w, int C, void* out, void*
 int qldnn_upsample2_bwd(const float* g, int B, int h, int w, int C, float* out, void* stream);
 int qldnn_concat(const void* a, int Ca, const void* b, int Cb, long long P, void* out, void* stream);
 int qldnn_split(const float* g, long long P, int Ca, int Cb, float* ga, float* gb, int accumulate_b, void* stream);
-int qldnn_head(const void* in, const float* w, float b, long long P, int C, float* out, void* stream);
+int qldnn_head(const void* in, const float* w, const float* b, long long P, int C, float* out, void* stream);
 int qldnn_head_bwd(const void* in, const float* g, const float* w, long long P, int C, float* din, float* dw,
                    float* db, void* stream);
 int qldnn_mse(const float* pred, const float* target, long long n, float* grad, float* loss, void* stream);
@@ -302,7 +303,9 @@ int qldnn_adam(float* p, const float* g, float* m, float* v, long long n, float 
                int t, void* p_bf16, void* stream);
 int qldnn_cast_bf16(const float* x, long long n, void* y, void* stream);
 int qldnn_add(float* y, const float* x, long long n, void* stream);
-int qldnn_pack_input(const int32_t* S, const int32_t* C, long long npix, float scale, void* out, void* stream);
+int qldnn_pack_input(const int32_t* S, const int32_t* C, long long npix, float scale, void* out, float* baseline,
+                     void* stream);
+int qldnn_zero(void* p, long long bytes, void* stream);
 
 /* Kernels this library has launched in this process (all contexts). */
 long long qld_launch_count(void);

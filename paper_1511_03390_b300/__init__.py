@@ -73,14 +73,15 @@ _SIGS = {
     "qldnn_upsample2_bwd": ([_p, _i, _i, _i, _i, _p, _p], _i),
     "qldnn_concat": ([_p, _i, _p, _i, _ll, _p, _p], _i),
     "qldnn_split": ([_p, _ll, _i, _i, _p, _p, _i, _p], _i),
-    "qldnn_head": ([_p, _p, ctypes.c_float, _ll, _i, _p, _p], _i),
+    "qldnn_head": ([_p, _p, _p, _ll, _i, _p, _p], _i),
     "qldnn_head_bwd": ([_p, _p, _p, _ll, _i, _p, _p, _p, _p], _i),
     "qldnn_mse": ([_p, _p, _ll, _p, _p, _p], _i),
     "qldnn_adam": ([_p, _p, _p, _p, _ll, ctypes.c_float, ctypes.c_float, ctypes.c_float, ctypes.c_float, _i, _p,
                     _p], _i),
     "qldnn_cast_bf16": ([_p, _ll, _p, _p], _i),
     "qldnn_add": ([_p, _p, _ll, _p], _i),
-    "qldnn_pack_input": ([_p, _p, _ll, ctypes.c_float, _p, _p], _i),
+    "qldnn_pack_input": ([_p, _p, _ll, ctypes.c_float, _p, _p, _p], _i),
+    "qldnn_zero": ([_p, _ll, _p], _i),
     "qld_server_create": ([_ll, _i], _p),
     "qld_server_destroy": ([_p], None),
     "qld_server_request": ([_p, _i, _i, _i, _i], _i),

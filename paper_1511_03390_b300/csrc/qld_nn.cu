@@ -146,8 +146,9 @@ __global__ void split_kernel(const float* __restrict__ g, long long P, int Ca, i
 }
 
 // 1x1 output head: out[p] = b + sum_c in[p][c] w[c] (f32 accumulate).
-__global__ void head_fwd_kernel(const __nv_bfloat16* __restrict__ in, const float* __restrict__ w, float b, long long P,
-                                int C, float* __restrict__ out) {
+__global__ void head_fwd_kernel(const __nv_bfloat16* __restrict__ in, const float* __restrict__ w,
+                                const float* __restrict__ bp, long long P, int C, float* __restrict__ out) {
+    const float b = *bp;
     for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < P; p += (long long)gridDim.x * blockDim.x) {
         float acc = b;
         for (int c = 0; c < C; ++c) acc = fmaf(__bfloat162float(in[p * C + c]), w[c], acc);
@@ -222,13 +223,15 @@ __global__ void add_kernel(float* __restrict__ y, const float* __restrict__ x, l
 // Network input from the short-window sums: channels (S, C, R) * scale, then
 // zeros up to 16 channels. R = sqrt(S^2 + C^2).
 __global__ void pack_input_kernel(const int32_t* __restrict__ S, const int32_t* __restrict__ C, long long n,
-                                  float scale, __nv_bfloat16* __restrict__ out) {
+                                  float scale, __nv_bfloat16* __restrict__ out, float* __restrict__ baseline) {
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
         const float s = (float)S[i], c = (float)C[i];
+        const float r = sqrtf(s * s + c * c) * scale;
+        if (baseline) baseline[i] = r;
         __nv_bfloat16* o = out + i * 16;
         o[0] = __float2bfloat16_rn(s * scale);
         o[1] = __float2bfloat16_rn(c * scale);
-        o[2] = __float2bfloat16_rn(sqrtf(s * s + c * c) * scale);
+        o[2] = __float2bfloat16_rn(r);
 #pragma unroll
         for (int k = 3; k < 16; ++k) o[k] = __float2bfloat16_rn(0.f);
     }
@@ -351,8 +354,8 @@ int qldnn_split(const float* g, long long P, int Ca, int Cb, float* ga, float* g
     return launched(1);
 }
 
-int qldnn_head(const void* in, const float* w, float b, long long P, int C, float* out, void* stream) {
-    if (!in || !w || !out || C > 256) return set_err(QLD_E_INVAL);
+int qldnn_head(const void* in, const float* w, const float* b, long long P, int C, float* out, void* stream) {
+    if (!in || !w || !b || !out || C > 256) return set_err(QLD_E_INVAL);
     head_fwd_kernel<<<grid_for(P), 256, 0, (cudaStream_t)stream>>>((const __nv_bfloat16*)in, w, b, P, C, out);
     return launched(1);
 }
@@ -391,10 +394,17 @@ int qldnn_add(float* y, const float* x, long long n, void* stream) {
     return launched(1);
 }
 
-int qldnn_pack_input(const int32_t* S, const int32_t* C, long long npix, float scale, void* out, void* stream) {
+int qldnn_pack_input(const int32_t* S, const int32_t* C, long long npix, float scale, void* out, float* baseline,
+                     void* stream) {
     if (!S || !C || !out || npix < 0) return set_err(QLD_E_INVAL);
-    pack_input_kernel<<<grid_for(npix), 256, 0, (cudaStream_t)stream>>>(S, C, npix, scale, (__nv_bfloat16*)out);
+    pack_input_kernel<<<grid_for(npix), 256, 0, (cudaStream_t)stream>>>(S, C, npix, scale, (__nv_bfloat16*)out,
+                                                                         baseline);
     return launched(1);
+}
+
+int qldnn_zero(void* p, long long bytes, void* stream) {
+    if (!p || bytes < 0) return set_err(QLD_E_INVAL);
+    return cudaMemsetAsync(p, 0, (size_t)bytes, (cudaStream_t)stream) == cudaSuccess ? QLD_OK : set_err(QLD_E_CUDA);
 }
 
 }  // extern "C"

@@ -1,0 +1,439 @@
+"""Learned short-window QLD.
+
+The paper has no learned component; it motivates shorter time series because
+they cut acquisition time and so latency (the tree/cow experiment: sharper
+contrast needs longer series, at the cost of a later first image). This
+module maps the I/Q maps of a short window (N = 32 frames) to the amplitude
+that plain QLD reaches with a long window (N = 1024 frames), using a 4-level
+U-Net with 32 base channels (1.06 M parameters) whose convolutions, pooling,
+upsampling, head, loss and Adam steps all run in the library's kernels
+(qldnn_* in include/qld.h): BF16 tensor-core implicit-GEMM convolutions with
+FP32 accumulation, forward and backward. Plain QLD stays the fallback and the
+judge: the training targets are plain-QLD amplitudes of simulated stacks, and
+the network predicts a correction to the short-window estimate 32 R_32.
+
+Units: network input channels are (S_32, C_32, R_32) * IN_SCALE; targets are
+R_1024 * TARGET_SCALE, with TARGET_SCALE = IN_SCALE / 32 so the short-window
+baseline 32 R_32 is the input's third channel.
+"""
+import math
+
+import numpy as np
+import torch
+
+from . import QLD_U16, nn, qld_create, qld_get_iq, qld_image, qld_push_frames, qld_reset, qld_sync
+
+N_SHORT = 32
+N_LONG = 1024
+IN_SCALE = 1.0 / 200.0
+TARGET_SCALE = IN_SCALE / N_SHORT
+CIN = 16  # input channels: S, C, R, zero padding
+
+# (name, input channels, output channels); every convolution is 3x3 + ReLU
+LAYERS = [("c0a", 16, 32), ("c0b", 32, 32), ("c1a", 32, 64), ("c1b", 64, 64), ("c2a", 64, 128), ("c2b", 128, 128),
+          ("c3a", 128, 128), ("c3b", 128, 128), ("d2a", 256, 128), ("d2b", 128, 64), ("d1a", 128, 64),
+          ("d1b", 64, 32), ("d0a", 64, 32), ("d0b", 32, 32)]
+HEAD_C = 32
+
+
+class Params:
+    """Master f32 weights, bf16 compute copies, gradients and Adam moments."""
+
+    def __init__(self, device="cuda", seed=0):
+        g = torch.Generator(device="cpu").manual_seed(seed)
+        self.device = torch.device(device)
+        self.t = 0
+        self.tensors = {}
+        for name, cin, cout in LAYERS:
+            std = math.sqrt(2.0 / (9 * cin))
+            self._add(name + ".w", torch.randn(9 * cin * cout, generator=g) * std, bf16=True)
+            self._add(name + ".b", torch.zeros(cout))
+        self._add("head.w", torch.randn(HEAD_C, generator=g) * 0.01)
+        self._add("head.b", torch.zeros(1))
+
+    def _add(self, name, value, bf16=False):
+        d = self.device
+        p = value.to(torch.float32).to(d).contiguous()
+        ent = {"p": p, "g": torch.zeros_like(p), "m": torch.zeros_like(p), "v": torch.zeros_like(p), "bf": None}
+        if bf16:
+            ent["bf"] = torch.empty(p.numel(), dtype=torch.bfloat16, device=d)
+            nn.cast_bf16(p, p.numel(), ent["bf"])
+        self.tensors[name] = ent
+
+    def __getitem__(self, name):
+        return self.tensors[name]
+
+    def count(self):
+        return sum(e["p"].numel() for e in self.tensors.values())
+
+    def zero_grad(self):
+        for e in self.tensors.values():
+            nn.zero(e["g"], e["g"].numel() * 4)
+
+    def adam(self, lr, b1=0.9, b2=0.999, eps=1e-8):
+        self.t += 1
+        for e in self.tensors.values():
+            nn.adam(e["p"], e["g"], e["m"], e["v"], e["p"].numel(), lr, b1, b2, eps, self.t, e["bf"])
+
+    def state_dict(self):
+        return {k: e["p"].detach().cpu().numpy() for k, e in self.tensors.items()}
+
+    def load_state_dict(self, sd):
+        for k, e in self.tensors.items():
+            e["p"].copy_(torch.from_numpy(np.asarray(sd[k], np.float32)))
+            if e["bf"] is not None:
+                nn.cast_bf16(e["p"], e["p"].numel(), e["bf"])
+
+
+class UNet:
+    """Activations and gradient buffers for one input shape (B, H, W);
+    H and W must be multiples of 8."""
+
+    def __init__(self, params, B, H, W):
+        assert H % 8 == 0 and W % 8 == 0
+        self.prm = params
+        self.B, self.H, self.W = B, H, W
+        d = params.device
+        self.dims = [(H >> l, W >> l) for l in range(4)]
+        self.P = [B * h * w for h, w in self.dims]
+        bf, f32 = torch.bfloat16, torch.float32
+
+        def act(level, c):
+            return torch.empty(self.P[level] * c, dtype=bf, device=d)
+
+        def grad(level, c):
+            return torch.empty(self.P[level] * c, dtype=f32, device=d)
+
+        self.a = {"x": act(0, CIN), "a0": act(0, 32), "e0": act(0, 32), "p0": act(1, 32), "a1": act(1, 64),
+                  "e1": act(1, 64), "p1": act(2, 64), "a2": act(2, 128), "e2": act(2, 128), "p2": act(3, 128),
+                  "a3": act(3, 128), "u3": act(3, 128), "up3": act(2, 128), "cat2": act(2, 256),
+                  "ad2": act(2, 128), "u2": act(2, 64), "up2": act(1, 64), "cat1": act(1, 128), "ad1": act(1, 64),
+                  "u1": act(1, 32), "up1": act(0, 32), "cat0": act(0, 64), "ad0": act(0, 32), "u0": act(0, 32)}
+        self.baseline = torch.empty(self.P[0], dtype=f32, device=d)
+        self.pred = torch.empty(self.P[0], dtype=f32, device=d)
+        self.gpred = torch.empty(self.P[0], dtype=f32, device=d)
+        self.loss = torch.zeros(1, dtype=f32, device=d)
+        self.g = {"u0": grad(0, 32), "ad0": grad(0, 32), "cat0": grad(0, 64), "up1": grad(0, 32), "e0": grad(0, 32),
+                  "a0": grad(0, 32), "u1": grad(1, 32), "ad1": grad(1, 64), "cat1": grad(1, 128),
+                  "up2": grad(1, 64), "e1": grad(1, 64), "a1": grad(1, 64), "p0": grad(1, 32), "u2": grad(2, 64),
+                  "ad2": grad(2, 128), "cat2": grad(2, 256), "up3": grad(2, 128), "e2": grad(2, 128),
+                  "a2": grad(2, 128), "p1": grad(2, 64), "u3": grad(3, 128), "a3": grad(3, 128),
+                  "p2": grad(3, 128)}
+        self.gz = torch.empty(max(self.P[l] * c for l, c in [(0, 32), (1, 64), (2, 128), (3, 128)]), dtype=bf,
+                              device=d)
+        self.wt = torch.empty(max(9 * ci * co for _, ci, co in LAYERS), dtype=bf, device=d)
+
+    # -- forward ------------------------------------------------------------
+    def _conv(self, name, level, x, y):
+        _, cin, cout = next(l for l in LAYERS if l[0] == name)
+        h, w = self.dims[level]
+        nn.conv3x3_fwd(x, self.prm[name + ".w"]["bf"], self.prm[name + ".b"]["p"], self.B, h, w, cin, cout, 1, y,
+                       None)
+
+    def pack(self, S, C):
+        """Network input and baseline from short-window sums (int32 [B*H*W])."""
+        nn.pack_input(S, C, self.P[0], IN_SCALE, self.a["x"], self.baseline)
+
+    def forward(self):
+        a, B = self.a, self.B
+        h, w = self.dims[0]
+        self._conv("c0a", 0, a["x"], a["a0"])
+        self._conv("c0b", 0, a["a0"], a["e0"])
+        nn.avgpool2(a["e0"], B, h, w, 32, a["p0"])
+        h, w = self.dims[1]
+        self._conv("c1a", 1, a["p0"], a["a1"])
+        self._conv("c1b", 1, a["a1"], a["e1"])
+        nn.avgpool2(a["e1"], B, h, w, 64, a["p1"])
+        h, w = self.dims[2]
+        self._conv("c2a", 2, a["p1"], a["a2"])
+        self._conv("c2b", 2, a["a2"], a["e2"])
+        nn.avgpool2(a["e2"], B, h, w, 128, a["p2"])
+        h, w = self.dims[3]
+        self._conv("c3a", 3, a["p2"], a["a3"])
+        self._conv("c3b", 3, a["a3"], a["u3"])
+        nn.upsample2(a["u3"], B, h, w, 128, a["up3"])
+        nn.concat(a["up3"], 128, a["e2"], 128, self.P[2], a["cat2"])
+        self._conv("d2a", 2, a["cat2"], a["ad2"])
+        self._conv("d2b", 2, a["ad2"], a["u2"])
+        h, w = self.dims[2]
+        nn.upsample2(a["u2"], B, h, w, 64, a["up2"])
+        nn.concat(a["up2"], 64, a["e1"], 64, self.P[1], a["cat1"])
+        self._conv("d1a", 1, a["cat1"], a["ad1"])
+        self._conv("d1b", 1, a["ad1"], a["u1"])
+        h, w = self.dims[1]
+        nn.upsample2(a["u1"], B, h, w, 32, a["up1"])
+        nn.concat(a["up1"], 32, a["e0"], 32, self.P[0], a["cat0"])
+        self._conv("d0a", 0, a["cat0"], a["ad0"])
+        self._conv("d0b", 0, a["ad0"], a["u0"])
+        nn.head(a["u0"], self.prm["head.w"]["p"], self.prm["head.b"]["p"], self.P[0], HEAD_C, self.pred)
+        nn.add(self.pred, self.baseline, self.P[0])
+        return self.pred
+
+    # -- backward -----------------------------------------------------------
+    def _conv_bwd(self, name, level, x, y, gy, gx):
+        """ReLU mask, weight and bias gradients, and (if gx) the data gradient."""
+        _, cin, cout = next(l for l in LAYERS if l[0] == name)
+        h, w = self.dims[level]
+        n = self.P[level] * cout
+        gz = self.gz[:n]
+        nn.relu_bwd(gy, y, n, gz)
+        nn.conv3x3_wgrad(x, gz, self.B, h, w, cin, cout, self.prm[name + ".w"]["g"])
+        nn.bias_grad(gz, self.P[level], cout, self.prm[name + ".b"]["g"])
+        if gx is not None:
+            nn.conv3x3_dgrad(gz, self.prm[name + ".w"]["bf"], self.B, h, w, cin, cout, self.wt, None, gx)
+
+    def loss_and_grad(self, target):
+        nn.zero(self.loss, 4)
+        nn.mse(self.pred, target, self.P[0], self.gpred, self.loss)
+
+    def backward(self):
+        a, g, B = self.a, self.g, self.B
+        nn.head_bwd(a["u0"], self.gpred, self.prm["head.w"]["p"], self.P[0], HEAD_C, g["u0"], self.prm["head.w"]["g"],
+                    self.prm["head.b"]["g"])
+        self._conv_bwd("d0b", 0, a["ad0"], a["u0"], g["u0"], g["ad0"])
+        self._conv_bwd("d0a", 0, a["cat0"], a["ad0"], g["ad0"], g["cat0"])
+        nn.split(g["cat0"], self.P[0], 32, 32, g["up1"], g["e0"], 0)
+        h, w = self.dims[1]
+        nn.upsample2_bwd(g["up1"], B, h, w, 32, g["u1"])
+        self._conv_bwd("d1b", 1, a["ad1"], a["u1"], g["u1"], g["ad1"])
+        self._conv_bwd("d1a", 1, a["cat1"], a["ad1"], g["ad1"], g["cat1"])
+        nn.split(g["cat1"], self.P[1], 64, 64, g["up2"], g["e1"], 0)
+        h, w = self.dims[2]
+        nn.upsample2_bwd(g["up2"], B, h, w, 64, g["u2"])
+        self._conv_bwd("d2b", 2, a["ad2"], a["u2"], g["u2"], g["ad2"])
+        self._conv_bwd("d2a", 2, a["cat2"], a["ad2"], g["ad2"], g["cat2"])
+        nn.split(g["cat2"], self.P[2], 128, 128, g["up3"], g["e2"], 0)
+        h, w = self.dims[3]
+        nn.upsample2_bwd(g["up3"], B, h, w, 128, g["u3"])
+        self._conv_bwd("c3b", 3, a["a3"], a["u3"], g["u3"], g["a3"])
+        self._conv_bwd("c3a", 3, a["p2"], a["a3"], g["a3"], g["p2"])
+        h, w = self.dims[2]
+        nn.avgpool2_bwd(g["p2"], B, h, w, 128, g["e2"], 1)
+        self._conv_bwd("c2b", 2, a["a2"], a["e2"], g["e2"], g["a2"])
+        self._conv_bwd("c2a", 2, a["p1"], a["a2"], g["a2"], g["p1"])
+        h, w = self.dims[1]
+        nn.avgpool2_bwd(g["p1"], B, h, w, 64, g["e1"], 1)
+        self._conv_bwd("c1b", 1, a["a1"], a["e1"], g["e1"], g["a1"])
+        self._conv_bwd("c1a", 1, a["p0"], a["a1"], g["a1"], g["p0"])
+        h, w = self.dims[0]
+        nn.avgpool2_bwd(g["p0"], B, h, w, 32, g["e0"], 1)
+        self._conv_bwd("c0b", 0, a["a0"], a["e0"], g["e0"], g["a0"])
+        self._conv_bwd("c0a", 0, a["x"], a["a0"], g["a0"], None)
+
+
+# ---- training data: seeded scattering scenes processed by plain QLD -------
+
+def random_scene_tables(rng, H, W, device, bg=2000.0, maxv=4095):
+    """Per-pixel Q16 generator tables of a random multi-source fog scene:
+    3-8 sources (squares or disks, 8-64 px), ballistic amplitude
+    2000 exp(-OD) with OD uniform in [4, 8], diffuse glow bg (0.5 + 0.5
+    blur/max) (Gaussian sigma 20 px), shot noise sd = sqrt(mean)."""
+    yy = torch.arange(H, device=device, dtype=torch.float32)[:, None]
+    xx = torch.arange(W, device=device, dtype=torch.float32)[None, :]
+    mask = torch.zeros((H, W), device=device)
+    for _ in range(int(rng.integers(3, 9))):
+        size = float(rng.integers(8, 65))
+        cy, cx = float(rng.uniform(0, H)), float(rng.uniform(0, W))
+        if rng.random() < 0.5:
+            m = ((yy - cy).abs() <= size / 2) & ((xx - cx).abs() <= size / 2)
+        else:
+            m = ((yy - cy) ** 2 + (xx - cx) ** 2) <= (size / 2) ** 2
+        mask = torch.maximum(mask, m.float())
+    sig = 20.0
+    r = int(4 * sig)
+    t = torch.arange(-r, r + 1, device=device, dtype=torch.float32)
+    k = torch.exp(-0.5 * (t / sig) ** 2)
+    k = k / k.sum()
+    blur = torch.nn.functional.conv2d(mask[None, None], k[None, None, None, :], padding=(0, r))
+    blur = torch.nn.functional.conv2d(blur, k[None, None, :, None], padding=(r, 0))[0, 0]
+    diffuse = bg * (0.5 + 0.5 * blur / blur.max().clamp_min(1e-12))
+    od = float(rng.uniform(4.0, 8.0))
+    amp = bg * math.exp(-od)
+    mu0 = diffuse
+    mu1 = diffuse + amp * mask
+    q = 65536.0
+    tables = [torch.round(v.flatten() * q).to(torch.int32).contiguous() for v in (mu0, mu1, mu0.sqrt(), mu1.sqrt())]
+    return tables, int(rng.integers(0, 4)), od
+
+
+class StackMaker:
+    """Makes training stacks on the device: a scene's N_LONG frames from the
+    seeded generator, pushed through plain QLD twice (windows N_SHORT and
+    N_LONG); returns the short-window sums and the long-window amplitude."""
+
+    def __init__(self, H, W, device="cuda", chunk=128):
+        self.H, self.W = H, W
+        self.npix = H * W
+        self.device = torch.device(device)
+        self.chunk = chunk
+        self.frames = torch.empty((chunk, self.npix), dtype=torch.uint16, device=self.device)
+        self.ctx_s = qld_create(H, W, N_SHORT, QLD_U16)
+        self.ctx_l = qld_create(H, W, N_LONG, QLD_U16)
+
+    def make(self, rng, seed):
+        import qldscene
+
+        tables, off, od = random_scene_tables(rng, self.H, self.W, self.device)
+        key = (seed & 0xFFFFFFFF, 0x1EA2)
+        qld_reset(self.ctx_s)
+        qld_reset(self.ctx_l)
+        for s0 in range(1, N_LONG + 1, self.chunk):
+            qldscene.generate_from_tables(self.frames, 2, self.npix, s0, self.chunk, *tables, off, key, 4095)
+            qld_push_frames(self.ctx_s, self.frames, self.chunk)
+            qld_push_frames(self.ctx_l, self.frames, self.chunk)
+        S = torch.empty(self.npix, dtype=torch.int32, device=self.device)
+        C = torch.empty_like(S)
+        R = torch.empty(self.npix, dtype=torch.float32, device=self.device)
+        qld_get_iq(self.ctx_s, S, C)
+        qld_image(self.ctx_l, R, None)
+        qld_sync(self.ctx_l)
+        return S, C, R, od
+
+    def close(self):
+        self.ctx_s.destroy()
+        self.ctx_l.destroy()
+
+
+def make_dataset(n, H=512, W=512, seed=0, device="cuda"):
+    """n stacks: short-window sums (int32 [n, H*W]) and scaled long-window
+    targets (f32 [n, H*W])."""
+    rng = np.random.default_rng(seed)
+    mk = StackMaker(H, W, device)
+    S = torch.empty((n, H * W), dtype=torch.int32, device=device)
+    C = torch.empty_like(S)
+    T = torch.empty((n, H * W), dtype=torch.float32, device=device)
+    ods = []
+    for i in range(n):
+        s, c, r, od = mk.make(rng, seed * 1000003 + i)
+        S[i].copy_(s)
+        C[i].copy_(c)
+        T[i].copy_(r * TARGET_SCALE)
+        ods.append(od)
+    mk.close()
+    return S, C, T, np.array(ods)
+
+
+def crop_batch(S, C, T, idx, ys, xs, crop, H, W):
+    """Gathers square crops (input marshalling) into contiguous buffers."""
+    B = len(idx)
+    Sb = torch.empty((B, crop, crop), dtype=torch.int32, device=S.device)
+    Cb = torch.empty_like(Sb)
+    Tb = torch.empty((B, crop, crop), dtype=torch.float32, device=S.device)
+    for j, (i, y, x) in enumerate(zip(idx, ys, xs)):
+        Sb[j] = S[i].view(H, W)[y:y + crop, x:x + crop]
+        Cb[j] = C[i].view(H, W)[y:y + crop, x:x + crop]
+        Tb[j] = T[i].view(H, W)[y:y + crop, x:x + crop]
+    return Sb.reshape(-1), Cb.reshape(-1), Tb.reshape(-1)
+
+
+def metrics(pred, target):
+    """(relative L2 error, PSNR in dB with the target's peak) of numpy arrays."""
+    pred = np.asarray(pred, np.float64)
+    target = np.asarray(target, np.float64)
+    mse = np.mean((pred - target) ** 2)
+    rel = math.sqrt(np.sum((pred - target) ** 2) / max(np.sum(target ** 2), 1e-300))
+    psnr = 10 * math.log10(max(target.max() ** 2, 1e-300) / max(mse, 1e-300))
+    return rel, psnr
+
+
+def evaluate(params, S, C, T, H, W, batch=2):
+    """Network and baseline (32 R_32) metrics over full frames."""
+    n = S.shape[0]
+    net = UNet(params, batch, H, W)
+    preds, bases = [], []
+    for i0 in range(0, n - n % batch, batch):
+        net.pack(S[i0:i0 + batch].reshape(-1), C[i0:i0 + batch].reshape(-1))
+        net.forward()
+        torch.cuda.synchronize()
+        preds.append(net.pred.cpu().numpy().copy())
+        bases.append(net.baseline.cpu().numpy().copy())
+    t = T[:len(preds) * batch].reshape(-1).cpu().numpy()
+    p = np.concatenate(preds)
+    b = np.concatenate(bases)
+    return {"network": metrics(p, t), "baseline": metrics(b, t)}
+
+
+def train(params, S, C, T, H, W, steps, batch=8, crop=256, lr=1e-3, seed=1, log_every=100, log=None):
+    """Adam on random crops of the dataset; cosine learning-rate decay."""
+    rng = np.random.default_rng(seed)
+    net = UNet(params, batch, crop, crop)
+    n = S.shape[0]
+    hist = []
+    for step in range(steps):
+        idx = rng.integers(0, n, batch)
+        ys = rng.integers(0, H - crop + 1, batch)
+        xs = rng.integers(0, W - crop + 1, batch)
+        Sb, Cb, Tb = crop_batch(S, C, T, idx, ys, xs, crop, H, W)
+        net.pack(Sb, Cb)
+        net.forward()
+        net.loss_and_grad(Tb)
+        params.zero_grad()
+        net.backward()
+        params.adam(lr * 0.5 * (1 + math.cos(math.pi * step / max(1, steps))))
+        if (step + 1) % log_every == 0 or step == 0:
+            loss = float(net.loss.item())
+            hist.append((step + 1, loss))
+            if log:
+                log("step %d loss %.6g" % (step + 1, loss))
+    return hist
+
+
+def save(params, path):
+    np.savez_compressed(path, **{k.replace(".", "__"): v.astype(np.float32) for k, v in params.state_dict().items()})
+
+
+def load(path, device="cuda"):
+    p = Params(device)
+    data = np.load(path)
+    p.load_state_dict({k.replace("__", "."): data[k] for k in data.files})
+    return p
+
+
+def main(argv=None):
+    """Trains the network on simulated stacks and reports metrics on
+    held-out stacks as JSON lines:
+
+        python -m paper_1511_03390_b300.learned --stacks 20000 --steps 20000 --out weights.npz
+    """
+    import argparse
+    import json
+    import time
+
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--stacks", type=int, default=256, help="training stacks (512x512, N_LONG frames each)")
+    ap.add_argument("--eval-stacks", type=int, default=16)
+    ap.add_argument("--size", type=int, default=512)
+    ap.add_argument("--steps", type=int, default=2000)
+    ap.add_argument("--batch", type=int, default=8)
+    ap.add_argument("--crop", type=int, default=256)
+    ap.add_argument("--lr", type=float, default=1e-3)
+    ap.add_argument("--seed", type=int, default=0)
+    ap.add_argument("--init", default=None, help="weights to start from")
+    ap.add_argument("--out", default=None)
+    a = ap.parse_args(argv)
+    t0 = time.time()
+    S, C, T, ods = make_dataset(a.stacks, a.size, a.size, seed=a.seed)
+    Se, Ce, Te, odse = make_dataset(a.eval_stacks, a.size, a.size, seed=a.seed + 99991)
+    torch.cuda.synchronize()
+    t1 = time.time()
+    print(json.dumps({"event": "data", "stacks": a.stacks, "eval_stacks": a.eval_stacks, "seconds": t1 - t0}),
+          flush=True)
+    prm = load(a.init) if a.init else Params(seed=a.seed)
+    hist = train(prm, S, C, T, a.size, a.size, a.steps, batch=a.batch, crop=a.crop, lr=a.lr, seed=a.seed + 1,
+                 log_every=max(1, a.steps // 20), log=lambda m: print(json.dumps({"event": "train", "msg": m}),
+                                                                           flush=True))
+    torch.cuda.synchronize()
+    t2 = time.time()
+    ev = evaluate(prm, Se, Ce, Te, a.size, a.size)
+    print(json.dumps({"event": "done", "params": prm.count(), "train_seconds": t2 - t1,
+                      "ms_per_step": (t2 - t1) / max(1, a.steps) * 1e3, "loss_first": hist[0][1],
+                      "loss_last": hist[-1][1], "eval_network_rel_l2": ev["network"][0],
+                      "eval_network_psnr": ev["network"][1], "eval_baseline_rel_l2": ev["baseline"][0],
+                      "eval_baseline_psnr": ev["baseline"][1], "od_range": [float(ods.min()), float(ods.max())]}),
+          flush=True)
+    if a.out:
+        save(prm, a.out)
+
+
+if __name__ == "__main__":
+    main()

@@ -44,6 +44,22 @@ def _load():
     return _lib
 
 
+def generate_from_tables(out, pixfmt, npix, s_first, count, mu0, mu1, sd0, sd1, phase_offset, key, maxv, stream=None):
+    """Frames s_first .. s_first+count-1 from per-pixel Q16 tables already on
+    the device (int32 tensors of npix values) into the contiguous device
+    tensor `out` (count * npix elements of the pixel format)."""
+    import torch
+
+    st = stream if stream is not None else torch.cuda.current_stream()
+    rc = _load().qs_generate(ctypes.c_void_p(out.data_ptr()), int(pixfmt), int(npix), int(npix), int(s_first),
+                             int(count), ctypes.c_void_p(mu0.data_ptr()), ctypes.c_void_p(mu1.data_ptr()),
+                             ctypes.c_void_p(sd0.data_ptr()), ctypes.c_void_p(sd1.data_ptr()), int(phase_offset),
+                             int(key[0]), int(key[1]), int(maxv), ctypes.c_void_p(st.cuda_stream))
+    if rc != 0:
+        raise RuntimeError("qs_generate failed with code %d" % rc)
+    return out
+
+
 class DeviceScene:
     """A Scene's tables resident on a CUDA device, generating frames there."""
 

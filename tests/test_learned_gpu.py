@@ -1,0 +1,68 @@
+"""The learned short-window path on the GPU: the whole U-Net's loss and
+parameter gradients (BF16 tensor-core kernels) against the FP64 CPU reference
+built from the oracle, and a short training run that lowers the loss and
+beats the short-window baseline 32 R_32 on held-out stacks."""
+import numpy as np
+import pytest
+import torch
+
+import paper_1511_03390_b300 as q
+from paper_1511_03390_b300 import learned
+from unet_reference import RefUNet
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(autouse=True)
+def _need_gpu():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+
+
+def test_unet_gradients_match_the_fp64_reference():
+    rng = np.random.default_rng(3)
+    B, H, W = 2, 16, 24
+    prm = learned.Params(seed=5)
+    for k in prm.tensors:  # non-zero biases and head so every path carries gradient
+        if k.endswith(".b"):
+            prm[k]["p"].copy_(torch.from_numpy(rng.standard_normal(prm[k]["p"].numel()).astype(np.float32) * 0.1))
+    prm["head.w"]["p"].copy_(torch.from_numpy(rng.standard_normal(32).astype(np.float32) * 0.3))
+    net = learned.UNet(prm, B, H, W)
+    S = torch.from_numpy(rng.integers(-3000, 3000, B * H * W).astype(np.int32)).cuda()
+    C = torch.from_numpy(rng.integers(-3000, 3000, B * H * W).astype(np.int32)).cuda()
+    T = torch.from_numpy(rng.uniform(0, 20, B * H * W).astype(np.float32)).cuda()
+    net.pack(S, C)
+    net.forward()
+    net.loss_and_grad(T)
+    prm.zero_grad()
+    net.backward()
+    torch.cuda.synchronize()
+    x = net.a["x"].float().cpu().numpy().astype(np.float64).reshape(B, H, W, 16)
+    base = net.baseline.cpu().numpy().astype(np.float64).reshape(B, H, W)
+    # the packed input: (S, C, R) * scale in bf16, R and the baseline from float32
+    s, c = S.cpu().numpy().astype(np.float32), C.cpu().numpy().astype(np.float32)
+    r32 = np.sqrt(s * s + c * c).astype(np.float32) * np.float32(learned.IN_SCALE)
+    assert np.allclose(base.ravel(), r32, rtol=1e-6, atol=0)
+    assert np.all(x[..., 3:] == 0)
+    ref = RefUNet({k: e["p"].cpu().numpy().astype(np.float64) for k, e in prm.tensors.items()}, round_bf16=True)
+    pred = ref.forward(x, base)
+    loss, gpred = ref.loss(pred, T.cpu().numpy().astype(np.float64).reshape(B, H, W))
+    grads = ref.backward(gpred)
+    assert abs(net.loss.item() - loss) <= 2e-3 * loss
+    for k, e in prm.tensors.items():
+        got = e["g"].cpu().numpy().astype(np.float64)
+        want = grads[k]
+        rel = np.linalg.norm(got - want) / max(np.linalg.norm(want), 1e-30)
+        cos = float(got @ want) / max(np.linalg.norm(got) * np.linalg.norm(want), 1e-30)
+        assert rel < 2e-2 and cos > 0.999, (k, rel, cos)
+
+
+def test_short_training_run_beats_the_short_window_baseline():
+    H = W = 128
+    S, C, T, _ = learned.make_dataset(40, H, W, seed=7)
+    prm = learned.Params(seed=1)
+    hist = learned.train(prm, S[:32], C[:32], T[:32], H, W, steps=300, batch=4, crop=64, lr=2e-3, log_every=50)
+    assert hist[-1][1] < 0.5 * hist[0][1]
+    ev = learned.evaluate(prm, S[32:], C[32:], T[32:], H, W, batch=2)
+    assert ev["network"][0] < ev["baseline"][0], ev
+    assert ev["network"][1] > ev["baseline"][1], ev

@@ -118,7 +118,7 @@ def test_small_layers_against_numpy():
     # head + mse
     w = torch.from_numpy(rng.standard_normal(C).astype(np.float32)).cuda()
     out = torch.empty(B * H * W, dtype=torch.float32, device="cuda")
-    q.nn.head(x, w, 0.5, B * H * W, C, out)
+    q.nn.head(x, w, torch.tensor([0.5], device="cuda"), B * H * W, C, out)
     ref_out = xr.reshape(-1, C) @ w.cpu().numpy().astype(np.float64) + 0.5
     close(out.cpu().numpy(), ref_out, 1e-5 * (np.abs(xr.reshape(-1, C)) @ np.abs(w.cpu().numpy())) + 1e-6, "head")
     t = torch.from_numpy(rng.standard_normal(B * H * W).astype(np.float32)).cuda()
