@@ -57,6 +57,7 @@ def parse_args():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-large", action="store_true", help="skip the 4096x4096 N=2048 (68.7 GB ring) stream")
     ap.add_argument("--no-serving", action="store_true", help="skip the 8-stream serving mix (45 GB of rings)")
+    ap.add_argument("--no-learned", action="store_true", help="skip the learned short-window path")
     ap.add_argument("--case", choices=["full", "small"], default="full",
                     help="small: N=256 and a 512-frame pool (1.5 GB on the device) for profiler captures")
     args = ap.parse_args()
@@ -399,6 +400,9 @@ def run_cuda(args, world, rank, local):
     serving = None
     if not args.no_serving and args.case == "full":
         serving = run_serving(q, torch, dev, st, peak)
+    learned_res = None
+    if not args.no_learned and args.case == "full":
+        learned_res = run_learned(q, torch, dev, st)
     traffic = profiled_traffic("bin_power")
     out = {
         "metric": METRIC,
@@ -435,6 +439,7 @@ def run_cuda(args, world, rank, local):
         "lockin_general": lockin,
         "packed12": packed,
         "serving": serving,
+        "learned": learned_res,
         "gpu_launches": launches,
         "clocks": clk,
         "e2e": e2e,
@@ -617,6 +622,74 @@ def run_serving(q, torch, dev, st, peak, ticks=300, paced_ticks=300, fps=200.0):
             "latency_us_at_%dfps" % int(fps): {"p50": lat[len(lat) // 2], "p99": lat[min(len(lat) - 1, int(0.99 * len(lat)))],
                                                "samples": len(lat),
                                                "what": "host clock from frames-in-HBM to all 8 images complete"}}
+
+
+def run_learned(q, torch, dev, st, samples=200, fps=200.0):
+    """The learned short-window path beside plain QLD on 512x512 uint16 fog
+    stacks: accuracy of the trained network (committed weights) and of the
+    short-window baseline 32 R_32 against the long-window plain-QLD amplitude
+    on held-out stacks, and the latency to an image -- compute only (frames
+    already in HBM) and including the acquisition of the window's frames at
+    `fps`."""
+    import numpy as np
+
+    from paper_1511_03390_b300 import learned as L
+
+    if not os.path.exists(L.WEIGHTS):
+        return {"unavailable": "no trained weights at %s" % L.WEIGHTS}
+    prm = L.load(L.WEIGHTS, dev)
+    Hs = Ws = 512
+    S, C, T, ods = L.make_dataset(16, Hs, Ws, seed=424242)
+    ev = L.evaluate(prm, S, C, T, Hs, Ws, batch=2)
+    # latency: plain QLD needs N_LONG frames, the learned path N_SHORT
+    from qldscene import DeviceScene, scene_fog
+
+    sc = scene_fog(6, seed=1004, H=Hs, W=Ws)
+    frames = torch.empty((L.N_LONG, Hs, Ws), dtype=torch.uint16, device=dev)
+    DeviceScene(sc, dev).generate_into(frames, 1, L.N_LONG)
+    ctx_l = q.qld_create(Hs, Ws, L.N_LONG, q.QLD_U16)
+    ctx_s = q.qld_create(Hs, Ws, L.N_SHORT, q.QLD_U16)
+    amp = torch.empty(Hs * Ws, dtype=torch.float32, device=dev)
+    Sd = torch.empty(Hs * Ws, dtype=torch.int32, device=dev)
+    Cd = torch.empty_like(Sd)
+    net = L.UNet(prm, 1, Hs, Ws, inference_only=True)
+
+    def plain():
+        q.qld_push_image(ctx_l, frames, L.N_LONG, st, amp, None)
+
+    def learned_path():
+        q.qld_push_frames(ctx_s, frames[-L.N_SHORT:], L.N_SHORT, st)
+        q.qld_get_iq(ctx_s, Sd, Cd)
+        net.pack(Sd, Cd)
+        net.forward()
+
+    out = {}
+    for name, fn, nfr in [("plain_qld_n1024", plain, L.N_LONG), ("learned_n32", learned_path, L.N_SHORT)]:
+        for _ in range(5):
+            fn()
+        torch.cuda.synchronize(dev)
+        lat = []
+        ev_done = torch.cuda.Event()
+        for _ in range(samples):
+            t0 = time.perf_counter()
+            fn()
+            ev_done.record(st)
+            ev_done.synchronize()
+            lat.append((time.perf_counter() - t0) * 1e3)
+        lat.sort()
+        p50, p99 = lat[len(lat) // 2], lat[min(len(lat) - 1, int(0.99 * len(lat)))]
+        out[name] = {"frames": nfr, "compute_ms_p50": p50, "compute_ms_p99": p99,
+                     "with_acquisition_ms_p99_at_%dfps" % int(fps): nfr / fps * 1e3 + p99}
+    ctx_l.destroy()
+    ctx_s.destroy()
+    del frames, S, C, T
+    torch.cuda.empty_cache()
+    return {"workload": "512x512 uint16 fog stacks (OD 4-8, random multi-source scenes); input I/Q from the last 32 "
+                        "frames, target plain-QLD amplitude over 1024 frames; 16 held-out stacks",
+            "params": prm.count(),
+            "network": {"rel_l2": ev["network"][0], "psnr_db": ev["network"][1]},
+            "baseline_32R32": {"rel_l2": ev["baseline"][0], "psnr_db": ev["baseline"][1]},
+            "latency": out}
 
 
 def run_e2e(args, q, torch, dev, st, pool):

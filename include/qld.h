@@ -306,6 +306,17 @@ int qldnn_add(float* y, const float* x, long long n, void* stream);
 int qldnn_pack_input(const int32_t* S, const int32_t* C, long long npix, float scale, void* out, float* baseline,
                      void* stream);
 int qldnn_zero(void* p, long long bytes, void* stream);
+/* The same forward convolution on the 5th-generation tensor cores
+ * (tcgen05.mma, accumulator in tensor memory, operands staged by cp.async in
+ * the canonical K-major layout). wk holds the weights K-major, as written by
+ * qldnn_kmajor_weights(w, Cin, Cout, 0, wk): wk[tap][co][ci]. With
+ * qldnn_kmajor_weights(w, Cin, Cout, 1, wk) (wk[tap][ci][co] = w[8-tap][ci][co])
+ * the call qldnn_conv3x3_fwd_tc(g, wk, NULL, B, H, W, Cout, Cin, 0, ...) is the
+ * data gradient. out_bf16 / out_f32 must be 16-byte aligned. status (device
+ * int, may be NULL) becomes 1 if a bounded wait inside the kernel ran out. */
+int qldnn_kmajor_weights(const void* w, int Cin, int Cout, int flip, void* wk, void* stream);
+int qldnn_conv3x3_fwd_tc(const void* in, const void* wk, const float* bias, int B, int H, int W, int Cin, int Cout,
+                         int relu, void* out_bf16, float* out_f32, int* status, void* stream);
 
 /* Kernels this library has launched in this process (all contexts). */
 long long qld_launch_count(void);

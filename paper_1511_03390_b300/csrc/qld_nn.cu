@@ -12,6 +12,7 @@
 #include "qld.h"
 #include "qld_internal.h"
 #include "qld_nn.cuh"
+#include "qld_nn_tc.cuh"
 
 using qldi::set_err;
 
@@ -399,6 +400,38 @@ int qldnn_pack_input(const int32_t* S, const int32_t* C, long long npix, float s
     if (!S || !C || !out || npix < 0) return set_err(QLD_E_INVAL);
     pack_input_kernel<<<grid_for(npix), 256, 0, (cudaStream_t)stream>>>(S, C, npix, scale, (__nv_bfloat16*)out,
                                                                          baseline);
+    return launched(1);
+}
+
+int qldnn_kmajor_weights(const void* w, int Cin, int Cout, int flip, void* wk, void* stream) {
+    if (!w || !wk || Cin < 1 || Cout < 1) return set_err(QLD_E_INVAL);
+    qldnn::kmajor_weights_kernel<<<grid_for(9ll * Cin * Cout), 256, 0, (cudaStream_t)stream>>>(
+        (const __nv_bfloat16*)w, Cin, Cout, flip, (__nv_bfloat16*)wk);
+    return launched(1);
+}
+
+int qldnn_conv3x3_fwd_tc(const void* in, const void* wk, const float* bias, int B, int H, int W, int Cin, int Cout,
+                         int relu, void* out_bf16, float* out_f32, int* status, void* stream) {
+    if (!in || !wk || (!out_bf16 && !out_f32) || B < 1 || H < 1 || W < 1 || Cin < 16 || Cin % 16 || Cout < 32 ||
+        Cout % 32 || !al(in, 16) || !al(wk, 16) || !al(out_bf16, 16) || !al(out_f32, 16))
+        return set_err(QLD_E_INVAL);
+    const long long P = (long long)B * H * W;
+    const cudaStream_t st = (cudaStream_t)stream;
+    const __nv_bfloat16* x = (const __nv_bfloat16*)in;
+    const __nv_bfloat16* k = (const __nv_bfloat16*)wk;
+    __nv_bfloat16* ob = (__nv_bfloat16*)out_bf16;
+    const unsigned gx = nblk(P, 128);
+    const bool bk32 = Cin % 32 == 0;
+    if (Cout % 128 == 0) {
+        if (bk32) qldnn::conv3x3_fwd_tc_kernel<128, 32><<<dim3(gx, Cout / 128), 128, 0, st>>>(x, k, bias, B, H, W, Cin, Cout, relu, ob, out_f32, status);
+        else qldnn::conv3x3_fwd_tc_kernel<128, 16><<<dim3(gx, Cout / 128), 128, 0, st>>>(x, k, bias, B, H, W, Cin, Cout, relu, ob, out_f32, status);
+    } else if (Cout % 64 == 0) {
+        if (bk32) qldnn::conv3x3_fwd_tc_kernel<64, 32><<<dim3(gx, Cout / 64), 128, 0, st>>>(x, k, bias, B, H, W, Cin, Cout, relu, ob, out_f32, status);
+        else qldnn::conv3x3_fwd_tc_kernel<64, 16><<<dim3(gx, Cout / 64), 128, 0, st>>>(x, k, bias, B, H, W, Cin, Cout, relu, ob, out_f32, status);
+    } else {
+        if (bk32) qldnn::conv3x3_fwd_tc_kernel<32, 32><<<dim3(gx, Cout / 32), 128, 0, st>>>(x, k, bias, B, H, W, Cin, Cout, relu, ob, out_f32, status);
+        else qldnn::conv3x3_fwd_tc_kernel<32, 16><<<dim3(gx, Cout / 32), 128, 0, st>>>(x, k, bias, B, H, W, Cin, Cout, relu, ob, out_f32, status);
+    }
     return launched(1);
 }
 

@@ -89,7 +89,7 @@ class UNet:
     """Activations and gradient buffers for one input shape (B, H, W);
     H and W must be multiples of 8."""
 
-    def __init__(self, params, B, H, W):
+    def __init__(self, params, B, H, W, inference_only=False):
         assert H % 8 == 0 and W % 8 == 0
         self.prm = params
         self.B, self.H, self.W = B, H, W
@@ -111,6 +111,8 @@ class UNet:
                   "u1": act(1, 32), "up1": act(0, 32), "cat0": act(0, 64), "ad0": act(0, 32), "u0": act(0, 32)}
         self.baseline = torch.empty(self.P[0], dtype=f32, device=d)
         self.pred = torch.empty(self.P[0], dtype=f32, device=d)
+        if inference_only:
+            return
         self.gpred = torch.empty(self.P[0], dtype=f32, device=d)
         self.loss = torch.zeros(1, dtype=f32, device=d)
         self.g = {"u0": grad(0, 32), "ad0": grad(0, 32), "cat0": grad(0, 64), "up1": grad(0, 32), "e0": grad(0, 32),
@@ -339,7 +341,7 @@ def metrics(pred, target):
 def evaluate(params, S, C, T, H, W, batch=2):
     """Network and baseline (32 R_32) metrics over full frames."""
     n = S.shape[0]
-    net = UNet(params, batch, H, W)
+    net = UNet(params, batch, H, W, inference_only=True)
     preds, bases = [], []
     for i0 in range(0, n - n % batch, batch):
         net.pack(S[i0:i0 + batch].reshape(-1), C[i0:i0 + batch].reshape(-1))
@@ -376,6 +378,9 @@ def train(params, S, C, T, H, W, steps, batch=8, crop=256, lr=1e-3, seed=1, log_
             if log:
                 log("step %d loss %.6g" % (step + 1, loss))
     return hist
+
+
+WEIGHTS = __import__("os").path.join(__import__("os").path.dirname(__file__), "weights", "unet_n32.npz")
 
 
 def save(params, path):

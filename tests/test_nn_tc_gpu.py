@@ -1,0 +1,66 @@
+"""The tensor-memory (tcgen05) convolution against the FP64 oracle and the
+warp-MMA kernel: forward with bias/ReLU and, with flipped weights, the data
+gradient. Same tolerance as the other convolution tests (FP32 accumulation
+relative to sum |x| |w|, plus bf16 output rounding)."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import paper_1511_03390_b300 as q
+from test_nn_gpu import ACC, bf16, close
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(autouse=True)
+def _need_gpu():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+
+
+@pytest.mark.parametrize("B,H,W,Cin,Cout,relu", [(1, 8, 16, 16, 32, 0), (2, 17, 13, 16, 64, 1), (1, 32, 40, 32, 64, 0),
+                                                 (1, 9, 130, 48, 96, 1), (3, 8, 8, 64, 128, 0),
+                                                 (1, 24, 24, 256, 128, 1)])
+def test_tc_conv_forward(B, H, W, Cin, Cout, relu):
+    rng = np.random.default_rng(B * H + Cin + 1)
+    x, xr = bf16(rng.standard_normal((B, H, W, Cin)))
+    w, wr = bf16(rng.standard_normal((3, 3, Cin, Cout)) / np.sqrt(9 * Cin))
+    bias = torch.from_numpy(rng.standard_normal(Cout).astype(np.float32)).cuda()
+    wk = torch.empty(9 * Cin * Cout, dtype=torch.bfloat16, device="cuda")
+    q.nn.kmajor_weights(w, Cin, Cout, 0, wk)
+    status = torch.zeros(1, dtype=torch.int32, device="cuda")
+    out_f = torch.empty((B, H, W, Cout), dtype=torch.float32, device="cuda")
+    out_b = torch.empty((B, H, W, Cout), dtype=torch.bfloat16, device="cuda")
+    q.nn.conv3x3_fwd_tc(x, wk, bias, B, H, W, Cin, Cout, relu, out_b, out_f, status)
+    torch.cuda.synchronize()
+    assert status.item() == 0
+    ref = oracle.conv3x3(xr, wr, bias.cpu().numpy().astype(np.float64))
+    if relu:
+        ref = np.maximum(ref, 0)
+    bound = ACC * oracle.conv3x3(np.abs(xr), np.abs(wr)) + 1e-6
+    close(out_f.cpu().numpy(), ref, bound, "tcgen05 forward f32")
+    close(out_b.float().cpu().numpy(), ref, bound + 2.0 ** -8 * np.abs(ref), "tcgen05 forward bf16")
+    # the warp-MMA kernel agrees within the same bound
+    out_m = torch.empty((B, H, W, Cout), dtype=torch.float32, device="cuda")
+    q.nn.conv3x3_fwd(x, w, bias, B, H, W, Cin, Cout, relu, None, out_m)
+    torch.cuda.synchronize()
+    close(out_f.cpu().numpy(), out_m.cpu().numpy().astype(np.float64), 2 * bound, "tcgen05 vs warp MMA")
+
+
+@pytest.mark.parametrize("B,H,W,Cin,Cout", [(2, 11, 14, 32, 32), (1, 24, 20, 64, 32), (1, 16, 16, 128, 256)])
+def test_tc_conv_data_gradient(B, H, W, Cin, Cout):
+    rng = np.random.default_rng(H * W + 3)
+    g, gr = bf16(rng.standard_normal((B, H, W, Cout)))
+    w, wr = bf16(rng.standard_normal((3, 3, Cin, Cout)) / np.sqrt(9 * Cin))
+    wk = torch.empty(9 * Cin * Cout, dtype=torch.bfloat16, device="cuda")
+    q.nn.kmajor_weights(w, Cin, Cout, 1, wk)
+    din = torch.empty((B, H, W, Cin), dtype=torch.float32, device="cuda")
+    status = torch.zeros(1, dtype=torch.int32, device="cuda")
+    q.nn.conv3x3_fwd_tc(g, wk, None, B, H, W, Cout, Cin, 0, None, din, status)
+    torch.cuda.synchronize()
+    assert status.item() == 0
+    xdummy = np.zeros((B, H, W, Cin))
+    ref = oracle.conv3x3_backward(xdummy, wr, gr)[0]
+    bound = ACC * oracle.conv3x3_backward(xdummy, np.abs(wr), np.abs(gr))[0] + 1e-6
+    close(din.cpu().numpy(), ref, bound, "tcgen05 data gradient")
