@@ -57,8 +57,19 @@ class Params:
         ent = {"p": p, "g": torch.zeros_like(p), "m": torch.zeros_like(p), "v": torch.zeros_like(p), "bf": None}
         if bf16:
             ent["bf"] = torch.empty(p.numel(), dtype=torch.bfloat16, device=d)
+            ent["wk"] = torch.empty(p.numel(), dtype=torch.bfloat16, device=d)  # [tap][co][ci]
+            ent["wf"] = torch.empty(p.numel(), dtype=torch.bfloat16, device=d)  # [8 - tap][ci][co]
             nn.cast_bf16(p, p.numel(), ent["bf"])
         self.tensors[name] = ent
+        if bf16:
+            self._refresh(name)
+
+    def _refresh(self, name):
+        """K-major and tap-flipped bf16 copies for the tensor-memory kernels."""
+        cin, cout = next((ci, co) for n, ci, co in LAYERS if n + ".w" == name)
+        e = self.tensors[name]
+        nn.kmajor_weights(e["bf"], cin, cout, 0, e["wk"])
+        nn.kmajor_weights(e["bf"], cin, cout, 1, e["wf"])
 
     def __getitem__(self, name):
         return self.tensors[name]
@@ -72,8 +83,10 @@ class Params:
 
     def adam(self, lr, b1=0.9, b2=0.999, eps=1e-8):
         self.t += 1
-        for e in self.tensors.values():
+        for name, e in self.tensors.items():
             nn.adam(e["p"], e["g"], e["m"], e["v"], e["p"].numel(), lr, b1, b2, eps, self.t, e["bf"])
+            if e["bf"] is not None:
+                self._refresh(name)
 
     def state_dict(self):
         return {k: e["p"].detach().cpu().numpy() for k, e in self.tensors.items()}
@@ -83,15 +96,20 @@ class Params:
             e["p"].copy_(torch.from_numpy(np.asarray(sd[k], np.float32)))
             if e["bf"] is not None:
                 nn.cast_bf16(e["p"], e["p"].numel(), e["bf"])
+                self._refresh(k)
 
 
 class UNet:
     """Activations and gradient buffers for one input shape (B, H, W);
-    H and W must be multiples of 8."""
+    H and W must be multiples of 8. use_tc selects the tensor-memory
+    (tcgen05) kernels for the forward and data-gradient convolutions, else
+    the warp-level MMA kernels; the weight gradient uses the latter."""
 
-    def __init__(self, params, B, H, W, inference_only=False):
+    def __init__(self, params, B, H, W, inference_only=False, use_tc=False):
         assert H % 8 == 0 and W % 8 == 0
         self.prm = params
+        self.use_tc = use_tc
+        self.status = torch.zeros(1, dtype=torch.int32, device=params.device)
         self.B, self.H, self.W = B, H, W
         d = params.device
         self.dims = [(H >> l, W >> l) for l in range(4)]
@@ -129,8 +147,12 @@ class UNet:
     def _conv(self, name, level, x, y):
         _, cin, cout = next(l for l in LAYERS if l[0] == name)
         h, w = self.dims[level]
-        nn.conv3x3_fwd(x, self.prm[name + ".w"]["bf"], self.prm[name + ".b"]["p"], self.B, h, w, cin, cout, 1, y,
-                       None)
+        if self.use_tc:
+            nn.conv3x3_fwd_tc(x, self.prm[name + ".w"]["wk"], self.prm[name + ".b"]["p"], self.B, h, w, cin, cout, 1,
+                              y, None, self.status)
+        else:
+            nn.conv3x3_fwd(x, self.prm[name + ".w"]["bf"], self.prm[name + ".b"]["p"], self.B, h, w, cin, cout, 1, y,
+                           None)
 
     def pack(self, S, C):
         """Network input and baseline from short-window sums (int32 [B*H*W])."""
@@ -182,7 +204,11 @@ class UNet:
         nn.conv3x3_wgrad(x, gz, self.B, h, w, cin, cout, self.prm[name + ".w"]["g"])
         nn.bias_grad(gz, self.P[level], cout, self.prm[name + ".b"]["g"])
         if gx is not None:
-            nn.conv3x3_dgrad(gz, self.prm[name + ".w"]["bf"], self.B, h, w, cin, cout, self.wt, None, gx)
+            if self.use_tc:
+                nn.conv3x3_fwd_tc(gz, self.prm[name + ".w"]["wf"], None, self.B, h, w, cout, cin, 0, None, gx,
+                                  self.status)
+            else:
+                nn.conv3x3_dgrad(gz, self.prm[name + ".w"]["bf"], self.B, h, w, cin, cout, self.wt, None, gx)
 
     def loss_and_grad(self, target):
         nn.zero(self.loss, 4)

@@ -19,7 +19,8 @@ def _need_gpu():
         pytest.skip("no CUDA device")
 
 
-def test_unet_gradients_match_the_fp64_reference():
+@pytest.mark.parametrize("use_tc", [True, False], ids=["tcgen05", "warp_mma"])
+def test_unet_gradients_match_the_fp64_reference(use_tc):
     rng = np.random.default_rng(3)
     B, H, W = 2, 16, 24
     prm = learned.Params(seed=5)
@@ -27,7 +28,7 @@ def test_unet_gradients_match_the_fp64_reference():
         if k.endswith(".b"):
             prm[k]["p"].copy_(torch.from_numpy(rng.standard_normal(prm[k]["p"].numel()).astype(np.float32) * 0.1))
     prm["head.w"]["p"].copy_(torch.from_numpy(rng.standard_normal(32).astype(np.float32) * 0.3))
-    net = learned.UNet(prm, B, H, W)
+    net = learned.UNet(prm, B, H, W, use_tc=use_tc)
     S = torch.from_numpy(rng.integers(-3000, 3000, B * H * W).astype(np.int32)).cuda()
     C = torch.from_numpy(rng.integers(-3000, 3000, B * H * W).astype(np.int32)).cuda()
     T = torch.from_numpy(rng.uniform(0, 20, B * H * W).astype(np.float32)).cuda()
@@ -37,6 +38,7 @@ def test_unet_gradients_match_the_fp64_reference():
     prm.zero_grad()
     net.backward()
     torch.cuda.synchronize()
+    assert net.status.item() == 0
     x = net.a["x"].float().cpu().numpy().astype(np.float64).reshape(B, H, W, 16)
     base = net.baseline.cpu().numpy().astype(np.float64).reshape(B, H, W)
     # the packed input: (S, C, R) * scale in bf16, R and the baseline from float32
