@@ -315,6 +315,19 @@ int qldnn_zero(void* p, long long bytes, void* stream);
  * data gradient. out_bf16 / out_f32 must be 16-byte aligned. status (device
  * int, may be NULL) becomes 1 if a bounded wait inside the kernel ran out. */
 int qldnn_kmajor_weights(const void* w, int Cin, int Cout, int flip, void* wk, void* stream);
+/* Warp-specialised version of qldnn_conv3x3_fwd_tc (same arguments and
+ * results; Cout must be 32, 64, 128 or 256, one tile of all output channels):
+ * producer warps keep a 4-stage shared-memory ring of gathered K steps ahead
+ * of a single MMA-issuing warp, synchronised by mbarriers. */
+int qldnn_conv3x3_fwd_tc2(const void* in, const void* wk, const float* bias, int B, int H, int W, int Cin, int Cout,
+                          int relu, void* out_bf16, float* out_f32, int* status, void* stream);
+/* Persistent TMA-fed version (same arguments and results; Cout 32, 64, 128
+ * or 256; Cin a multiple of 16): output tiles of 8 x 16 pixels, the input
+ * halo staged once per channel chunk by the tensor-memory accelerator (zero
+ * fill at the image border), two TMEM accumulators so one tile's read-out
+ * overlaps the next tile's MMAs. Launches one CTA per SM. */
+int qldnn_conv3x3_fwd_tma(const void* in, const void* wk, const float* bias, int B, int H, int W, int Cin, int Cout,
+                          int relu, void* out_bf16, float* out_f32, int* status, void* stream);
 int qldnn_conv3x3_fwd_tc(const void* in, const void* wk, const float* bias, int B, int H, int W, int Cin, int Cout,
                          int relu, void* out_bf16, float* out_f32, int* status, void* stream);
 

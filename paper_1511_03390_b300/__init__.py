@@ -84,6 +84,8 @@ _SIGS = {
     "qldnn_zero": ([_p, _ll, _p], _i),
     "qldnn_kmajor_weights": ([_p, _i, _i, _i, _p, _p], _i),
     "qldnn_conv3x3_fwd_tc": ([_p, _p, _p, _i, _i, _i, _i, _i, _i, _p, _p, _p, _p], _i),
+    "qldnn_conv3x3_fwd_tc2": ([_p, _p, _p, _i, _i, _i, _i, _i, _i, _p, _p, _p, _p], _i),
+    "qldnn_conv3x3_fwd_tma": ([_p, _p, _p, _i, _i, _i, _i, _i, _i, _p, _p, _p, _p], _i),
     "qld_server_create": ([_ll, _i], _p),
     "qld_server_destroy": ([_p], None),
     "qld_server_request": ([_p, _i, _i, _i, _i], _i),

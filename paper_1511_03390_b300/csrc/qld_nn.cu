@@ -5,7 +5,9 @@
 // they become the operand of a tensor-core GEMM, then bf16. Weights: f32
 // master copies (Adam) and bf16 compute copies [9][Cin][Cout].
 
+#include <atomic>
 #include <cstdint>
+#include <mutex>
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
@@ -13,6 +15,7 @@
 #include "qld_internal.h"
 #include "qld_nn.cuh"
 #include "qld_nn_tc.cuh"
+#include "qld_nn_tma.cuh"
 
 using qldi::set_err;
 
@@ -246,6 +249,99 @@ unsigned grid_for(long long n) {
 
 }  // namespace
 
+namespace {
+template <int N, int BK>
+int launch_tc2(const __nv_bfloat16* x, const __nv_bfloat16* k, const float* bias, int B, int H, int W, int Cin,
+               int Cout, int relu, __nv_bfloat16* ob, float* of, int* status, cudaStream_t st) {
+    constexpr int STAGES = 4;
+    const int smem = qldnn::TcPipe<N, BK, STAGES>::kSmem;
+    static bool attr_set = false;  // per instantiation
+    if (!attr_set) {
+        if (cudaFuncSetAttribute(qldnn::conv3x3_fwd_tc2_kernel<N, BK, STAGES>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 smem) != cudaSuccess)
+            return set_err(QLD_E_CUDA);
+        attr_set = true;
+    }
+    const long long P = (long long)B * H * W;
+    qldnn::conv3x3_fwd_tc2_kernel<N, BK, STAGES><<<nblk(P, 128), 160, smem, st>>>(x, k, bias, B, H, W, Cin, Cout, relu, ob,
+                                                                                 of, status);
+    return launched(1);
+}
+}  // namespace
+
+namespace {
+// cuTensorMapEncodeTiled, fetched once from the driver through the runtime
+// (no link-time dependency on the driver library).
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                  const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+EncodeTiledFn encode_tiled() {
+    static EncodeTiledFn fn = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void* f = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<EncodeTiledFn>(f);
+    });
+    return fn;
+}
+
+int sm_count(int dev) {
+    static std::atomic<int> cache[64];
+    if (dev < 0 || dev >= 64) return 0;
+    int n = cache[dev].load();
+    if (n == 0) {
+        if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 0;
+        cache[dev].store(n);
+    }
+    return n;
+}
+
+template <int N, int SWB>
+int launch_tma(const void* in, const void* wk, const float* bias, int B, int H, int W, int Cin, int Cout, int relu,
+               __nv_bfloat16* ob, float* of, int* status, cudaStream_t st) {
+    using L = qldnn::TmaConv<N, SWB>;
+    EncodeTiledFn enc = encode_tiled();
+    int dev = 0;
+    if (!enc || cudaGetDevice(&dev) != cudaSuccess) return set_err(QLD_E_CUDA);
+    const int nsm = sm_count(dev);
+    if (nsm <= 0) return set_err(QLD_E_CUDA);
+    const CUtensorMapSwizzle sw =
+        SWB == 128 ? CU_TENSOR_MAP_SWIZZLE_128B : (SWB == 64 ? CU_TENSOR_MAP_SWIZZLE_64B : CU_TENSOR_MAP_SWIZZLE_32B);
+    CUtensorMap mi, mw;
+    const cuuint64_t gdim[4] = {(cuuint64_t)Cin, (cuuint64_t)W, (cuuint64_t)H, (cuuint64_t)B};
+    const cuuint64_t gstr[3] = {(cuuint64_t)Cin * 2, (cuuint64_t)W * Cin * 2, (cuuint64_t)H * W * Cin * 2};
+    const cuuint32_t box[4] = {(cuuint32_t)L::BK, 16, 10, 1};
+    const cuuint32_t one[4] = {1, 1, 1, 1};
+    if (enc(&mi, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, const_cast<void*>(in), gdim, gstr, box, one,
+            CU_TENSOR_MAP_INTERLEAVE_NONE, sw, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+        return set_err(QLD_E_CUDA);
+    const cuuint64_t wdim[2] = {(cuuint64_t)Cin, (cuuint64_t)9 * Cout};
+    const cuuint64_t wstr[1] = {(cuuint64_t)Cin * 2};
+    const cuuint32_t wbox[2] = {(cuuint32_t)L::BK, (cuuint32_t)N};
+    if (enc(&mw, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(wk), wdim, wstr, wbox, one,
+            CU_TENSOR_MAP_INTERLEAVE_NONE, sw, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+        return set_err(QLD_E_CUDA);
+    static std::atomic<unsigned long long> attr_done{0};  // per instantiation, one bit per device
+    if (dev < 64 && !(attr_done.load() >> dev & 1ull)) {
+        if (cudaFuncSetAttribute(qldnn::conv3x3_fwd_tma_kernel<N, SWB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 L::kSmem) != cudaSuccess)
+            return set_err(QLD_E_CUDA);
+        attr_done.fetch_or(1ull << dev);
+    }
+    const long long ntiles = (long long)B * ((H + 7) / 8) * ((W + 15) / 16);
+    const unsigned grid = (unsigned)(ntiles < nsm ? ntiles : nsm);
+    qldnn::conv3x3_fwd_tma_kernel<N, SWB><<<grid, 192, L::kSmem, st>>>(mi, mw, bias, B, H, W, Cin, Cout, relu, ob, of,
+                                                                        status);
+    return launched(1);
+}
+}  // namespace
+
 extern "C" {
 
 int qldnn_conv3x3_fwd(const void* in, const void* w, const float* bias, int B, int H, int W, int Cin, int Cout,
@@ -433,6 +529,47 @@ int qldnn_conv3x3_fwd_tc(const void* in, const void* wk, const float* bias, int 
         else qldnn::conv3x3_fwd_tc_kernel<32, 16><<<dim3(gx, Cout / 32), 128, 0, st>>>(x, k, bias, B, H, W, Cin, Cout, relu, ob, out_f32, status);
     }
     return launched(1);
+}
+
+
+int qldnn_conv3x3_fwd_tc2(const void* in, const void* wk, const float* bias, int B, int H, int W, int Cin, int Cout,
+                          int relu, void* out_bf16, float* out_f32, int* status, void* stream) {
+    if (!in || !wk || (!out_bf16 && !out_f32) || B < 1 || H < 1 || W < 1 || Cin < 16 || Cin % 16 ||
+        (Cout != 32 && Cout != 64 && Cout != 128 && Cout != 256) || !al(in, 16) || !al(wk, 16) ||
+        !al(out_bf16, 16) || !al(out_f32, 16))
+        return set_err(QLD_E_INVAL);
+    const __nv_bfloat16* x = (const __nv_bfloat16*)in;
+    const __nv_bfloat16* k = (const __nv_bfloat16*)wk;
+    __nv_bfloat16* ob = (__nv_bfloat16*)out_bf16;
+    const cudaStream_t st = (cudaStream_t)stream;
+    const int bk = Cin % 64 == 0 ? 64 : (Cin % 32 == 0 ? 32 : 16);
+#define QLD_TC2(NN, KK) \
+    if (Cout == NN && bk == KK) return launch_tc2<NN, KK>(x, k, bias, B, H, W, Cin, Cout, relu, ob, out_f32, status, st);
+    QLD_TC2(32, 16) QLD_TC2(32, 32) QLD_TC2(32, 64)
+    QLD_TC2(64, 16) QLD_TC2(64, 32) QLD_TC2(64, 64)
+    QLD_TC2(128, 16) QLD_TC2(128, 32) QLD_TC2(128, 64)
+    QLD_TC2(256, 16) QLD_TC2(256, 32) QLD_TC2(256, 64)
+#undef QLD_TC2
+    return set_err(QLD_E_INVAL);
+}
+
+int qldnn_conv3x3_fwd_tma(const void* in, const void* wk, const float* bias, int B, int H, int W, int Cin, int Cout,
+                          int relu, void* out_bf16, float* out_f32, int* status, void* stream) {
+    if (!in || !wk || (!out_bf16 && !out_f32) || B < 1 || H < 1 || W < 1 || Cin < 16 || Cin % 16 ||
+        (Cout != 32 && Cout != 64 && Cout != 128 && Cout != 256) || !al(in, 16) || !al(wk, 16) ||
+        !al(out_bf16, 16) || !al(out_f32, 16) || (long long)B * H * W * Cin >= (1ll << 40))
+        return set_err(QLD_E_INVAL);
+    __nv_bfloat16* ob = (__nv_bfloat16*)out_bf16;
+    const cudaStream_t st = (cudaStream_t)stream;
+    const int swb = Cin % 64 == 0 ? 128 : (Cin % 32 == 0 ? 64 : 32);
+#define QLD_TMA(NN, SS) \
+    if (Cout == NN && swb == SS) return launch_tma<NN, SS>(in, wk, bias, B, H, W, Cin, Cout, relu, ob, out_f32, status, st);
+    QLD_TMA(32, 32) QLD_TMA(32, 64) QLD_TMA(32, 128)
+    QLD_TMA(64, 32) QLD_TMA(64, 64) QLD_TMA(64, 128)
+    QLD_TMA(128, 32) QLD_TMA(128, 64) QLD_TMA(128, 128)
+    QLD_TMA(256, 32) QLD_TMA(256, 64) QLD_TMA(256, 128)
+#undef QLD_TMA
+    return set_err(QLD_E_INVAL);
 }
 
 int qldnn_zero(void* p, long long bytes, void* stream) {

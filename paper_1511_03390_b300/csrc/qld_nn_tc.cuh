@@ -184,7 +184,8 @@ __global__ void __launch_bounds__(128) conv3x3_fwd_tc_kernel(const __nv_bfloat16
     }
     tc_fence_after();
 
-    if (done) {
+    // tcgen05.ld is warp-collective: take the TMEM read-out only if every lane got through
+    if (__all_sync(0xffffffffu, done)) {
         const long long p = p0 + warp * 32 + lane;
         const uint32_t trow = tmem + ((uint32_t)(warp * 32) << 16);
 #pragma unroll
@@ -240,6 +241,192 @@ static __global__ void kmajor_weights_kernel(const __nv_bfloat16* __restrict__ w
             wk[((long long)(8 - tap) * Cin + ci) * Cout + co] = w[e];
         else
             wk[((long long)tap * Cout + co) * Cin + ci] = w[e];
+    }
+}
+
+}  // namespace qldnn
+
+namespace qldnn {
+
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];\n" ::"r"(smem_u32(bar)) : "memory");
+}
+
+// 16-byte global -> shared copy cached in L1 as well: the nine taps of a tile
+// read overlapping rows of the input.
+__device__ __forceinline__ void cp_async16_ca(void* smem, const void* gmem, int src_bytes) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 16, %2;\n" ::"r"(smem_u32(smem)), "l"(gmem), "r"(src_bytes));
+}
+
+template <int N, int BK, int STAGES>
+struct TcPipe {
+    static constexpr int kA = 128 * BK * 2;  // bytes of one A tile
+    static constexpr int kB = N * BK * 2;    // bytes of one B tile
+    static constexpr int kStage = kA + kB;
+    static constexpr int kBars = (2 * STAGES + 1) * 8;
+    static constexpr int kSmem = STAGES * kStage + kBars + 16;
+};
+
+// Warp-specialised version of conv3x3_fwd_tc_kernel. 160 threads: warps 0-3
+// gather the K steps into a STAGES-deep ring (each thread: one pixel row of A
+// and a share of B) and, LAG steps later, once their copies have landed,
+// fence them for the tensor-core (async) proxy and arrive on the step's
+// "full" barrier; warp 4 waits on "full", issues the step's BK/16 MMAs
+// (M128 x N x K16, whole Cout per tile: N = Cout <= 256) and commits to the
+// step's "empty" barrier, which releases the buffer to the producers; a last
+// commit to "done" releases the epilogue (warps 0-3, TMEM lanes 32w..32w+31).
+// Bounded waits everywhere: a role that gives up sets *status and goes on, so
+// every role terminates and TMEM is always freed.
+template <int N, int BK, int STAGES>
+__global__ void __launch_bounds__(160) conv3x3_fwd_tc2_kernel(const __nv_bfloat16* __restrict__ in,
+                                                              const __nv_bfloat16* __restrict__ wk,
+                                                              const float* __restrict__ bias, int B, int H, int W,
+                                                              int Cin, int Cout, int relu, __nv_bfloat16* out_bf,
+                                                              float* out_f, int* status) {
+    using L = TcPipe<N, BK, STAGES>;
+    constexpr int LAG = STAGES - 2;
+    static_assert(LAG >= 1, "need at least three stages");
+    extern __shared__ __align__(1024) unsigned char dsm[];
+    uint64_t* full = reinterpret_cast<uint64_t*>(dsm + STAGES * L::kStage);
+    uint64_t* empty = full + STAGES;
+    uint64_t* done = empty + STAGES;
+    uint32_t* tslot = reinterpret_cast<uint32_t*>(done + 1);
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const long long P = (long long)B * H * W;
+    const long long p0 = (long long)blockIdx.x * 128;
+    const int csteps = Cin / BK;
+    const int ksteps = 9 * csteps;
+    constexpr uint32_t kIdesc = umma_idesc_bf16(128, N);
+    constexpr long long kSpin = 1ll << 20;
+
+    if (warp == 4) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(smem_u32(tslot)),
+                     "r"(N));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n" ::);
+    }
+    if (tid == 0) {
+        for (int b = 0; b < STAGES; ++b) {
+            mbar_init(&full[b], 128);
+            mbar_init(&empty[b], 1);
+        }
+        mbar_init(done, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;\n" ::);
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *tslot;
+    bool ok_all = true;
+
+    if (warp < 4) {
+        // ---------------------------------------------------------- producers
+        const long long pm = p0 + tid;
+        int py = 0, px = 0;
+        long long pb = 0;
+        if (pm < P) {
+            pb = pm / ((long long)H * W);
+            const long long r = pm - pb * H * W;
+            py = (int)(r / W);
+            px = (int)(r - (long long)py * W);
+        }
+        for (int ks = 0; ks < ksteps; ++ks) {
+            const int b = ks % STAGES;
+            if (ks >= STAGES && !mbar_wait_bounded(&empty[b], (uint32_t)(((ks / STAGES) - 1) & 1), kSpin))
+                ok_all = false;
+            const int tap = ks / csteps, cc = ks - tap * csteps;
+            const int yy = py + tap / 3 - 1, xx = px + tap % 3 - 1;
+            const bool ok = pm < P && yy >= 0 && yy < H && xx >= 0 && xx < W;
+            const __nv_bfloat16* src = ok ? in + (((pb * H + yy) * W + xx) * Cin + cc * BK) : in;
+            unsigned char* abase = dsm + b * L::kStage;
+            unsigned char* bbase = abase + L::kA;
+#pragma unroll
+            for (int c = 0; c < BK / 8; ++c) cp_async16_ca(abase + kmajor_off<BK>(tid, c * 8), src + 8 * c, ok ? 16 : 0);
+            for (int i = tid; i < N * (BK / 8); i += 128) {
+                const int n = i / (BK / 8), c = i % (BK / 8);
+                cp_async16(bbase + kmajor_off<BK>(n, c * 8),
+                           wk + (((long long)tap * Cout + n) * Cin + cc * BK + c * 8), 16);
+            }
+            cp_async_commit();
+            if (ks >= LAG) {
+                cp_async_wait<LAG>();
+                asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+                mbar_arrive(&full[(ks - LAG) % STAGES]);
+            }
+        }
+        cp_async_wait<0>();
+        asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+        for (int k = ksteps - LAG < 0 ? 0 : ksteps - LAG; k < ksteps; ++k) mbar_arrive(&full[k % STAGES]);
+    } else if (lane == 0) {
+        // ------------------------------------------------------- MMA issuer
+        for (int ks = 0; ks < ksteps; ++ks) {
+            const int b = ks % STAGES;
+            const bool ready = mbar_wait_bounded(&full[b], (uint32_t)((ks / STAGES) & 1), kSpin);
+            if (!ready) ok_all = false;
+            tc_fence_after();
+            if (ready) {
+                const uint32_t a0 = smem_u32(dsm + b * L::kStage), b0 = a0 + L::kA;
+#pragma unroll
+                for (int kk = 0; kk < BK / 16; ++kk)
+                    tc_mma(tmem, umma_smem_desc(a0 + kk * 256, 128, BK * 16), umma_smem_desc(b0 + kk * 256, 128, BK * 16),
+                           kIdesc, (ks > 0 || kk > 0) ? 1u : 0u);
+            }
+            tc_commit(&empty[b]);
+        }
+        tc_commit(done);
+    }
+
+    if (warp < 4) {
+        // --------------------------------------------------------- epilogue
+        const bool fin = mbar_wait_bounded(done, 0, kSpin);
+        if (!fin) {
+            ok_all = false;
+            mbar_wait_bounded(done, 0, kSpin);  // bounded drain before TMEM is freed
+        }
+        tc_fence_after();
+        // tcgen05.ld is warp-collective: take the read-out only if every lane got through
+        if (__all_sync(0xffffffffu, ok_all)) {
+            const long long p = p0 + warp * 32 + lane;
+            const uint32_t trow = tmem + ((uint32_t)(warp * 32) << 16);
+#pragma unroll 1
+            for (int c0 = 0; c0 < N; c0 += 16) {
+                uint32_t r[16];
+                tc_ld16(trow + (uint32_t)c0, r);
+                asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
+                if (p < P) {
+                    float v[16];
+#pragma unroll
+                    for (int j = 0; j < 16; ++j) {
+                        v[j] = __uint_as_float(r[j]) + (bias ? bias[c0 + j] : 0.f);
+                        if (relu) v[j] = fmaxf(v[j], 0.f);
+                    }
+                    if (out_bf) {
+                        uint32_t pk[8];
+#pragma unroll
+                        for (int j = 0; j < 8; ++j) {
+                            const __nv_bfloat162 h2 = __floats2bfloat162_rn(v[2 * j], v[2 * j + 1]);
+                            pk[j] = *reinterpret_cast<const uint32_t*>(&h2);
+                        }
+                        uint4* o = reinterpret_cast<uint4*>(out_bf + p * Cout + c0);
+                        o[0] = make_uint4(pk[0], pk[1], pk[2], pk[3]);
+                        o[1] = make_uint4(pk[4], pk[5], pk[6], pk[7]);
+                    }
+                    if (out_f) {
+                        float4* o = reinterpret_cast<float4*>(out_f + p * Cout + c0);
+#pragma unroll
+                        for (int j = 0; j < 4; ++j)
+                            o[j] = make_float4(v[4 * j], v[4 * j + 1], v[4 * j + 2], v[4 * j + 3]);
+                    }
+                }
+            }
+        }
+    }
+    if (!ok_all && status) atomicExch(status, 1);
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 4) {
+        __syncwarp();
+        tc_fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(N));
     }
 }
 

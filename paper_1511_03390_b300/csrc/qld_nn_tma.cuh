@@ -1,0 +1,318 @@
+// qld_nn_tma.cuh -- persistent, TMA-fed 3x3 convolution forward on the
+// 5th-generation tensor cores.
+//
+// Output tile: 8 rows x 16 columns of one image = M 128 pixels, all N = Cout
+// output channels (32, 64, 128 or 256). K runs over channel chunks of
+// BK = SWB/2 channels (outer) and the nine taps (inner).
+//
+// Input staging without im2col: for each channel chunk the tile's input halo
+// (10 rows x 16 columns) is loaded three times by the tensor-memory
+// accelerator, shifted by one column each (x0-1, x0, x0+1). TMA fills the
+// out-of-image borders with zeros, which is exactly the convolution's zero
+// padding. In the halo copy for column shift kx, output pixel (y, x) of the
+// tile sits in row (y + ky) * 16 + x for tap row ky, so the A operand of tap
+// (ky, kx) is that copy starting ky * 16 rows in: a plain offset of the
+// matrix descriptor. The nine taps thus read 3 x 160 staged pixel rows instead
+// of 9 x 128 gathered ones. Weights (K-major, wk[tap][co][ci]) come in one
+// TMA box of N rows x BK channels per tap.
+//
+// Shared memory: both operands use the swizzled K-major layout TMA writes
+// when a box row is exactly the swizzle span (SWB = 128, 64 or 32 bytes):
+// 8-row atoms of 8 * SWB bytes. A K16 step inside a row moves the descriptor
+// start 32 bytes.
+//
+// Roles (192 threads, one CTA per SM, persistent over tiles):
+//   warp 0  one thread issues the TMA loads into a 2-stage halo ring and an
+//           SB-stage weight ring (mbarrier expect_tx / complete_tx);
+//   warp 1  allocates TMEM (two accumulators of N columns), one thread issues
+//           tcgen05.mma M128 x N x K16 and commits to the rings' "empty"
+//           barriers and, per tile, to the accumulator's "full" barrier;
+//   warps 2-5 epilogue: tcgen05.ld of the accumulator (warp w reads TMEM
+//           lanes 32 (w mod 4) ..), bias, ReLU, bf16/f32 stores, then release
+//           the accumulator, so the next tile's MMAs overlap the read-out.
+// Every wait is bounded (about a second of wall time) and also gives up once
+// another role has flagged a failure; the producer then waits (bounded) for
+// its copies in flight, the MMA thread for its MMAs, and TMEM is freed. A
+// failure records 1 in *status.
+
+#pragma once
+
+#include <cuda.h>
+
+#include "qld_nn_tc.cuh"
+
+namespace qldnn {
+
+// Matrix descriptor of a K-major operand in a swizzled layout: rows of SWB
+// bytes, 8-row atoms SBO = 8 * SWB bytes apart (leading offset unused).
+template <int SWB>
+__device__ __forceinline__ uint64_t umma_desc_sw(uint32_t saddr) {
+    constexpr uint64_t layout = SWB == 128 ? 2 : (SWB == 64 ? 4 : 6);
+    uint64_t d = 0;
+    d |= (uint64_t)((saddr >> 4) & 0x3FFFu);
+    d |= (uint64_t)1 << 16;
+    d |= (uint64_t)(((8 * SWB) >> 4) & 0x3FFF) << 32;
+    d |= (uint64_t)1 << 46;
+    d |= layout << 61;
+    return d;
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, uint64_t* bar, int c0, int c1) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4}], [%2];\n" ::"r"(
+            smem_u32(dst)),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(smem_u32(bar)), "r"(c0), "r"(c1)
+        : "memory");
+}
+
+__device__ __forceinline__ void tma_load_4d(void* dst, const CUtensorMap* map, uint64_t* bar, int c0, int c1, int c2,
+                                            int c3) {
+    asm volatile(
+        "cp.async.bulk.tensor.4d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4, %5, %6}], "
+        "[%2];\n" ::"r"(smem_u32(dst)),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(smem_u32(bar)), "r"(c0), "r"(c1), "r"(c2), "r"(c3)
+        : "memory");
+}
+
+__device__ __forceinline__ uint64_t global_ns() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %globaltimer;\n" : "=l"(t));
+    return t;
+}
+
+// Wait for phase `parity` of `bar` for at most about one second of wall time;
+// with `fail` non-null, also give up as soon as another role has set *fail
+// (and set it on a time-out).
+__device__ __forceinline__ bool wait_timed(uint64_t* bar, uint32_t parity, volatile int* fail) {
+    const uint64_t t0 = global_ns();
+    for (uint32_t i = 1;; ++i) {
+        if (mbar_try_wait(bar, parity)) return true;
+        if ((i & 63) == 0) {
+            if (fail && *fail) return false;
+            if (global_ns() - t0 > 1000000000ull) break;
+        }
+    }
+    if (fail) *fail = 1;
+    return false;
+}
+
+__device__ __forceinline__ bool wait_or_fail(uint64_t* bar, uint32_t parity, volatile int* fail) {
+    return wait_timed(bar, parity, fail);
+}
+
+template <int N, int SWB>
+struct TmaConv {
+    static constexpr int BK = SWB / 2;                      // channels per chunk
+    static constexpr int HALO = 10 * 16 * SWB;              // one column-shifted halo copy
+    static constexpr int SA = 2;                            // halo stages
+    static constexpr int BSTAGE = N * SWB;                  // one tap's weights
+    static constexpr int SB = N >= 256 ? 3 : (N >= 128 ? 4 : 8);
+    static constexpr int kA = SA * 3 * HALO;
+    static constexpr int kB = SB * BSTAGE;
+    static constexpr int kBars = (2 * SA + 2 * SB + 5) * 8;
+    static constexpr int kSmem = 1024 + kA + kB + kBars + 16;  // 1024: slack to align the base
+    static constexpr int kTmemCols = 2 * N;
+};
+
+template <int N, int SWB>
+__global__ void __launch_bounds__(192, 1)
+    conv3x3_fwd_tma_kernel(const __grid_constant__ CUtensorMap map_in, const __grid_constant__ CUtensorMap map_w,
+                           const float* __restrict__ bias, int B, int H, int W, int Cin, int Cout, int relu,
+                           __nv_bfloat16* out_bf, float* out_f, int* status) {
+    using L = TmaConv<N, SWB>;
+    extern __shared__ unsigned char dsm_raw[];
+    unsigned char* dsm = dsm_raw + ((1024u - (smem_u32(dsm_raw) & 1023u)) & 1023u);
+    unsigned char* sA = dsm;
+    unsigned char* sB = dsm + L::kA;
+    uint64_t* fullA = reinterpret_cast<uint64_t*>(sB + L::kB);
+    uint64_t* emptyA = fullA + L::SA;
+    uint64_t* fullB = emptyA + L::SA;
+    uint64_t* emptyB = fullB + L::SB;
+    uint64_t* tfull = emptyB + L::SB;
+    uint64_t* tempty = tfull + 2;
+    uint64_t* drain = tempty + 2;
+    uint32_t* tslot = reinterpret_cast<uint32_t*>(drain + 1);
+    volatile int* fail = reinterpret_cast<volatile int*>(tslot + 1);
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int tiles_x = (W + 15) >> 4, tiles_y = (H + 7) >> 3;
+    const int ntiles = B * tiles_x * tiles_y;
+    const int csteps = Cin / L::BK;
+    constexpr uint32_t kIdesc = umma_idesc_bf16(128, N);
+
+    if (warp == 1) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(smem_u32(tslot)),
+                     "r"(L::kTmemCols));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n" ::);
+    }
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < L::SA; ++s) {
+            mbar_init(&fullA[s], 1);
+            mbar_init(&emptyA[s], 1);
+        }
+        for (int s = 0; s < L::SB; ++s) {
+            mbar_init(&fullB[s], 1);
+            mbar_init(&emptyB[s], 1);
+        }
+        for (int s = 0; s < 2; ++s) {
+            mbar_init(&tfull[s], 1);
+            mbar_init(&tempty[s], 128);
+        }
+        mbar_init(drain, 1);
+        *fail = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;\n" ::);
+        asm volatile("prefetch.tensormap [%0];\n" ::"l"(reinterpret_cast<uint64_t>(&map_in)) : "memory");
+        asm volatile("prefetch.tensormap [%0];\n" ::"l"(reinterpret_cast<uint64_t>(&map_w)) : "memory");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *tslot;
+
+    if (warp == 0) {
+        if (lane == 0) {
+            // ------------------------------------------------------------ TMA producer
+            int ia = 0, ib = 0;
+            bool ok = true;
+            for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
+                const int tx = t % tiles_x, r = t / tiles_x, ty = r % tiles_y, b = r / tiles_y;
+                const int x0 = tx * 16, y0 = ty * 8;
+                for (int cc = 0; cc < csteps && ok; ++cc) {
+                    const int sa = ia % L::SA;
+                    if (ia >= L::SA && !(ok = wait_or_fail(&emptyA[sa], (uint32_t)(((ia / L::SA) - 1) & 1), fail)))
+                        break;
+                    mbar_expect_tx(&fullA[sa], 3 * L::HALO);
+                    for (int j = 0; j < 3; ++j)
+                        tma_load_4d(sA + (sa * 3 + j) * L::HALO, &map_in, &fullA[sa], cc * L::BK, x0 + j - 1, y0 - 1, b);
+                    ++ia;
+                    for (int tap = 0; tap < 9; ++tap) {
+                        const int sb = ib % L::SB;
+                        if (ib >= L::SB && !(ok = wait_or_fail(&emptyB[sb], (uint32_t)(((ib / L::SB) - 1) & 1), fail)))
+                            break;
+                        mbar_expect_tx(&fullB[sb], L::BSTAGE);
+                        tma_load_2d(sB + sb * L::BSTAGE, &map_w, &fullB[sb], cc * L::BK, tap * Cout);
+                        ++ib;
+                    }
+                }
+            }
+            // no copy may still be in flight when the CTA leaves: wait for the
+            // last load issued into each stage (the earlier ones completed
+            // before it could be issued)
+            for (int s = 0; s < L::SA; ++s) {
+                const int k = ia - 1 - ((ia - 1 - s) % L::SA + L::SA) % L::SA;
+                if (k >= 0) wait_timed(&fullA[s], (uint32_t)((k / L::SA) & 1), nullptr);
+            }
+            for (int s = 0; s < L::SB; ++s) {
+                const int k = ib - 1 - ((ib - 1 - s) % L::SB + L::SB) % L::SB;
+                if (k >= 0) wait_timed(&fullB[s], (uint32_t)((k / L::SB) & 1), nullptr);
+            }
+        }
+    } else if (warp == 1) {
+        if (lane == 0) {
+            // --------------------------------------------------------- MMA issuer
+            int ia = 0, ib = 0, it = 0;
+            bool ok = true;
+            for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
+                const int acc = it & 1;
+                if (it >= 2 && !(ok = wait_or_fail(&tempty[acc], (uint32_t)(((it >> 1) - 1) & 1), fail))) break;
+                tc_fence_after();
+                const uint32_t d = tmem + (uint32_t)(acc * N);
+                for (int cc = 0; cc < csteps && ok; ++cc) {
+                    const int sa = ia % L::SA;
+                    if (!(ok = wait_or_fail(&fullA[sa], (uint32_t)((ia / L::SA) & 1), fail))) break;
+                    tc_fence_after();
+                    const uint32_t a0 = smem_u32(sA + sa * 3 * L::HALO);
+                    for (int tap = 0; tap < 9; ++tap) {
+                        const int sb = ib % L::SB;
+                        if (!(ok = wait_or_fail(&fullB[sb], (uint32_t)((ib / L::SB) & 1), fail))) break;
+                        tc_fence_after();
+                        const uint32_t abase = a0 + (uint32_t)((tap % 3) * L::HALO + (tap / 3) * 16 * SWB);
+                        const uint32_t bbase = smem_u32(sB + sb * L::BSTAGE);
+#pragma unroll
+                        for (int kk = 0; kk < L::BK / 16; ++kk)
+                            tc_mma(d, umma_desc_sw<SWB>(abase + kk * 32), umma_desc_sw<SWB>(bbase + kk * 32), kIdesc,
+                                   (cc | tap | kk) ? 1u : 0u);
+                        tc_commit(&emptyB[sb]);
+                        ++ib;
+                    }
+                    if (!ok) break;
+                    tc_commit(&emptyA[sa]);
+                    ++ia;
+                }
+                if (!ok) break;
+                tc_commit(&tfull[acc]);
+                ++it;
+            }
+            // every MMA issued has completed before TMEM can be freed
+            tc_commit(drain);
+            wait_timed(drain, 0, nullptr);
+        }
+    } else {
+        // ---------------------------------------------------------------- epilogue
+        const int qw = warp & 3;  // TMEM lane quarter this warp may read
+        const int m = qw * 32 + lane;
+        const int my = m >> 4, mx = m & 15;
+        int it = 0;
+        for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
+            const int acc = it & 1;
+            const bool got = wait_or_fail(&tfull[acc], (uint32_t)((it >> 1) & 1), fail);
+            if (!__all_sync(0xffffffffu, got)) break;  // tcgen05.ld below is warp-collective
+            tc_fence_after();
+            const int tx = t % tiles_x, r = t / tiles_x, ty = r % tiles_y, b = r / tiles_y;
+            const int y = ty * 8 + my, x = tx * 16 + mx;
+            const bool inside = y < H && x < W;
+            const long long p = ((long long)b * H + y) * W + x;
+            const uint32_t taddr = tmem + ((uint32_t)(qw * 32) << 16) + (uint32_t)(acc * N);
+#pragma unroll 1
+            for (int c0 = 0; c0 < N; c0 += 16) {
+                uint32_t rr[16];
+                tc_ld16(taddr + (uint32_t)c0, rr);
+                asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
+                if (inside) {
+                    float v[16];
+#pragma unroll
+                    for (int j = 0; j < 16; ++j) {
+                        v[j] = __uint_as_float(rr[j]) + (bias ? bias[c0 + j] : 0.f);
+                        if (relu) v[j] = fmaxf(v[j], 0.f);
+                    }
+                    if (out_bf) {
+                        uint32_t pk[8];
+#pragma unroll
+                        for (int j = 0; j < 8; ++j) {
+                            const __nv_bfloat162 h2 = __floats2bfloat162_rn(v[2 * j], v[2 * j + 1]);
+                            pk[j] = *reinterpret_cast<const uint32_t*>(&h2);
+                        }
+                        uint4* o = reinterpret_cast<uint4*>(out_bf + p * Cout + c0);
+                        o[0] = make_uint4(pk[0], pk[1], pk[2], pk[3]);
+                        o[1] = make_uint4(pk[4], pk[5], pk[6], pk[7]);
+                    }
+                    if (out_f) {
+                        float4* o = reinterpret_cast<float4*>(out_f + p * Cout + c0);
+#pragma unroll
+                        for (int j = 0; j < 4; ++j)
+                            o[j] = make_float4(v[4 * j], v[4 * j + 1], v[4 * j + 2], v[4 * j + 3]);
+                    }
+                }
+            }
+            tc_fence_before();
+            mbar_arrive(&tempty[acc]);
+            ++it;
+        }
+    }
+
+    tc_fence_before();
+    __syncthreads();
+    if (threadIdx.x == 0 && *fail && status) atomicExch(status, 1);
+    if (warp == 1) {
+        __syncwarp();
+        tc_fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(L::kTmemCols));
+    }
+}
+
+}  // namespace qldnn

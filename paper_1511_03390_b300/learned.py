@@ -101,14 +101,18 @@ class Params:
 
 class UNet:
     """Activations and gradient buffers for one input shape (B, H, W);
-    H and W must be multiples of 8. use_tc selects the tensor-memory
-    (tcgen05) kernels for the forward and data-gradient convolutions, else
-    the warp-level MMA kernels; the weight gradient uses the latter."""
+    H and W must be multiples of 8. `conv` picks the kernel of the forward
+    and data-gradient convolutions: "tma" (default; persistent TMA-fed
+    tcgen05 kernel), "tcgen05" (gathering tcgen05 kernel) or "warp_mma"
+    (warp-level MMA); the weight gradient always uses the warp-level MMA."""
 
-    def __init__(self, params, B, H, W, inference_only=False, use_tc=False):
+    CONVS = ("tma", "tcgen05", "warp_mma")
+
+    def __init__(self, params, B, H, W, inference_only=False, conv="tma"):
         assert H % 8 == 0 and W % 8 == 0
+        assert conv in self.CONVS, conv
         self.prm = params
-        self.use_tc = use_tc
+        self.conv = conv
         self.status = torch.zeros(1, dtype=torch.int32, device=params.device)
         self.B, self.H, self.W = B, H, W
         d = params.device
@@ -147,9 +151,10 @@ class UNet:
     def _conv(self, name, level, x, y):
         _, cin, cout = next(l for l in LAYERS if l[0] == name)
         h, w = self.dims[level]
-        if self.use_tc:
-            nn.conv3x3_fwd_tc(x, self.prm[name + ".w"]["wk"], self.prm[name + ".b"]["p"], self.B, h, w, cin, cout, 1,
-                              y, None, self.status)
+        if self.conv != "warp_mma":
+            fn = nn.conv3x3_fwd_tma if self.conv == "tma" else nn.conv3x3_fwd_tc
+            fn(x, self.prm[name + ".w"]["wk"], self.prm[name + ".b"]["p"], self.B, h, w, cin, cout, 1, y, None,
+               self.status)
         else:
             nn.conv3x3_fwd(x, self.prm[name + ".w"]["bf"], self.prm[name + ".b"]["p"], self.B, h, w, cin, cout, 1, y,
                            None)
@@ -204,9 +209,9 @@ class UNet:
         nn.conv3x3_wgrad(x, gz, self.B, h, w, cin, cout, self.prm[name + ".w"]["g"])
         nn.bias_grad(gz, self.P[level], cout, self.prm[name + ".b"]["g"])
         if gx is not None:
-            if self.use_tc:
-                nn.conv3x3_fwd_tc(gz, self.prm[name + ".w"]["wf"], None, self.B, h, w, cout, cin, 0, None, gx,
-                                  self.status)
+            if self.conv != "warp_mma":
+                fn = nn.conv3x3_fwd_tma if self.conv == "tma" else nn.conv3x3_fwd_tc
+                fn(gz, self.prm[name + ".w"]["wf"], None, self.B, h, w, cout, cin, 0, None, gx, self.status)
             else:
                 nn.conv3x3_dgrad(gz, self.prm[name + ".w"]["bf"], self.B, h, w, cin, cout, self.wt, None, gx)
 

@@ -19,8 +19,8 @@ def _need_gpu():
         pytest.skip("no CUDA device")
 
 
-@pytest.mark.parametrize("use_tc", [True, False], ids=["tcgen05", "warp_mma"])
-def test_unet_gradients_match_the_fp64_reference(use_tc):
+@pytest.mark.parametrize("conv", learned.UNet.CONVS)
+def test_unet_gradients_match_the_fp64_reference(conv):
     rng = np.random.default_rng(3)
     B, H, W = 2, 16, 24
     prm = learned.Params(seed=5)
@@ -28,7 +28,7 @@ def test_unet_gradients_match_the_fp64_reference(use_tc):
         if k.endswith(".b"):
             prm[k]["p"].copy_(torch.from_numpy(rng.standard_normal(prm[k]["p"].numel()).astype(np.float32) * 0.1))
     prm["head.w"]["p"].copy_(torch.from_numpy(rng.standard_normal(32).astype(np.float32) * 0.3))
-    net = learned.UNet(prm, B, H, W, use_tc=use_tc)
+    net = learned.UNet(prm, B, H, W, conv=conv)
     S = torch.from_numpy(rng.integers(-3000, 3000, B * H * W).astype(np.int32)).cuda()
     C = torch.from_numpy(rng.integers(-3000, 3000, B * H * W).astype(np.int32)).cuda()
     T = torch.from_numpy(rng.uniform(0, 20, B * H * W).astype(np.float32)).cuda()

@@ -1,6 +1,6 @@
-"""The tensor-memory (tcgen05) convolution against the FP64 oracle and the
-warp-MMA kernel: forward with bias/ReLU and, with flipped weights, the data
-gradient. Same tolerance as the other convolution tests (FP32 accumulation
+"""The tensor-memory (tcgen05) convolutions (the two-buffer kernel, the
+warp-specialised pipelined one and the persistent TMA-fed one) against the FP64 oracle and the warp-MMA
+kernel: forward with bias/ReLU and, with flipped weights, the data gradient. Same tolerance as the other convolution tests (FP32 accumulation
 relative to sum |x| |w|, plus bf16 output rounding)."""
 import numpy as np
 import pytest
@@ -19,10 +19,23 @@ def _need_gpu():
         pytest.skip("no CUDA device")
 
 
+KERNELS = ["conv3x3_fwd_tc", "conv3x3_fwd_tc2", "conv3x3_fwd_tma"]
+
+
+def _tc(kernel, Cout):
+    if kernel != "conv3x3_fwd_tc" and Cout not in (32, 64, 128, 256):
+        pytest.skip("the pipelined kernels cover Cout in {32, 64, 128, 256}")
+    return getattr(q.nn, kernel)
+
+
+@pytest.mark.parametrize("kernel", KERNELS)
 @pytest.mark.parametrize("B,H,W,Cin,Cout,relu", [(1, 8, 16, 16, 32, 0), (2, 17, 13, 16, 64, 1), (1, 32, 40, 32, 64, 0),
                                                  (1, 9, 130, 48, 96, 1), (3, 8, 8, 64, 128, 0),
-                                                 (1, 24, 24, 256, 128, 1)])
-def test_tc_conv_forward(B, H, W, Cin, Cout, relu):
+                                                 (1, 24, 24, 256, 128, 1), (2, 19, 21, 128, 256, 1),
+                                                 (1, 7, 5, 64, 32, 0), (1, 9, 130, 48, 64, 1),
+                                                 (4, 96, 160, 32, 32, 1)])
+def test_tc_conv_forward(kernel, B, H, W, Cin, Cout, relu):
+    conv = _tc(kernel, Cout)
     rng = np.random.default_rng(B * H + Cin + 1)
     x, xr = bf16(rng.standard_normal((B, H, W, Cin)))
     w, wr = bf16(rng.standard_normal((3, 3, Cin, Cout)) / np.sqrt(9 * Cin))
@@ -32,7 +45,7 @@ def test_tc_conv_forward(B, H, W, Cin, Cout, relu):
     status = torch.zeros(1, dtype=torch.int32, device="cuda")
     out_f = torch.empty((B, H, W, Cout), dtype=torch.float32, device="cuda")
     out_b = torch.empty((B, H, W, Cout), dtype=torch.bfloat16, device="cuda")
-    q.nn.conv3x3_fwd_tc(x, wk, bias, B, H, W, Cin, Cout, relu, out_b, out_f, status)
+    conv(x, wk, bias, B, H, W, Cin, Cout, relu, out_b, out_f, status)
     torch.cuda.synchronize()
     assert status.item() == 0
     ref = oracle.conv3x3(xr, wr, bias.cpu().numpy().astype(np.float64))
@@ -48,8 +61,10 @@ def test_tc_conv_forward(B, H, W, Cin, Cout, relu):
     close(out_f.cpu().numpy(), out_m.cpu().numpy().astype(np.float64), 2 * bound, "tcgen05 vs warp MMA")
 
 
+@pytest.mark.parametrize("kernel", KERNELS)
 @pytest.mark.parametrize("B,H,W,Cin,Cout", [(2, 11, 14, 32, 32), (1, 24, 20, 64, 32), (1, 16, 16, 128, 256)])
-def test_tc_conv_data_gradient(B, H, W, Cin, Cout):
+def test_tc_conv_data_gradient(kernel, B, H, W, Cin, Cout):
+    conv = _tc(kernel, Cin)
     rng = np.random.default_rng(H * W + 3)
     g, gr = bf16(rng.standard_normal((B, H, W, Cout)))
     w, wr = bf16(rng.standard_normal((3, 3, Cin, Cout)) / np.sqrt(9 * Cin))
@@ -57,7 +72,7 @@ def test_tc_conv_data_gradient(B, H, W, Cin, Cout):
     q.nn.kmajor_weights(w, Cin, Cout, 1, wk)
     din = torch.empty((B, H, W, Cin), dtype=torch.float32, device="cuda")
     status = torch.zeros(1, dtype=torch.int32, device="cuda")
-    q.nn.conv3x3_fwd_tc(g, wk, None, B, H, W, Cout, Cin, 0, None, din, status)
+    conv(g, wk, None, B, H, W, Cout, Cin, 0, None, din, status)
     torch.cuda.synchronize()
     assert status.item() == 0
     xdummy = np.zeros((B, H, W, Cin))
