@@ -372,15 +372,21 @@ def metrics(pred, target):
 def evaluate(params, S, C, T, H, W, batch=2):
     """Network and baseline (32 R_32) metrics over full frames."""
     n = S.shape[0]
-    net = UNet(params, batch, H, W, inference_only=True)
+    if n < 1:
+        raise ValueError("evaluate needs at least one stack")
+    nets = {}
     preds, bases = [], []
-    for i0 in range(0, n - n % batch, batch):
-        net.pack(S[i0:i0 + batch].reshape(-1), C[i0:i0 + batch].reshape(-1))
+    for i0 in range(0, n, batch):
+        b = min(batch, n - i0)  # the last batch may be short
+        if b not in nets:
+            nets[b] = UNet(params, b, H, W, inference_only=True)
+        net = nets[b]
+        net.pack(S[i0:i0 + b].reshape(-1), C[i0:i0 + b].reshape(-1))
         net.forward()
         torch.cuda.synchronize()
         preds.append(net.pred.cpu().numpy().copy())
         bases.append(net.baseline.cpu().numpy().copy())
-    t = T[:len(preds) * batch].reshape(-1).cpu().numpy()
+    t = T[:n].reshape(-1).cpu().numpy()
     p = np.concatenate(preds)
     b = np.concatenate(bases)
     return {"network": metrics(p, t), "baseline": metrics(b, t)}
