@@ -279,7 +279,10 @@ int qld_server_shape(const qld_server* srv, int* threads, int* vectors_per_threa
  *    weights, refreshing an optional bf16 copy), qldnn_cast_bf16, qldnn_add,
  *    qldnn_pack_input (network input: S, C, sqrt(S^2 + C^2) times `scale`,
  *    zero-padded to 16 channels; optionally the scaled amplitude in f32 as
- *    `baseline`), qldnn_zero (clears a device buffer).
+ *    `baseline`; out 16-byte aligned), qldnn_zero (clears a device buffer).
+ * Pooling, upsampling, concatenation and the head move 8 channels (16 bytes)
+ * per thread when the channel counts are multiples of 8 and the pointers
+ * 16-byte aligned, else one element per thread.
  * All return QLD_OK or QLD_E_INVAL / QLD_E_CUDA. */
 int qldnn_conv3x3_fwd(const void* in, const void* w, const float* bias, int B, int H, int W, int Cin, int Cout,
                       int relu, void* out_bf16, float* out_f32, void* stream);
@@ -294,6 +297,11 @@ int qldnn_avgpool2_bwd(const float* g, int B, int H, int W, int C, float* out, i
 int qldnn_upsample2(const void* in, int B, int h, int w, int C, void* out, void* stream);
 int qldnn_upsample2_bwd(const float* g, int B, int h, int w, int C, float* out, void* stream);
 int qldnn_concat(const void* a, int Ca, const void* b, int Cb, long long P, void* out, void* stream);
+/* Decoder skip input in one pass: out [B][2h][2w][Cu + Ce] bf16 = the
+ * nearest 2x upsampling of u [B][h][w][Cu] followed by e [B][2h][2w][Ce]
+ * along channels (Cu, Ce multiples of 8; pointers 16-byte aligned). */
+int qldnn_upsample_concat(const void* u, int Cu, const void* e, int Ce, int B, int h, int w, void* out,
+                          void* stream);
 int qldnn_split(const float* g, long long P, int Ca, int Cb, float* ga, float* gb, int accumulate_b, void* stream);
 int qldnn_head(const void* in, const float* w, const float* b, long long P, int C, float* out, void* stream);
 int qldnn_head_bwd(const void* in, const float* g, const float* w, long long P, int C, float* din, float* dw,

@@ -72,6 +72,7 @@ _SIGS = {
     "qldnn_upsample2": ([_p, _i, _i, _i, _i, _p, _p], _i),
     "qldnn_upsample2_bwd": ([_p, _i, _i, _i, _i, _p, _p], _i),
     "qldnn_concat": ([_p, _i, _p, _i, _ll, _p, _p], _i),
+    "qldnn_upsample_concat": ([_p, _i, _p, _i, _i, _i, _i, _p, _p], _i),
     "qldnn_split": ([_p, _ll, _i, _i, _p, _p, _i, _p], _i),
     "qldnn_head": ([_p, _p, _p, _ll, _i, _p, _p], _i),
     "qldnn_head_bwd": ([_p, _p, _p, _ll, _i, _p, _p, _p, _p], _i),

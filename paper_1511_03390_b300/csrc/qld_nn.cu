@@ -226,18 +226,124 @@ __global__ void add_kernel(float* __restrict__ y, const float* __restrict__ x, l
 
 // Network input from the short-window sums: channels (S, C, R) * scale, then
 // zeros up to 16 channels. R = sqrt(S^2 + C^2).
+// ---- 16-byte (8 x bf16 channel) versions of the forward glue kernels; used
+// whenever every channel count involved is a multiple of 8.
+__device__ __forceinline__ void unpack8(const uint4 q, float* f) {
+    const __nv_bfloat162* h = reinterpret_cast<const __nv_bfloat162*>(&q);
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        const float2 t = __bfloat1622float2(h[j]);
+        f[2 * j] = t.x;
+        f[2 * j + 1] = t.y;
+    }
+}
+
+__device__ __forceinline__ uint4 pack8(const float* f) {
+    uint4 q;
+    uint32_t* u = reinterpret_cast<uint32_t*>(&q);
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        const __nv_bfloat162 h2 = __floats2bfloat162_rn(f[2 * j], f[2 * j + 1]);
+        u[j] = *reinterpret_cast<const uint32_t*>(&h2);
+    }
+    return q;
+}
+
+__global__ void avgpool2_fwd_v8_kernel(const uint4* __restrict__ in, int B, int H, int W, int C8,
+                                       uint4* __restrict__ out) {
+    const int h = H / 2, w = W / 2;
+    const long long n = (long long)B * h * w * C8;
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x) {
+        const int c = (int)(e % C8);
+        long long r = e / C8;
+        const int x = (int)(r % w);
+        r /= w;
+        const int y = (int)(r % h);
+        const long long b = r / h;
+        const long long base = ((b * H + 2 * y) * W + 2 * x) * C8 + c;
+        float f0[8], f1[8], f2[8], f3[8], o[8];
+        unpack8(__ldg(in + base), f0);
+        unpack8(__ldg(in + base + C8), f1);
+        unpack8(__ldg(in + base + (long long)W * C8), f2);
+        unpack8(__ldg(in + base + (long long)W * C8 + C8), f3);
+#pragma unroll
+        for (int j = 0; j < 8; ++j) o[j] = 0.25f * (f0[j] + f1[j] + f2[j] + f3[j]);
+        out[e] = pack8(o);
+    }
+}
+
+__global__ void upsample2_fwd_v8_kernel(const uint4* __restrict__ in, int B, int h, int w, int C8,
+                                        uint4* __restrict__ out) {
+    const long long n = (long long)B * 2 * h * 2 * w * C8;
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x) {
+        const int c = (int)(e % C8);
+        long long r = e / C8;
+        const int x = (int)(r % (2 * w));
+        r /= 2 * w;
+        const int y = (int)(r % (2 * h));
+        const long long b = r / (2 * h);
+        out[e] = __ldg(in + ((b * h + y / 2) * w + x / 2) * C8 + c);
+    }
+}
+
+__global__ void concat_v8_kernel(const uint4* __restrict__ a, int Ca8, const uint4* __restrict__ b, int Cb8,
+                                 long long P, uint4* __restrict__ out) {
+    const int C8 = Ca8 + Cb8;
+    const long long n = P * C8;
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x) {
+        const long long p = e / C8;
+        const int c = (int)(e - p * C8);
+        out[e] = c < Ca8 ? __ldg(a + p * Ca8 + c) : __ldg(b + p * Cb8 + (c - Ca8));
+    }
+}
+
+// out[b][Y][X] = [ u[b][Y/2][X/2] (Cu channels) , e[b][Y][X] (Ce channels) ]
+// at the full resolution 2h x 2w: nearest 2x upsampling of u fused with the
+// channel concatenation.
+__global__ void upsample_concat_v8_kernel(const uint4* __restrict__ u, int Cu8, const uint4* __restrict__ e, int Ce8,
+                                          int B, int h, int w, uint4* __restrict__ out) {
+    const int C8 = Cu8 + Ce8;
+    const long long n = (long long)B * 4 * h * w * C8;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        const long long p = i / C8;
+        const int c = (int)(i - p * C8);
+        if (c < Cu8) {
+            const int x = (int)(p % (2 * w));
+            const long long r = p / (2 * w);
+            const int y = (int)(r % (2 * h));
+            const long long b = r / (2 * h);
+            out[i] = __ldg(u + ((b * h + y / 2) * w + x / 2) * Cu8 + c);
+        } else {
+            out[i] = __ldg(e + p * Ce8 + (c - Cu8));
+        }
+    }
+}
+
+__global__ void head_fwd_v8_kernel(const uint4* __restrict__ in, const float* __restrict__ w,
+                                   const float* __restrict__ bp, long long P, int C8, float* __restrict__ out) {
+    const float b = *bp;
+    for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < P; p += (long long)gridDim.x * blockDim.x) {
+        float acc = b;
+        for (int g = 0; g < C8; ++g) {
+            float f[8];
+            unpack8(__ldg(in + p * C8 + g), f);
+#pragma unroll
+            for (int j = 0; j < 8; ++j) acc = fmaf(f[j], __ldg(w + 8 * g + j), acc);
+        }
+        out[p] = acc;
+    }
+}
+
 __global__ void pack_input_kernel(const int32_t* __restrict__ S, const int32_t* __restrict__ C, long long n,
                                   float scale, __nv_bfloat16* __restrict__ out, float* __restrict__ baseline) {
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
         const float s = (float)S[i], c = (float)C[i];
         const float r = sqrtf(s * s + c * c) * scale;
         if (baseline) baseline[i] = r;
-        __nv_bfloat16* o = out + i * 16;
-        o[0] = __float2bfloat16_rn(s * scale);
-        o[1] = __float2bfloat16_rn(c * scale);
-        o[2] = __float2bfloat16_rn(r);
-#pragma unroll
-        for (int k = 3; k < 16; ++k) o[k] = __float2bfloat16_rn(0.f);
+        float f[8] = {s * scale, c * scale, r, 0.f, 0.f, 0.f, 0.f, 0.f};
+        uint4* o = reinterpret_cast<uint4*>(out + i * 16);  // 16 channels: S, C, R, then zeros
+        o[0] = pack8(f);
+        o[1] = make_uint4(0u, 0u, 0u, 0u);
     }
 }
 
@@ -413,8 +519,12 @@ int qldnn_relu_bwd(const float* g, const void* act, long long n, void* out_bf16,
 
 int qldnn_avgpool2(const void* in, int B, int H, int W, int C, void* out, void* stream) {
     if (!in || !out || H % 2 || W % 2) return set_err(QLD_E_INVAL);
-    avgpool2_fwd_kernel<<<grid_for((long long)B * H * W * C / 4), 256, 0, (cudaStream_t)stream>>>(
-        (const __nv_bfloat16*)in, B, H, W, C, (__nv_bfloat16*)out);
+    if (C % 8 == 0 && al(in, 16) && al(out, 16))
+        avgpool2_fwd_v8_kernel<<<grid_for((long long)B * H * W * C / 32), 256, 0, (cudaStream_t)stream>>>(
+            (const uint4*)in, B, H, W, C / 8, (uint4*)out);
+    else
+        avgpool2_fwd_kernel<<<grid_for((long long)B * H * W * C / 4), 256, 0, (cudaStream_t)stream>>>(
+            (const __nv_bfloat16*)in, B, H, W, C, (__nv_bfloat16*)out);
     return launched(1);
 }
 
@@ -427,8 +537,12 @@ int qldnn_avgpool2_bwd(const float* g, int B, int H, int W, int C, float* out, i
 
 int qldnn_upsample2(const void* in, int B, int h, int w, int C, void* out, void* stream) {
     if (!in || !out) return set_err(QLD_E_INVAL);
-    upsample2_fwd_kernel<<<grid_for(4ll * B * h * w * C), 256, 0, (cudaStream_t)stream>>>(
-        (const __nv_bfloat16*)in, B, h, w, C, (__nv_bfloat16*)out);
+    if (C % 8 == 0 && al(in, 16) && al(out, 16))
+        upsample2_fwd_v8_kernel<<<grid_for(4ll * B * h * w * C / 8), 256, 0, (cudaStream_t)stream>>>(
+            (const uint4*)in, B, h, w, C / 8, (uint4*)out);
+    else
+        upsample2_fwd_kernel<<<grid_for(4ll * B * h * w * C), 256, 0, (cudaStream_t)stream>>>(
+            (const __nv_bfloat16*)in, B, h, w, C, (__nv_bfloat16*)out);
     return launched(1);
 }
 
@@ -440,8 +554,21 @@ int qldnn_upsample2_bwd(const float* g, int B, int h, int w, int C, float* out, 
 
 int qldnn_concat(const void* a, int Ca, const void* b, int Cb, long long P, void* out, void* stream) {
     if (!a || !b || !out) return set_err(QLD_E_INVAL);
-    concat_kernel<<<grid_for(P * (Ca + Cb)), 256, 0, (cudaStream_t)stream>>>(
-        (const __nv_bfloat16*)a, Ca, (const __nv_bfloat16*)b, Cb, P, (__nv_bfloat16*)out);
+    if (Ca % 8 == 0 && Cb % 8 == 0 && al(a, 16) && al(b, 16) && al(out, 16))
+        concat_v8_kernel<<<grid_for(P * (Ca + Cb) / 8), 256, 0, (cudaStream_t)stream>>>(
+            (const uint4*)a, Ca / 8, (const uint4*)b, Cb / 8, P, (uint4*)out);
+    else
+        concat_kernel<<<grid_for(P * (Ca + Cb)), 256, 0, (cudaStream_t)stream>>>(
+            (const __nv_bfloat16*)a, Ca, (const __nv_bfloat16*)b, Cb, P, (__nv_bfloat16*)out);
+    return launched(1);
+}
+
+int qldnn_upsample_concat(const void* u, int Cu, const void* e, int Ce, int B, int h, int w, void* out, void* stream) {
+    if (!u || !e || !out || B < 1 || h < 1 || w < 1 || Cu < 8 || Ce < 8 || Cu % 8 || Ce % 8 || !al(u, 16) ||
+        !al(e, 16) || !al(out, 16))
+        return set_err(QLD_E_INVAL);
+    upsample_concat_v8_kernel<<<grid_for(4ll * B * h * w * (Cu + Ce) / 8), 256, 0, (cudaStream_t)stream>>>(
+        (const uint4*)u, Cu / 8, (const uint4*)e, Ce / 8, B, h, w, (uint4*)out);
     return launched(1);
 }
 
@@ -453,7 +580,10 @@ int qldnn_split(const float* g, long long P, int Ca, int Cb, float* ga, float* g
 
 int qldnn_head(const void* in, const float* w, const float* b, long long P, int C, float* out, void* stream) {
     if (!in || !w || !b || !out || C > 256) return set_err(QLD_E_INVAL);
-    head_fwd_kernel<<<grid_for(P), 256, 0, (cudaStream_t)stream>>>((const __nv_bfloat16*)in, w, b, P, C, out);
+    if (C % 8 == 0 && al(in, 16))
+        head_fwd_v8_kernel<<<grid_for(P), 256, 0, (cudaStream_t)stream>>>((const uint4*)in, w, b, P, C / 8, out);
+    else
+        head_fwd_kernel<<<grid_for(P), 256, 0, (cudaStream_t)stream>>>((const __nv_bfloat16*)in, w, b, P, C, out);
     return launched(1);
 }
 
@@ -493,7 +623,7 @@ int qldnn_add(float* y, const float* x, long long n, void* stream) {
 
 int qldnn_pack_input(const int32_t* S, const int32_t* C, long long npix, float scale, void* out, float* baseline,
                      void* stream) {
-    if (!S || !C || !out || npix < 0) return set_err(QLD_E_INVAL);
+    if (!S || !C || !out || npix < 0 || !al(out, 16)) return set_err(QLD_E_INVAL);
     pack_input_kernel<<<grid_for(npix), 256, 0, (cudaStream_t)stream>>>(S, C, npix, scale, (__nv_bfloat16*)out,
                                                                          baseline);
     return launched(1);

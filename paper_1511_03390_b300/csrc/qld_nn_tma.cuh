@@ -111,8 +111,11 @@ struct TmaConv {
     static constexpr int HALO = 10 * 16 * SWB;              // one column-shifted halo copy
     static constexpr int SA = 2;                            // halo stages
     static constexpr int BSTAGE = N * SWB;                  // one tap's weights
-    static constexpr int SB = N >= 256 ? 3 : (N >= 128 ? 4 : 8);
     static constexpr int kA = SA * 3 * HALO;
+    // weight stages: as many as fit beside the halo ring in 227 KB (at most 12)
+    static constexpr int kFree = 232448 - 1024 - kA - 64 * 8 - 16;
+    static constexpr int SB = kFree / BSTAGE > 12 ? 12 : kFree / BSTAGE;
+    static_assert(SB >= 2, "weight ring too small");
     static constexpr int kB = SB * BSTAGE;
     static constexpr int kBars = (2 * SA + 2 * SB + 5) * 8;
     static constexpr int kSmem = 1024 + kA + kB + kBars + 16;  // 1024: slack to align the base

@@ -34,6 +34,8 @@ LAYERS = [("c0a", 16, 32), ("c0b", 32, 32), ("c1a", 32, 64), ("c1b", 64, 64), ("
           ("c3a", 128, 128), ("c3b", 128, 128), ("d2a", 256, 128), ("d2b", 128, 64), ("d1a", 128, 64),
           ("d1b", 64, 32), ("d0a", 64, 32), ("d0b", 32, 32)]
 HEAD_C = 32
+# resolution level (0 = full, l = 1/2^l) at which each layer's name prefix runs
+LEVEL = {"c0": 0, "c1": 1, "c2": 2, "c3": 3, "d2": 2, "d1": 1, "d0": 0}
 
 
 class Params:
@@ -128,9 +130,9 @@ class UNet:
 
         self.a = {"x": act(0, CIN), "a0": act(0, 32), "e0": act(0, 32), "p0": act(1, 32), "a1": act(1, 64),
                   "e1": act(1, 64), "p1": act(2, 64), "a2": act(2, 128), "e2": act(2, 128), "p2": act(3, 128),
-                  "a3": act(3, 128), "u3": act(3, 128), "up3": act(2, 128), "cat2": act(2, 256),
-                  "ad2": act(2, 128), "u2": act(2, 64), "up2": act(1, 64), "cat1": act(1, 128), "ad1": act(1, 64),
-                  "u1": act(1, 32), "up1": act(0, 32), "cat0": act(0, 64), "ad0": act(0, 32), "u0": act(0, 32)}
+                  "a3": act(3, 128), "u3": act(3, 128), "cat2": act(2, 256),
+                  "ad2": act(2, 128), "u2": act(2, 64), "cat1": act(1, 128), "ad1": act(1, 64),
+                  "u1": act(1, 32), "cat0": act(0, 64), "ad0": act(0, 32), "u0": act(0, 32)}
         self.baseline = torch.empty(self.P[0], dtype=f32, device=d)
         self.pred = torch.empty(self.P[0], dtype=f32, device=d)
         if inference_only:
@@ -159,6 +161,31 @@ class UNet:
             nn.conv3x3_fwd(x, self.prm[name + ".w"]["bf"], self.prm[name + ".b"]["p"], self.B, h, w, cin, cout, 1, y,
                            None)
 
+    def capture(self):
+        """Record input packing and the forward pass as one CUDA graph over
+        this object's fixed buffers (inputs: self.S_in, self.C_in, int32
+        [B*H*W]); replay() then runs the whole network as one launch on the
+        current stream. The first, uncaptured pass sets the kernels'
+        launch attributes."""
+        d = self.prm.device
+        self.S_in = torch.zeros(self.P[0], dtype=torch.int32, device=d)
+        self.C_in = torch.zeros_like(self.S_in)
+        side = torch.cuda.Stream(d)
+        side.wait_stream(torch.cuda.current_stream(d))
+        with torch.cuda.stream(side):
+            self.pack(self.S_in, self.C_in)
+            self.forward()
+        torch.cuda.current_stream(d).wait_stream(side)
+        self.graph = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(self.graph):
+            self.pack(self.S_in, self.C_in)
+            self.forward()
+        return self
+
+    def replay(self):
+        self.graph.replay()
+        return self.pred
+
     def pack(self, S, C):
         """Network input and baseline from short-window sums (int32 [B*H*W])."""
         nn.pack_input(S, C, self.P[0], IN_SCALE, self.a["x"], self.baseline)
@@ -180,18 +207,15 @@ class UNet:
         h, w = self.dims[3]
         self._conv("c3a", 3, a["p2"], a["a3"])
         self._conv("c3b", 3, a["a3"], a["u3"])
-        nn.upsample2(a["u3"], B, h, w, 128, a["up3"])
-        nn.concat(a["up3"], 128, a["e2"], 128, self.P[2], a["cat2"])
+        nn.upsample_concat(a["u3"], 128, a["e2"], 128, B, h, w, a["cat2"])
         self._conv("d2a", 2, a["cat2"], a["ad2"])
         self._conv("d2b", 2, a["ad2"], a["u2"])
         h, w = self.dims[2]
-        nn.upsample2(a["u2"], B, h, w, 64, a["up2"])
-        nn.concat(a["up2"], 64, a["e1"], 64, self.P[1], a["cat1"])
+        nn.upsample_concat(a["u2"], 64, a["e1"], 64, B, h, w, a["cat1"])
         self._conv("d1a", 1, a["cat1"], a["ad1"])
         self._conv("d1b", 1, a["ad1"], a["u1"])
         h, w = self.dims[1]
-        nn.upsample2(a["u1"], B, h, w, 32, a["up1"])
-        nn.concat(a["up1"], 32, a["e0"], 32, self.P[0], a["cat0"])
+        nn.upsample_concat(a["u1"], 32, a["e0"], 32, B, h, w, a["cat0"])
         self._conv("d0a", 0, a["cat0"], a["ad0"])
         self._conv("d0b", 0, a["ad0"], a["u0"])
         nn.head(a["u0"], self.prm["head.w"]["p"], self.prm["head.b"]["p"], self.P[0], HEAD_C, self.pred)

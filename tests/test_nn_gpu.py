@@ -86,9 +86,10 @@ def test_conv_weight_gradient(B, H, W, Cin, Cout):
     close(db.cpu().numpy(), refb, ACC * bndb + 1e-6, "bias gradient")
 
 
-def test_small_layers_against_numpy():
+@pytest.mark.parametrize("C", [16, 12], ids=["8-channel vectors", "scalar"])
+def test_small_layers_against_numpy(C):
     rng = np.random.default_rng(7)
-    B, H, W, C = 2, 6, 10, 16
+    B, H, W = 2, 6, 10
     x, xr = bf16(rng.standard_normal((B, H, W, C)))
     pooled = torch.empty((B, H // 2, W // 2, C), dtype=torch.bfloat16, device="cuda")
     q.nn.avgpool2(x, B, H, W, C, pooled)
@@ -106,10 +107,10 @@ def test_small_layers_against_numpy():
     q.nn.upsample2_bwd(gu, B, H, W, C, gd)
     close(gd.cpu().numpy(), gu.cpu().numpy().reshape(B, H, 2, W, 2, C).sum(axis=(2, 4)), 1e-5, "upsample2 backward")
     y, yr = bf16(rng.standard_normal((B, H, W, 32)))
-    cat = torch.empty((B, H, W, 48), dtype=torch.bfloat16, device="cuda")
+    cat = torch.empty((B, H, W, C + 32), dtype=torch.bfloat16, device="cuda")
     q.nn.concat(x, C, y, 32, B * H * W, cat)
     close(cat.float().cpu().numpy(), np.concatenate([xr, yr], axis=3), 0, "concat")
-    gc = torch.from_numpy(rng.standard_normal((B, H, W, 48)).astype(np.float32)).cuda()
+    gc = torch.from_numpy(rng.standard_normal((B, H, W, C + 32)).astype(np.float32)).cuda()
     ga = torch.empty((B, H, W, C), dtype=torch.float32, device="cuda")
     gb = torch.ones((B, H, W, 32), dtype=torch.float32, device="cuda")
     q.nn.split(gc, B * H * W, C, 32, ga, gb, 1)
@@ -153,3 +154,17 @@ def test_small_layers_against_numpy():
     gg = gr.cpu().numpy().astype(np.float64)
     # first Adam step: m_hat = g, v_hat = g^2, so p moves by lr * g / (|g| + eps)
     close(p.cpu().numpy(), p0 - 1e-2 * gg / (np.abs(gg) + 1e-8), 1e-6, "adam step")
+
+
+def test_upsample_concat_matches_upsample_then_concat():
+    rng = np.random.default_rng(8)
+    B, h, w, Cu, Ce = 2, 5, 7, 16, 24
+    u, ur = bf16(rng.standard_normal((B, h, w, Cu)))
+    e, er = bf16(rng.standard_normal((B, 2 * h, 2 * w, Ce)))
+    out = torch.empty((B, 2 * h, 2 * w, Cu + Ce), dtype=torch.bfloat16, device="cuda")
+    q.nn.upsample_concat(u, Cu, e, Ce, B, h, w, out)
+    torch.cuda.synchronize()
+    want = np.concatenate([np.repeat(np.repeat(ur, 2, 1), 2, 2), er], axis=3)
+    close(out.float().cpu().numpy(), want, 0, "upsample_concat")
+    with pytest.raises(q.QLDError):
+        q.nn.upsample_concat(u, 12, e, Ce, B, h, w, out)
