@@ -336,6 +336,16 @@ int qldnn_conv3x3_fwd_tc2(const void* in, const void* wk, const float* bias, int
  * overlaps the next tile's MMAs. Launches one CTA per SM. */
 int qldnn_conv3x3_fwd_tma(const void* in, const void* wk, const float* bias, int B, int H, int W, int Cin, int Cout,
                           int relu, void* out_bf16, float* out_f32, int* status, void* stream);
+/* Weight gradient of the 3x3 convolution on the tensor cores: dw [9][Cin][Cout]
+ * f32 += sum over pixels of in (shifted by the tap) x g, in [B][H][W][Cin]
+ * and g [B][H][W][Cout] bf16 (the caller zeroes dw; 16-byte aligned). Cin is
+ * 16, 32, 64 or a multiple of 128; Cout is 32, 64 or 128. TMA-fed, operands
+ * read MN-major from the NHWC tiles, FP32 accumulation in TMEM per work item
+ * (column shift kx, 128-channel block, range of 8 x 16-pixel tiles), then
+ * 16-byte float atomics into dw (the summation order across items is not
+ * fixed). *status = 1 if a pipeline wait timed out. */
+int qldnn_conv3x3_wgrad_tma(const void* in, const void* g, int B, int H, int W, int Cin, int Cout, float* dw,
+                            int* status, void* stream);
 int qldnn_conv3x3_fwd_tc(const void* in, const void* wk, const float* bias, int B, int H, int W, int Cin, int Cout,
                          int relu, void* out_bf16, float* out_f32, int* status, void* stream);
 

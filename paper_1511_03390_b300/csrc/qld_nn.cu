@@ -446,6 +446,52 @@ int launch_tma(const void* in, const void* wk, const float* bias, int B, int H, 
                                                                         status);
     return launched(1);
 }
+
+template <int N, int SWA, bool STACK>
+int launch_wgrad_tma(const void* in, const void* g, int B, int H, int W, int Cin, int Cout, float* dw, int* status,
+                     cudaStream_t st) {
+    using L = qldnn::WgradTma<N, SWA, STACK>;
+    EncodeTiledFn enc = encode_tiled();
+    int dev = 0;
+    if (!enc || cudaGetDevice(&dev) != cudaSuccess) return set_err(QLD_E_CUDA);
+    const int nsm = sm_count(dev);
+    if (nsm <= 0) return set_err(QLD_E_CUDA);
+    auto swz = [](int sw) {
+        return sw == 128 ? CU_TENSOR_MAP_SWIZZLE_128B : (sw == 64 ? CU_TENSOR_MAP_SWIZZLE_64B : CU_TENSOR_MAP_SWIZZLE_32B);
+    };
+    const cuuint32_t one[4] = {1, 1, 1, 1};
+    CUtensorMap mi, mg;
+    const cuuint64_t idim[4] = {(cuuint64_t)Cin, (cuuint64_t)W, (cuuint64_t)H, (cuuint64_t)B};
+    const cuuint64_t istr[3] = {(cuuint64_t)Cin * 2, (cuuint64_t)W * Cin * 2, (cuuint64_t)H * W * Cin * 2};
+    const cuuint32_t ibox[4] = {(cuuint32_t)L::EA, 16, 10, 1};
+    if (enc(&mi, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, const_cast<void*>(in), idim, istr, ibox, one,
+            CU_TENSOR_MAP_INTERLEAVE_NONE, swz(SWA), CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+        return set_err(QLD_E_CUDA);
+    const cuuint64_t gdim[4] = {(cuuint64_t)Cout, (cuuint64_t)W, (cuuint64_t)H, (cuuint64_t)B};
+    const cuuint64_t gstr[3] = {(cuuint64_t)Cout * 2, (cuuint64_t)W * Cout * 2, (cuuint64_t)H * W * Cout * 2};
+    const cuuint32_t gbox[4] = {(cuuint32_t)L::EB, 16, 8, 1};
+    if (enc(&mg, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, const_cast<void*>(g), gdim, gstr, gbox, one,
+            CU_TENSOR_MAP_INTERLEAVE_NONE, swz(L::SWBB), CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+        return set_err(QLD_E_CUDA);
+    static std::atomic<unsigned long long> attr_done{0};
+    if (dev < 64 && !(attr_done.load() >> dev & 1ull)) {
+        if (cudaFuncSetAttribute(qldnn::conv3x3_wgrad_tma_kernel<N, SWA, STACK>,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, L::kSmem) != cudaSuccess)
+            return set_err(QLD_E_CUDA);
+        attr_done.fetch_or(1ull << dev);
+    }
+    const long long ntiles = (long long)B * ((H + 7) / 8) * ((W + 15) / 16);
+    const int ncb = STACK ? 1 : Cin / 128;
+    // one wave: about one work item per SM, each a contiguous range of tiles
+    long long nsplit = nsm / (3 * ncb);
+    if (nsplit < 1) nsplit = 1;
+    if (nsplit > ntiles) nsplit = ntiles;
+    qldnn::conv3x3_wgrad_tma_kernel<N, SWA, STACK><<<(unsigned)(3 * ncb * nsplit), 192, L::kSmem, st>>>(
+        mi, mg, B, H, W, Cin, Cout, (int)nsplit, dw, status);
+    return launched(1);
+}
 }  // namespace
 
 extern "C" {
@@ -699,6 +745,23 @@ int qldnn_conv3x3_fwd_tma(const void* in, const void* wk, const float* bias, int
     QLD_TMA(128, 32) QLD_TMA(128, 64) QLD_TMA(128, 128)
     QLD_TMA(256, 32) QLD_TMA(256, 64) QLD_TMA(256, 128)
 #undef QLD_TMA
+    return set_err(QLD_E_INVAL);
+}
+
+int qldnn_conv3x3_wgrad_tma(const void* in, const void* g, int B, int H, int W, int Cin, int Cout, float* dw,
+                            int* status, void* stream) {
+    const bool stack = Cin == 16 || Cin == 32 || Cin == 64;
+    if (!in || !g || !dw || B < 1 || H < 1 || W < 1 || !(stack || (Cin % 128 == 0 && Cin > 0)) ||
+        (Cout != 32 && Cout != 64 && Cout != 128) || !al(in, 16) || !al(g, 16) || !al(dw, 16) ||
+        (long long)B * H * W * (Cin > Cout ? Cin : Cout) >= (1ll << 40))
+        return set_err(QLD_E_INVAL);
+    const cudaStream_t st = (cudaStream_t)stream;
+#define QLD_WG(NN, CI, SW, STK) \
+    if (Cout == NN && (STK ? Cin == CI : !stack)) return launch_wgrad_tma<NN, SW, STK>(in, g, B, H, W, Cin, Cout, dw, status, st);
+    QLD_WG(32, 16, 32, true) QLD_WG(32, 32, 64, true) QLD_WG(32, 64, 128, true) QLD_WG(32, 0, 128, false)
+    QLD_WG(64, 16, 32, true) QLD_WG(64, 32, 64, true) QLD_WG(64, 64, 128, true) QLD_WG(64, 0, 128, false)
+    QLD_WG(128, 16, 32, true) QLD_WG(128, 32, 64, true) QLD_WG(128, 64, 128, true) QLD_WG(128, 0, 128, false)
+#undef QLD_WG
     return set_err(QLD_E_INVAL);
 }
 

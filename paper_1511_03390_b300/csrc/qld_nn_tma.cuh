@@ -318,4 +318,206 @@ __global__ void __launch_bounds__(192, 1)
     }
 }
 
+
+// ---------------------------------------------------------------------------
+// Weight gradient on the tensor cores: dW[3 ky + kx][ci][co] +=
+//   sum over pixels p of in[p shifted by (ky-1, kx-1)][ci] * g[p][co].
+// As a GEMM per tap: D (M = ci, N = co) += A (M x K) B^T (K x N) with K = the
+// pixels. Both operands come straight from the NHWC tensors in the layout the
+// forward kernel stages them in -- pixel rows of channels -- which for this
+// GEMM is MN-major (M resp. N contiguous, K = pixel rows): 8-row atoms of
+// 8 * SW bytes at stride SBO along K, blocks of SW/2 channels at stride LBO
+// along M or N.
+//
+// One CTA = one work item (kx, 128-channel block of ci, range of output
+// tiles). Per 8 x 16-pixel output tile it TMA-loads the kx-shifted input halo
+// (10 x 16 pixels) and the tile's output gradient (8 x 16 pixels x Cout).
+// The three tap rows ky of this kx read the halo from pixel row 16 ky on.
+//   Cin % 128 == 0 ("channel blocks"): M = 128 channels as two 64-channel
+//     blocks (two TMA boxes, LBO = one halo copy); three TMEM accumulators,
+//     one per ky.
+//   Cin = 16, 32 or 64 ("stacked taps"): M = 128 rows are 128 / Cin tap rows
+//     ky of Cin channels each, the ky blocks LBO = 16 pixel rows apart in the
+//     same halo copy; ceil(3 Cin / 128) accumulators; rows of ky >= 3 are
+//     computed on neighbouring shared memory and dropped.
+// At the end the epilogue warps read the accumulators (tcgen05.ld) and add
+// them into dW with 16-byte float atomics. Roles, bounded waits and the
+// failure path are those of conv3x3_fwd_tma_kernel.
+template <int N, int SWA, bool STACK>
+struct WgradTma {
+    static constexpr int EA = SWA / 2;                         // channels per A block
+    static constexpr int SWBB = N >= 64 ? 128 : 64;            // B rows: Cout channels, 64 or 32 per block
+    static constexpr int EB = SWBB / 2;
+    static constexpr int NBB = N / EB;                         // B blocks
+    static constexpr int HALO = 10 * 16 * SWA;                 // one halo copy of one A block
+    static constexpr int ABYTES = (STACK ? 1 : 2) * HALO;
+    static constexpr int BBYTES = NBB * 128 * SWBB;            // 128 pixel rows per B block
+    static constexpr int NACC = STACK ? (3 * EA + 127) / 128 : 3;
+    static constexpr int STAGE = ABYTES + BBYTES;
+    static constexpr int kPad = 4096;                          // reads past the last A stage stay inside
+    static constexpr int kFree = 232448 - 1024 - kPad - 256;
+    static constexpr int ST = kFree / STAGE > 6 ? 6 : kFree / STAGE;
+    static_assert(ST >= 2, "stage ring too small");
+    static constexpr int kSmem = 1024 + ST * STAGE + kPad + 256;
+    static constexpr int kCols = NACC * N <= 32 ? 32 : (NACC * N <= 64 ? 64 : (NACC * N <= 128 ? 128 : (NACC * N <= 256 ? 256 : 512)));
+};
+
+// Matrix descriptor of an MN-major swizzled operand: LBO = stride between
+// channel blocks, SBO = stride between 8-pixel-row groups.
+template <int SW>
+__device__ __forceinline__ uint64_t umma_desc_mn(uint32_t saddr, uint32_t lbo) {
+    constexpr uint64_t layout = SW == 128 ? 2 : (SW == 64 ? 4 : 6);
+    uint64_t d = 0;
+    d |= (uint64_t)((saddr >> 4) & 0x3FFFu);
+    d |= (uint64_t)((lbo >> 4) & 0x3FFFu) << 16;
+    d |= (uint64_t)(((8 * SW) >> 4) & 0x3FFF) << 32;
+    d |= (uint64_t)1 << 46;
+    d |= layout << 61;
+    return d;
+}
+
+template <int N, int SWA, bool STACK>
+__global__ void __launch_bounds__(192, 1)
+    conv3x3_wgrad_tma_kernel(const __grid_constant__ CUtensorMap map_in, const __grid_constant__ CUtensorMap map_g,
+                             int B, int H, int W, int Cin, int Cout, int nsplit, float* __restrict__ dw,
+                             int* status) {
+    using L = WgradTma<N, SWA, STACK>;
+    extern __shared__ unsigned char dsm_raw[];
+    unsigned char* dsm = dsm_raw + ((1024u - (smem_u32(dsm_raw) & 1023u)) & 1023u);
+    // [B stages][A stages][pad][barriers]: every operand read, however far a
+    // stacked-tap block runs past its halo copy, stays inside the allocation
+    unsigned char* sB = dsm;
+    unsigned char* sA = dsm + L::ST * L::BBYTES;
+    uint64_t* full = reinterpret_cast<uint64_t*>(sA + L::ST * L::ABYTES + L::kPad);
+    uint64_t* empty = full + L::ST;
+    uint64_t* done = empty + L::ST;
+    uint32_t* tslot = reinterpret_cast<uint32_t*>(done + 1);
+    volatile int* fail = reinterpret_cast<volatile int*>(tslot + 1);
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int tiles_x = (W + 15) >> 4, tiles_y = (H + 7) >> 3;
+    const long long ntiles = (long long)B * tiles_x * tiles_y;
+    const int ncb = STACK ? 1 : Cin / 128;
+    const int kx = blockIdx.x % 3;
+    const int cb = (blockIdx.x / 3) % ncb;
+    const int split = blockIdx.x / (3 * ncb);
+    const long long t_begin = ntiles * split / nsplit, t_end = ntiles * (split + 1) / nsplit;
+    constexpr uint32_t kIdesc = umma_idesc_bf16(128, N) | (1u << 15) | (1u << 16);  // A and B MN-major
+
+    if (warp == 1) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(smem_u32(tslot)),
+                     "r"(L::kCols));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n" ::);
+    }
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < L::ST; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], 1);
+        }
+        mbar_init(done, 1);
+        *fail = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;\n" ::);
+        asm volatile("prefetch.tensormap [%0];\n" ::"l"(reinterpret_cast<uint64_t>(&map_in)) : "memory");
+        asm volatile("prefetch.tensormap [%0];\n" ::"l"(reinterpret_cast<uint64_t>(&map_g)) : "memory");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *tslot;
+
+    if (warp == 0) {
+        if (lane == 0) {
+            // ------------------------------------------------------------ TMA producer
+            int i = 0;
+            bool ok = true;
+            for (long long t = t_begin; t < t_end && ok; ++t, ++i) {
+                const int s = i % L::ST;
+                if (i >= L::ST && !(ok = wait_or_fail(&empty[s], (uint32_t)(((i / L::ST) - 1) & 1), fail))) break;
+                const int tx = (int)(t % tiles_x);
+                const long long r = t / tiles_x;
+                const int ty = (int)(r % tiles_y), b = (int)(r / tiles_y);
+                mbar_expect_tx(&full[s], L::STAGE);
+                unsigned char* a = sA + s * L::ABYTES;
+                unsigned char* g = sB + s * L::BBYTES;
+                for (int j = 0; j < (STACK ? 1 : 2); ++j)
+                    tma_load_4d(a + j * L::HALO, &map_in, &full[s], cb * 128 + j * 64, tx * 16 + kx - 1, ty * 8 - 1, b);
+                for (int j = 0; j < L::NBB; ++j)
+                    tma_load_4d(g + j * 128 * L::SWBB, &map_g, &full[s], j * L::EB, tx * 16, ty * 8, b);
+            }
+            // wait for the last load issued into each stage
+            for (int s = 0; s < L::ST; ++s) {
+                const int k = i - 1 - ((i - 1 - s) % L::ST + L::ST) % L::ST;
+                if (k >= 0) wait_timed(&full[s], (uint32_t)((k / L::ST) & 1), nullptr);
+            }
+        }
+    } else if (warp == 1) {
+        if (lane == 0) {
+            // --------------------------------------------------------- MMA issuer
+            int i = 0;
+            bool ok = true;
+            for (long long t = t_begin; t < t_end; ++t, ++i) {
+                const int s = i % L::ST;
+                if (!(ok = wait_or_fail(&full[s], (uint32_t)((i / L::ST) & 1), fail))) break;
+                tc_fence_after();
+                const uint32_t a0 = smem_u32(sA + s * L::ABYTES), b0 = smem_u32(sB + s * L::BBYTES);
+                constexpr uint32_t lboA = STACK ? 16 * SWA : L::HALO;
+                constexpr uint32_t lboB = 128 * L::SWBB;
+                constexpr int kyPerAcc = STACK ? 128 / L::EA : 1;
+#pragma unroll
+                for (int acc = 0; acc < L::NACC; ++acc) {
+                    const uint32_t abase = a0 + (uint32_t)(acc * kyPerAcc * 16 * SWA);
+#pragma unroll
+                    for (int k = 0; k < 8; ++k)  // 128 pixels = 8 K16 steps of 16 pixel rows
+                        tc_mma(tmem + (uint32_t)(acc * N), umma_desc_mn<SWA>(abase + k * 16 * SWA, lboA),
+                               umma_desc_mn<L::SWBB>(b0 + k * 16 * L::SWBB, lboB), kIdesc,
+                               (i > 0 || k > 0) ? 1u : 0u);
+                }
+                tc_commit(&empty[s]);
+            }
+            (void)ok;
+            tc_commit(done);  // arrives once every MMA issued has completed
+        }
+    } else {
+        // ---------------------------------------------------------------- epilogue
+        const bool fin = wait_timed(done, 0, nullptr);
+        if (!fin) *fail = 1;
+        tc_fence_after();
+        const int qw = warp & 3;
+        const int m = qw * 32 + lane;
+        if (__all_sync(0xffffffffu, fin && !*fail) && t_end > t_begin) {
+            constexpr int kyPerAcc = STACK ? 128 / L::EA : 1;
+#pragma unroll 1
+            for (int acc = 0; acc < L::NACC; ++acc) {
+                const int ky = STACK ? acc * kyPerAcc + m / L::EA : acc;
+                const int ci = STACK ? m % L::EA : cb * 128 + m;
+                const bool valid = ky < 3;
+                float* drow = dw + ((long long)(3 * ky + kx) * Cin + ci) * Cout;
+                const uint32_t taddr = tmem + ((uint32_t)(qw * 32) << 16) + (uint32_t)(acc * N);
+#pragma unroll 1
+                for (int c0 = 0; c0 < N; c0 += 16) {
+                    uint32_t rr[16];
+                    tc_ld16(taddr + (uint32_t)c0, rr);
+                    asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
+                    if (valid) {
+#pragma unroll
+                        for (int j = 0; j < 4; ++j)
+                            atomicAdd(reinterpret_cast<float4*>(drow + c0 + 4 * j),
+                                      make_float4(__uint_as_float(rr[4 * j]), __uint_as_float(rr[4 * j + 1]),
+                                                  __uint_as_float(rr[4 * j + 2]), __uint_as_float(rr[4 * j + 3])));
+                    }
+                }
+            }
+        }
+    }
+
+    tc_fence_before();
+    __syncthreads();
+    if (threadIdx.x == 0 && *fail && status) atomicExch(status, 1);
+    if (warp == 1) {
+        __syncwarp();
+        tc_fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(L::kCols));
+    }
+}
+
 }  // namespace qldnn

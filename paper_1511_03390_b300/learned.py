@@ -106,7 +106,8 @@ class UNet:
     H and W must be multiples of 8. `conv` picks the kernel of the forward
     and data-gradient convolutions: "tma" (default; persistent TMA-fed
     tcgen05 kernel), "tcgen05" (gathering tcgen05 kernel) or "warp_mma"
-    (warp-level MMA); the weight gradient always uses the warp-level MMA."""
+    (warp-level MMA). The weight gradient runs on the TMA-fed tcgen05 kernel
+    unless "warp_mma" is chosen."""
 
     CONVS = ("tma", "tcgen05", "warp_mma")
 
@@ -230,7 +231,10 @@ class UNet:
         n = self.P[level] * cout
         gz = self.gz[:n]
         nn.relu_bwd(gy, y, n, gz)
-        nn.conv3x3_wgrad(x, gz, self.B, h, w, cin, cout, self.prm[name + ".w"]["g"])
+        if self.conv == "warp_mma":
+            nn.conv3x3_wgrad(x, gz, self.B, h, w, cin, cout, self.prm[name + ".w"]["g"])
+        else:
+            nn.conv3x3_wgrad_tma(x, gz, self.B, h, w, cin, cout, self.prm[name + ".w"]["g"], self.status)
         nn.bias_grad(gz, self.P[level], cout, self.prm[name + ".b"]["g"])
         if gx is not None:
             if self.conv != "warp_mma":

@@ -79,3 +79,53 @@ def test_tc_conv_data_gradient(kernel, B, H, W, Cin, Cout):
     ref = oracle.conv3x3_backward(xdummy, wr, gr)[0]
     bound = ACC * oracle.conv3x3_backward(xdummy, np.abs(wr), np.abs(gr))[0] + 1e-6
     close(din.cpu().numpy(), ref, bound, "tcgen05 data gradient")
+
+
+# The weight gradient sums over every pixel (up to ~4e4 products per entry
+# here, plus cross-CTA float atomics in no fixed order): FP32 accumulation
+# error of order sqrt(n) * 2^-24 * sum |x| |g|, bounded here by 1e-4 * sum |x| |g|.
+ACC_W = 1e-4
+
+
+def _abs_wgrad(x, g):
+    """sum over pixels of |x shifted by the tap| |g|: the scale of the
+    tolerance (not the reference), by one matrix product per tap."""
+    B, H, W, Cin = x.shape
+    xp = np.pad(np.abs(x), ((0, 0), (1, 1), (1, 1), (0, 0)))
+    ga = np.abs(g).reshape(-1, g.shape[3])
+    out = np.empty((3, 3, Cin, g.shape[3]))
+    for ky in range(3):
+        for kx in range(3):
+            out[ky, kx] = xp[:, ky:ky + H, kx:kx + W, :].reshape(-1, Cin).T @ ga
+    return out
+
+
+@pytest.mark.parametrize("B,H,W,Cin,Cout", [(2, 13, 21, 16, 32), (1, 9, 30, 32, 32), (2, 17, 15, 32, 64),
+                                            (1, 24, 20, 64, 64), (2, 11, 19, 64, 32), (1, 16, 24, 64, 128),
+                                            (1, 20, 18, 128, 128), (2, 9, 33, 256, 128), (1, 12, 16, 128, 64),
+                                            (1, 10, 12, 16, 128), (2, 128, 160, 16, 32), (1, 64, 208, 256, 32)])
+def test_tma_weight_gradient(B, H, W, Cin, Cout):
+    rng = np.random.default_rng(B * 1000 + H * W + Cin + Cout)
+    x, xr = bf16(rng.standard_normal((B, H, W, Cin)))
+    g, gr = bf16(rng.standard_normal((B, H, W, Cout)))
+    dw = torch.zeros(9 * Cin * Cout, dtype=torch.float32, device="cuda")
+    status = torch.zeros(1, dtype=torch.int32, device="cuda")
+    q.nn.conv3x3_wgrad_tma(x, g, B, H, W, Cin, Cout, dw, status)
+    torch.cuda.synchronize()
+    assert status.item() == 0
+    ref = oracle.conv3x3_backward(xr, np.zeros((3, 3, Cin, Cout)), gr)[1]
+    bnd = _abs_wgrad(xr, gr)
+    close(dw.cpu().numpy().reshape(3, 3, Cin, Cout), ref, ACC_W * bnd + 1e-6, "tcgen05 weight gradient")
+    # accumulates into dw: a second call doubles it
+    q.nn.conv3x3_wgrad_tma(x, g, B, H, W, Cin, Cout, dw, status)
+    torch.cuda.synchronize()
+    close(dw.cpu().numpy().reshape(3, 3, Cin, Cout), 2 * ref, 2 * ACC_W * bnd + 1e-6, "accumulated twice")
+
+
+def test_tma_weight_gradient_rejects_unsupported_shapes():
+    x = torch.zeros(4 * 4 * 48, dtype=torch.bfloat16, device="cuda")
+    g = torch.zeros(4 * 4 * 256, dtype=torch.bfloat16, device="cuda")
+    dw = torch.zeros(9 * 48 * 256, dtype=torch.float32, device="cuda")
+    for cin, cout in [(48, 32), (96, 64), (64, 256), (64, 48)]:
+        with pytest.raises(q.QLDError):
+            q.nn.conv3x3_wgrad_tma(x, g, 1, 4, 4, cin, cout, dw, None)
