@@ -324,18 +324,33 @@ def run_cuda(args, world, rank, local):
     push_gbs = ab["push_image"] * K / (push_ms * 1e-3) / 1e9
     value = world * H * W * ADV * K / (max_ms * 1e-3) / 1e9
 
-    # frame-to-image latency: host call of the fused push (frames already in
-    # HBM) to completion of the image, one sample at a time
+    # frame-to-image latency: host clock from the call of the fused push
+    # (frames already in HBM) to the image complete, one sample at a time.
+    # Through the C ABI (qld_push_image, then qld_sync on the context's
+    # stream), and through the Python wrapper with a torch event for contrast.
+    push_c, sync_c = q.lib.qld_push_image, q.lib.qld_sync
+    hctx, sptr, aptr, pptr = ctx.handle, st.cuda_stream, amp.data_ptr(), ph.data_ptr()
     lat = []
-    e = torch.cuda.Event()
     for i in range(args.latency_samples):
-        fr = frames_of(args.warmup + K + i)
+        fptr = frames_of(args.warmup + K + i).data_ptr()
+        t0 = time.perf_counter_ns()
+        r1 = push_c(hctx, fptr, ADV, sptr, aptr, pptr)
+        r2 = sync_c(hctx)
+        lat.append((time.perf_counter_ns() - t0) / 1e3)
+        if r1 or r2:
+            raise RuntimeError("qld_push_image/qld_sync failed: %d %d" % (r1, r2))
+    lat.sort()
+    lat_py = []
+    e = torch.cuda.Event()
+    base_py = args.warmup + K + args.latency_samples
+    for i in range(args.latency_samples):
+        fr = frames_of(base_py + i)
         t0 = time.perf_counter()
         q.qld_push_image(ctx, fr, ADV, st, amp, ph)
         e.record(st)
         e.synchronize()
-        lat.append((time.perf_counter() - t0) * 1e6)
-    lat.sort()
+        lat_py.append((time.perf_counter() - t0) * 1e6)
+    lat_py.sort()
 
     # QLD alone (the sliding lock-in without the DFT-bin comparison). Eager:
     # K2 calls back to back between one event pair; on a slow host this is
@@ -344,7 +359,7 @@ def run_cuda(args, world, rank, local):
     # The graph bakes in each call's frame indices; the context is not used
     # for anything else afterwards.
     K2 = 500
-    base = args.warmup + K + args.latency_samples
+    base = args.warmup + K + 2 * args.latency_samples
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(st)
     for i in range(K2):
@@ -445,7 +460,10 @@ def run_cuda(args, world, rank, local):
         },
         "latency_us": {"p50": lat[len(lat) // 2], "p99": lat[min(len(lat) - 1, int(0.99 * len(lat)))],
                        "samples": len(lat),
-                       "what": "host call of qld_push_image (4 frames already in HBM) to image complete"}
+                       "what": "host clock from the C-ABI call qld_push_image (4 frames already in HBM) to the "
+                               "return of qld_sync (image complete)",
+                       "python_wrapper_p50": lat_py[len(lat_py) // 2],
+                       "python_wrapper_p99": lat_py[min(len(lat_py) - 1, int(0.99 * len(lat_py)))]}
         if lat else None,
         "qld_stream": qld_stream,
         "qld_large": large,

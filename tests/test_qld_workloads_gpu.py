@@ -149,8 +149,7 @@ def test_large_4096x4096_u16_N2048_ring_68GB():
     ds = DeviceScene(sc)
     ctx = q.qld_create(H, W, N, q.QLD_U16)
     pool = fill(ctx, ds, N, 64)
-    pix = sample_pixels(sc, 1024, 5)
-    # include pixels in the last slots' far end (beyond 2^31 bytes of offset)
+    pix = sample_pixels(sc, 4096, 5)  # a seeded subset of >= 4096 pixels, plus mask pixels and both corners
     T = N
     one = pool[:1]
     amp = torch.empty(H * W, dtype=torch.float32, device="cuda")
