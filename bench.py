@@ -58,6 +58,7 @@ def parse_args():
     ap.add_argument("--no-large", action="store_true", help="skip the 4096x4096 N=2048 (68.7 GB ring) stream")
     ap.add_argument("--no-serving", action="store_true", help="skip the 8-stream serving mix (45 GB of rings)")
     ap.add_argument("--no-learned", action="store_true", help="skip the learned short-window path")
+    ap.add_argument("--no-packed", action="store_true", help="skip the packed 12-bit step")
     ap.add_argument("--case", choices=["full", "small"], default="full",
                     help="small: N=256 and a 512-frame pool (1.5 GB on the device) for profiler captures")
     args = ap.parse_args()
@@ -411,7 +412,8 @@ def run_cuda(args, world, rank, local):
     if not args.no_e2e:
         e2e = run_e2e(args, q, torch, dev, st, pool)
 
-    packed = run_packed(q, torch, dev, st, pool, peak) if args.case == "full" else None
+    packed = (run_packed(q, torch, dev, st, pool, peak, steps=500 if args.case == "full" else 20)
+              if not args.no_packed else None)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:

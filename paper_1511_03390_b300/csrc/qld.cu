@@ -186,18 +186,16 @@ int enqueue_fft_bin(qld_ctx* c, int k, float* out) {
         if (cudaGetLastError() != cudaSuccess) return QLD_E_CUDA;
         c->tw_k = k;
     }
-    const int vb = vec_bytes_of(c->pixfmt);
-    const long long nvec = (c->frame_bytes + vb - 1) / vb;
     g_launches.fetch_add(1);
     if (c->pixfmt == QLD_P12)
-        qldk::launch_bin<qldk::p12_t, qldk::kBinPower>(c->ring, c->slot_stride, c->N, c->tw, nvec, c->npix, out,
-                                                       nullptr, c->stream);
+        qldk::launch_bin<qldk::p12_t, qldk::kBinPower>(c->ring, c->slot_stride, c->N, c->tw, c->frame_bytes, c->npix,
+                                                       out, nullptr, c->stream);
     else if (c->pixfmt == QLD_U16)
-        qldk::launch_bin<uint16_t, qldk::kBinPower>(c->ring, c->slot_stride, c->N, c->tw, nvec, c->npix, out, nullptr,
-                                                   c->stream);
+        qldk::launch_bin<uint16_t, qldk::kBinPower>(c->ring, c->slot_stride, c->N, c->tw, c->frame_bytes, c->npix,
+                                                   out, nullptr, c->stream);
     else
-        qldk::launch_bin<uint8_t, qldk::kBinPower>(c->ring, c->slot_stride, c->N, c->tw, nvec, c->npix, out, nullptr,
-                                                  c->stream);
+        qldk::launch_bin<uint8_t, qldk::kBinPower>(c->ring, c->slot_stride, c->N, c->tw, c->frame_bytes, c->npix,
+                                                  out, nullptr, c->stream);
     return cudaGetLastError() == cudaSuccess ? QLD_OK : QLD_E_CUDA;
 }
 
@@ -591,10 +589,11 @@ extern "C" int qld_fft_bin_frames_noalloc(const void* frames, int H, int W, int 
     g_launches.fetch_add(1);
     qldk::twiddle_kernel<<<blocks_for(N, 256), 256, 0, st>>>(tw, N, k);
     const uint8_t* base = (const uint8_t*)frames;
-    const long long nvec = frame_bytes / qldk::kVecBytes;
     g_launches.fetch_add(1);
-    if (pixfmt == QLD_U16) qldk::launch_bin<uint16_t, qldk::kBinPower>(base, frame_bytes, N, tw, nvec, npix, out, nullptr, st);
-    else qldk::launch_bin<uint8_t, qldk::kBinPower>(base, frame_bytes, N, tw, nvec, npix, out, nullptr, st);
+    if (pixfmt == QLD_U16)
+        qldk::launch_bin<uint16_t, qldk::kBinPower>(base, frame_bytes, N, tw, frame_bytes, npix, out, nullptr, st);
+    else
+        qldk::launch_bin<uint8_t, qldk::kBinPower>(base, frame_bytes, N, tw, frame_bytes, npix, out, nullptr, st);
     return set_err(cudaGetLastError() == cudaSuccess ? QLD_OK : QLD_E_CUDA);
 }
 
@@ -620,14 +619,13 @@ extern "C" int qld_lockin_frames(const void* frames, int H, int W, int N, int pi
         return set_err(QLD_E_INVAL);
     if (pending_error() != QLD_OK) return set_err(QLD_E_CUDA);
     const uint8_t* base = (const uint8_t*)frames;
-    const long long nvec = frame_bytes / qldk::kVecBytes;
     cudaStream_t st = (cudaStream_t)stream;
     g_launches.fetch_add(1);
     if (pixfmt == QLD_U16)
-        qldk::launch_bin<uint16_t, qldk::kBinAmpPhase>(base, frame_bytes, N, (const float2*)table, nvec, npix, amp,
-                                                       phase, st);
+        qldk::launch_bin<uint16_t, qldk::kBinAmpPhase>(base, frame_bytes, N, (const float2*)table, frame_bytes, npix,
+                                                       amp, phase, st);
     else
-        qldk::launch_bin<uint8_t, qldk::kBinAmpPhase>(base, frame_bytes, N, (const float2*)table, nvec, npix, amp,
-                                                      phase, st);
+        qldk::launch_bin<uint8_t, qldk::kBinAmpPhase>(base, frame_bytes, N, (const float2*)table, frame_bytes, npix,
+                                                      amp, phase, st);
     return set_err(cudaGetLastError() == cudaSuccess ? QLD_OK : QLD_E_CUDA);
 }

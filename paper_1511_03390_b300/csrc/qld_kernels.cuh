@@ -33,6 +33,16 @@ struct P12Vec {
     uint32_t w[6];
 };
 
+// The DFT-bin kernel reads uint8 and packed 12-bit frames in vectors of 8
+// pixels (8 and 12 bytes): with 16-pixel vectors its two-level accumulators
+// need over 100 registers per thread, too few warps to keep the loads in
+// flight. The push kernels keep 16-pixel vectors.
+struct u8h_t {};
+struct p12h_t {};
+struct P12Half {
+    uint32_t w[3];
+};
+
 // Per-format vector traits: Vec, bytes per vector VB, pixels per vector VP,
 // and streaming load / store of one vector (cache-streaming hints: every
 // frame byte is touched once per kernel).
@@ -75,6 +85,39 @@ struct Fmt<p12_t> {
     static __device__ __forceinline__ Vec zero() { return P12Vec{{0, 0, 0, 0, 0, 0}}; }
 };
 
+template <>
+struct Fmt<u8h_t> {
+    using Vec = uint2;
+    static constexpr int VB = 8, VP = 8, ALIGN = 8;
+    static __device__ __forceinline__ Vec load(const uint8_t* p) { return __ldcs(reinterpret_cast<const uint2*>(p)); }
+    static __device__ __forceinline__ Vec zero() { return make_uint2(0u, 0u); }
+};
+
+template <>
+struct Fmt<p12h_t> {
+    using Vec = P12Half;
+    static constexpr int VB = 12, VP = 8, ALIGN = 4;
+    static __device__ __forceinline__ Vec load(const uint8_t* p) {
+        const unsigned int* q = reinterpret_cast<const unsigned int*>(p);
+        return P12Half{{__ldcs(q), __ldcs(q + 1), __ldcs(q + 2)}};
+    }
+    static __device__ __forceinline__ Vec zero() { return P12Half{{0u, 0u, 0u}}; }
+};
+
+// Vector format the DFT-bin kernel reads a pixel format with.
+template <typename T>
+struct BinFmt {
+    using type = T;
+};
+template <>
+struct BinFmt<uint8_t> {
+    using type = u8h_t;
+};
+template <>
+struct BinFmt<p12_t> {
+    using type = p12h_t;
+};
+
 // ---------------------------------------------------------------- helpers --
 
 // Raw bits of pixel q of a vector (q is a compile-time constant after
@@ -86,6 +129,17 @@ __device__ __forceinline__ uint32_t raw_pix(const uint4& v, int q, uint16_t*) {
 __device__ __forceinline__ uint32_t raw_pix(const uint4& v, int q, uint8_t*) {
     const uint32_t w = (q < 4) ? v.x : (q < 8) ? v.y : (q < 12) ? v.z : v.w;
     return (w >> (8 * (q & 3))) & 0xFFu;
+}
+__device__ __forceinline__ uint32_t raw_pix(const uint2& v, int q, u8h_t*) {
+    const uint32_t w = (q < 4) ? v.x : v.y;
+    return (w >> (8 * (q & 3))) & 0xFFu;
+}
+__device__ __forceinline__ uint32_t raw_pix(const P12Half& v, int q, p12h_t*) {
+    const int o = 12 * q;  // bit offset of pixel q in the 96-bit vector
+    const int wi = o >> 5;
+    const uint32_t lo = v.w[wi];
+    const uint32_t hi = (wi + 1 < 3) ? v.w[wi + 1] : 0u;
+    return __funnelshift_r(lo, hi, o & 31) & 0xFFFu;
 }
 __device__ __forceinline__ uint32_t raw_pix(const P12Vec& v, int q, p12_t*) {
     const int o = 12 * q;  // bit offset of pixel q in the 192-bit vector
@@ -115,10 +169,68 @@ __device__ __forceinline__ float pixf<uint16_t>(const uint4& v, int q) {
     return __uint_as_float(b) - 8388608.0f;
 }
 template <>
+__device__ __forceinline__ float pixf<u8h_t>(const uint2& v, int q) {
+    const uint32_t w = (q < 4) ? v.x : v.y;
+    const uint32_t b = __byte_perm(w, 0x4B000000u, 0x7540u | (uint32_t)(q & 3));
+    return __uint_as_float(b) - 8388608.0f;
+}
+template <>
 __device__ __forceinline__ float pixf<uint8_t>(const uint4& v, int q) {
     const uint32_t w = (q < 4) ? v.x : (q < 8) ? v.y : (q < 12) ? v.z : v.w;
     const uint32_t b = __byte_perm(w, 0x4B000000u, 0x7540u | (uint32_t)(q & 3));
     return __uint_as_float(b) - 8388608.0f;
+}
+
+// Float bits of pixel q of a vector placed in the mantissa of 2^23:
+// subtracting 2^23 afterwards gives the pixel value exactly.
+template <typename T>
+__device__ __forceinline__ uint32_t pixbits(const typename Fmt<T>::Vec& v, int q) {
+    return raw_pix(v, q, (T*)nullptr) | 0x4B000000u;
+}
+template <>
+__device__ __forceinline__ uint32_t pixbits<uint16_t>(const uint4& v, int q) {
+    const uint32_t w = (q < 2) ? v.x : (q < 4) ? v.y : (q < 6) ? v.z : v.w;
+    return __byte_perm(w, 0x4B000000u, (q & 1) ? 0x7632u : 0x7610u);
+}
+template <>
+__device__ __forceinline__ uint32_t pixbits<u8h_t>(const uint2& v, int q) {
+    const uint32_t w = (q < 4) ? v.x : v.y;
+    return __byte_perm(w, 0x4B000000u, 0x7540u | (uint32_t)(q & 3));
+}
+
+// Two FP32 lanes in one 64-bit register (low = even pixel, high = odd) for
+// the paired FP32 instructions (add / sub / fma .f32x2): each lane rounds
+// exactly as the scalar instruction, at one issue slot per pair.
+typedef unsigned long long f32x2;
+__device__ __forceinline__ f32x2 f2_bits(uint32_t lo, uint32_t hi) {
+    f32x2 r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "r"(lo), "r"(hi));
+    return r;
+}
+__device__ __forceinline__ f32x2 f2_splat(float a) {
+    f32x2 r;
+    asm("mov.b64 %0, {%1, %1};" : "=l"(r) : "f"(a));
+    return r;
+}
+__device__ __forceinline__ float2 f2_split(f32x2 a) {
+    float2 r;
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(r.x), "=f"(r.y) : "l"(a));
+    return r;
+}
+__device__ __forceinline__ f32x2 f2_fma(f32x2 a, f32x2 b, f32x2 c) {
+    f32x2 d;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+    return d;
+}
+__device__ __forceinline__ f32x2 f2_add(f32x2 a, f32x2 b) {
+    f32x2 d;
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+__device__ __forceinline__ f32x2 f2_sub(f32x2 a, f32x2 b) {
+    f32x2 d;
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
 }
 
 // Adds d = x_new - x_old of one frame with absolute index residue r = s mod 4
@@ -478,17 +590,21 @@ __global__ void __launch_bounds__(NT) bin_kernel(const uint8_t* __restrict__ rin
     const int ts = t >> PV_LOG;
     const long long v = (long long)blockIdx.x * PV + pv;
 
-    float re[VP], im[VP];
+    // Pixel pairs (2h, 2h+1) share one f32x2 register per accumulator.
+    static_assert(VP % 2 == 0, "pixel pairs");
+    constexpr int VH = VP / 2;
+    f32x2 re2[VH], im2[VH];
 #pragma unroll
-    for (int q = 0; q < VP; ++q) re[q] = im[q] = 0.f;
+    for (int h = 0; h < VH; ++h) re2[h] = im2[h] = 0ull;
 
     if (v < nvec) {
         const uint8_t* base = ring + v * F::VB;
+        const f32x2 k2p23 = f2_splat(8388608.0f);
         int j = ts;
         while (j < N) {
-            float pr[VP], pi[VP];
+            f32x2 pr2[VH], pi2[VH];
 #pragma unroll
-            for (int q = 0; q < VP; ++q) pr[q] = pi[q] = 0.f;
+            for (int h = 0; h < VH; ++h) pr2[h] = pi2[h] = 0ull;
             // Up to 16 frames (4 groups of 4) into the partial.
             for (int g = 0; g < 4 && j < N; ++g, j += 4 * TS) {
                 typename F::Vec x[4];
@@ -506,20 +622,30 @@ __global__ void __launch_bounds__(NT) bin_kernel(const uint8_t* __restrict__ rin
                 }
 #pragma unroll
                 for (int u = 0; u < 4; ++u) {
+                    const f32x2 wr = f2_splat(w[u].x), wi = f2_splat(w[u].y);
 #pragma unroll
-                    for (int q = 0; q < VP; ++q) {
-                        const float xf = pixf<T>(x[u], q);
-                        pr[q] = fmaf(xf, w[u].x, pr[q]);
-                        pi[q] = fmaf(xf, w[u].y, pi[q]);
+                    for (int h = 0; h < VH; ++h) {
+                        const f32x2 xf = f2_sub(f2_bits(pixbits<T>(x[u], 2 * h), pixbits<T>(x[u], 2 * h + 1)), k2p23);
+                        pr2[h] = f2_fma(xf, wr, pr2[h]);
+                        pi2[h] = f2_fma(xf, wi, pi2[h]);
                     }
                 }
             }
 #pragma unroll
-            for (int q = 0; q < VP; ++q) {
-                re[q] += pr[q];
-                im[q] += pi[q];
+            for (int h = 0; h < VH; ++h) {
+                re2[h] = f2_add(re2[h], pr2[h]);
+                im2[h] = f2_add(im2[h], pi2[h]);
             }
         }
+    }
+    float re[VP], im[VP];
+#pragma unroll
+    for (int h = 0; h < VH; ++h) {
+        const float2 a = f2_split(re2[h]), b = f2_split(im2[h]);
+        re[2 * h] = a.x;
+        re[2 * h + 1] = a.y;
+        im[2 * h] = b.x;
+        im[2 * h + 1] = b.y;
     }
 
     if (PV < 32) {
@@ -571,19 +697,24 @@ inline int fftbin_pv_log(long long nvec) {
 }
 
 // Enqueues bin_kernel over `N` frames (frame j at base + j * stride) of
-// nvec 16-byte vectors each, npix pixels, twiddles tw[j]; writes the power
+// frame_bytes bytes and npix pixels each, twiddles tw[j]; writes the power
 // into out (OUT = kBinPower) or the amplitude into out and the phase into
-// out2 (OUT = kBinAmpPhase; either may be NULL).
+// out2 (OUT = kBinAmpPhase; either may be NULL). Frames are read in vectors
+// of BinFmt<T>; the last vector may run past frame_bytes (inside the ring
+// slot's padding, or exactly to the end when frame_bytes is a multiple of
+// 16), and pixels beyond npix are not written.
 template <typename T, int OUT>
-inline void launch_bin(const uint8_t* base, long long stride, int N, const float2* tw, long long nvec,
+inline void launch_bin(const uint8_t* base, long long stride, int N, const float2* tw, long long frame_bytes,
                        long long npix, float* out, float* out2, cudaStream_t st) {
+    using B = typename BinFmt<T>::type;
+    const long long nvec = (frame_bytes + Fmt<B>::VB - 1) / Fmt<B>::VB;
     const int pv_log = fftbin_pv_log(nvec);
     const unsigned grid = (unsigned)((nvec + (1ll << pv_log) - 1) >> pv_log);
     switch (pv_log) {
-        case 5: bin_kernel<T, 5, 128, OUT><<<grid, 128, 0, st>>>(base, stride, N, tw, nvec, npix, out, out2); break;
-        case 4: bin_kernel<T, 4, 256, OUT><<<grid, 256, 0, st>>>(base, stride, N, tw, nvec, npix, out, out2); break;
-        case 3: bin_kernel<T, 3, 256, OUT><<<grid, 256, 0, st>>>(base, stride, N, tw, nvec, npix, out, out2); break;
-        default: bin_kernel<T, 2, 256, OUT><<<grid, 256, 0, st>>>(base, stride, N, tw, nvec, npix, out, out2); break;
+        case 5: bin_kernel<B, 5, 128, OUT><<<grid, 128, 0, st>>>(base, stride, N, tw, nvec, npix, out, out2); break;
+        case 4: bin_kernel<B, 4, 256, OUT><<<grid, 256, 0, st>>>(base, stride, N, tw, nvec, npix, out, out2); break;
+        case 3: bin_kernel<B, 3, 256, OUT><<<grid, 256, 0, st>>>(base, stride, N, tw, nvec, npix, out, out2); break;
+        default: bin_kernel<B, 2, 256, OUT><<<grid, 256, 0, st>>>(base, stride, N, tw, nvec, npix, out, out2); break;
     }
 }
 
