@@ -292,6 +292,11 @@ int qldnn_conv3x3_wgrad(const void* in, const void* g, int B, int H, int W, int 
                         void* stream);
 int qldnn_bias_grad(const void* g, long long P, int C, float* db, void* stream);
 int qldnn_relu_bwd(const float* g, const void* act, long long n, void* out_bf16, void* stream);
+/* qldnn_relu_bwd and qldnn_bias_grad in one pass over [P][C] (C % 8 == 0,
+ * C <= 256, pointers 16-byte aligned): out = bf16(g * (act > 0)), db [C] +=
+ * the per-channel sums of those bf16 values. */
+int qldnn_relu_bwd_bias(const float* g, const void* act, long long P, int C, void* out_bf16, float* db,
+                        void* stream);
 int qldnn_avgpool2(const void* in, int B, int H, int W, int C, void* out, void* stream);
 int qldnn_avgpool2_bwd(const float* g, int B, int H, int W, int C, float* out, int accumulate, void* stream);
 int qldnn_upsample2(const void* in, int B, int h, int w, int C, void* out, void* stream);

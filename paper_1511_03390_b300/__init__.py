@@ -67,6 +67,7 @@ _SIGS = {
     "qldnn_conv3x3_wgrad": ([_p, _p, _i, _i, _i, _i, _i, _p, _p], _i),
     "qldnn_bias_grad": ([_p, _ll, _i, _p, _p], _i),
     "qldnn_relu_bwd": ([_p, _p, _ll, _p, _p], _i),
+    "qldnn_relu_bwd_bias": ([_p, _p, _ll, _i, _p, _p, _p], _i),
     "qldnn_avgpool2": ([_p, _i, _i, _i, _i, _p, _p], _i),
     "qldnn_avgpool2_bwd": ([_p, _i, _i, _i, _i, _p, _i, _p], _i),
     "qldnn_upsample2": ([_p, _i, _i, _i, _i, _p, _p], _i),

@@ -334,6 +334,188 @@ __global__ void head_fwd_v8_kernel(const uint4* __restrict__ in, const float* __
     }
 }
 
+// ---- 16-byte versions of the backward glue kernels (4 f32 / 8 bf16 channels
+// per thread), used whenever the channel counts allow.
+__global__ void relu_bwd_v4_kernel(const float4* __restrict__ g, const uint2* __restrict__ act, long long n4,
+                                   uint2* __restrict__ out) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n4; i += (long long)gridDim.x * blockDim.x) {
+        const float4 gv = __ldg(g + i);
+        const uint2 av = __ldg(act + i);
+        const float2 a01 = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&av.x));
+        const float2 a23 = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&av.y));
+        const __nv_bfloat162 o01 = __floats2bfloat162_rn(a01.x > 0.f ? gv.x : 0.f, a01.y > 0.f ? gv.y : 0.f);
+        const __nv_bfloat162 o23 = __floats2bfloat162_rn(a23.x > 0.f ? gv.z : 0.f, a23.y > 0.f ? gv.w : 0.f);
+        out[i] = make_uint2(*reinterpret_cast<const uint32_t*>(&o01), *reinterpret_cast<const uint32_t*>(&o23));
+    }
+}
+
+__global__ void avgpool2_bwd_v4_kernel(const float4* __restrict__ g, int B, int H, int W, int C4,
+                                       float4* __restrict__ out, int accumulate) {
+    const long long n = (long long)B * H * W * C4;
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x) {
+        const int c = (int)(e % C4);
+        long long r = e / C4;
+        const int x = (int)(r % W);
+        r /= W;
+        const int y = (int)(r % H);
+        const long long b = r / H;
+        const float4 gv = __ldg(g + ((b * (H / 2) + y / 2) * (W / 2) + x / 2) * C4 + c);
+        float4 v = make_float4(0.25f * gv.x, 0.25f * gv.y, 0.25f * gv.z, 0.25f * gv.w);
+        if (accumulate) {
+            const float4 o = out[e];
+            v = make_float4(o.x + v.x, o.y + v.y, o.z + v.z, o.w + v.w);
+        }
+        out[e] = v;
+    }
+}
+
+__global__ void upsample2_bwd_v4_kernel(const float4* __restrict__ g, int B, int h, int w, int C4,
+                                        float4* __restrict__ out) {
+    const long long n = (long long)B * h * w * C4;
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x) {
+        const int c = (int)(e % C4);
+        long long r = e / C4;
+        const int x = (int)(r % w);
+        r /= w;
+        const int y = (int)(r % h);
+        const long long b = r / h;
+        const long long base = ((b * 2 * h + 2 * y) * (2 * w) + 2 * x) * C4 + c;
+        const long long row = (long long)2 * w * C4;
+        const float4 a = __ldg(g + base), b1 = __ldg(g + base + C4), c1 = __ldg(g + base + row),
+                     d = __ldg(g + base + row + C4);
+        out[e] = make_float4(a.x + b1.x + c1.x + d.x, a.y + b1.y + c1.y + d.y, a.z + b1.z + c1.z + d.z,
+                             a.w + b1.w + c1.w + d.w);
+    }
+}
+
+__global__ void split_v4_kernel(const float4* __restrict__ g, long long P, int Ca4, int Cb4, float4* __restrict__ ga,
+                                float4* __restrict__ gb, int accumulate_b) {
+    const int C4 = Ca4 + Cb4;
+    const long long n = P * C4;
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x) {
+        const long long p = e / C4;
+        const int c = (int)(e - p * C4);
+        const float4 v = __ldg(g + e);
+        if (c < Ca4) {
+            ga[p * Ca4 + c] = v;
+        } else {
+            float4* d = gb + p * Cb4 + (c - Ca4);
+            if (accumulate_b) {
+                const float4 o = *d;
+                *d = make_float4(o.x + v.x, o.y + v.y, o.z + v.z, o.w + v.w);
+            } else {
+                *d = v;
+            }
+        }
+    }
+}
+
+// db[c] += sum over pixels of g[p][c] (bf16), C % 8 == 0, C <= 256: each
+// thread keeps 8 channel sums in registers over a strided range of pixels,
+// the block adds them up in shared memory, then one atomic per channel per
+// block (a grid of a few hundred blocks).
+__global__ void bias_grad_v8_kernel(const uint4* __restrict__ g, long long P, int C, float* __restrict__ db) {
+    __shared__ float sacc[256];
+    const int G8 = C / 8;
+    const int lanes = 256 / G8;
+    for (int c = threadIdx.x; c < C; c += blockDim.x) sacc[c] = 0.f;
+    __syncthreads();
+    if ((int)threadIdx.x < lanes * G8) {
+        const int gi = threadIdx.x % G8;
+        const int l = threadIdx.x / G8;
+        float acc[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+        for (long long p = (long long)blockIdx.x * lanes + l; p < P; p += (long long)gridDim.x * lanes) {
+            float f[8];
+            unpack8(__ldg(g + p * G8 + gi), f);
+#pragma unroll
+            for (int j = 0; j < 8; ++j) acc[j] += f[j];
+        }
+#pragma unroll
+        for (int j = 0; j < 8; ++j) atomicAdd(&sacc[8 * gi + j], acc[j]);
+    }
+    __syncthreads();
+    for (int c = threadIdx.x; c < C; c += blockDim.x) atomicAdd(&db[c], sacc[c]);
+}
+
+// ReLU backward fused with the bias gradient: out[p][c] = bf16(act > 0 ? g : 0)
+// and db[c] += sum over pixels of that bf16 value (C % 8 == 0, C <= 256);
+// the reduction is that of bias_grad_v8_kernel.
+__global__ void relu_bwd_bias_v8_kernel(const float4* __restrict__ g, const uint4* __restrict__ act, long long P,
+                                        int C, uint4* __restrict__ out, float* __restrict__ db) {
+    __shared__ float sacc[256];
+    const int G8 = C / 8;
+    const int lanes = 256 / G8;
+    for (int c = threadIdx.x; c < C; c += blockDim.x) sacc[c] = 0.f;
+    __syncthreads();
+    if ((int)threadIdx.x < lanes * G8) {
+        const int gi = threadIdx.x % G8;
+        const int l = threadIdx.x / G8;
+        float acc[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+        for (long long p = (long long)blockIdx.x * lanes + l; p < P; p += (long long)gridDim.x * lanes) {
+            const long long e = p * G8 + gi;
+            const float4 g0 = __ldg(g + 2 * e), g1 = __ldg(g + 2 * e + 1);
+            float a[8];
+            unpack8(__ldg(act + e), a);
+            const float gv[8] = {g0.x, g0.y, g0.z, g0.w, g1.x, g1.y, g1.z, g1.w};
+            float o[8];
+#pragma unroll
+            for (int j = 0; j < 8; ++j) o[j] = a[j] > 0.f ? gv[j] : 0.f;
+            const uint4 q = pack8(o);
+            out[e] = q;
+            float r[8];
+            unpack8(q, r);  // the bias gradient sums the stored (bf16) values
+#pragma unroll
+            for (int j = 0; j < 8; ++j) acc[j] += r[j];
+        }
+#pragma unroll
+        for (int j = 0; j < 8; ++j) atomicAdd(&sacc[8 * gi + j], acc[j]);
+    }
+    __syncthreads();
+    for (int c = threadIdx.x; c < C; c += blockDim.x) atomicAdd(&db[c], sacc[c]);
+}
+
+// head backward for CT channels (CT % 8 == 0): one pixel per thread, the
+// weight-gradient partials in registers, reduced across the warp with
+// shuffles, then per block in shared memory, then one atomic per channel.
+template <int CT>
+__global__ void head_bwd_v8_kernel(const uint4* __restrict__ in, const float* __restrict__ g,
+                                   const float* __restrict__ w, long long P, float4* __restrict__ din,
+                                   float* __restrict__ dw, float* __restrict__ db) {
+    __shared__ float sdw[CT + 1];
+    for (int c = threadIdx.x; c <= CT; c += blockDim.x) sdw[c] = 0.f;
+    __syncthreads();
+    float acc[CT];
+#pragma unroll
+    for (int c = 0; c < CT; ++c) acc[c] = 0.f;
+    float pdb = 0.f;
+    for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < P; p += (long long)gridDim.x * blockDim.x) {
+        const float gp = __ldg(g + p);
+        pdb += gp;
+#pragma unroll
+        for (int q = 0; q < CT / 8; ++q) {
+            float f[8];
+            unpack8(__ldg(in + p * (CT / 8) + q), f);
+#pragma unroll
+            for (int j = 0; j < 8; ++j) acc[8 * q + j] = fmaf(f[j], gp, acc[8 * q + j]);
+        }
+#pragma unroll
+        for (int q = 0; q < CT / 4; ++q)
+            din[p * (CT / 4) + q] = make_float4(gp * __ldg(w + 4 * q), gp * __ldg(w + 4 * q + 1),
+                                                gp * __ldg(w + 4 * q + 2), gp * __ldg(w + 4 * q + 3));
+    }
+#pragma unroll
+    for (int c = 0; c < CT; ++c) {
+        float v = acc[c];
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        if ((threadIdx.x & 31) == 0) atomicAdd(&sdw[c], v);
+    }
+    for (int o = 16; o > 0; o >>= 1) pdb += __shfl_xor_sync(0xffffffffu, pdb, o);
+    if ((threadIdx.x & 31) == 0) atomicAdd(&sdw[CT], pdb);
+    __syncthreads();
+    for (int c = threadIdx.x; c < CT; c += blockDim.x) atomicAdd(&dw[c], sdw[c]);
+    if (threadIdx.x == 0) atomicAdd(db, sdw[CT]);
+}
+
 __global__ void pack_input_kernel(const int32_t* __restrict__ S, const int32_t* __restrict__ C, long long n,
                                   float scale, __nv_bfloat16* __restrict__ out, float* __restrict__ baseline) {
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
@@ -552,14 +734,41 @@ int qldnn_conv3x3_dgrad(const void* g, const void* w, int B, int H, int W, int C
 
 int qldnn_bias_grad(const void* g, long long P, int C, float* db, void* stream) {
     if (!g || !db || C < 1 || C > 256) return set_err(QLD_E_INVAL);
-    bias_grad_kernel<<<grid_for(P / (256 / C) + 1), 256, 0, (cudaStream_t)stream>>>((const __nv_bfloat16*)g, P, C, db);
+    if (C % 8 == 0 && al(g, 16)) {
+        const long long rows_per_block = 256 / (C / 8);
+        long long nb = (P + rows_per_block - 1) / rows_per_block;
+        if (nb > 296) nb = 296;
+        if (nb < 1) nb = 1;
+        bias_grad_v8_kernel<<<(unsigned)nb, 256, 0, (cudaStream_t)stream>>>((const uint4*)g, P, C, db);
+    } else {
+        bias_grad_kernel<<<grid_for(P / (256 / C) + 1), 256, 0, (cudaStream_t)stream>>>((const __nv_bfloat16*)g, P,
+                                                                                        C, db);
+    }
     return launched(1);
 }
 
 int qldnn_relu_bwd(const float* g, const void* act, long long n, void* out_bf16, void* stream) {
     if (!g || !act || !out_bf16 || n < 0) return set_err(QLD_E_INVAL);
-    relu_bwd_kernel<<<grid_for(n), 256, 0, (cudaStream_t)stream>>>(g, (const __nv_bfloat16*)act, n,
-                                                                     (__nv_bfloat16*)out_bf16);
+    if (n % 4 == 0 && al(g, 16) && al(act, 8) && al(out_bf16, 8))
+        relu_bwd_v4_kernel<<<grid_for(n / 4), 256, 0, (cudaStream_t)stream>>>((const float4*)g, (const uint2*)act,
+                                                                               n / 4, (uint2*)out_bf16);
+    else
+        relu_bwd_kernel<<<grid_for(n), 256, 0, (cudaStream_t)stream>>>(g, (const __nv_bfloat16*)act, n,
+                                                                         (__nv_bfloat16*)out_bf16);
+    return launched(1);
+}
+
+int qldnn_relu_bwd_bias(const float* g, const void* act, long long P, int C, void* out_bf16, float* db,
+                        void* stream) {
+    if (!g || !act || !out_bf16 || !db || P < 0 || C < 8 || C > 256 || C % 8 || !al(g, 16) || !al(act, 16) ||
+        !al(out_bf16, 16))
+        return set_err(QLD_E_INVAL);
+    const long long rows_per_block = 256 / (C / 8);
+    long long nb = (P + rows_per_block - 1) / rows_per_block;
+    if (nb > 296) nb = 296;
+    if (nb < 1) nb = 1;
+    relu_bwd_bias_v8_kernel<<<(unsigned)nb, 256, 0, (cudaStream_t)stream>>>((const float4*)g, (const uint4*)act, P, C,
+                                                                             (uint4*)out_bf16, db);
     return launched(1);
 }
 
@@ -576,8 +785,12 @@ int qldnn_avgpool2(const void* in, int B, int H, int W, int C, void* out, void* 
 
 int qldnn_avgpool2_bwd(const float* g, int B, int H, int W, int C, float* out, int accumulate, void* stream) {
     if (!g || !out || H % 2 || W % 2) return set_err(QLD_E_INVAL);
-    avgpool2_bwd_kernel<<<grid_for((long long)B * H * W * C), 256, 0, (cudaStream_t)stream>>>(g, B, H, W, C, out,
-                                                                                               accumulate);
+    if (C % 4 == 0 && al(g, 16) && al(out, 16))
+        avgpool2_bwd_v4_kernel<<<grid_for((long long)B * H * W * C / 4), 256, 0, (cudaStream_t)stream>>>(
+            (const float4*)g, B, H, W, C / 4, (float4*)out, accumulate);
+    else
+        avgpool2_bwd_kernel<<<grid_for((long long)B * H * W * C), 256, 0, (cudaStream_t)stream>>>(g, B, H, W, C, out,
+                                                                                                   accumulate);
     return launched(1);
 }
 
@@ -594,7 +807,11 @@ int qldnn_upsample2(const void* in, int B, int h, int w, int C, void* out, void*
 
 int qldnn_upsample2_bwd(const float* g, int B, int h, int w, int C, float* out, void* stream) {
     if (!g || !out) return set_err(QLD_E_INVAL);
-    upsample2_bwd_kernel<<<grid_for((long long)B * h * w * C), 256, 0, (cudaStream_t)stream>>>(g, B, h, w, C, out);
+    if (C % 4 == 0 && al(g, 16) && al(out, 16))
+        upsample2_bwd_v4_kernel<<<grid_for((long long)B * h * w * C / 4), 256, 0, (cudaStream_t)stream>>>(
+            (const float4*)g, B, h, w, C / 4, (float4*)out);
+    else
+        upsample2_bwd_kernel<<<grid_for((long long)B * h * w * C), 256, 0, (cudaStream_t)stream>>>(g, B, h, w, C, out);
     return launched(1);
 }
 
@@ -620,7 +837,11 @@ int qldnn_upsample_concat(const void* u, int Cu, const void* e, int Ce, int B, i
 
 int qldnn_split(const float* g, long long P, int Ca, int Cb, float* ga, float* gb, int accumulate_b, void* stream) {
     if (!g || !ga || !gb) return set_err(QLD_E_INVAL);
-    split_kernel<<<grid_for(P * (Ca + Cb)), 256, 0, (cudaStream_t)stream>>>(g, P, Ca, Cb, ga, gb, accumulate_b);
+    if (Ca % 4 == 0 && Cb % 4 == 0 && al(g, 16) && al(ga, 16) && al(gb, 16))
+        split_v4_kernel<<<grid_for(P * (Ca + Cb) / 4), 256, 0, (cudaStream_t)stream>>>(
+            (const float4*)g, P, Ca / 4, Cb / 4, (float4*)ga, (float4*)gb, accumulate_b);
+    else
+        split_kernel<<<grid_for(P * (Ca + Cb)), 256, 0, (cudaStream_t)stream>>>(g, P, Ca, Cb, ga, gb, accumulate_b);
     return launched(1);
 }
 
@@ -636,7 +857,19 @@ int qldnn_head(const void* in, const float* w, const float* b, long long P, int 
 int qldnn_head_bwd(const void* in, const float* g, const float* w, long long P, int C, float* din, float* dw,
                    float* db, void* stream) {
     if (!in || !g || !w || !din || !dw || !db || C > 256) return set_err(QLD_E_INVAL);
-    head_bwd_kernel<<<grid_for(P), 256, 0, (cudaStream_t)stream>>>((const __nv_bfloat16*)in, g, w, P, C, din, dw, db);
+    const bool v8 = al(in, 16) && al(din, 16);
+    long long nb = (P + 255) / 256;
+    if (nb > 296) nb = 296;
+    if (nb < 1) nb = 1;
+    if (v8 && C == 32)
+        head_bwd_v8_kernel<32><<<(unsigned)nb, 256, 0, (cudaStream_t)stream>>>((const uint4*)in, g, w, P, (float4*)din,
+                                                                               dw, db);
+    else if (v8 && C == 16)
+        head_bwd_v8_kernel<16><<<(unsigned)nb, 256, 0, (cudaStream_t)stream>>>((const uint4*)in, g, w, P, (float4*)din,
+                                                                               dw, db);
+    else
+        head_bwd_kernel<<<grid_for(P), 256, 0, (cudaStream_t)stream>>>((const __nv_bfloat16*)in, g, w, P, C, din, dw,
+                                                                      db);
     return launched(1);
 }
 

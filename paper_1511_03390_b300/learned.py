@@ -230,12 +230,11 @@ class UNet:
         h, w = self.dims[level]
         n = self.P[level] * cout
         gz = self.gz[:n]
-        nn.relu_bwd(gy, y, n, gz)
+        nn.relu_bwd_bias(gy, y, self.P[level], cout, gz, self.prm[name + ".b"]["g"])
         if self.conv == "warp_mma":
             nn.conv3x3_wgrad(x, gz, self.B, h, w, cin, cout, self.prm[name + ".w"]["g"])
         else:
             nn.conv3x3_wgrad_tma(x, gz, self.B, h, w, cin, cout, self.prm[name + ".w"]["g"], self.status)
-        nn.bias_grad(gz, self.P[level], cout, self.prm[name + ".b"]["g"])
         if gx is not None:
             if self.conv != "warp_mma":
                 fn = nn.conv3x3_fwd_tma if self.conv == "tma" else nn.conv3x3_fwd_tc

@@ -86,7 +86,7 @@ def test_conv_weight_gradient(B, H, W, Cin, Cout):
     close(db.cpu().numpy(), refb, ACC * bndb + 1e-6, "bias gradient")
 
 
-@pytest.mark.parametrize("C", [16, 12], ids=["8-channel vectors", "scalar"])
+@pytest.mark.parametrize("C", [16, 32, 12], ids=["8-channel vectors", "32 channels", "scalar"])
 def test_small_layers_against_numpy(C):
     rng = np.random.default_rng(7)
     B, H, W = 2, 6, 10
@@ -168,3 +168,25 @@ def test_upsample_concat_matches_upsample_then_concat():
     close(out.float().cpu().numpy(), want, 0, "upsample_concat")
     with pytest.raises(q.QLDError):
         q.nn.upsample_concat(u, 12, e, Ce, B, h, w, out)
+
+
+@pytest.mark.parametrize("P,C", [(1000, 32), (333, 96), (4096, 256)])
+def test_relu_bwd_bias_matches_the_separate_kernels(P, C):
+    """The fused ReLU backward + bias gradient: the masked bf16 gradient is
+    bit-identical to qldnn_relu_bwd, the bias gradient is the per-channel sum
+    of those bf16 values (FP32 accumulation bound)."""
+    rng = np.random.default_rng(P + C)
+    g = torch.from_numpy(rng.standard_normal((P, C)).astype(np.float32)).cuda()
+    act, _ = bf16(rng.standard_normal((P, C)))
+    out_ref = torch.empty((P, C), dtype=torch.bfloat16, device="cuda")
+    q.nn.relu_bwd(g, act, P * C, out_ref)
+    out = torch.empty_like(out_ref)
+    db = torch.full((C,), 0.5, dtype=torch.float32, device="cuda")  # accumulates into db
+    q.nn.relu_bwd_bias(g, act, P, C, out, db)
+    torch.cuda.synchronize()
+    assert torch.equal(out, out_ref)
+    o = out_ref.float().cpu().numpy().astype(np.float64)
+    want = o.sum(axis=0) + 0.5
+    close(db.cpu().numpy(), want, ACC * np.abs(o).sum(axis=0) + 1e-6, "fused bias gradient")
+    with pytest.raises(q.QLDError):
+        q.nn.relu_bwd_bias(g, act, P, 12, out, db)
