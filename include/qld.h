@@ -341,6 +341,14 @@ int qldnn_conv3x3_fwd_tc2(const void* in, const void* wk, const float* bias, int
  * overlaps the next tile's MMAs. Launches one CTA per SM. */
 int qldnn_conv3x3_fwd_tma(const void* in, const void* wk, const float* bias, int B, int H, int W, int Cin, int Cout,
                           int relu, void* out_bf16, float* out_f32, int* status, void* stream);
+/* The same with the kernel variant chosen by the caller: qldnn_conv3x3_fwd_tma
+ * keeps the weights resident in shared memory when 9 Cin Cout bf16 fit beside
+ * two halo stages (loaded once per CTA, only the halos streamed) and streams
+ * them per tile otherwise; force_stream != 0 always streams them (tests and
+ * measurements of both variants). */
+int qldnn_conv3x3_fwd_tma_mode(const void* in, const void* wk, const float* bias, int B, int H, int W, int Cin,
+                               int Cout, int relu, void* out_bf16, float* out_f32, int* status, int force_stream,
+                               void* stream);
 /* Weight gradient of the 3x3 convolution on the tensor cores: dw [9][Cin][Cout]
  * f32 += sum over pixels of in (shifted by the tap) x g, in [B][H][W][Cin]
  * and g [B][H][W][Cout] bf16 (the caller zeroes dw; 16-byte aligned). Cin is

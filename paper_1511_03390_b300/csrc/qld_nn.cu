@@ -590,7 +590,7 @@ int sm_count(int dev) {
 
 template <int N, int SWB>
 int launch_tma(const void* in, const void* wk, const float* bias, int B, int H, int W, int Cin, int Cout, int relu,
-               __nv_bfloat16* ob, float* of, int* status, cudaStream_t st) {
+               __nv_bfloat16* ob, float* of, int* status, cudaStream_t st, bool force_stream) {
     using L = qldnn::TmaConv<N, SWB>;
     EncodeTiledFn enc = encode_tiled();
     int dev = 0;
@@ -615,6 +615,24 @@ int launch_tma(const void* in, const void* wk, const float* bias, int B, int H, 
             CU_TENSOR_MAP_INTERLEAVE_NONE, sw, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
         return set_err(QLD_E_CUDA);
+    const long long ntiles = (long long)B * ((H + 7) / 8) * ((W + 15) / 16);
+    const unsigned grid = (unsigned)(ntiles < nsm ? ntiles : nsm);
+    // weights resident in shared memory when they fit beside two or more halo stages
+    using R = qldnn::TmaConvRes<N, SWB>;
+    int sa = 0;
+    while (sa < R::kMaxSA && R::smem(sa + 1, Cin) <= 232448) ++sa;
+    if (sa >= 2 && !force_stream) {
+        static std::atomic<unsigned long long> attr_res{0};
+        if (dev < 64 && !(attr_res.load() >> dev & 1ull)) {
+            if (cudaFuncSetAttribute(qldnn::conv3x3_fwd_tma_wres_kernel<N, SWB>,
+                                     cudaFuncAttributeMaxDynamicSharedMemorySize, 232448) != cudaSuccess)
+                return set_err(QLD_E_CUDA);
+            attr_res.fetch_or(1ull << dev);
+        }
+        qldnn::conv3x3_fwd_tma_wres_kernel<N, SWB><<<grid, 192, (size_t)R::smem(sa, Cin), st>>>(
+            mi, mw, bias, B, H, W, Cin, Cout, relu, ob, of, status, sa);
+        return launched(1);
+    }
     static std::atomic<unsigned long long> attr_done{0};  // per instantiation, one bit per device
     if (dev < 64 && !(attr_done.load() >> dev & 1ull)) {
         if (cudaFuncSetAttribute(qldnn::conv3x3_fwd_tma_kernel<N, SWB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -622,8 +640,6 @@ int launch_tma(const void* in, const void* wk, const float* bias, int B, int H, 
             return set_err(QLD_E_CUDA);
         attr_done.fetch_or(1ull << dev);
     }
-    const long long ntiles = (long long)B * ((H + 7) / 8) * ((W + 15) / 16);
-    const unsigned grid = (unsigned)(ntiles < nsm ? ntiles : nsm);
     qldnn::conv3x3_fwd_tma_kernel<N, SWB><<<grid, 192, L::kSmem, st>>>(mi, mw, bias, B, H, W, Cin, Cout, relu, ob, of,
                                                                         status);
     return launched(1);
@@ -962,8 +978,18 @@ int qldnn_conv3x3_fwd_tc2(const void* in, const void* wk, const float* bias, int
     return set_err(QLD_E_INVAL);
 }
 
+int qldnn_conv3x3_fwd_tma_mode(const void* in, const void* wk, const float* bias, int B, int H, int W, int Cin,
+                               int Cout, int relu, void* out_bf16, float* out_f32, int* status, int force_stream,
+                               void* stream);
+
 int qldnn_conv3x3_fwd_tma(const void* in, const void* wk, const float* bias, int B, int H, int W, int Cin, int Cout,
                           int relu, void* out_bf16, float* out_f32, int* status, void* stream) {
+    return qldnn_conv3x3_fwd_tma_mode(in, wk, bias, B, H, W, Cin, Cout, relu, out_bf16, out_f32, status, 0, stream);
+}
+
+int qldnn_conv3x3_fwd_tma_mode(const void* in, const void* wk, const float* bias, int B, int H, int W, int Cin,
+                               int Cout, int relu, void* out_bf16, float* out_f32, int* status, int force_stream,
+                               void* stream) {
     if (!in || !wk || (!out_bf16 && !out_f32) || B < 1 || H < 1 || W < 1 || Cin < 16 || Cin % 16 ||
         (Cout != 32 && Cout != 64 && Cout != 128 && Cout != 256) || !al(in, 16) || !al(wk, 16) ||
         !al(out_bf16, 16) || !al(out_f32, 16) || (long long)B * H * W * Cin >= (1ll << 40))
@@ -972,7 +998,8 @@ int qldnn_conv3x3_fwd_tma(const void* in, const void* wk, const float* bias, int
     const cudaStream_t st = (cudaStream_t)stream;
     const int swb = Cin % 64 == 0 ? 128 : (Cin % 32 == 0 ? 64 : 32);
 #define QLD_TMA(NN, SS) \
-    if (Cout == NN && swb == SS) return launch_tma<NN, SS>(in, wk, bias, B, H, W, Cin, Cout, relu, ob, out_f32, status, st);
+    if (Cout == NN && swb == SS) \
+        return launch_tma<NN, SS>(in, wk, bias, B, H, W, Cin, Cout, relu, ob, out_f32, status, st, force_stream != 0);
     QLD_TMA(32, 32) QLD_TMA(32, 64) QLD_TMA(32, 128)
     QLD_TMA(64, 32) QLD_TMA(64, 64) QLD_TMA(64, 128)
     QLD_TMA(128, 32) QLD_TMA(128, 64) QLD_TMA(128, 128)

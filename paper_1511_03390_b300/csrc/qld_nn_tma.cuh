@@ -105,6 +105,64 @@ __device__ __forceinline__ bool wait_or_fail(uint64_t* bar, uint32_t parity, vol
     return wait_timed(bar, parity, fail);
 }
 
+// Epilogue warps (4 of them, warp w reads TMEM lanes 32 (w mod 4) ..) of the
+// persistent TMA convolutions: per tile, wait for its accumulator, add the
+// bias, apply ReLU, store bf16 / f32, release the accumulator.
+template <int N>
+__device__ __forceinline__ void conv_epilogue(uint32_t tmem, uint64_t* tfull, uint64_t* tempty, volatile int* fail,
+                                              int warp, int lane, int ntiles, int tiles_x, int tiles_y, int H, int W,
+                                              int Cout, const float* __restrict__ bias, int relu,
+                                              __nv_bfloat16* out_bf, float* out_f) {
+    const int qw = warp & 3;  // TMEM lane quarter this warp may read
+    const int m = qw * 32 + lane;
+    const int my = m >> 4, mx = m & 15;
+    int it = 0;
+    for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
+        const int acc = it & 1;
+        const bool got = wait_or_fail(&tfull[acc], (uint32_t)((it >> 1) & 1), fail);
+        if (!__all_sync(0xffffffffu, got)) break;  // tcgen05.ld below is warp-collective
+        tc_fence_after();
+        const int tx = t % tiles_x, r = t / tiles_x, ty = r % tiles_y, b = r / tiles_y;
+        const int y = ty * 8 + my, x = tx * 16 + mx;
+        const bool inside = y < H && x < W;
+        const long long p = ((long long)b * H + y) * W + x;
+        const uint32_t taddr = tmem + ((uint32_t)(qw * 32) << 16) + (uint32_t)(acc * N);
+#pragma unroll 1
+        for (int c0 = 0; c0 < N; c0 += 16) {
+            uint32_t rr[16];
+            tc_ld16(taddr + (uint32_t)c0, rr);
+            asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
+            if (inside) {
+                float v[16];
+#pragma unroll
+                for (int j = 0; j < 16; ++j) {
+                    v[j] = __uint_as_float(rr[j]) + (bias ? bias[c0 + j] : 0.f);
+                    if (relu) v[j] = fmaxf(v[j], 0.f);
+                }
+                if (out_bf) {
+                    uint32_t pk[8];
+#pragma unroll
+                    for (int j = 0; j < 8; ++j) {
+                        const __nv_bfloat162 h2 = __floats2bfloat162_rn(v[2 * j], v[2 * j + 1]);
+                        pk[j] = *reinterpret_cast<const uint32_t*>(&h2);
+                    }
+                    uint4* o = reinterpret_cast<uint4*>(out_bf + p * Cout + c0);
+                    o[0] = make_uint4(pk[0], pk[1], pk[2], pk[3]);
+                    o[1] = make_uint4(pk[4], pk[5], pk[6], pk[7]);
+                }
+                if (out_f) {
+                    float4* o = reinterpret_cast<float4*>(out_f + p * Cout + c0);
+#pragma unroll
+                    for (int j = 0; j < 4; ++j) o[j] = make_float4(v[4 * j], v[4 * j + 1], v[4 * j + 2], v[4 * j + 3]);
+                }
+            }
+        }
+        tc_fence_before();
+        mbar_arrive(&tempty[acc]);
+        ++it;
+    }
+}
+
 template <int N, int SWB>
 struct TmaConv {
     static constexpr int BK = SWB / 2;                      // channels per chunk
@@ -256,56 +314,8 @@ __global__ void __launch_bounds__(192, 1)
             wait_timed(drain, 0, nullptr);
         }
     } else {
-        // ---------------------------------------------------------------- epilogue
-        const int qw = warp & 3;  // TMEM lane quarter this warp may read
-        const int m = qw * 32 + lane;
-        const int my = m >> 4, mx = m & 15;
-        int it = 0;
-        for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
-            const int acc = it & 1;
-            const bool got = wait_or_fail(&tfull[acc], (uint32_t)((it >> 1) & 1), fail);
-            if (!__all_sync(0xffffffffu, got)) break;  // tcgen05.ld below is warp-collective
-            tc_fence_after();
-            const int tx = t % tiles_x, r = t / tiles_x, ty = r % tiles_y, b = r / tiles_y;
-            const int y = ty * 8 + my, x = tx * 16 + mx;
-            const bool inside = y < H && x < W;
-            const long long p = ((long long)b * H + y) * W + x;
-            const uint32_t taddr = tmem + ((uint32_t)(qw * 32) << 16) + (uint32_t)(acc * N);
-#pragma unroll 1
-            for (int c0 = 0; c0 < N; c0 += 16) {
-                uint32_t rr[16];
-                tc_ld16(taddr + (uint32_t)c0, rr);
-                asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
-                if (inside) {
-                    float v[16];
-#pragma unroll
-                    for (int j = 0; j < 16; ++j) {
-                        v[j] = __uint_as_float(rr[j]) + (bias ? bias[c0 + j] : 0.f);
-                        if (relu) v[j] = fmaxf(v[j], 0.f);
-                    }
-                    if (out_bf) {
-                        uint32_t pk[8];
-#pragma unroll
-                        for (int j = 0; j < 8; ++j) {
-                            const __nv_bfloat162 h2 = __floats2bfloat162_rn(v[2 * j], v[2 * j + 1]);
-                            pk[j] = *reinterpret_cast<const uint32_t*>(&h2);
-                        }
-                        uint4* o = reinterpret_cast<uint4*>(out_bf + p * Cout + c0);
-                        o[0] = make_uint4(pk[0], pk[1], pk[2], pk[3]);
-                        o[1] = make_uint4(pk[4], pk[5], pk[6], pk[7]);
-                    }
-                    if (out_f) {
-                        float4* o = reinterpret_cast<float4*>(out_f + p * Cout + c0);
-#pragma unroll
-                        for (int j = 0; j < 4; ++j)
-                            o[j] = make_float4(v[4 * j], v[4 * j + 1], v[4 * j + 2], v[4 * j + 3]);
-                    }
-                }
-            }
-            tc_fence_before();
-            mbar_arrive(&tempty[acc]);
-            ++it;
-        }
+        conv_epilogue<N>(tmem, tfull, tempty, fail, warp, lane, ntiles, tiles_x, tiles_y, H, W, Cout, bias, relu,
+                         out_bf, out_f);
     }
 
     tc_fence_before();
@@ -318,6 +328,159 @@ __global__ void __launch_bounds__(192, 1)
     }
 }
 
+
+// ---------------------------------------------------------------------------
+// Weights-resident version for layers whose weights (9 Cin Cout bf16) fit in
+// shared memory beside at least two halo stages: the producer loads them once
+// per persistent CTA (9 csteps TMA boxes on one barrier) and then streams only
+// the halos through an SA-stage ring (SA chosen at launch, at most kMaxSA), so
+// neither the L2 nor the ring depth is spent on weights tile after tile.
+// Same tiles, operand layouts, MMAs, epilogue and failure handling as
+// conv3x3_fwd_tma_kernel.
+template <int N, int SWB>
+struct TmaConvRes {
+    static constexpr int BK = SWB / 2;
+    static constexpr int HALO = 10 * 16 * SWB;
+    static constexpr int ASTAGE = 3 * HALO;
+    static constexpr int BSTAGE = N * SWB;
+    static constexpr int kMaxSA = 8;
+    static constexpr int kBars = (2 * kMaxSA + 6) * 8;
+    static constexpr int kTmemCols = 2 * N;
+    // dynamic shared memory for SA halo stages and Cin input channels
+    static constexpr long long smem(int SA, int Cin) {
+        return 1024 + (long long)SA * ASTAGE + 9ll * (Cin / BK) * BSTAGE + kBars + 16;
+    }
+};
+
+template <int N, int SWB>
+__global__ void __launch_bounds__(192, 1)
+    conv3x3_fwd_tma_wres_kernel(const __grid_constant__ CUtensorMap map_in, const __grid_constant__ CUtensorMap map_w,
+                                const float* __restrict__ bias, int B, int H, int W, int Cin, int Cout, int relu,
+                                __nv_bfloat16* out_bf, float* out_f, int* status, int SA) {
+    using L = TmaConvRes<N, SWB>;
+    extern __shared__ unsigned char dsm_raw[];
+    unsigned char* dsm = dsm_raw + ((1024u - (smem_u32(dsm_raw) & 1023u)) & 1023u);
+    const int csteps = Cin / L::BK;
+    unsigned char* sA = dsm;
+    unsigned char* sW = dsm + SA * L::ASTAGE;
+    uint64_t* fullA = reinterpret_cast<uint64_t*>(sW + 9 * csteps * L::BSTAGE);
+    uint64_t* emptyA = fullA + L::kMaxSA;
+    uint64_t* wfull = emptyA + L::kMaxSA;
+    uint64_t* tfull = wfull + 1;
+    uint64_t* tempty = tfull + 2;
+    uint64_t* drain = tempty + 2;
+    uint32_t* tslot = reinterpret_cast<uint32_t*>(drain + 1);
+    volatile int* fail = reinterpret_cast<volatile int*>(tslot + 1);
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int tiles_x = (W + 15) >> 4, tiles_y = (H + 7) >> 3;
+    const int ntiles = B * tiles_x * tiles_y;
+    constexpr uint32_t kIdesc = umma_idesc_bf16(128, N);
+
+    if (warp == 1) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(smem_u32(tslot)),
+                     "r"(L::kTmemCols));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n" ::);
+    }
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < SA; ++s) {
+            mbar_init(&fullA[s], 1);
+            mbar_init(&emptyA[s], 1);
+        }
+        mbar_init(wfull, 1);
+        for (int s = 0; s < 2; ++s) {
+            mbar_init(&tfull[s], 1);
+            mbar_init(&tempty[s], 128);
+        }
+        mbar_init(drain, 1);
+        *fail = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;\n" ::);
+        asm volatile("prefetch.tensormap [%0];\n" ::"l"(reinterpret_cast<uint64_t>(&map_in)) : "memory");
+        asm volatile("prefetch.tensormap [%0];\n" ::"l"(reinterpret_cast<uint64_t>(&map_w)) : "memory");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *tslot;
+
+    if (warp == 0) {
+        if (lane == 0) {
+            // ------------------------------------------------------------ TMA producer
+            mbar_expect_tx(wfull, (uint32_t)(9 * csteps * L::BSTAGE));
+            for (int cc = 0; cc < csteps; ++cc)
+                for (int tap = 0; tap < 9; ++tap)
+                    tma_load_2d(sW + (cc * 9 + tap) * L::BSTAGE, &map_w, wfull, cc * L::BK, tap * Cout);
+            int ia = 0;
+            bool ok = true;
+            for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
+                const int tx = t % tiles_x, r = t / tiles_x, ty = r % tiles_y, b = r / tiles_y;
+                const int x0 = tx * 16, y0 = ty * 8;
+                for (int cc = 0; cc < csteps; ++cc) {
+                    const int sa = ia % SA;
+                    if (ia >= SA && !(ok = wait_or_fail(&emptyA[sa], (uint32_t)(((ia / SA) - 1) & 1), fail))) break;
+                    mbar_expect_tx(&fullA[sa], 3 * L::HALO);
+                    for (int j = 0; j < 3; ++j)
+                        tma_load_4d(sA + (sa * 3 + j) * L::HALO, &map_in, &fullA[sa], cc * L::BK, x0 + j - 1, y0 - 1, b);
+                    ++ia;
+                }
+            }
+            // no copy may still be in flight when the CTA leaves
+            wait_timed(wfull, 0, nullptr);
+            for (int s = 0; s < SA; ++s) {
+                const int k = ia - 1 - ((ia - 1 - s) % SA + SA) % SA;
+                if (k >= 0) wait_timed(&fullA[s], (uint32_t)((k / SA) & 1), nullptr);
+            }
+        }
+    } else if (warp == 1) {
+        if (lane == 0) {
+            // --------------------------------------------------------- MMA issuer
+            bool ok = wait_or_fail(wfull, 0, fail);
+            tc_fence_after();
+            int ia = 0, it = 0;
+            const uint32_t w0 = smem_u32(sW);
+            for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
+                const int acc = it & 1;
+                if (it >= 2 && !(ok = wait_or_fail(&tempty[acc], (uint32_t)(((it >> 1) - 1) & 1), fail))) break;
+                tc_fence_after();
+                const uint32_t d = tmem + (uint32_t)(acc * N);
+                for (int cc = 0; cc < csteps && ok; ++cc) {
+                    const int sa = ia % SA;
+                    if (!(ok = wait_or_fail(&fullA[sa], (uint32_t)((ia / SA) & 1), fail))) break;
+                    tc_fence_after();
+                    const uint32_t a0 = smem_u32(sA + sa * 3 * L::HALO);
+#pragma unroll 1
+                    for (int tap = 0; tap < 9; ++tap) {
+                        const uint32_t abase = a0 + (uint32_t)((tap % 3) * L::HALO + (tap / 3) * 16 * SWB);
+                        const uint32_t bbase = w0 + (uint32_t)((cc * 9 + tap) * L::BSTAGE);
+#pragma unroll
+                        for (int kk = 0; kk < L::BK / 16; ++kk)
+                            tc_mma(d, umma_desc_sw<SWB>(abase + kk * 32), umma_desc_sw<SWB>(bbase + kk * 32), kIdesc,
+                                   (cc | tap | kk) ? 1u : 0u);
+                    }
+                    tc_commit(&emptyA[sa]);
+                    ++ia;
+                }
+                if (!ok) break;
+                tc_commit(&tfull[acc]);
+                ++it;
+            }
+            tc_commit(drain);
+            wait_timed(drain, 0, nullptr);
+        }
+    } else {
+        conv_epilogue<N>(tmem, tfull, tempty, fail, warp, lane, ntiles, tiles_x, tiles_y, H, W, Cout, bias, relu,
+                         out_bf, out_f);
+    }
+
+    tc_fence_before();
+    __syncthreads();
+    if (threadIdx.x == 0 && *fail && status) atomicExch(status, 1);
+    if (warp == 1) {
+        __syncwarp();
+        tc_fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(L::kTmemCols));
+    }
+}
 
 // ---------------------------------------------------------------------------
 // Weight gradient on the tensor cores: dW[3 ky + kx][ci][co] +=

@@ -1,5 +1,6 @@
 """The tensor-memory (tcgen05) convolutions (the two-buffer kernel, the
-warp-specialised pipelined one and the persistent TMA-fed one) against the FP64 oracle and the warp-MMA
+warp-specialised pipelined one and the persistent TMA-fed one in both its
+weights-resident and weight-streaming variants) against the FP64 oracle and the warp-MMA
 kernel: forward with bias/ReLU and, with flipped weights, the data gradient. Same tolerance as the other convolution tests (FP32 accumulation
 relative to sum |x| |w|, plus bf16 output rounding)."""
 import numpy as np
@@ -19,12 +20,16 @@ def _need_gpu():
         pytest.skip("no CUDA device")
 
 
-KERNELS = ["conv3x3_fwd_tc", "conv3x3_fwd_tc2", "conv3x3_fwd_tma"]
+# conv3x3_fwd_tma keeps small layers' weights resident in shared memory;
+# "conv3x3_fwd_tma_stream" forces its weight-streaming variant on every shape.
+KERNELS = ["conv3x3_fwd_tc", "conv3x3_fwd_tc2", "conv3x3_fwd_tma", "conv3x3_fwd_tma_stream"]
 
 
 def _tc(kernel, Cout):
     if kernel != "conv3x3_fwd_tc" and Cout not in (32, 64, 128, 256):
         pytest.skip("the pipelined kernels cover Cout in {32, 64, 128, 256}")
+    if kernel == "conv3x3_fwd_tma_stream":
+        return lambda *a: q.nn.conv3x3_fwd_tma_mode(*a, 1)
     return getattr(q.nn, kernel)
 
 
