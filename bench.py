@@ -606,10 +606,17 @@ def run_serving(q, torch, dev, st, peak, ticks=300, paced_ticks=300, fps=200.0):
     shape_idx, tuned_us = q.qld_server_autotune(srv, st)
     shape = q.qld_server_shape(srv)
 
-    def one_tick(k):
+    # per tick: one frame per stream handed over in one qld_server_submit_many
+    # call (arrays prepared once per pool frame), then one tick
+    batches = []
+    for j in range(P):
+        bt = q.SubmitBatch(len(tickets))
         for i, t in enumerate(tickets):
-            j = k % P
-            q.qld_server_submit(srv, t, pools[i][j:j + 1], 1)
+            bt.set(i, srv, t, pools[i][j:j + 1], 1)
+        batches.append(bt)
+
+    def one_tick(k):
+        batches[k % P].submit(srv, len(tickets))
         q.qld_server_tick(srv, st)
 
     for k in range(5):

@@ -246,6 +246,10 @@ int qld_server_request(qld_server* srv, int H, int W, int N, int pixfmt);
 int qld_server_state(qld_server* srv, int ticket);
 int qld_server_close(qld_server* srv, int ticket);
 int qld_server_submit(qld_server* srv, int ticket, const void* frames, int count);
+/* n submissions in one call (host arrays: tickets[i], frames[i], counts[i],
+ * each as for qld_server_submit, distinct tickets). All are checked first;
+ * on an error none is taken. */
+int qld_server_submit_many(qld_server* srv, int n, const int* tickets, const void* const* frames, const int* counts);
 int qld_server_tick(qld_server* srv, void* stream);
 int qld_server_image(qld_server* srv, int ticket, float** amp, float** phase);
 int qld_server_iq(qld_server* srv, int ticket, int32_t* S, int32_t* C);

@@ -22,6 +22,7 @@ __all__ = [
     "qld_mem_in_use", "qld_launch_count", "qld_fft_bin_frames_noalloc", "QLD_NOALLOC_MAX_N",
     "qld_lockin_table", "qld_lockin_frames", "Server", "QLD_SERVER_MAX_STREAMS", "qld_server_create",
     "qld_server_destroy", "qld_server_request", "qld_server_state", "qld_server_close", "qld_server_submit",
+    "qld_server_submit_many",
     "qld_server_tick", "qld_server_image", "qld_server_iq", "qld_server_frames_pushed", "qld_server_mem_in_use",
     "qld_server_sync", "qld_server_autotune", "qld_server_shape", "nn", "LIB_PATH", "lib",
 ]
@@ -96,6 +97,7 @@ _SIGS = {
     "qld_server_state": ([_p, _i], _i),
     "qld_server_close": ([_p, _i], _i),
     "qld_server_submit": ([_p, _i, _p, _i], _i),
+    "qld_server_submit_many": ([_p, _i, _p, _p, _p], _i),
     "qld_server_tick": ([_p, _p], _i),
     "qld_server_image": ([_p, _i, ctypes.POINTER(_p), ctypes.POINTER(_p)], _i),
     "qld_server_iq": ([_p, _i, _p, _p], _i),
@@ -386,6 +388,29 @@ def qld_server_submit(srv, ticket, frames, count=None):
     n = _count_of(frames, count, fb)
     return _check(lib.qld_server_submit(_sh(srv), int(ticket), _addr(frames, n * fb, "frames"), n),
                   "qld_server_submit")
+
+
+class SubmitBatch:
+    """Reusable host arrays for qld_server_submit_many: set(i, ticket, frames,
+    count) fills entry i (device frames, checked like qld_server_submit),
+    submit(srv, n) hands over entries 0..n-1 in one call."""
+
+    def __init__(self, capacity):
+        self.tickets = (ctypes.c_int * capacity)()
+        self.frames = (ctypes.c_void_p * capacity)()
+        self.counts = (ctypes.c_int * capacity)()
+
+    def set(self, i, srv, ticket, frames, count=None):
+        H, W, N, fmt = srv.shapes[ticket]
+        fb = H * W // 2 * 3 if fmt == QLD_P12 else H * W * fmt
+        n = _count_of(frames, count, fb)
+        self.tickets[i] = int(ticket)
+        self.frames[i] = _addr(frames, n * fb, "frames")
+        self.counts[i] = n
+
+    def submit(self, srv, n):
+        return _check(lib.qld_server_submit_many(_sh(srv), int(n), self.tickets, self.frames, self.counts),
+                      "qld_server_submit_many")
 
 
 def qld_server_tick(srv, stream=None):

@@ -56,10 +56,12 @@ struct qld_server {
     int max_streams;
     std::vector<SrvStream> streams;  // index = ticket
     std::deque<int> waiting;         // tickets in arrival order
+    // descriptors: one block [header | items] on the device and two pinned
+    // host blocks (alternating ticks), so a tick copies them in one transfer
     qldk::BatchHeader* hdr_dev;
-    qldk::BatchItem* items_dev;
+    qldk::BatchItem* items_dev;      // inside the hdr_dev block
     qldk::BatchHeader* hdr_host[2];  // pinned
-    qldk::BatchItem* items_host[2];  // pinned
+    qldk::BatchItem* items_host[2];  // inside the hdr_host[b] blocks
     cudaEvent_t used[2];
     bool used_valid[2];
     cudaGraphExec_t graph[2];
@@ -70,6 +72,13 @@ struct qld_server {
 };
 
 namespace {
+
+// Bytes of a descriptor block: the header (rounded up to 16 bytes), then the items.
+constexpr size_t kHdrBytes = (sizeof(qldk::BatchHeader) + 15) / 16 * 16;
+size_t desc_bytes(int max_streams) { return kHdrBytes + sizeof(qldk::BatchItem) * (size_t)max_streams; }
+qldk::BatchItem* items_of(qldk::BatchHeader* h) {
+    return reinterpret_cast<qldk::BatchItem*>(reinterpret_cast<unsigned char*>(h) + kHdrBytes);
+}
 
 int active_count(const qld_server* s) {
     int n = 0;
@@ -164,9 +173,7 @@ int ensure_graphs(qld_server* s) {
         }
         cudaGraph_t g = nullptr;
         if (cudaStreamBeginCapture(s->cap, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return QLD_E_CUDA;
-        cudaMemcpyAsync(s->hdr_dev, s->hdr_host[b], sizeof(qldk::BatchHeader), cudaMemcpyHostToDevice, s->cap);
-        cudaMemcpyAsync(s->items_dev, s->items_host[b], sizeof(qldk::BatchItem) * s->max_streams,
-                        cudaMemcpyHostToDevice, s->cap);
+        cudaMemcpyAsync(s->hdr_dev, s->hdr_host[b], desc_bytes(s->max_streams), cudaMemcpyHostToDevice, s->cap);
         qldk::launch_batch(qldk::kBatchShapes[s->shape], s->num_sms, s->hdr_dev, s->items_dev, s->cap);
         if (cudaStreamEndCapture(s->cap, &g) != cudaSuccess || !g) {
             cudaGetLastError();
@@ -213,18 +220,15 @@ qld_server* qld_server_create(long long hbm_budget_bytes, int max_streams) {
     s->flip = 0;
     bool ok = cudaGetDevice(&s->device) == cudaSuccess &&
               cudaDeviceGetAttribute(&s->num_sms, cudaDevAttrMultiProcessorCount, s->device) == cudaSuccess &&
-              cudaMalloc(&s->hdr_dev, sizeof(qldk::BatchHeader)) == cudaSuccess &&
-              cudaMalloc(&s->items_dev, sizeof(qldk::BatchItem) * max_streams) == cudaSuccess &&
+              cudaMalloc(&s->hdr_dev, desc_bytes(max_streams)) == cudaSuccess &&
               cudaStreamCreateWithFlags(&s->cap, cudaStreamNonBlocking) == cudaSuccess;
-    for (int b = 0; ok && b < 2; ++b)
-        ok = cudaHostAlloc(&s->hdr_host[b], sizeof(qldk::BatchHeader), cudaHostAllocDefault) == cudaSuccess &&
-             cudaHostAlloc(&s->items_host[b], sizeof(qldk::BatchItem) * max_streams, cudaHostAllocDefault) ==
-                 cudaSuccess &&
+    if (ok) s->items_dev = items_of(s->hdr_dev);
+    for (int b = 0; ok && b < 2; ++b) {
+        ok = cudaHostAlloc(&s->hdr_host[b], desc_bytes(max_streams), cudaHostAllocDefault) == cudaSuccess &&
              cudaEventCreateWithFlags(&s->used[b], cudaEventDisableTiming) == cudaSuccess;
-    if (ok) {
-        for (int b = 0; b < 2; ++b) {
-            std::memset(s->hdr_host[b], 0, sizeof(qldk::BatchHeader));
-            std::memset(s->items_host[b], 0, sizeof(qldk::BatchItem) * max_streams);
+        if (ok) {
+            s->items_host[b] = items_of(s->hdr_host[b]);
+            std::memset(s->hdr_host[b], 0, desc_bytes(max_streams));
         }
     }
     if (!ok) {
@@ -243,11 +247,9 @@ void qld_server_destroy(qld_server* s) {
     for (int b = 0; b < 2; ++b) {
         if (s->graph[b]) cudaGraphExecDestroy(s->graph[b]);
         if (s->hdr_host[b]) cudaFreeHost(s->hdr_host[b]);
-        if (s->items_host[b]) cudaFreeHost(s->items_host[b]);
         if (s->used[b]) cudaEventDestroy(s->used[b]);
     }
     if (s->hdr_dev) cudaFree(s->hdr_dev);
-    if (s->items_dev) cudaFree(s->items_dev);
     if (s->cap) cudaStreamDestroy(s->cap);
     delete s;
 }
@@ -303,6 +305,27 @@ int qld_server_submit(qld_server* s, int ticket, const void* frames, int count) 
     if (count > 0 && ((uintptr_t)frames % qldi::vec_align_of(t->pixfmt)) != 0) return set_err(QLD_E_INVAL);
     t->pending = frames;
     t->pending_count = count;
+    return QLD_OK;
+}
+
+int qld_server_submit_many(qld_server* s, int n, const int* tickets, const void* const* frames, const int* counts) {
+    if (!s || n < 0 || (n > 0 && (!tickets || !frames || !counts))) return set_err(QLD_E_INVAL);
+    // validate everything first: either every submission is taken or none
+    for (int i = 0; i < n; ++i) {
+        const SrvStream* t = get_stream(s, tickets[i]);
+        const int count = counts[i];
+        if (!t || count < 0 || (count > 0 && !frames[i])) return set_err(QLD_E_INVAL);
+        if (t->state == 1) return set_err(QLD_E_NOT_READY);
+        if (t->state != 0 || t->pending_count > 0) return set_err(QLD_E_INVAL);
+        if (count > 0 && ((uintptr_t)frames[i] % qldi::vec_align_of(t->pixfmt)) != 0) return set_err(QLD_E_INVAL);
+        for (int j = 0; j < i; ++j)
+            if (tickets[j] == tickets[i]) return set_err(QLD_E_INVAL);  // one submission per stream per tick
+    }
+    for (int i = 0; i < n; ++i) {
+        SrvStream* t = get_stream(s, tickets[i]);
+        t->pending = frames[i];
+        t->pending_count = counts[i];
+    }
     return QLD_OK;
 }
 

@@ -65,7 +65,7 @@ def ctx_state(ctx):
     return S.cpu().numpy(), C.cpu().numpy(), amp.cpu().numpy(), ph.cpu().numpy()
 
 
-def run_mix(autotune=False, ticks=10, seed=0):
+def run_mix(autotune=False, ticks=10, seed=0, batched=False):
     rng = np.random.default_rng(seed)
     srv = q.qld_server_create(1 << 36)
     tickets = [q.qld_server_request(srv, *m) for m in MIX]
@@ -73,7 +73,9 @@ def run_mix(autotune=False, ticks=10, seed=0):
     alone = [q.qld_create(*m) for m in MIX]
     history = [np.zeros((0, m[0] * m[1]), np.uint8 if m[3] == q.QLD_U8 else np.uint16) for m in MIX]
     keep = []
+    batch = q.SubmitBatch(len(MIX))
     for tick in range(ticks):
+        nb = 0
         for i, (t, m) in enumerate(zip(tickets, MIX)):
             H, W, N, fmt = m
             pattern = [1, 2, 0, 3, 1, N + 1, 1, 4, 0, 2]
@@ -82,9 +84,15 @@ def run_mix(autotune=False, ticks=10, seed=0):
                 continue
             x, dev = frames_for(rng, H, W, fmt, count)
             keep.append(dev)
-            q.qld_server_submit(srv, t, dev, count)
+            if batched:
+                batch.set(nb, srv, t, dev, count)
+                nb += 1
+            else:
+                q.qld_server_submit(srv, t, dev, count)
             q.qld_push_frames(alone[i], dev, count)
             history[i] = np.concatenate([history[i], x])
+        if batched:
+            batch.submit(srv, nb)
         assert q.qld_server_tick(srv) >= 1
         if autotune and tick == 2:
             k, us = q.qld_server_autotune(srv)
@@ -112,6 +120,32 @@ def test_each_stream_in_the_mix_equals_it_alone():
 
 def test_autotuned_shape_gives_the_same_results():
     run_mix(autotune=True, seed=1)
+
+
+def test_submit_many_equals_single_submits():
+    run_mix(seed=2, batched=True)
+
+
+def test_submit_many_takes_all_or_nothing():
+    rng = np.random.default_rng(6)
+    srv = q.qld_server_create(1 << 34)
+    a = q.qld_server_request(srv, 32, 64, 8, q.QLD_U16)
+    b = q.qld_server_request(srv, 16, 32, 4, q.QLD_U8)
+    _, da = frames_for(rng, 32, 64, q.QLD_U16, 1)
+    _, db = frames_for(rng, 16, 32, q.QLD_U8, 1)
+    batch = q.SubmitBatch(3)
+    batch.set(0, srv, a, da, 1)
+    batch.set(1, srv, b, db, 1)
+    batch.set(2, srv, a, da, 1)  # the same stream twice in one tick
+    with pytest.raises(q.QLDError) as e:
+        batch.submit(srv, 3)
+    assert e.value.status == q.QLD_E_INVAL
+    assert q.qld_server_tick(srv) == 0  # nothing was taken
+    batch.submit(srv, 2)
+    assert q.qld_server_tick(srv) == 2
+    q.qld_server_sync(srv)
+    assert q.qld_server_frames_pushed(srv, a) == 1 and q.qld_server_frames_pushed(srv, b) == 1
+    srv.destroy()
 
 
 def test_admission_by_budget_in_arrival_order():
