@@ -413,6 +413,15 @@ class SubmitBatch:
                       "qld_server_submit_many")
 
 
+def qld_server_submit_many(srv, submissions):
+    """Hands over [(ticket, frames, count or None), ...] in one call."""
+    b = SubmitBatch(max(1, len(submissions)))
+    for i, sub in enumerate(submissions):
+        ticket, frames = sub[0], sub[1]
+        b.set(i, srv, ticket, frames, sub[2] if len(sub) > 2 else None)
+    return b.submit(srv, len(submissions))
+
+
 def qld_server_tick(srv, stream=None):
     n = lib.qld_server_tick(_sh(srv), _stream(stream))
     if n < 0:

@@ -141,7 +141,7 @@ def test_submit_many_takes_all_or_nothing():
         batch.submit(srv, 3)
     assert e.value.status == q.QLD_E_INVAL
     assert q.qld_server_tick(srv) == 0  # nothing was taken
-    batch.submit(srv, 2)
+    q.qld_server_submit_many(srv, [(a, da, 1), (b, db)])
     assert q.qld_server_tick(srv) == 2
     q.qld_server_sync(srv)
     assert q.qld_server_frames_pushed(srv, a) == 1 and q.qld_server_frames_pushed(srv, b) == 1
