@@ -43,6 +43,7 @@ POOL = 2048  # frames resident in HBM (4 GiB), cycled: every step reads fresh fr
 WORKLOAD = ("fog scene OD 6, 1024x1024 uint16 (12-bit), N=1024 sliding window advanced 4 frames/step; "
             "per step: push+amplitude/phase image (fused) and DFT-bin power at k=N/4")
 FALLBACK_HBM_GBS = 6400.0
+NOMINAL_HBM_GBS = 8000.0  # the ~8 TB/s nominal figure the 70 % target is stated against
 
 
 def parse_args():
@@ -238,6 +239,18 @@ def oracle_steps(band, rows, nthreads, max_steps, budget_s):
     return times
 
 
+def cpu_model():
+    """The host CPU's model name from /proc/cpuinfo, or None."""
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                if line.startswith("model name"):
+                    return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    return None
+
+
 def cpu_baseline_from_band(band, rows, budget_s, steps=64):
     nthreads = os.cpu_count() or 1
     t = oracle_steps(band, rows, nthreads, steps, budget_s)
@@ -253,6 +266,7 @@ def cpu_baseline_from_band(band, rows, budget_s, steps=64):
                    "N=%d frames and the DFT bin k=N/4, %d threads; value per pixel-frame ingested, scaled "
                    "from the band" % (rows, H, rows * W, len(t), N, nthreads)),
         "single_thread_value": pf / statistics.median(t1) / 1e9,
+        "cpu_model": cpu_model(),
         "ms_per_step_sample": per_step * 1e3,
     }
 
@@ -452,7 +466,8 @@ def run_cuda(args, world, rank, local):
                    "l2": "inputs larger than L2: 4 GiB frame pool cycled + 2 GiB window read by the DFT bin each step"},
         "roofline": {"bound": "hbm", "kernel": "bin_kernel<uint16_t,5,128,power> (qld_fft_bin)", "achieved": fft_gbs, "peak": peak,
                      "unit": "GB/s", "frac": fft_gbs / peak, "peak_kind": peak_kind,
-                     "algorithmic_bytes_per_launch": ab["fft_bin"], "traffic": traffic},
+                     "algorithmic_bytes_per_launch": ab["fft_bin"], "traffic": traffic,
+                     "nominal_peak": NOMINAL_HBM_GBS, "frac_of_nominal": fft_gbs / NOMINAL_HBM_GBS},
         "kernels": {
             "push_image": {"ms_per_launch": push_ms / K, "algorithmic_bytes": ab["push_image"], "achieved_gbs": push_gbs,
                            "frac": push_gbs / peak, "qld_only_gpf_s": H * W * ADV / (push_ms / K * 1e-3) / 1e9},
@@ -866,7 +881,8 @@ def run_reference(args):
         "data": "synthetic (seeded scattered-light scene generator)",
         "config": {"workload": WORKLOAD, "H": H, "W": W, "N": N, "advance": ADV, "pixfmt": "uint16 12-bit",
                    "od": OD, "dft_bin_k": K_BIN},
-        "cpu_baseline": {"value": value, "unit": UNIT, "cores": nthreads, "kind": "oracle", "sample": sample},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": nthreads, "kind": "oracle", "sample": sample,
+                         "cpu_model": cpu_model()},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
 
