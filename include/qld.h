@@ -345,13 +345,16 @@ int qldnn_conv3x3_fwd_tc2(const void* in, const void* wk, const float* bias, int
  * overlaps the next tile's MMAs. Launches one CTA per SM. */
 int qldnn_conv3x3_fwd_tma(const void* in, const void* wk, const float* bias, int B, int H, int W, int Cin, int Cout,
                           int relu, void* out_bf16, float* out_f32, int* status, void* stream);
-/* The same with the kernel variant chosen by the caller: qldnn_conv3x3_fwd_tma
- * keeps the weights resident in shared memory when 9 Cin Cout bf16 fit beside
- * two halo stages (loaded once per CTA, only the halos streamed) and streams
- * them per tile otherwise; force_stream != 0 always streams them (tests and
- * measurements of both variants). */
+/* The same with the kernel variant chosen by the caller. qldnn_conv3x3_fwd_tma
+ * keeps the weights resident in shared memory when 9 Cin (Cout / splits) bf16
+ * fit beside two halo stages (loaded once per CTA, only the halos streamed)
+ * and streams them per tile otherwise; when a layer has at most half as many
+ * output tiles as there are SMs it splits each tile's output channels over 2
+ * or 4 CTAs (at least 32 channels each, weights resident). mode bit 0 set: always stream the weights; mode >> 4
+ * (0 = automatic, else 1, 2 or 4): the CTAs per tile. For tests and
+ * measurements of every variant. */
 int qldnn_conv3x3_fwd_tma_mode(const void* in, const void* wk, const float* bias, int B, int H, int W, int Cin,
-                               int Cout, int relu, void* out_bf16, float* out_f32, int* status, int force_stream,
+                               int Cout, int relu, void* out_bf16, float* out_f32, int* status, int mode,
                                void* stream);
 /* Weight gradient of the 3x3 convolution on the tensor cores: dw [9][Cin][Cout]
  * f32 += sum over pixels of in (shifted by the tap) x g, in [B][H][W][Cin]

@@ -616,7 +616,10 @@ int launch_tma(const void* in, const void* wk, const float* bias, int B, int H, 
             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
         return set_err(QLD_E_CUDA);
     const long long ntiles = (long long)B * ((H + 7) / 8) * ((W + 15) / 16);
-    const unsigned grid = (unsigned)(ntiles < nsm ? ntiles : nsm);
+    const int nsplit = Cout / N;  // CTAs per tile, one output-channel slice each
+    long long items = ntiles * nsplit;
+    const long long cap = (long long)(nsm / nsplit) * nsplit;
+    const unsigned grid = (unsigned)(items < cap ? items : cap);
     // weights resident in shared memory when they fit beside two or more halo stages
     using R = qldnn::TmaConvRes<N, SWB>;
     int sa = 0;
@@ -630,7 +633,7 @@ int launch_tma(const void* in, const void* wk, const float* bias, int B, int H, 
             attr_res.fetch_or(1ull << dev);
         }
         qldnn::conv3x3_fwd_tma_wres_kernel<N, SWB><<<grid, 192, (size_t)R::smem(sa, Cin), st>>>(
-            mi, mw, bias, B, H, W, Cin, Cout, relu, ob, of, status, sa);
+            mi, mw, bias, B, H, W, Cin, Cout, relu, ob, of, status, sa, nsplit);
         return launched(1);
     }
     static std::atomic<unsigned long long> attr_done{0};  // per instantiation, one bit per device
@@ -641,7 +644,7 @@ int launch_tma(const void* in, const void* wk, const float* bias, int B, int H, 
         attr_done.fetch_or(1ull << dev);
     }
     qldnn::conv3x3_fwd_tma_kernel<N, SWB><<<grid, 192, L::kSmem, st>>>(mi, mw, bias, B, H, W, Cin, Cout, relu, ob, of,
-                                                                        status);
+                                                                        status, nsplit);
     return launched(1);
 }
 
@@ -979,7 +982,7 @@ int qldnn_conv3x3_fwd_tc2(const void* in, const void* wk, const float* bias, int
 }
 
 int qldnn_conv3x3_fwd_tma_mode(const void* in, const void* wk, const float* bias, int B, int H, int W, int Cin,
-                               int Cout, int relu, void* out_bf16, float* out_f32, int* status, int force_stream,
+                               int Cout, int relu, void* out_bf16, float* out_f32, int* status, int mode,
                                void* stream);
 
 int qldnn_conv3x3_fwd_tma(const void* in, const void* wk, const float* bias, int B, int H, int W, int Cin, int Cout,
@@ -988,8 +991,13 @@ int qldnn_conv3x3_fwd_tma(const void* in, const void* wk, const float* bias, int
 }
 
 int qldnn_conv3x3_fwd_tma_mode(const void* in, const void* wk, const float* bias, int B, int H, int W, int Cin,
-                               int Cout, int relu, void* out_bf16, float* out_f32, int* status, int force_stream,
+                               int Cout, int relu, void* out_bf16, float* out_f32, int* status, int mode,
                                void* stream) {
+    // mode: bit 0 forces the weight-streaming variant; bits 4.. (if non-zero)
+    // force the number of CTAs per tile (1, 2 or 4)
+    const int force_stream = mode & 1;
+    const int split_mode = (mode >> 4) & 0xF;
+    if (split_mode != 0 && split_mode != 1 && split_mode != 2 && split_mode != 4) return set_err(QLD_E_INVAL);
     if (!in || !wk || (!out_bf16 && !out_f32) || B < 1 || H < 1 || W < 1 || Cin < 16 || Cin % 16 ||
         (Cout != 32 && Cout != 64 && Cout != 128 && Cout != 256) || !al(in, 16) || !al(wk, 16) ||
         !al(out_bf16, 16) || !al(out_f32, 16) || (long long)B * H * W * Cin >= (1ll << 40))
@@ -997,8 +1005,29 @@ int qldnn_conv3x3_fwd_tma_mode(const void* in, const void* wk, const float* bias
     __nv_bfloat16* ob = (__nv_bfloat16*)out_bf16;
     const cudaStream_t st = (cudaStream_t)stream;
     const int swb = Cin % 64 == 0 ? 128 : (Cin % 32 == 0 ? 64 : 32);
+    // fewer tiles than SMs: split each tile's output channels over 2 or 4 CTAs
+    int dev = 0, nsm = 148;
+    if (cudaGetDevice(&dev) == cudaSuccess) {
+        const int n = sm_count(dev);
+        if (n > 0) nsm = n;
+    }
+    const long long ntiles = (long long)B * ((H + 7) / 8) * ((W + 15) / 16);
+    // split only into slices whose weights stay resident: a streamed slice
+    // reloads the whole input halo per CTA and runs narrower MMAs (slower)
+    auto resident = [&](int nco) {
+        const long long halo3 = 3ll * 160 * swb;
+        return 1024 + 2 * halo3 + 9ll * Cin * nco * 2 + 256 <= 232448;
+    };
+    // and only when at most half the SMs would otherwise get a tile: with
+    // more, the narrower MMAs and repeated halo loads cost more than it gains
+    int nsplit = 1;
+    for (int cand = 2; cand <= 4 && 2 * ntiles <= nsm && ntiles * nsplit < nsm; cand *= 2)
+        if (Cout / cand >= 32 && resident(Cout / cand)) nsplit = cand;
+    if (split_mode > 0) nsplit = split_mode;
+    if (Cout % nsplit || Cout / nsplit < 32) return set_err(QLD_E_INVAL);
+    const int nco = Cout / nsplit;
 #define QLD_TMA(NN, SS) \
-    if (Cout == NN && swb == SS) \
+    if (nco == NN && swb == SS) \
         return launch_tma<NN, SS>(in, wk, bias, B, H, W, Cin, Cout, relu, ob, out_f32, status, st, force_stream != 0);
     QLD_TMA(32, 32) QLD_TMA(32, 64) QLD_TMA(32, 128)
     QLD_TMA(64, 32) QLD_TMA(64, 64) QLD_TMA(64, 128)

@@ -1,9 +1,11 @@
 // qld_nn_tma.cuh -- persistent, TMA-fed 3x3 convolution forward on the
 // 5th-generation tensor cores.
 //
-// Output tile: 8 rows x 16 columns of one image = M 128 pixels, all N = Cout
-// output channels (32, 64, 128 or 256). K runs over channel chunks of
-// BK = SWB/2 channels (outer) and the nine taps (inner).
+// Output tile: 8 rows x 16 columns of one image = M 128 pixels, N = Cout /
+// nsplit output channels (32, 64, 128 or 256): when a layer has fewer tiles
+// than SMs, nsplit CTAs share each tile, CTA b taking channel slice
+// b mod nsplit for all its tiles (gridDim.x is a multiple of nsplit). K runs
+// over channel chunks of BK = SWB/2 channels (outer) and the nine taps (inner).
 //
 // Input staging without im2col: for each channel chunk the tile's input halo
 // (10 rows x 16 columns) is loaded three times by the tensor-memory
@@ -112,12 +114,16 @@ template <int N>
 __device__ __forceinline__ void conv_epilogue(uint32_t tmem, uint64_t* tfull, uint64_t* tempty, volatile int* fail,
                                               int warp, int lane, int ntiles, int tiles_x, int tiles_y, int H, int W,
                                               int Cout, const float* __restrict__ bias, int relu,
-                                              __nv_bfloat16* out_bf, float* out_f) {
+                                              __nv_bfloat16* out_bf, float* out_f, int nsplit) {
     const int qw = warp & 3;  // TMEM lane quarter this warp may read
     const int m = qw * 32 + lane;
     const int my = m >> 4, mx = m & 15;
+    const int co0 = (blockIdx.x % nsplit) * N;  // this CTA's slice of the output channels
+    if (bias) bias += co0;
+    if (out_bf) out_bf += co0;
+    if (out_f) out_f += co0;
     int it = 0;
-    for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
+    for (int t = blockIdx.x / nsplit; t < ntiles; t += gridDim.x / nsplit) {
         const int acc = it & 1;
         const bool got = wait_or_fail(&tfull[acc], (uint32_t)((it >> 1) & 1), fail);
         if (!__all_sync(0xffffffffu, got)) break;  // tcgen05.ld below is warp-collective
@@ -184,7 +190,7 @@ template <int N, int SWB>
 __global__ void __launch_bounds__(192, 1)
     conv3x3_fwd_tma_kernel(const __grid_constant__ CUtensorMap map_in, const __grid_constant__ CUtensorMap map_w,
                            const float* __restrict__ bias, int B, int H, int W, int Cin, int Cout, int relu,
-                           __nv_bfloat16* out_bf, float* out_f, int* status) {
+                           __nv_bfloat16* out_bf, float* out_f, int* status, int nsplit) {
     using L = TmaConv<N, SWB>;
     extern __shared__ unsigned char dsm_raw[];
     unsigned char* dsm = dsm_raw + ((1024u - (smem_u32(dsm_raw) & 1023u)) & 1023u);
@@ -204,6 +210,7 @@ __global__ void __launch_bounds__(192, 1)
     const int tiles_x = (W + 15) >> 4, tiles_y = (H + 7) >> 3;
     const int ntiles = B * tiles_x * tiles_y;
     const int csteps = Cin / L::BK;
+    const int co0 = (blockIdx.x % nsplit) * N;  // this CTA's slice of the output channels
     constexpr uint32_t kIdesc = umma_idesc_bf16(128, N);
 
     if (warp == 1) {
@@ -240,7 +247,7 @@ __global__ void __launch_bounds__(192, 1)
             // ------------------------------------------------------------ TMA producer
             int ia = 0, ib = 0;
             bool ok = true;
-            for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
+            for (int t = blockIdx.x / nsplit; t < ntiles && ok; t += gridDim.x / nsplit) {
                 const int tx = t % tiles_x, r = t / tiles_x, ty = r % tiles_y, b = r / tiles_y;
                 const int x0 = tx * 16, y0 = ty * 8;
                 for (int cc = 0; cc < csteps && ok; ++cc) {
@@ -256,7 +263,7 @@ __global__ void __launch_bounds__(192, 1)
                         if (ib >= L::SB && !(ok = wait_or_fail(&emptyB[sb], (uint32_t)(((ib / L::SB) - 1) & 1), fail)))
                             break;
                         mbar_expect_tx(&fullB[sb], L::BSTAGE);
-                        tma_load_2d(sB + sb * L::BSTAGE, &map_w, &fullB[sb], cc * L::BK, tap * Cout);
+                        tma_load_2d(sB + sb * L::BSTAGE, &map_w, &fullB[sb], cc * L::BK, tap * Cout + co0);
                         ++ib;
                     }
                 }
@@ -278,7 +285,7 @@ __global__ void __launch_bounds__(192, 1)
             // --------------------------------------------------------- MMA issuer
             int ia = 0, ib = 0, it = 0;
             bool ok = true;
-            for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
+            for (int t = blockIdx.x / nsplit; t < ntiles && ok; t += gridDim.x / nsplit) {
                 const int acc = it & 1;
                 if (it >= 2 && !(ok = wait_or_fail(&tempty[acc], (uint32_t)(((it >> 1) - 1) & 1), fail))) break;
                 tc_fence_after();
@@ -315,7 +322,7 @@ __global__ void __launch_bounds__(192, 1)
         }
     } else {
         conv_epilogue<N>(tmem, tfull, tempty, fail, warp, lane, ntiles, tiles_x, tiles_y, H, W, Cout, bias, relu,
-                         out_bf, out_f);
+                         out_bf, out_f, nsplit);
     }
 
     tc_fence_before();
@@ -356,7 +363,7 @@ template <int N, int SWB>
 __global__ void __launch_bounds__(192, 1)
     conv3x3_fwd_tma_wres_kernel(const __grid_constant__ CUtensorMap map_in, const __grid_constant__ CUtensorMap map_w,
                                 const float* __restrict__ bias, int B, int H, int W, int Cin, int Cout, int relu,
-                                __nv_bfloat16* out_bf, float* out_f, int* status, int SA) {
+                                __nv_bfloat16* out_bf, float* out_f, int* status, int SA, int nsplit) {
     using L = TmaConvRes<N, SWB>;
     extern __shared__ unsigned char dsm_raw[];
     unsigned char* dsm = dsm_raw + ((1024u - (smem_u32(dsm_raw) & 1023u)) & 1023u);
@@ -375,6 +382,7 @@ __global__ void __launch_bounds__(192, 1)
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int tiles_x = (W + 15) >> 4, tiles_y = (H + 7) >> 3;
     const int ntiles = B * tiles_x * tiles_y;
+    const int co0 = (blockIdx.x % nsplit) * N;  // this CTA's slice of the output channels
     constexpr uint32_t kIdesc = umma_idesc_bf16(128, N);
 
     if (warp == 1) {
@@ -409,10 +417,10 @@ __global__ void __launch_bounds__(192, 1)
             mbar_expect_tx(wfull, (uint32_t)(9 * csteps * L::BSTAGE));
             for (int cc = 0; cc < csteps; ++cc)
                 for (int tap = 0; tap < 9; ++tap)
-                    tma_load_2d(sW + (cc * 9 + tap) * L::BSTAGE, &map_w, wfull, cc * L::BK, tap * Cout);
+                    tma_load_2d(sW + (cc * 9 + tap) * L::BSTAGE, &map_w, wfull, cc * L::BK, tap * Cout + co0);
             int ia = 0;
             bool ok = true;
-            for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
+            for (int t = blockIdx.x / nsplit; t < ntiles && ok; t += gridDim.x / nsplit) {
                 const int tx = t % tiles_x, r = t / tiles_x, ty = r % tiles_y, b = r / tiles_y;
                 const int x0 = tx * 16, y0 = ty * 8;
                 for (int cc = 0; cc < csteps; ++cc) {
@@ -438,7 +446,7 @@ __global__ void __launch_bounds__(192, 1)
             tc_fence_after();
             int ia = 0, it = 0;
             const uint32_t w0 = smem_u32(sW);
-            for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
+            for (int t = blockIdx.x / nsplit; t < ntiles && ok; t += gridDim.x / nsplit) {
                 const int acc = it & 1;
                 if (it >= 2 && !(ok = wait_or_fail(&tempty[acc], (uint32_t)(((it >> 1) - 1) & 1), fail))) break;
                 tc_fence_after();
@@ -469,7 +477,7 @@ __global__ void __launch_bounds__(192, 1)
         }
     } else {
         conv_epilogue<N>(tmem, tfull, tempty, fail, warp, lane, ntiles, tiles_x, tiles_y, H, W, Cout, bias, relu,
-                         out_bf, out_f);
+                         out_bf, out_f, nsplit);
     }
 
     tc_fence_before();

@@ -20,16 +20,23 @@ def _need_gpu():
         pytest.skip("no CUDA device")
 
 
-# conv3x3_fwd_tma keeps small layers' weights resident in shared memory;
-# "conv3x3_fwd_tma_stream" forces its weight-streaming variant on every shape.
-KERNELS = ["conv3x3_fwd_tc", "conv3x3_fwd_tc2", "conv3x3_fwd_tma", "conv3x3_fwd_tma_stream"]
+# conv3x3_fwd_tma keeps small layers' weights resident in shared memory and
+# splits small layers' output channels over several CTAs per tile;
+# "conv3x3_fwd_tma_stream" forces its weight-streaming variant, "..._split2" /
+# "..._split4" force 2 / 4 CTAs per tile, on every shape they apply to.
+KERNELS = ["conv3x3_fwd_tc", "conv3x3_fwd_tc2", "conv3x3_fwd_tma", "conv3x3_fwd_tma_stream",
+           "conv3x3_fwd_tma_split2", "conv3x3_fwd_tma_split4"]
+MODES = {"conv3x3_fwd_tma_stream": 1, "conv3x3_fwd_tma_split2": 2 << 4, "conv3x3_fwd_tma_split4": 4 << 4}
 
 
 def _tc(kernel, Cout):
     if kernel != "conv3x3_fwd_tc" and Cout not in (32, 64, 128, 256):
         pytest.skip("the pipelined kernels cover Cout in {32, 64, 128, 256}")
-    if kernel == "conv3x3_fwd_tma_stream":
-        return lambda *a: q.nn.conv3x3_fwd_tma_mode(*a, 1)
+    if kernel in MODES:
+        mode = MODES[kernel]
+        if Cout // max(1, mode >> 4) < 32:
+            pytest.skip("at least 32 output channels per CTA")
+        return lambda *a: q.nn.conv3x3_fwd_tma_mode(*a, mode)
     return getattr(q.nn, kernel)
 
 
