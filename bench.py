@@ -442,8 +442,11 @@ def run_cuda(args, world, rank, local):
         torch.cuda.empty_cache()
         large = run_large(q, torch, dev, st, peak)
     serving = None
-    if not args.no_serving and args.case == "full":
-        serving = run_serving(q, torch, dev, st, peak)
+    if not args.no_serving:
+        # the small case keeps the mix's frame sizes (same bytes per tick) with
+        # N = 8 windows, so its rings take well under 1 GB
+        mix = SERVING_MIX if args.case == "full" else [(h, w, 8, f) for (h, w, n, f) in SERVING_MIX]
+        serving = run_serving(q, torch, dev, st, peak, mix=mix)
     learned_res = None
     if not args.no_learned and args.case == "full":
         learned_res = run_learned(q, torch, dev, st)
@@ -587,7 +590,18 @@ def run_packed(q, torch, dev, st, pool, peak, steps=500):
 SERVING_MIX = [(480, 640, 256, 1)] * 2 + [(1024, 1280, 1024, 2)] * 4 + [(2048, 2048, 2048, 2)] * 2
 
 
-def run_serving(q, torch, dev, st, peak, ticks=300, paced_ticks=300, fps=200.0):
+def _runs(mix):
+    """[(stream shape, how many in a row)] of a serving mix."""
+    out = []
+    for m in mix:
+        if out and out[-1][0] == m:
+            out[-1][1] += 1
+        else:
+            out.append([m, 1])
+    return [(m, c) for m, c in out]
+
+
+def run_serving(q, torch, dev, st, peak, ticks=300, paced_ticks=300, fps=200.0, mix=None):
     """Eight camera streams of uneven size (2 x 640x480 uint8 N=256, 4 x
     1280x1024 uint16 N=1024, 2 x 2048x2048 uint16 N=2048) served by one
     qld_server: admission by HBM footprint, autotuned launch shape, one
@@ -596,13 +610,15 @@ def run_serving(q, torch, dev, st, peak, ticks=300, paced_ticks=300, fps=200.0):
     ticks paced at `fps` (frames already in HBM when the tick's clock starts)."""
     from qldscene import DeviceScene, scene_fog, scene_plain
 
+    mix = mix or SERVING_MIX
+
     P = 32
-    budget = sum(q.qld_footprint_bytes(*m) + 8 * m[0] * m[1] for m in SERVING_MIX)
+    budget = sum(q.qld_footprint_bytes(*m) + 8 * m[0] * m[1] for m in mix)
     srv = q.qld_server_create(budget)
-    tickets = [q.qld_server_request(srv, *m) for m in SERVING_MIX]
+    tickets = [q.qld_server_request(srv, *m) for m in mix]
     admitted = sum(q.qld_server_state(srv, t) == 0 for t in tickets)
     pools = []
-    for i, (Hs, Ws, Ns, fmt) in enumerate(SERVING_MIX):
+    for i, (Hs, Ws, Ns, fmt) in enumerate(mix):
         sc = scene_plain(seed=1003 + i, H=Hs, W=Ws) if fmt == 1 else scene_fog(6, seed=1003 + i, H=Hs, W=Ws)
         dt = torch.uint8 if fmt == 1 else torch.uint16
         pool = torch.empty((P, Hs, Ws), dtype=dt, device=dev)
@@ -610,9 +626,9 @@ def run_serving(q, torch, dev, st, peak, ticks=300, paced_ticks=300, fps=200.0):
         pools.append(pool)
     # fill every window
     pushed = [0] * len(tickets)
-    while min(pushed[i] - SERVING_MIX[i][2] for i in range(len(tickets))) < 0:
+    while min(pushed[i] - mix[i][2] for i in range(len(tickets))) < 0:
         for i, t in enumerate(tickets):
-            n = min(P, max(0, SERVING_MIX[i][2] - pushed[i]))
+            n = min(P, max(0, mix[i][2] - pushed[i]))
             if n:
                 q.qld_server_submit(srv, t, pools[i][:n], n)
                 pushed[i] += n
@@ -644,8 +660,8 @@ def run_serving(q, torch, dev, st, peak, ticks=300, paced_ticks=300, fps=200.0):
     e1.record(st)
     e1.synchronize()
     tick_us = e0.elapsed_time(e1) * 1e3 / ticks
-    npix_tick = sum(m[0] * m[1] for m in SERVING_MIX)
-    bytes_tick = sum(m[0] * m[1] * (3 * m[3] + 24) for m in SERVING_MIX)
+    npix_tick = sum(m[0] * m[1] for m in mix)
+    bytes_tick = sum(m[0] * m[1] * (3 * m[3] + 24) for m in mix)
 
     lat = []
     ev = torch.cuda.Event()
@@ -666,8 +682,10 @@ def run_serving(q, torch, dev, st, peak, ticks=300, paced_ticks=300, fps=200.0):
     srv.destroy()
     del pools
     torch.cuda.empty_cache()
-    return {"workload": "8 streams: 2x640x480 uint8 N=256, 4x1280x1024 uint16 N=1024, 2x2048x2048 uint16 N=2048; "
-                        "one new frame per stream per tick, one graph-replayed persistent launch per tick",
+    return {"workload": "8 streams: " + ", ".join("%dx%dx%d %s N=%d" % (c, m[1], m[0], "uint8" if m[3] == 1 else "uint16",
+                                                                     m[2])
+                                                  for m, c in _runs(mix)) +
+                        "; one new frame per stream per tick, one graph-replayed persistent launch per tick",
             "admitted": admitted, "server_mem_gb": mem / 1e9, "budget_gb": budget / 1e9,
             "autotuned_shape": {"index": shape_idx, "threads": shape[0], "vectors_per_thread": shape[1],
                                 "ctas_per_sm": shape[2], "tuning_us_per_tick": tuned_us},

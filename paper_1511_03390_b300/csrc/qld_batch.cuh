@@ -16,7 +16,7 @@ namespace qldk {
 
 // One stream's share of a batch.
 struct BatchItem {
-    PushArgs a;       // nvec counts Fmt<T>::VB-byte vectors (vector path only)
+    PushArgs a;       // nvec counts batch_vec_bytes(fmt)-byte vectors (8 pixels each)
     int fmt;          // 1 = uint8, 2 = uint16, 3 = packed 12-bit
     int reset;        // the push holds at least N frames: rebuild the window
     int epi;          // write the amplitude / phase image after the push
@@ -31,11 +31,11 @@ struct BatchHeader {
 template <typename T>
 __device__ __forceinline__ void push_vector_mode(const PushArgs& a, int reset, int epi, long long v) {
     if (reset) {
-        if (epi) push_vector<T, true, true>(a, v);
-        else push_vector<T, true, false>(a, v);
+        if (epi) push_vector<T, true, true, false>(a, v);
+        else push_vector<T, true, false, false>(a, v);
     } else {
-        if (epi) push_vector<T, false, true>(a, v);
-        else push_vector<T, false, false>(a, v);
+        if (epi) push_vector<T, false, true, false>(a, v);
+        else push_vector<T, false, false, false>(a, v);
     }
 }
 
@@ -63,11 +63,14 @@ __global__ void __launch_bounds__(NT) batch_push_kernel(const BatchHeader* __res
             const long long v = vbase + (long long)k * NT + threadIdx.x;
             if (v >= a.nvec) break;
             if (fmt == 2) push_vector_mode<uint16_t>(a, reset, epi, v);
-            else if (fmt == 1) push_vector_mode<uint8_t>(a, reset, epi, v);
-            else push_vector_mode<p12_t>(a, reset, epi, v);
+            else if (fmt == 1) push_vector_mode<u8h_t>(a, reset, epi, v);
+            else push_vector_mode<p12h_t>(a, reset, epi, v);
         }
     }
 }
+
+// Bytes of the 8-pixel vectors the batch kernel reads a pixel format in.
+inline int batch_vec_bytes(int pixfmt) { return pixfmt == 2 ? 16 : (pixfmt == 1 ? 8 : 12); }
 
 // Launch shapes the autotuner chooses from: threads per CTA, vectors per
 // thread per tile, resident CTAs per SM of the persistent grid.
@@ -75,8 +78,8 @@ struct BatchShape {
     int threads, vpt, ctas_per_sm;
 };
 
-constexpr BatchShape kBatchShapes[] = {{128, 1, 4}, {128, 2, 4}, {128, 4, 4}, {256, 1, 2},
-                                       {256, 2, 2}, {256, 1, 4}, {128, 1, 8}, {64, 2, 8}};
+constexpr BatchShape kBatchShapes[] = {{128, 1, 4}, {128, 2, 4}, {128, 4, 4}, {256, 1, 2}, {256, 2, 2}, {256, 1, 4},
+                                       {128, 1, 8}, {64, 2, 8},  {128, 2, 8}, {256, 2, 4}, {128, 4, 8}};
 constexpr int kNumBatchShapes = (int)(sizeof(kBatchShapes) / sizeof(kBatchShapes[0]));
 
 inline long long batch_tile_vectors(const BatchShape& s) { return (long long)s.threads * s.vpt; }

@@ -33,10 +33,10 @@ struct P12Vec {
     uint32_t w[6];
 };
 
-// The DFT-bin kernel reads uint8 and packed 12-bit frames in vectors of 8
-// pixels (8 and 12 bytes): with 16-pixel vectors its two-level accumulators
-// need over 100 registers per thread, too few warps to keep the loads in
-// flight. The push kernels keep 16-pixel vectors.
+// uint8 and packed 12-bit frames in vectors of 8 pixels (8 and 12 bytes), for
+// the DFT-bin kernel and the multi-stream batch push: with 16-pixel vectors
+// those need over 100 registers per thread, too few warps to keep the loads
+// in flight. The single-stream push kernel keeps 16-pixel vectors.
 struct u8h_t {};
 struct p12h_t {};
 struct P12Half {
@@ -90,6 +90,7 @@ struct Fmt<u8h_t> {
     using Vec = uint2;
     static constexpr int VB = 8, VP = 8, ALIGN = 8;
     static __device__ __forceinline__ Vec load(const uint8_t* p) { return __ldcs(reinterpret_cast<const uint2*>(p)); }
+    static __device__ __forceinline__ void store(uint8_t* p, const Vec& v) { __stcs(reinterpret_cast<uint2*>(p), v); }
     static __device__ __forceinline__ Vec zero() { return make_uint2(0u, 0u); }
 };
 
@@ -100,6 +101,12 @@ struct Fmt<p12h_t> {
     static __device__ __forceinline__ Vec load(const uint8_t* p) {
         const unsigned int* q = reinterpret_cast<const unsigned int*>(p);
         return P12Half{{__ldcs(q), __ldcs(q + 1), __ldcs(q + 2)}};
+    }
+    static __device__ __forceinline__ void store(uint8_t* p, const Vec& v) {
+        unsigned int* q = reinterpret_cast<unsigned int*>(p);
+        __stcs(q, v.w[0]);
+        __stcs(q + 1, v.w[1]);
+        __stcs(q + 2, v.w[2]);
     }
     static __device__ __forceinline__ Vec zero() { return P12Half{{0u, 0u, 0u}}; }
 };
@@ -334,7 +341,11 @@ struct PushArgs {
 // window is rebuilt from the applied frames alone (a push of at least N
 // frames), so the sums start at zero and the expiring slots are not read.
 // EPI: also write the amplitude / phase image.
-template <typename T, bool RESET, bool EPI>
+// GROUP4: frames are taken four at a time with all eight loads issued before
+// any store (the single-stream push kernel, where one push carries several
+// frames); without it one frame at a time, which needs far fewer registers
+// (the batch kernel, whose pushes carry one frame per stream per tick).
+template <typename T, bool RESET, bool EPI, bool GROUP4 = true>
 __device__ __forceinline__ void push_vector(const PushArgs& a, long long v) {
     using F = Fmt<T>;
     using Vec = typename F::Vec;
@@ -361,7 +372,7 @@ __device__ __forceinline__ void push_vector(const PushArgs& a, long long v) {
     int f = 0;
     // Groups of four frames: all loads are issued before any store so eight
     // 128-bit loads per thread are in flight.
-    for (; f + 4 <= a.nf; f += 4) {
+    for (; GROUP4 && f + 4 <= a.nf; f += 4) {
         Vec xn[4], xo[4];
 #pragma unroll
         for (int u = 0; u < 4; ++u) xo[u] = F::zero();

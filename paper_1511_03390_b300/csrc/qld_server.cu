@@ -147,7 +147,7 @@ int build_items(qld_server* s, qldk::BatchItem* items, qldk::BatchHeader* hdr, s
         a.S = c->S;
         a.C = c->C;
         a.npix = c->npix;
-        a.nvec = c->frame_bytes / qldi::vec_bytes_of(c->pixfmt);
+        a.nvec = c->frame_bytes / qldk::batch_vec_bytes(c->pixfmt);
         a.amp = t.amp;
         a.phase = t.phase;
         a.out_aligned = 1;
