@@ -356,6 +356,23 @@ int qldnn_conv3x3_fwd_tma(const void* in, const void* wk, const float* bias, int
 int qldnn_conv3x3_fwd_tma_mode(const void* in, const void* wk, const float* bias, int B, int H, int W, int Cin,
                                int Cout, int relu, void* out_bf16, float* out_f32, int* status, int mode,
                                void* stream);
+/* The persistent TMA convolution with the layer's neighbours fused into its
+ * epilogue (inference of the learned network). Any of:
+ *   out_bf16  the activation, rows of ldo >= Cout channels (a multiple of 8):
+ *             with ldo > Cout it fills a channel slice of a concatenated tensor
+ *   pool_bf16 [B][H/2][W/2][Cout], the 2x2 average of the bf16 activation
+ *             (H and W even)
+ *   up_bf16   [B][2H][2W], rows of ldu channels: the nearest 2x upsampling,
+ *             e.g. into the first channels of the next level's skip concat
+ *   head      pred [B][H][W] f32 = head_b[0] + sum_c act[c] head_w[c] +
+ *             baseline[p] (head_w [Cout], head_b, baseline, pred all given)
+ * The pooled, upsampled and head outputs equal qldnn_avgpool2,
+ * qldnn_upsample_concat and qldnn_head + qldnn_add on the bf16 activation bit
+ * for bit. Pointers 16-byte aligned. */
+int qldnn_conv3x3_fwd_tma_epi(const void* in, const void* wk, const float* bias, int B, int H, int W, int Cin,
+                              int Cout, int relu, void* out_bf16, long long ldo, void* pool_bf16, void* up_bf16,
+                              long long ldu, const float* head_w, const float* head_b, const float* baseline,
+                              float* pred, int* status, void* stream);
 /* Weight gradient of the 3x3 convolution on the tensor cores: dw [9][Cin][Cout]
  * f32 += sum over pixels of in (shifted by the tap) x g, in [B][H][W][Cin]
  * and g [B][H][W][Cout] bf16 (the caller zeroes dw; 16-byte aligned). Cin is

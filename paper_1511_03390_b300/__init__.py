@@ -90,6 +90,8 @@ _SIGS = {
     "qldnn_conv3x3_fwd_tc2": ([_p, _p, _p, _i, _i, _i, _i, _i, _i, _p, _p, _p, _p], _i),
     "qldnn_conv3x3_fwd_tma": ([_p, _p, _p, _i, _i, _i, _i, _i, _i, _p, _p, _p, _p], _i),
     "qldnn_conv3x3_fwd_tma_mode": ([_p, _p, _p, _i, _i, _i, _i, _i, _i, _p, _p, _p, _i, _p], _i),
+    "qldnn_conv3x3_fwd_tma_epi": ([_p, _p, _p, _i, _i, _i, _i, _i, _i, _p, _ll, _p, _p, _ll, _p, _p, _p, _p, _p, _p],
+                                  _i),
     "qldnn_conv3x3_wgrad_tma": ([_p, _p, _i, _i, _i, _i, _i, _p, _p, _p], _i),
     "qld_server_create": ([_ll, _i], _p),
     "qld_server_destroy": ([_p], None),

@@ -590,7 +590,7 @@ int sm_count(int dev) {
 
 template <int N, int SWB>
 int launch_tma(const void* in, const void* wk, const float* bias, int B, int H, int W, int Cin, int Cout, int relu,
-               __nv_bfloat16* ob, float* of, int* status, cudaStream_t st, bool force_stream) {
+               const qldnn::ConvEpi& epi, int* status, cudaStream_t st, bool force_stream) {
     using L = qldnn::TmaConv<N, SWB>;
     EncodeTiledFn enc = encode_tiled();
     int dev = 0;
@@ -633,7 +633,7 @@ int launch_tma(const void* in, const void* wk, const float* bias, int B, int H, 
             attr_res.fetch_or(1ull << dev);
         }
         qldnn::conv3x3_fwd_tma_wres_kernel<N, SWB><<<grid, 192, (size_t)R::smem(sa, Cin), st>>>(
-            mi, mw, bias, B, H, W, Cin, Cout, relu, ob, of, status, sa, nsplit);
+            mi, mw, bias, B, H, W, Cin, Cout, relu, epi, status, sa, nsplit);
         return launched(1);
     }
     static std::atomic<unsigned long long> attr_done{0};  // per instantiation, one bit per device
@@ -643,7 +643,7 @@ int launch_tma(const void* in, const void* wk, const float* bias, int B, int H, 
             return set_err(QLD_E_CUDA);
         attr_done.fetch_or(1ull << dev);
     }
-    qldnn::conv3x3_fwd_tma_kernel<N, SWB><<<grid, 192, L::kSmem, st>>>(mi, mw, bias, B, H, W, Cin, Cout, relu, ob, of,
+    qldnn::conv3x3_fwd_tma_kernel<N, SWB><<<grid, 192, L::kSmem, st>>>(mi, mw, bias, B, H, W, Cin, Cout, relu, epi,
                                                                         status, nsplit);
     return launched(1);
 }
@@ -692,6 +692,50 @@ int launch_wgrad_tma(const void* in, const void* g, int B, int H, int W, int Cin
     qldnn::conv3x3_wgrad_tma_kernel<N, SWA, STACK><<<(unsigned)(3 * ncb * nsplit), 192, L::kSmem, st>>>(
         mi, mg, B, H, W, Cin, Cout, (int)nsplit, dw, status);
     return launched(1);
+}
+
+// Chooses the variant (weights resident or streamed, CTAs per tile) and the
+// template instance of the persistent TMA convolution; mode as in
+// qldnn_conv3x3_fwd_tma_mode.
+int conv_tma_dispatch(const void* in, const void* wk, const float* bias, int B, int H, int W, int Cin, int Cout,
+                      int relu, const qldnn::ConvEpi& epi, int* status, int mode, cudaStream_t st) {
+    const int force_stream = mode & 1;
+    const int split_mode = (mode >> 4) & 0xF;
+    if (split_mode != 0 && split_mode != 1 && split_mode != 2 && split_mode != 4) return set_err(QLD_E_INVAL);
+    if (!in || !wk || B < 1 || H < 1 || W < 1 || Cin < 16 || Cin % 16 ||
+        (Cout != 32 && Cout != 64 && Cout != 128 && Cout != 256) || !al(in, 16) || !al(wk, 16) ||
+        (long long)B * H * W * Cin >= (1ll << 40))
+        return set_err(QLD_E_INVAL);
+    const int swb = Cin % 64 == 0 ? 128 : (Cin % 32 == 0 ? 64 : 32);
+    // fewer tiles than SMs: split each tile's output channels over 2 or 4 CTAs
+    int dev = 0, nsm = 148;
+    if (cudaGetDevice(&dev) == cudaSuccess) {
+        const int n = sm_count(dev);
+        if (n > 0) nsm = n;
+    }
+    const long long ntiles = (long long)B * ((H + 7) / 8) * ((W + 15) / 16);
+    // split only into slices whose weights stay resident: a streamed slice
+    // reloads the whole input halo per CTA and runs narrower MMAs (slower)
+    auto resident = [&](int nco) {
+        const long long halo3 = 3ll * 160 * swb;
+        return 1024 + 2 * halo3 + 9ll * Cin * nco * 2 + 256 <= 232448;
+    };
+    // and only when at most half the SMs would otherwise get a tile: with
+    // more, the narrower MMAs and repeated halo loads cost more than it gains
+    int nsplit = 1;
+    for (int cand = 2; cand <= 4 && 2 * ntiles <= nsm && ntiles * nsplit < nsm; cand *= 2)
+        if (Cout / cand >= 32 && resident(Cout / cand)) nsplit = cand;
+    if (split_mode > 0) nsplit = split_mode;
+    if (Cout % nsplit || Cout / nsplit < 32) return set_err(QLD_E_INVAL);
+    const int nco = Cout / nsplit;
+#define QLD_TMA(NN, SS) \
+    if (nco == NN && swb == SS) return launch_tma<NN, SS>(in, wk, bias, B, H, W, Cin, Cout, relu, epi, status, st, force_stream != 0);
+    QLD_TMA(32, 32) QLD_TMA(32, 64) QLD_TMA(32, 128)
+    QLD_TMA(64, 32) QLD_TMA(64, 64) QLD_TMA(64, 128)
+    QLD_TMA(128, 32) QLD_TMA(128, 64) QLD_TMA(128, 128)
+    QLD_TMA(256, 32) QLD_TMA(256, 64) QLD_TMA(256, 128)
+#undef QLD_TMA
+    return set_err(QLD_E_INVAL);
 }
 }  // namespace
 
@@ -995,46 +1039,39 @@ int qldnn_conv3x3_fwd_tma_mode(const void* in, const void* wk, const float* bias
                                void* stream) {
     // mode: bit 0 forces the weight-streaming variant; bits 4.. (if non-zero)
     // force the number of CTAs per tile (1, 2 or 4)
-    const int force_stream = mode & 1;
-    const int split_mode = (mode >> 4) & 0xF;
-    if (split_mode != 0 && split_mode != 1 && split_mode != 2 && split_mode != 4) return set_err(QLD_E_INVAL);
-    if (!in || !wk || (!out_bf16 && !out_f32) || B < 1 || H < 1 || W < 1 || Cin < 16 || Cin % 16 ||
-        (Cout != 32 && Cout != 64 && Cout != 128 && Cout != 256) || !al(in, 16) || !al(wk, 16) ||
-        !al(out_bf16, 16) || !al(out_f32, 16) || (long long)B * H * W * Cin >= (1ll << 40))
-        return set_err(QLD_E_INVAL);
-    __nv_bfloat16* ob = (__nv_bfloat16*)out_bf16;
-    const cudaStream_t st = (cudaStream_t)stream;
-    const int swb = Cin % 64 == 0 ? 128 : (Cin % 32 == 0 ? 64 : 32);
-    // fewer tiles than SMs: split each tile's output channels over 2 or 4 CTAs
-    int dev = 0, nsm = 148;
-    if (cudaGetDevice(&dev) == cudaSuccess) {
-        const int n = sm_count(dev);
-        if (n > 0) nsm = n;
-    }
-    const long long ntiles = (long long)B * ((H + 7) / 8) * ((W + 15) / 16);
-    // split only into slices whose weights stay resident: a streamed slice
-    // reloads the whole input halo per CTA and runs narrower MMAs (slower)
-    auto resident = [&](int nco) {
-        const long long halo3 = 3ll * 160 * swb;
-        return 1024 + 2 * halo3 + 9ll * Cin * nco * 2 + 256 <= 232448;
-    };
-    // and only when at most half the SMs would otherwise get a tile: with
-    // more, the narrower MMAs and repeated halo loads cost more than it gains
-    int nsplit = 1;
-    for (int cand = 2; cand <= 4 && 2 * ntiles <= nsm && ntiles * nsplit < nsm; cand *= 2)
-        if (Cout / cand >= 32 && resident(Cout / cand)) nsplit = cand;
-    if (split_mode > 0) nsplit = split_mode;
-    if (Cout % nsplit || Cout / nsplit < 32) return set_err(QLD_E_INVAL);
-    const int nco = Cout / nsplit;
-#define QLD_TMA(NN, SS) \
-    if (nco == NN && swb == SS) \
-        return launch_tma<NN, SS>(in, wk, bias, B, H, W, Cin, Cout, relu, ob, out_f32, status, st, force_stream != 0);
-    QLD_TMA(32, 32) QLD_TMA(32, 64) QLD_TMA(32, 128)
-    QLD_TMA(64, 32) QLD_TMA(64, 64) QLD_TMA(64, 128)
-    QLD_TMA(128, 32) QLD_TMA(128, 64) QLD_TMA(128, 128)
-    QLD_TMA(256, 32) QLD_TMA(256, 64) QLD_TMA(256, 128)
-#undef QLD_TMA
-    return set_err(QLD_E_INVAL);
+    if (!out_bf16 && !out_f32) return set_err(QLD_E_INVAL);
+    if (!al(out_bf16, 16) || !al(out_f32, 16)) return set_err(QLD_E_INVAL);
+    qldnn::ConvEpi epi{};
+    epi.out = (__nv_bfloat16*)out_bf16;
+    epi.ldo = Cout;
+    epi.out_f = out_f32;
+    return conv_tma_dispatch(in, wk, bias, B, H, W, Cin, Cout, relu, epi, status, mode, (cudaStream_t)stream);
+}
+
+int qldnn_conv3x3_fwd_tma_epi(const void* in, const void* wk, const float* bias, int B, int H, int W, int Cin,
+                              int Cout, int relu, void* out_bf16, long long ldo, void* pool_bf16, void* up_bf16,
+                              long long ldu, const float* head_w, const float* head_b, const float* baseline,
+                              float* pred, int* status, void* stream) {
+    const bool head = head_w || head_b || baseline || pred;
+    if (!out_bf16 && !pool_bf16 && !up_bf16 && !head) return set_err(QLD_E_INVAL);
+    if (out_bf16 && (!al(out_bf16, 16) || ldo < Cout || ldo % 8)) return set_err(QLD_E_INVAL);
+    if (pool_bf16 && (!al(pool_bf16, 16) || H % 2 || W % 2)) return set_err(QLD_E_INVAL);
+    if (up_bf16 && (!al(up_bf16, 16) || ldu < Cout || ldu % 8)) return set_err(QLD_E_INVAL);
+    if (head && (!head_w || !head_b || !baseline || !pred)) return set_err(QLD_E_INVAL);
+    qldnn::ConvEpi epi{};
+    epi.out = (__nv_bfloat16*)out_bf16;
+    epi.ldo = ldo;
+    epi.pool = (__nv_bfloat16*)pool_bf16;
+    epi.ldp = Cout;
+    epi.up = (__nv_bfloat16*)up_bf16;
+    epi.ldu = ldu;
+    epi.head_w = head_w;
+    epi.head_b = head_b;
+    epi.base = baseline;
+    epi.pred = pred;
+    // the head needs every output channel of a pixel in one CTA
+    return conv_tma_dispatch(in, wk, bias, B, H, W, Cin, Cout, relu, epi, status, head ? (1 << 4) : 0,
+                             (cudaStream_t)stream);
 }
 
 int qldnn_conv3x3_wgrad_tma(const void* in, const void* g, int B, int H, int W, int Cin, int Cout, float* dw,

@@ -107,21 +107,53 @@ __device__ __forceinline__ bool wait_or_fail(uint64_t* bar, uint32_t parity, vol
     return wait_timed(bar, parity, fail);
 }
 
+// Outputs of a persistent TMA convolution's epilogue. Every pointer may be
+// null. bf16 outputs are rows of `ld*` channels (>= Cout, a multiple of 8)
+// whose first Cout hold this layer: a layer can write straight into a slice
+// of a wider (concatenated) tensor.
+//   out   [B][H][W] x ldo, the activation (bf16)
+//   out_f [B][H][W][Cout] f32 (data gradients)
+//   pool  [B][H/2][W/2] x ldp, 2x2 average of the bf16 activations (H, W even)
+//   up    [B][2H][2W] x ldu, nearest 2x upsampling of the bf16 activations
+//   head  pred[p] = head_b + sum_c act_bf16[p][c] head_w[c] + base[p] (f32; all
+//         Cout channels in one CTA), the network's 1x1 output layer
+// The pooled and head values use the same operation order as the standalone
+// pooling / head / add kernels, so results are bit-identical to running them.
+struct ConvEpi {
+    __nv_bfloat16* out;
+    long long ldo;
+    float* out_f;
+    __nv_bfloat16* pool;
+    long long ldp;
+    __nv_bfloat16* up;
+    long long ldu;
+    const float* head_w;
+    const float* head_b;
+    const float* base;
+    float* pred;
+};
+
 // Epilogue warps (4 of them, warp w reads TMEM lanes 32 (w mod 4) ..) of the
 // persistent TMA convolutions: per tile, wait for its accumulator, add the
-// bias, apply ReLU, store bf16 / f32, release the accumulator.
+// bias, apply ReLU, write the outputs `epi` asks for, release the accumulator.
+// Pixel m = 32 (w mod 4) + lane of the tile is (y, x) = (m / 16, m mod 16), so
+// a warp holds two whole rows and the 2x2 pooling partners of lane l are the
+// lanes l ^ 1, l ^ 16 and l ^ 17.
 template <int N>
 __device__ __forceinline__ void conv_epilogue(uint32_t tmem, uint64_t* tfull, uint64_t* tempty, volatile int* fail,
                                               int warp, int lane, int ntiles, int tiles_x, int tiles_y, int H, int W,
-                                              int Cout, const float* __restrict__ bias, int relu,
-                                              __nv_bfloat16* out_bf, float* out_f, int nsplit) {
+                                              int Cout, const float* __restrict__ bias, int relu, ConvEpi epi,
+                                              int nsplit) {
     const int qw = warp & 3;  // TMEM lane quarter this warp may read
     const int m = qw * 32 + lane;
     const int my = m >> 4, mx = m & 15;
     const int co0 = (blockIdx.x % nsplit) * N;  // this CTA's slice of the output channels
     if (bias) bias += co0;
-    if (out_bf) out_bf += co0;
-    if (out_f) out_f += co0;
+    if (epi.out) epi.out += co0;
+    if (epi.out_f) epi.out_f += co0;
+    if (epi.pool) epi.pool += co0;
+    if (epi.up) epi.up += co0;
+    const bool pool_writer = (lane & 17) == 0;  // even x, even y
     int it = 0;
     for (int t = blockIdx.x / nsplit; t < ntiles; t += gridDim.x / nsplit) {
         const int acc = it & 1;
@@ -133,36 +165,80 @@ __device__ __forceinline__ void conv_epilogue(uint32_t tmem, uint64_t* tfull, ui
         const bool inside = y < H && x < W;
         const long long p = ((long long)b * H + y) * W + x;
         const uint32_t taddr = tmem + ((uint32_t)(qw * 32) << 16) + (uint32_t)(acc * N);
+        float hacc = epi.head_w ? *epi.head_b : 0.f;
 #pragma unroll 1
         for (int c0 = 0; c0 < N; c0 += 16) {
             uint32_t rr[16];
             tc_ld16(taddr + (uint32_t)c0, rr);
             asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
-            if (inside) {
-                float v[16];
+            float v[16];
 #pragma unroll
-                for (int j = 0; j < 16; ++j) {
-                    v[j] = __uint_as_float(rr[j]) + (bias ? bias[c0 + j] : 0.f);
-                    if (relu) v[j] = fmaxf(v[j], 0.f);
-                }
-                if (out_bf) {
-                    uint32_t pk[8];
+            for (int j = 0; j < 16; ++j) {
+                v[j] = __uint_as_float(rr[j]) + (bias ? bias[c0 + j] : 0.f);
+                if (relu) v[j] = fmaxf(v[j], 0.f);
+            }
+            uint32_t pk[8];
 #pragma unroll
-                    for (int j = 0; j < 8; ++j) {
-                        const __nv_bfloat162 h2 = __floats2bfloat162_rn(v[2 * j], v[2 * j + 1]);
-                        pk[j] = *reinterpret_cast<const uint32_t*>(&h2);
-                    }
-                    uint4* o = reinterpret_cast<uint4*>(out_bf + p * Cout + c0);
+            for (int j = 0; j < 8; ++j) {
+                const __nv_bfloat162 h2 = __floats2bfloat162_rn(v[2 * j], v[2 * j + 1]);
+                pk[j] = *reinterpret_cast<const uint32_t*>(&h2);
+            }
+            if (epi.out && inside) {
+                uint4* o = reinterpret_cast<uint4*>(epi.out + p * epi.ldo + c0);
+                o[0] = make_uint4(pk[0], pk[1], pk[2], pk[3]);
+                o[1] = make_uint4(pk[4], pk[5], pk[6], pk[7]);
+            }
+            if (epi.out_f && inside) {
+                float4* o = reinterpret_cast<float4*>(epi.out_f + p * Cout + c0);
+#pragma unroll
+                for (int j = 0; j < 4; ++j) o[j] = make_float4(v[4 * j], v[4 * j + 1], v[4 * j + 2], v[4 * j + 3]);
+            }
+            if (epi.up && inside) {
+#pragma unroll
+                for (int d = 0; d < 4; ++d) {
+                    const long long q = ((long long)b * 2 * H + 2 * y + (d >> 1)) * (2ll * W) + 2 * x + (d & 1);
+                    uint4* o = reinterpret_cast<uint4*>(epi.up + q * epi.ldu + c0);
                     o[0] = make_uint4(pk[0], pk[1], pk[2], pk[3]);
                     o[1] = make_uint4(pk[4], pk[5], pk[6], pk[7]);
                 }
-                if (out_f) {
-                    float4* o = reinterpret_cast<float4*>(out_f + p * Cout + c0);
+            }
+            if (epi.pool || epi.head_w) {
+                float f[16];  // the stored (bf16) values
 #pragma unroll
-                    for (int j = 0; j < 4; ++j) o[j] = make_float4(v[4 * j], v[4 * j + 1], v[4 * j + 2], v[4 * j + 3]);
+                for (int j = 0; j < 8; ++j) {
+                    const float2 t2 = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&pk[j]));
+                    f[2 * j] = t2.x;
+                    f[2 * j + 1] = t2.y;
+                }
+                if (epi.pool) {  // warp-uniform: every lane shuffles
+                    float o[16];
+#pragma unroll
+                    for (int j = 0; j < 16; ++j) {
+                        const float a1 = __shfl_xor_sync(0xffffffffu, f[j], 1);
+                        const float a2 = __shfl_xor_sync(0xffffffffu, f[j], 16);
+                        const float a3 = __shfl_xor_sync(0xffffffffu, f[j], 17);
+                        o[j] = 0.25f * (f[j] + a1 + a2 + a3);
+                    }
+                    if (pool_writer && inside) {
+                        uint32_t q2[8];
+#pragma unroll
+                        for (int j = 0; j < 8; ++j) {
+                            const __nv_bfloat162 h2 = __floats2bfloat162_rn(o[2 * j], o[2 * j + 1]);
+                            q2[j] = *reinterpret_cast<const uint32_t*>(&h2);
+                        }
+                        const long long pp = ((long long)b * (H / 2) + y / 2) * (W / 2) + x / 2;
+                        uint4* po = reinterpret_cast<uint4*>(epi.pool + pp * epi.ldp + c0);
+                        po[0] = make_uint4(q2[0], q2[1], q2[2], q2[3]);
+                        po[1] = make_uint4(q2[4], q2[5], q2[6], q2[7]);
+                    }
+                }
+                if (epi.head_w) {
+#pragma unroll
+                    for (int j = 0; j < 16; ++j) hacc = fmaf(f[j], epi.head_w[c0 + j], hacc);
                 }
             }
         }
+        if (epi.head_w && inside) epi.pred[p] = hacc + epi.base[p];
         tc_fence_before();
         mbar_arrive(&tempty[acc]);
         ++it;
@@ -190,7 +266,7 @@ template <int N, int SWB>
 __global__ void __launch_bounds__(192, 1)
     conv3x3_fwd_tma_kernel(const __grid_constant__ CUtensorMap map_in, const __grid_constant__ CUtensorMap map_w,
                            const float* __restrict__ bias, int B, int H, int W, int Cin, int Cout, int relu,
-                           __nv_bfloat16* out_bf, float* out_f, int* status, int nsplit) {
+                           const ConvEpi epi, int* status, int nsplit) {
     using L = TmaConv<N, SWB>;
     extern __shared__ unsigned char dsm_raw[];
     unsigned char* dsm = dsm_raw + ((1024u - (smem_u32(dsm_raw) & 1023u)) & 1023u);
@@ -321,8 +397,8 @@ __global__ void __launch_bounds__(192, 1)
             wait_timed(drain, 0, nullptr);
         }
     } else {
-        conv_epilogue<N>(tmem, tfull, tempty, fail, warp, lane, ntiles, tiles_x, tiles_y, H, W, Cout, bias, relu,
-                         out_bf, out_f, nsplit);
+        conv_epilogue<N>(tmem, tfull, tempty, fail, warp, lane, ntiles, tiles_x, tiles_y, H, W, Cout, bias, relu, epi,
+                         nsplit);
     }
 
     tc_fence_before();
@@ -363,7 +439,7 @@ template <int N, int SWB>
 __global__ void __launch_bounds__(192, 1)
     conv3x3_fwd_tma_wres_kernel(const __grid_constant__ CUtensorMap map_in, const __grid_constant__ CUtensorMap map_w,
                                 const float* __restrict__ bias, int B, int H, int W, int Cin, int Cout, int relu,
-                                __nv_bfloat16* out_bf, float* out_f, int* status, int SA, int nsplit) {
+                                const ConvEpi epi, int* status, int SA, int nsplit) {
     using L = TmaConvRes<N, SWB>;
     extern __shared__ unsigned char dsm_raw[];
     unsigned char* dsm = dsm_raw + ((1024u - (smem_u32(dsm_raw) & 1023u)) & 1023u);
@@ -476,8 +552,8 @@ __global__ void __launch_bounds__(192, 1)
             wait_timed(drain, 0, nullptr);
         }
     } else {
-        conv_epilogue<N>(tmem, tfull, tempty, fail, warp, lane, ntiles, tiles_x, tiles_y, H, W, Cout, bias, relu,
-                         out_bf, out_f, nsplit);
+        conv_epilogue<N>(tmem, tfull, tempty, fail, warp, lane, ntiles, tiles_x, tiles_y, H, W, Cout, bias, relu, epi,
+                         nsplit);
     }
 
     tc_fence_before();

@@ -116,6 +116,9 @@ class UNet:
         assert conv in self.CONVS, conv
         self.prm = params
         self.conv = conv
+        # inference with the TMA kernel: pooling, upsampling + skip concat and
+        # the head run inside the convolutions' epilogues
+        self.fused = inference_only and conv == "tma"
         self.status = torch.zeros(1, dtype=torch.int32, device=params.device)
         self.B, self.H, self.W = B, H, W
         d = params.device
@@ -191,7 +194,43 @@ class UNet:
         """Network input and baseline from short-window sums (int32 [B*H*W])."""
         nn.pack_input(S, C, self.P[0], IN_SCALE, self.a["x"], self.baseline)
 
+    def _conv_epi(self, name, level, x, out=None, ldo=0, pool=None, up=None, ldu=0, head=False):
+        _, cin, cout = next(l for l in LAYERS if l[0] == name)
+        h, w = self.dims[level]
+        hw = hb = base = pred = None
+        if head:
+            hw, hb, base, pred = self.prm["head.w"]["p"], self.prm["head.b"]["p"], self.baseline, self.pred
+        nn.conv3x3_fwd_tma_epi(x, self.prm[name + ".w"]["wk"], self.prm[name + ".b"]["p"], self.B, h, w, cin, cout, 1,
+                               out, ldo or cout, pool, up, ldu or cout, hw, hb, base, pred, self.status)
+
+    def _forward_fused(self):
+        """The forward pass with pooling, upsample + skip concatenation and the
+        head fused into the convolutions (bit-identical to the unfused pass):
+        each encoder block's second convolution writes its activation into the
+        skip half of the concat buffer and its 2x2 average into the next
+        level's input; each decoder block's second convolution writes its 2x
+        upsampling into the first half of the next concat buffer; the last
+        one computes the prediction directly."""
+        a = self.a
+        self._conv("c0a", 0, a["x"], a["a0"])
+        self._conv_epi("c0b", 0, a["a0"], out=a["cat0"][32:], ldo=64, pool=a["p0"])
+        self._conv("c1a", 1, a["p0"], a["a1"])
+        self._conv_epi("c1b", 1, a["a1"], out=a["cat1"][64:], ldo=128, pool=a["p1"])
+        self._conv("c2a", 2, a["p1"], a["a2"])
+        self._conv_epi("c2b", 2, a["a2"], out=a["cat2"][128:], ldo=256, pool=a["p2"])
+        self._conv("c3a", 3, a["p2"], a["a3"])
+        self._conv_epi("c3b", 3, a["a3"], up=a["cat2"], ldu=256)
+        self._conv("d2a", 2, a["cat2"], a["ad2"])
+        self._conv_epi("d2b", 2, a["ad2"], up=a["cat1"], ldu=128)
+        self._conv("d1a", 1, a["cat1"], a["ad1"])
+        self._conv_epi("d1b", 1, a["ad1"], up=a["cat0"], ldu=64)
+        self._conv("d0a", 0, a["cat0"], a["ad0"])
+        self._conv_epi("d0b", 0, a["ad0"], head=True)
+        return self.pred
+
     def forward(self):
+        if self.fused:
+            return self._forward_fused()
         a, B = self.a, self.B
         h, w = self.dims[0]
         self._conv("c0a", 0, a["x"], a["a0"])

@@ -104,3 +104,28 @@ def test_graph_replay_matches_eager_forward():
         torch.cuda.synchronize()
         assert graph.status.item() == 0 and eager.status.item() == 0
         assert torch.equal(got, want)
+
+
+@pytest.mark.parametrize("B,H,W", [(1, 64, 96), (2, 32, 48)])
+def test_fused_inference_forward_matches_the_layer_by_layer_pass(B, H, W):
+    """Inference nets fuse pooling, upsample + concat and the head into the
+    convolution epilogues; training nets run them as separate kernels. The
+    predictions must agree bit for bit."""
+    rng = np.random.default_rng(B * H + W)
+    prm = learned.Params(seed=9)
+    for k in prm.tensors:  # non-zero biases and head
+        if k.endswith(".b"):
+            prm[k]["p"].copy_(torch.from_numpy(rng.standard_normal(prm[k]["p"].numel()).astype(np.float32) * 0.1))
+    prm["head.w"]["p"].copy_(torch.from_numpy(rng.standard_normal(32).astype(np.float32) * 0.3))
+    fused = learned.UNet(prm, B, H, W, inference_only=True)
+    plain = learned.UNet(prm, B, H, W)
+    assert fused.fused and not plain.fused
+    S = torch.from_numpy(rng.integers(-5000, 5000, B * H * W).astype(np.int32)).cuda()
+    C = torch.from_numpy(rng.integers(-5000, 5000, B * H * W).astype(np.int32)).cuda()
+    fused.pack(S, C)
+    plain.pack(S, C)
+    want = plain.forward().clone()
+    got = fused.forward()
+    torch.cuda.synchronize()
+    assert fused.status.item() == 0 and plain.status.item() == 0
+    assert torch.equal(got, want)
