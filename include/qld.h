@@ -332,6 +332,17 @@ int qldnn_zero(void* p, long long bytes, void* stream);
  * data gradient. out_bf16 / out_f32 must be 16-byte aligned. status (device
  * int, may be NULL) becomes 1 if a bounded wait inside the kernel ran out. */
 int qldnn_kmajor_weights(const void* w, int Cin, int Cout, int flip, void* wk, void* stream);
+/* The learned network's first layer fused with its input packing: out =
+ * act(conv3x3(pack(S, C)) + bias) where pack is qldnn_pack_input's tensor
+ * (channels s, c, sqrt(s^2 + c^2) times `scale` in bf16, zeros after them);
+ * only the weights of input channels 0..2 of w [9][Cin][Cout] bf16 enter.
+ * Computed on the FP32 cores (27 x Cout per pixel). S, C int32 [B][H][W];
+ * out [B][H][W] rows of ldo >= Cout channels (a multiple of 8, 16-byte
+ * aligned), Cout 32 or 64; baseline [B][H][W] f32 (or NULL) = the scaled
+ * amplitude, as qldnn_pack_input writes it. */
+int qldnn_input_conv3x3(const int32_t* S, const int32_t* C, int B, int H, int W, float scale, const void* w,
+                        int Cin, int Cout, const float* bias, int relu, void* out_bf16, long long ldo, float* baseline,
+                        void* stream);
 /* Warp-specialised version of qldnn_conv3x3_fwd_tc (same arguments and
  * results; Cout must be 32, 64, 128 or 256, one tile of all output channels):
  * producer warps keep a 4-stage shared-memory ring of gathered K steps ahead

@@ -516,6 +516,142 @@ __global__ void head_bwd_v8_kernel(const uint4* __restrict__ in, const float* __
     if (threadIdx.x == 0) atomicAdd(db, sdw[CT]);
 }
 
+// The network's first convolution fused with its input packing. The packed
+// input (qldnn_pack_input) has channels (s, c, sqrt(s^2 + c^2)) * scale in
+// bf16 and zeros after them, so only the weights of input channels 0..2
+// contribute: a 27 x CO contraction per pixel, done here on the FP32 cores
+// (tensor-core tiles would multiply 13 zero channels out of 16). A CTA takes
+// a 16 x 16 output tile: the three channels of its 18 x 18 input halo are
+// computed once into shared memory with exactly the packing's operations,
+// each thread accumulates one pixel's CO outputs (taps, then channels, in
+// FP32), adds the bias, applies ReLU and stores bf16; the baseline (the
+// scaled amplitude, f32) of its pixels is written as qldnn_pack_input does.
+// Two FP32 lanes in one 64-bit register for the paired FMA (fma.rn.f32x2:
+// each lane rounds as fmaf, one issue slot per pair).
+__device__ __forceinline__ unsigned long long splat2(float a) {
+    unsigned long long r;
+    asm("mov.b64 %0, {%1, %1};" : "=l"(r) : "f"(a));
+    return r;
+}
+__device__ __forceinline__ unsigned long long fma2(unsigned long long a, unsigned long long b, unsigned long long c) {
+    unsigned long long d;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+    return d;
+}
+__device__ __forceinline__ float2 split2(unsigned long long a) {
+    float2 r;
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(r.x), "=f"(r.y) : "l"(a));
+    return r;
+}
+
+template <int CO>
+__global__ void __launch_bounds__(128) input_conv3x3_kernel(const int32_t* __restrict__ S, const int32_t* __restrict__ C,
+                                                            int B, int H, int W, float scale,
+                                                            const __nv_bfloat16* __restrict__ w, int Cin,
+                                                            const float* __restrict__ bias, int relu,
+                                                            __nv_bfloat16* __restrict__ out, long long ldo,
+                                                            float* __restrict__ baseline) {
+    // Persistent over tiles (weights staged once per CTA). 128 threads,
+    // thread t: pixels (t / 16, t mod 16) and (t / 16 + 8, t mod 16) of the
+    // tile, so each weight read from shared memory (4 channels at a time)
+    // serves 8 FMAs.
+    __shared__ float xin[3][18][18];
+    __shared__ float4 ws[27][CO / 4];
+    const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+    const int tiles_x = (W + 15) >> 4, tiles_y = (H + 15) >> 4;
+    const long long ntiles = (long long)B * tiles_x * tiles_y;
+    float* wsf = reinterpret_cast<float*>(ws);
+    for (int i = threadIdx.x; i < 27 * CO; i += 128) {
+        const int tc = i / CO, co = i - tc * CO;
+        const int tap = tc / 3, ci = tc - tap * 3;
+        wsf[i] = __bfloat162float(w[((long long)tap * Cin + ci) * CO + co]);
+    }
+    for (long long t0 = blockIdx.x; t0 < ntiles; t0 += gridDim.x) {
+        long long t = t0;
+        const int bx = (int)(t % tiles_x);
+        t /= tiles_x;
+        const int by = (int)(t % tiles_y);
+        const int b = (int)(t / tiles_y);
+        const int x0 = bx * 16, y0 = by * 16;
+        // the halo's sums: every load issued before any use (3 per thread)
+        int32_t sv[3], cv[3];
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            const int i = threadIdx.x + 128 * k;
+            const int yy = i / 18, xx = i - yy * 18;
+            const int gy = y0 + yy - 1, gx = x0 + xx - 1;
+            const bool ok = i < 18 * 18 && gy >= 0 && gy < H && gx >= 0 && gx < W;
+            const long long p = ok ? ((long long)b * H + gy) * W + gx : 0;  // in bounds either way
+            sv[k] = ok ? __ldg(S + p) : 0;
+            cv[k] = ok ? __ldg(C + p) : 0;
+        }
+        __syncthreads();  // the previous tile's reads of xin are done
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            const int i = threadIdx.x + 128 * k;
+            if (i < 18 * 18) {
+                const int yy = i / 18, xx = i - yy * 18;
+                const float s0 = (float)sv[k], c0 = (float)cv[k];
+                const float r = sqrtf(s0 * s0 + c0 * c0) * scale;
+                xin[0][yy][xx] = __bfloat162float(__float2bfloat16_rn(s0 * scale));
+                xin[1][yy][xx] = __bfloat162float(__float2bfloat16_rn(c0 * scale));
+                xin[2][yy][xx] = __bfloat162float(__float2bfloat16_rn(r));
+            }
+        }
+        __syncthreads();
+        unsigned long long a0[CO / 2], a1[CO / 2];  // channel pairs
+#pragma unroll
+        for (int h = 0; h < CO / 2; ++h) a0[h] = a1[h] = 0ull;
+#pragma unroll 1
+        for (int tap = 0; tap < 9; ++tap) {
+#pragma unroll
+            for (int ci = 0; ci < 3; ++ci) {
+                const unsigned long long xa = splat2(xin[ci][ty + tap / 3][tx + tap % 3]);
+                const unsigned long long xb = splat2(xin[ci][ty + 8 + tap / 3][tx + tap % 3]);
+                const ulonglong2* wrow = reinterpret_cast<const ulonglong2*>(ws[tap * 3 + ci]);
+#pragma unroll
+                for (int q = 0; q < CO / 4; ++q) {
+                    const ulonglong2 w2 = wrow[q];  // channels (4q, 4q+1) and (4q+2, 4q+3)
+                    a0[2 * q] = fma2(xa, w2.x, a0[2 * q]);
+                    a0[2 * q + 1] = fma2(xa, w2.y, a0[2 * q + 1]);
+                    a1[2 * q] = fma2(xb, w2.x, a1[2 * q]);
+                    a1[2 * q + 1] = fma2(xb, w2.y, a1[2 * q + 1]);
+                }
+            }
+        }
+        float acc0[CO], acc1[CO];
+#pragma unroll
+        for (int h = 0; h < CO / 2; ++h) {
+            const float2 u = split2(a0[h]), v = split2(a1[h]);
+            acc0[2 * h] = u.x;
+            acc0[2 * h + 1] = u.y;
+            acc1[2 * h] = v.x;
+            acc1[2 * h + 1] = v.y;
+        }
+#pragma unroll
+        for (int half = 0; half < 2; ++half) {
+            const int gy = y0 + ty + 8 * half, gx = x0 + tx;
+            if (gy >= H || gx >= W) continue;
+            const long long p = ((long long)b * H + gy) * W + gx;
+            const float* acc = half ? acc1 : acc0;
+#pragma unroll
+            for (int q = 0; q < CO / 8; ++q) {
+                float f[8];
+#pragma unroll
+                for (int j = 0; j < 8; ++j) {
+                    const float v = acc[8 * q + j] + (bias ? bias[8 * q + j] : 0.f);
+                    f[j] = relu ? fmaxf(v, 0.f) : v;
+                }
+                reinterpret_cast<uint4*>(out + p * ldo)[q] = pack8(f);
+            }
+            if (baseline) {
+                const float s0 = (float)S[p], c0 = (float)C[p];
+                baseline[p] = sqrtf(s0 * s0 + c0 * c0) * scale;
+            }
+        }
+    }
+}
+
 __global__ void pack_input_kernel(const int32_t* __restrict__ S, const int32_t* __restrict__ C, long long n,
                                   float scale, __nv_bfloat16* __restrict__ out, float* __restrict__ baseline) {
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
@@ -968,6 +1104,26 @@ int qldnn_pack_input(const int32_t* S, const int32_t* C, long long npix, float s
     if (!S || !C || !out || npix < 0 || !al(out, 16)) return set_err(QLD_E_INVAL);
     pack_input_kernel<<<grid_for(npix), 256, 0, (cudaStream_t)stream>>>(S, C, npix, scale, (__nv_bfloat16*)out,
                                                                          baseline);
+    return launched(1);
+}
+
+int qldnn_input_conv3x3(const int32_t* S, const int32_t* C, int B, int H, int W, float scale, const void* w,
+                        int Cin, int Cout, const float* bias, int relu, void* out_bf16, long long ldo, float* baseline,
+                        void* stream) {
+    if (!S || !C || !w || !out_bf16 || B < 1 || H < 1 || W < 1 || Cin < 3 || (Cout != 32 && Cout != 64) ||
+        ldo < Cout || ldo % 8 || !al(out_bf16, 16) || !al(baseline, 4))
+        return set_err(QLD_E_INVAL);
+    const long long tiles = (long long)B * ((H + 15) / 16) * ((W + 15) / 16);
+    int dev = 0, nsm = 148;
+    if (cudaGetDevice(&dev) == cudaSuccess && sm_count(dev) > 0) nsm = sm_count(dev);
+    const long long grid = tiles < 4ll * nsm ? tiles : 4ll * nsm;  // persistent: 4 CTAs per SM
+    const cudaStream_t st = (cudaStream_t)stream;
+    if (Cout == 32)
+        input_conv3x3_kernel<32><<<(unsigned)grid, 128, 0, st>>>(S, C, B, H, W, scale, (const __nv_bfloat16*)w, Cin,
+                                                                  bias, relu, (__nv_bfloat16*)out_bf16, ldo, baseline);
+    else
+        input_conv3x3_kernel<64><<<(unsigned)grid, 128, 0, st>>>(S, C, B, H, W, scale, (const __nv_bfloat16*)w, Cin,
+                                                                  bias, relu, (__nv_bfloat16*)out_bf16, ldo, baseline);
     return launched(1);
 }
 

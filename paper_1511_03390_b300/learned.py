@@ -111,14 +111,17 @@ class UNet:
 
     CONVS = ("tma", "tcgen05", "warp_mma")
 
-    def __init__(self, params, B, H, W, inference_only=False, conv="tma"):
+    def __init__(self, params, B, H, W, inference_only=False, conv="tma", fuse_input=True):
         assert H % 8 == 0 and W % 8 == 0
         assert conv in self.CONVS, conv
         self.prm = params
         self.conv = conv
         # inference with the TMA kernel: pooling, upsampling + skip concat and
-        # the head run inside the convolutions' epilogues
+        # the head run inside the convolutions' epilogues, and (fuse_input)
+        # the input packing inside the first convolution
         self.fused = inference_only and conv == "tma"
+        self.fuse_input = self.fused and fuse_input
+        self._iq = None
         self.status = torch.zeros(1, dtype=torch.int32, device=params.device)
         self.B, self.H, self.W = B, H, W
         d = params.device
@@ -191,7 +194,12 @@ class UNet:
         return self.pred
 
     def pack(self, S, C):
-        """Network input and baseline from short-window sums (int32 [B*H*W])."""
+        """Network input and baseline from short-window sums (int32 [B*H*W]).
+        With the fused input layer this only records S and C: the first
+        convolution of forward() packs them itself."""
+        if self.fuse_input:
+            self._iq = (S, C)
+            return
         nn.pack_input(S, C, self.P[0], IN_SCALE, self.a["x"], self.baseline)
 
     def _conv_epi(self, name, level, x, out=None, ldo=0, pool=None, up=None, ldu=0, head=False):
@@ -212,7 +220,13 @@ class UNet:
         upsampling into the first half of the next concat buffer; the last
         one computes the prediction directly."""
         a = self.a
-        self._conv("c0a", 0, a["x"], a["a0"])
+        if self.fuse_input:
+            S, C = self._iq
+            h, w = self.dims[0]
+            nn.input_conv3x3(S, C, self.B, h, w, IN_SCALE, self.prm["c0a.w"]["bf"], CIN, 32, self.prm["c0a.b"]["p"],
+                             1, a["a0"], 32, self.baseline)
+        else:
+            self._conv("c0a", 0, a["x"], a["a0"])
         self._conv_epi("c0b", 0, a["a0"], out=a["cat0"][32:], ldo=64, pool=a["p0"])
         self._conv("c1a", 1, a["p0"], a["a1"])
         self._conv_epi("c1b", 1, a["a1"], out=a["cat1"][64:], ldo=128, pool=a["p1"])

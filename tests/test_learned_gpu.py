@@ -117,7 +117,7 @@ def test_fused_inference_forward_matches_the_layer_by_layer_pass(B, H, W):
         if k.endswith(".b"):
             prm[k]["p"].copy_(torch.from_numpy(rng.standard_normal(prm[k]["p"].numel()).astype(np.float32) * 0.1))
     prm["head.w"]["p"].copy_(torch.from_numpy(rng.standard_normal(32).astype(np.float32) * 0.3))
-    fused = learned.UNet(prm, B, H, W, inference_only=True)
+    fused = learned.UNet(prm, B, H, W, inference_only=True, fuse_input=False)
     plain = learned.UNet(prm, B, H, W)
     assert fused.fused and not plain.fused
     S = torch.from_numpy(rng.integers(-5000, 5000, B * H * W).astype(np.int32)).cuda()
@@ -129,3 +129,39 @@ def test_fused_inference_forward_matches_the_layer_by_layer_pass(B, H, W):
     torch.cuda.synchronize()
     assert fused.status.item() == 0 and plain.status.item() == 0
     assert torch.equal(got, want)
+    # the first layer on the FP32 cores (input packing fused) sums in another
+    # order: predictions agree to FP32 accumulation and bf16 storage rounding
+    full = learned.UNet(prm, B, H, W, inference_only=True)
+    full.pack(S, C)
+    got2 = full.forward()
+    torch.cuda.synchronize()
+    assert torch.equal(full.baseline, plain.baseline)
+    rel = (torch.linalg.norm(got2 - want) / torch.linalg.norm(want)).item()
+    assert rel < 1e-2, rel
+
+
+@pytest.mark.parametrize("B,H,W,Cout", [(1, 16, 16, 32), (2, 37, 50, 32), (1, 40, 24, 64)])
+def test_input_conv_matches_the_oracle_on_the_packed_input(B, H, W, Cout):
+    """qldnn_input_conv3x3 = ReLU(conv3x3(pack(S, C)) + bias) against the FP64
+    oracle on the packed tensor the GPU builds (16 channels, zeros after 3),
+    and its baseline = qldnn_pack_input's."""
+    import oracle
+    from test_nn_gpu import ACC, bf16, close
+
+    rng = np.random.default_rng(H * W + Cout)
+    S = torch.from_numpy(rng.integers(-9000, 9000, B * H * W).astype(np.int32)).cuda()
+    C = torch.from_numpy(rng.integers(-9000, 9000, B * H * W).astype(np.int32)).cuda()
+    x = torch.empty(B * H * W * 16, dtype=torch.bfloat16, device="cuda")
+    base = torch.empty(B * H * W, dtype=torch.float32, device="cuda")
+    q.nn.pack_input(S, C, B * H * W, learned.IN_SCALE, x, base)
+    w, wr = bf16(rng.standard_normal((3, 3, 16, Cout)) / 12)
+    bias = torch.from_numpy(rng.standard_normal(Cout).astype(np.float32) * 0.1).cuda()
+    out = torch.empty(B * H * W * Cout, dtype=torch.bfloat16, device="cuda")
+    base2 = torch.empty_like(base)
+    q.nn.input_conv3x3(S, C, B, H, W, learned.IN_SCALE, w, 16, Cout, bias, 1, out, Cout, base2)
+    torch.cuda.synchronize()
+    assert torch.equal(base, base2)
+    xr = x.float().cpu().numpy().astype(np.float64).reshape(B, H, W, 16)
+    ref = np.maximum(oracle.conv3x3(xr, wr, bias.cpu().numpy().astype(np.float64)), 0)
+    bound = ACC * oracle.conv3x3(np.abs(xr), np.abs(wr)) + 1e-6
+    close(out.float().cpu().numpy().reshape(B, H, W, Cout), ref, bound + 2.0 ** -8 * np.abs(ref), "input conv")
