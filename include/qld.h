@@ -380,6 +380,14 @@ int qldnn_conv3x3_fwd_tma_mode(const void* in, const void* wk, const float* bias
  * The pooled, upsampled and head outputs equal qldnn_avgpool2,
  * qldnn_upsample_concat and qldnn_head + qldnn_add on the bf16 activation bit
  * for bit. Pointers 16-byte aligned. */
+/* Self-test of the failure path shared by the tcgen05 kernels' bounded waits
+ * (the paper has no counterpart): one role waits on an mbarrier nothing ever
+ * arrives on for limit_ns (1 us .. 2 s) and must time out and raise the
+ * failure flag; a second role, waiting with a one-minute limit, must then give
+ * up at once. out (device, 3 x int64): [0] = 1 if the first wait timed out,
+ * [1] = 1 if the second left because of the flag, [2] = the kernel's device
+ * time in ns. Nothing faults; the context stays usable. */
+int qldnn_wait_selftest(long long limit_ns, long long* out, void* stream);
 int qldnn_conv3x3_fwd_tma_epi(const void* in, const void* wk, const float* bias, int B, int H, int W, int Cin,
                               int Cout, int relu, void* out_bf16, long long ldo, void* pool_bf16, void* up_bf16,
                               long long ldu, const float* head_w, const float* head_b, const float* baseline,

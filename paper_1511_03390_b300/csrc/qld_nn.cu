@@ -1247,6 +1247,12 @@ int qldnn_conv3x3_wgrad_tma(const void* in, const void* g, int B, int H, int W, 
     return set_err(QLD_E_INVAL);
 }
 
+int qldnn_wait_selftest(long long limit_ns, long long* out, void* stream) {
+    if (!out || limit_ns < 1000 || limit_ns > 2000000000ll || !al(out, 8)) return set_err(QLD_E_INVAL);
+    qldnn::wait_selftest_kernel<<<1, 64, 0, (cudaStream_t)stream>>>((uint64_t)limit_ns, out);
+    return launched(1);
+}
+
 int qldnn_zero(void* p, long long bytes, void* stream) {
     if (!p || bytes < 0) return set_err(QLD_E_INVAL);
     return cudaMemsetAsync(p, 0, (size_t)bytes, (cudaStream_t)stream) == cudaSuccess ? QLD_OK : set_err(QLD_E_CUDA);

@@ -87,20 +87,51 @@ __device__ __forceinline__ uint64_t global_ns() {
     return t;
 }
 
-// Wait for phase `parity` of `bar` for at most about one second of wall time;
-// with `fail` non-null, also give up as soon as another role has set *fail
-// (and set it on a time-out).
-__device__ __forceinline__ bool wait_timed(uint64_t* bar, uint32_t parity, volatile int* fail) {
+// Wait for phase `parity` of `bar` for at most `limit_ns` of wall time (one
+// second unless given); with `fail` non-null, also give up as soon as another
+// role has set *fail (and set it on a time-out).
+__device__ __forceinline__ bool wait_timed(uint64_t* bar, uint32_t parity, volatile int* fail,
+                                           uint64_t limit_ns = 1000000000ull) {
     const uint64_t t0 = global_ns();
     for (uint32_t i = 1;; ++i) {
         if (mbar_try_wait(bar, parity)) return true;
         if ((i & 63) == 0) {
             if (fail && *fail) return false;
-            if (global_ns() - t0 > 1000000000ull) break;
+            if (global_ns() - t0 > limit_ns) break;
         }
     }
     if (fail) *fail = 1;
     return false;
+}
+
+// Self-test of the failure path of the bounded waits (no fault, no hang):
+// lane 0 of warp 0 waits on an mbarrier nothing arrives on, with a short
+// limit, and so times out and raises the shared failure flag; lane 0 of warp 1
+// waits on another such barrier with a one-minute limit and must leave as soon
+// as it sees the flag. out[0] = 1 if the first wait timed out, out[1] = 1 if
+// the second gave up because of the flag, out[2] = device nanoseconds the
+// kernel took.
+__global__ void __launch_bounds__(64) wait_selftest_kernel(uint64_t limit_ns, long long* out) {
+    __shared__ uint64_t bars[2];
+    __shared__ int fail;
+    const uint64_t t0 = global_ns();
+    if (threadIdx.x == 0) {
+        mbar_init(&bars[0], 1);
+        mbar_init(&bars[1], 1);
+        fail = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;\n" ::);
+    }
+    __syncthreads();
+    volatile int* f = &fail;
+    bool r0 = true, r1 = true;
+    if (threadIdx.x == 0) r0 = wait_timed(&bars[0], 0, f, limit_ns);
+    if (threadIdx.x == 32) r1 = wait_timed(&bars[1], 0, f, 60000000000ull);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        out[0] = r0 ? 0 : 1;
+        out[2] = (long long)(global_ns() - t0);
+    }
+    if (threadIdx.x == 32) out[1] = (!r1 && *f) ? 1 : 0;
 }
 
 __device__ __forceinline__ bool wait_or_fail(uint64_t* bar, uint32_t parity, volatile int* fail) {

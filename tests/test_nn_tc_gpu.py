@@ -141,3 +141,28 @@ def test_tma_weight_gradient_rejects_unsupported_shapes():
     for cin, cout in [(48, 32), (96, 64), (64, 256), (64, 48)]:
         with pytest.raises(q.QLDError):
             q.nn.conv3x3_wgrad_tma(x, g, 1, 4, 4, cin, cout, dw, None)
+
+
+def test_bounded_wait_times_out_raises_the_flag_and_leaves_the_context_usable():
+    """The failure path of the tcgen05 kernels' bounded waits: a wait on an
+    mbarrier nothing arrives on gives up after its limit and raises the
+    failure flag, a second role with a one-minute limit leaves at once, and
+    the next kernels run normally (no fault, no hang)."""
+    out = torch.zeros(3, dtype=torch.int64, device="cuda")
+    q.nn.wait_selftest(5_000_000, out)  # 5 ms
+    torch.cuda.synchronize()
+    timed_out, left_on_flag, ns = out.cpu().tolist()
+    assert timed_out == 1 and left_on_flag == 1
+    assert 5_000_000 <= ns < 1_000_000_000, ns
+    # the context is still usable: a convolution afterwards reports no failure
+    x = torch.randn(1 * 8 * 16 * 32, device="cuda").to(torch.bfloat16)
+    w = (torch.randn(9 * 32 * 32, device="cuda") * 0.05).to(torch.bfloat16)
+    wk = torch.empty_like(w)
+    q.nn.kmajor_weights(w, 32, 32, 0, wk)
+    y = torch.empty(8 * 16 * 32, dtype=torch.bfloat16, device="cuda")
+    status = torch.zeros(1, dtype=torch.int32, device="cuda")
+    q.nn.conv3x3_fwd_tma(x, wk, None, 1, 8, 16, 32, 32, 1, y, None, status)
+    torch.cuda.synchronize()
+    assert status.item() == 0
+    with pytest.raises(q.QLDError):
+        q.nn.wait_selftest(10, out)  # below the 1 us minimum
