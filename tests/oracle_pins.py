@@ -131,6 +131,51 @@ def pin_ramp(o):
             _assert_eq(C, [ec * P], "ramp C s0=%d N=%d" % (s0, N))
 
 
+# The sums are linear in the frames and blind to a constant offset (a whole
+# number of periods sums each table to 0), exactly, in integers:
+# S(a x + b y + c) = a S(x) + b S(y), and the same for C; the DFT bin is
+# linear too and its offset term vanishes for k != 0.
+def pin_linearity_and_offset(o):
+    rng = np.random.default_rng(21)
+    for N, s0 in [(8, 3), (64, 1), (256, 1002)]:
+        x = rng.integers(0, 1000, (N, 5)).astype(np.int64)
+        y = rng.integers(0, 1000, (N, 5)).astype(np.int64)
+        z = 3 * x + 2 * y + 7  # <= 5007: fits uint16
+        Sx, Cx = o.quadrature_sums(x.astype(np.uint16), s0=s0)
+        Sy, Cy = o.quadrature_sums(y.astype(np.uint16), s0=s0)
+        Sz, Cz = o.quadrature_sums(z.astype(np.uint16), s0=s0)
+        _assert_eq(Sz, 3 * np.asarray(Sx) + 2 * np.asarray(Sy), "linearity S N=%d" % N)
+        _assert_eq(Cz, 3 * np.asarray(Cx) + 2 * np.asarray(Cy), "linearity C N=%d" % N)
+        for k in (1, N // 4, N // 2 - 1):
+            rx, ix, _ = o.dft_bin(x.astype(np.uint16), k, s0=s0)
+            ry, iy, _ = o.dft_bin(y.astype(np.uint16), k, s0=s0)
+            rz, iz, _ = o.dft_bin(z.astype(np.uint16), k, s0=s0)
+            scale = float(np.abs(z).sum(axis=0).max())
+            _assert_close(rz, 3 * np.asarray(rx) + 2 * np.asarray(ry), 0, 1e-12 * scale, "DFT linearity re")
+            _assert_close(iz, 3 * np.asarray(ix) + 2 * np.asarray(iy), 0, 1e-12 * scale, "DFT linearity im")
+
+
+# Noise only: for frames of i.i.d. integer noise of variance v, S and C are
+# sums of N/2 terms +-x each, so E[S^2] = E[C^2] = (N/2) v and E[R^2] = N v.
+# Uniform integers on 0..M have v = ((M+1)^2 - 1) / 12; over 20,000 pixels the
+# sample mean of R^2 is within 3 % of N v with overwhelming probability (its
+# relative standard deviation is about 1 / sqrt(20000) = 0.7 %).
+def pin_noise_power(o):
+    rng = np.random.default_rng(22)
+    M = 255
+    v = ((M + 1) ** 2 - 1) / 12.0
+    for N, s0 in [(16, 1), (64, 7)]:
+        x = rng.integers(0, M + 1, (N, 20000)).astype(np.uint16)
+        S, C = o.quadrature_sums(x, s0=s0)
+        S = np.asarray(S, np.float64)
+        C = np.asarray(C, np.float64)
+        r2 = float(np.mean(S * S + C * C))
+        if abs(r2 / (N * v) - 1) > 0.03:
+            raise AssertionError("noise power N=%d: mean R^2 %.1f, expected N v = %.1f" % (N, r2, N * v))
+        if abs(np.mean(S * S) / (N / 2 * v) - 1) > 0.04 or abs(np.mean(C * C) / (N / 2 * v) - 1) > 0.04:
+            raise AssertionError("noise power N=%d: S and C should each carry half" % N)
+
+
 # Against numpy's FFT of the window y_i = x_{s0+i}: Y_k = sum_i y_i e^{-2 pi i k i/N},
 # so the absolute-index bin is X_k = e^{-2 pi i k s0 / N} Y_k.
 def pin_dft_vs_numpy(o):
@@ -369,6 +414,8 @@ ALL_PINS = [
     pin_square_wave,
     pin_tone,
     pin_zeros,
+    pin_linearity_and_offset,
+    pin_noise_power,
     pin_ramp,
     pin_dft_vs_numpy,
     pin_parseval,
