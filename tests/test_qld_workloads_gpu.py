@@ -162,3 +162,75 @@ def test_large_4096x4096_u16_N2048_ring_68GB():
     sampled_check(ctx, sc, T, N, pix, bins=(N // 4,), amp_ph=(amp.cpu().numpy(), ph.cpu().numpy()))
     del pool
     ctx.destroy()
+
+
+SERVING_MIX = [(480, 640, 256, q.QLD_U8)] * 2 + [(1024, 1280, 1024, q.QLD_U16)] * 4 + [(2048, 2048, 2048, q.QLD_U16)] * 2
+
+
+@pytest.mark.large
+def test_serving_mix_full_size_sampled_pixels():
+    """The eight-stream serving mix at full size (45.5 GB of rings) through
+    qld_server: the windows filled by the server's own batched ticks (64
+    frames per stream per tick), then three single-frame ticks; sampled
+    pixels of every stream against the oracle (sums bit-exact, images within
+    tolerance)."""
+    from qldscene import scene_plain
+
+    budget = sum(q.qld_footprint_bytes(*m) + 8 * m[0] * m[1] for m in SERVING_MIX)
+    free, _ = torch.cuda.mem_get_info()
+    if free < budget + (6 << 30):
+        pytest.skip("needs %.1f GB free device memory" % ((budget + (6 << 30)) / 1e9))
+    srv = q.qld_server_create(budget)
+    tickets = [q.qld_server_request(srv, *m) for m in SERVING_MIX]
+    assert all(q.qld_server_state(srv, t) == 0 for t in tickets)
+    scenes = [scene_plain(seed=2003 + i, H=m[0], W=m[1]) if m[3] == q.QLD_U8 else
+              scene_fog(6, seed=2003 + i, H=m[0], W=m[1]) for i, m in enumerate(SERVING_MIX)]
+    dss = [DeviceScene(sc) for sc in scenes]
+    chunk = 64
+    pools = [torch.empty((chunk, m[0], m[1]), dtype=torch.uint8 if m[3] == q.QLD_U8 else torch.uint16,
+                         device="cuda") for m in SERVING_MIX]
+    pushed = [0] * len(SERVING_MIX)
+    targets = [m[2] + 3 for m in SERVING_MIX]
+    while min(p - t for p, t in zip(pushed, targets)) < 0:
+        subs = []
+        for i, m in enumerate(SERVING_MIX):
+            left = targets[i] - pushed[i]
+            n = min(chunk, left) if pushed[i] < m[2] else min(1, left)
+            if n:
+                dss[i].generate_into(pools[i][:n], pushed[i] + 1, n)
+                subs.append((tickets[i], pools[i][:n], n))
+                pushed[i] += n
+        q.qld_server_submit_many(srv, subs)
+        q.qld_server_tick(srv)
+        q.qld_server_sync(srv)  # the pools are refilled for the next tick
+    for i, (t, m) in enumerate(zip(tickets, SERVING_MIX)):
+        H, W, N, fmt = m
+        npix = H * W
+        assert q.qld_server_frames_pushed(srv, t) == pushed[i]
+        S = torch.empty(npix, dtype=torch.int32, device="cuda")
+        C = torch.empty_like(S)
+        q.qld_server_iq(srv, t, S, C)
+        a, p = q.qld_server_image(srv, t)
+        amp = torch.empty(npix, dtype=torch.float32, device="cuda")
+        ph = torch.empty_like(amp)
+        for addr, dst in ((a, amp), (p, ph)):
+            src = torch.as_tensor(_DeviceView(addr, npix), device="cuda")
+            dst.copy_(src)
+        torch.cuda.synchronize()
+        pix = sample_pixels(scenes[i], 512, 100 + i)
+        T = pushed[i]
+        s0 = T - N + 1
+        win = scenes[i].frames(s0, N, pix=pix)
+        S_r, C_r = oracle.quadrature_sums(win, s0=s0)
+        check_sums(S.cpu().numpy()[pix], C.cpu().numpy()[pix], S_r, C_r, "stream %d" % i)
+        R, phr = oracle.amplitude_phase(S_r, C_r)
+        check_amp_phase(amp.cpu().numpy()[pix], ph.cpu().numpy()[pix], R, phr, "stream %d" % i)
+    del pools
+    srv.destroy()
+
+
+class _DeviceView:
+    """A zero-copy float32 view of library-owned device memory for torch."""
+
+    def __init__(self, addr, n):
+        self.__cuda_array_interface__ = {"shape": (n,), "typestr": "<f4", "data": (addr, False), "version": 3}
