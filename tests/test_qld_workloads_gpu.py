@@ -90,6 +90,44 @@ def test_fog_1024x1024_u16_N1024_sliding_by_4(od):
     ctx.destroy()
 
 
+def _pack12_device(x):
+    """[n, H, W] uint16 (values < 4096) -> [n, H*W*3/2] uint8, two pixels in
+    three bytes, least significant bits first (the QLD_P12 layout)."""
+    n = x.shape[0]
+    xi = x.reshape(n, -1).view(torch.int16).to(torch.int32) & 0xFFFF
+    a, b = xi[:, 0::2], xi[:, 1::2]
+    return torch.stack([a & 0xFF, (a >> 8) | ((b & 0xF) << 4), b >> 4], dim=-1).to(torch.uint8).reshape(n, -1)
+
+
+def test_fog_1024x1024_packed12_N1024_sliding_by_4():
+    """The benchmark step on packed 12-bit frames at full size (the packed12
+    block of bench.py): the window filled with packed frames, then three
+    fused push+image steps of 4 frames; sampled pixels against the oracle on
+    the unpacked frames regenerated on the host, DFT bins included."""
+    H = W = 1024
+    N = 1024
+    sc = scene_fog(6, H=H, W=W)
+    ds = DeviceScene(sc)
+    ctx = q.qld_create(H, W, N, q.QLD_P12)
+    buf = torch.empty((256, H, W), dtype=torch.uint16, device="cuda")
+    s = 1
+    while s <= N:
+        ds.generate_into(buf, s, 256)
+        q.qld_push_frames(ctx, _pack12_device(buf), 256)
+        s += 256
+    pix = sample_pixels(sc, 2048, 66)
+    amp = torch.empty(H * W, dtype=torch.float32, device="cuda")
+    ph = torch.empty_like(amp)
+    T = N
+    for i in range(3):
+        ds.generate_into(buf[:4], T + 1, 4)
+        q.qld_push_image(ctx, _pack12_device(buf[:4]), 4, None, amp, ph)
+        T += 4
+    q.qld_sync(ctx)
+    sampled_check(ctx, sc, T, N, pix, bins=(N // 4, N // 4 + 1, 3), amp_ph=(amp.cpu().numpy(), ph.cpu().numpy()))
+    ctx.destroy()
+
+
 def test_640x480_u8_N256_full_frame():
     """640x480 uint8, N = 256: whole frame against the oracle (random frames,
     pushed in uneven batches)."""
