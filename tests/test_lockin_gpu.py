@@ -151,3 +151,31 @@ def test_fig1_analog_source_on_an_fft_bin():
     c = fig1_cnrs(fs=100.0)
     assert abs(c["fft82"] - c["qld82"]) < 0.1 * c["qld82"]
     assert abs(c["wrong31"]) < 0.5
+
+
+def test_lockin_full_size_sampled_pixels():
+    """The size bench.py times: 1024 caller frames of 1024x1024 uint16 (fog
+    scene from the device generator) at 23 Hz sampled at 102 frames/s;
+    sampled pixels against the oracle on frames regenerated on the host."""
+    from qldscene import DeviceScene, scene_fog
+
+    H = W = 1024
+    N = 1024
+    s0 = 1
+    omega_dt = 2 * math.pi * 23 / 102
+    sc = scene_fog(6, seed=1002, H=H, W=W)
+    frames = torch.empty((N, H, W), dtype=torch.uint16, device="cuda")
+    DeviceScene(sc).generate_into(frames, s0, N)
+    table = torch.empty(2 * N, dtype=torch.float32, device="cuda")
+    amp = torch.empty(H * W, dtype=torch.float32, device="cuda")
+    ph = torch.empty_like(amp)
+    q.qld_lockin_table(omega_dt, s0, N, table)
+    q.qld_lockin_frames(frames, H, W, N, q.QLD_U16, table, amp, ph)
+    torch.cuda.synchronize()
+    rng = np.random.default_rng(77)
+    pix = np.unique(np.concatenate([rng.choice(H * W, 2048, replace=False),
+                                    rng.choice(np.flatnonzero(sc.mask.ravel()), 256, replace=False), [0, H * W - 1]]))
+    win = sc.frames(s0, N, pix=pix)
+    S, C, R, phr = oracle.lockin_general(win, omega_dt, s0=s0)
+    check_lockin(amp.cpu().numpy()[pix], ph.cpu().numpy()[pix], R, phr, win.astype(np.int64).sum(axis=0), "full size")
+    del frames
