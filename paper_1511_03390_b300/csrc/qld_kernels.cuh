@@ -240,6 +240,78 @@ __device__ __forceinline__ f32x2 f2_sub(f32x2 a, f32x2 b) {
     return d;
 }
 
+// Float bits b[q] of the pixels of a vector for the DFT bin: pixel q is
+// exactly b[q] - bin_offset<T>(q) as floats. Generic formats place the
+// integer in the mantissa of 2^23 (pixbits).
+template <typename T>
+__device__ __forceinline__ void bin_bits(const typename Fmt<T>::Vec& v, uint32_t (&b)[Fmt<T>::VP]) {
+#pragma unroll
+    for (int q = 0; q < Fmt<T>::VP; ++q) b[q] = pixbits<T>(v, q);
+}
+template <typename T>
+__device__ __forceinline__ constexpr float bin_offset(int) {
+    return 8388608.0f;
+}
+
+__device__ __forceinline__ uint32_t mul_hi_add(uint32_t a, uint32_t b, uint32_t c) {
+    uint32_t d;
+    asm("mad.hi.u32 %0, %1, %2, %3;" : "=r"(d) : "r"(a), "r"(b), "r"(c));
+    return d;
+}
+__device__ __forceinline__ uint32_t mul_lo(uint32_t a, uint32_t b) {
+    uint32_t d;
+    asm("mul.lo.u32 %0, %1, %2;" : "=r"(d) : "r"(a), "r"(b));
+    return d;
+}
+
+// Packed 12-bit: the 8 fields of the words w0, w1, w2 sit at bits [0,12),
+// [12,24), [24,36), [36,48), [48,60), [60,72), [72,84), [84,96) of the
+// 96-bit vector. The integer ALU is the busiest pipe of the bin kernel on
+// this format, so the fields are cut with as few ALU instructions as
+// possible:
+//  - a field wholly inside the mantissa (bits [s, s+12) with s + 12 <= 23:
+//    pixels 0, 3, 6 at s = 0, 4, 8) is masked in place and given the
+//    exponent of 2^(23-s), which makes the float 2^(23-s) + p exactly;
+//  - a field at the top of a word (pixels 1, 4 after a left shift by a
+//    multiply, pixel 7 as it is) comes down by a multiply-high whose addend is
+//    the exponent of 2^23: these run on the multiply pipe, not the ALU;
+//  - the two fields that straddle words (pixels 2, 5) take a funnel shift
+//    and a mask.
+template <>
+__device__ __forceinline__ void bin_bits<p12h_t>(const P12Half& v, uint32_t (&b)[8]) {
+    const uint32_t w0 = v.w[0], w1 = v.w[1], w2 = v.w[2];
+    constexpr uint32_t e23 = 0x4B000000u;  // exponent bits of 2^23
+    b[0] = (w0 & 0xFFFu) | e23;
+    b[1] = mul_hi_add(mul_lo(w0, 1u << 8), 1u << 12, e23);
+    b[2] = (__funnelshift_r(w0, w1, 24) & 0xFFFu) | e23;
+    b[3] = (w1 & 0xFFF0u) | ((127u + 19u) << 23);
+    b[4] = mul_hi_add(mul_lo(w1, 1u << 4), 1u << 12, e23);
+    b[5] = (__funnelshift_r(w1, w2, 28) & 0xFFFu) | e23;
+    b[6] = (w2 & 0xFFF00u) | ((127u + 15u) << 23);
+    b[7] = mul_hi_add(w2, 1u << 12, e23);
+}
+template <>
+__device__ __forceinline__ constexpr float bin_offset<p12h_t>(int q) {
+    return q == 3 ? 524288.0f : q == 6 ? 32768.0f : 8388608.0f;
+}
+
+// Frames per load group of the DFT bin (loads in flight per thread): the
+// 8- and 12-byte vectors of uint8 and packed 12-bit frames take eight, so a
+// thread keeps as many bytes in flight as with four 16-byte uint16 vectors
+// (measured on 1024^2 frames, N = 1024: uint8 +6 %, packed 12-bit +7 %).
+template <typename T>
+struct BinGroup {
+    static constexpr int UF = 4;
+};
+template <>
+struct BinGroup<u8h_t> {
+    static constexpr int UF = 8;
+};
+template <>
+struct BinGroup<p12h_t> {
+    static constexpr int UF = 8;
+};
+
 // Adds d = x_new - x_old of one frame with absolute index residue r = s mod 4
 // to the quadrature sums: sin(pi s/2) = 1, 0, -1, 0 and cos(pi s/2) = 0, -1,
 // 0, 1 for r = 1, 2, 3, 0, so exactly one of S, C changes. r is the same for
@@ -579,7 +651,7 @@ enum BinOut { kBinPower = 0, kBinAmpPhase = 1 };
 // Pixel-tiled single-bin DFT over the N ring slots. A CTA of NT threads
 // covers PV = 2^PV_LOG pixel vectors and splits the time axis into NT/PV
 // slices: thread t takes vector t mod PV and frames j = t/PV, t/PV + NT/PV,
-// ..., four loads in flight. Each thread accumulates in float32, flushing a
+// ..., BinGroup<T>::UF loads in flight. Each thread accumulates in float32, flushing a
 // partial every 16 frames into a running sum to keep rounding small. When
 // PV < 32 one warp holds 32/PV time slices of the same pixels and they are
 // combined with warp shuffles; the warps' partials are then combined in
@@ -610,18 +682,22 @@ __global__ void __launch_bounds__(NT) bin_kernel(const uint8_t* __restrict__ rin
 
     if (v < nvec) {
         const uint8_t* base = ring + v * F::VB;
-        const f32x2 k2p23 = f2_splat(8388608.0f);
+        f32x2 koff[VH];
+#pragma unroll
+        for (int h = 0; h < VH; ++h)
+            koff[h] = f2_bits(__float_as_uint(bin_offset<T>(2 * h)), __float_as_uint(bin_offset<T>(2 * h + 1)));
+        constexpr int UF = BinGroup<T>::UF;
         int j = ts;
         while (j < N) {
             f32x2 pr2[VH], pi2[VH];
 #pragma unroll
             for (int h = 0; h < VH; ++h) pr2[h] = pi2[h] = 0ull;
-            // Up to 16 frames (4 groups of 4) into the partial.
-            for (int g = 0; g < 4 && j < N; ++g, j += 4 * TS) {
-                typename F::Vec x[4];
-                float2 w[4];
+            // Up to 16 frames (16 / UF groups of UF) into the partial.
+            for (int g = 0; g < 16 / UF && j < N; ++g, j += UF * TS) {
+                typename F::Vec x[UF];
+                float2 w[UF];
 #pragma unroll
-                for (int u = 0; u < 4; ++u) {
+                for (int u = 0; u < UF; ++u) {
                     const int jj = j + u * TS;
                     if (jj < N) {
                         x[u] = F::load(base + (long long)jj * slot_stride);
@@ -632,11 +708,13 @@ __global__ void __launch_bounds__(NT) bin_kernel(const uint8_t* __restrict__ rin
                     }
                 }
 #pragma unroll
-                for (int u = 0; u < 4; ++u) {
+                for (int u = 0; u < UF; ++u) {
                     const f32x2 wr = f2_splat(w[u].x), wi = f2_splat(w[u].y);
+                    uint32_t b[VP];
+                    bin_bits<T>(x[u], b);
 #pragma unroll
                     for (int h = 0; h < VH; ++h) {
-                        const f32x2 xf = f2_sub(f2_bits(pixbits<T>(x[u], 2 * h), pixbits<T>(x[u], 2 * h + 1)), k2p23);
+                        const f32x2 xf = f2_sub(f2_bits(b[2 * h], b[2 * h + 1]), koff[h]);
                         pr2[h] = f2_fma(xf, wr, pr2[h]);
                         pi2[h] = f2_fma(xf, wi, pi2[h]);
                     }
