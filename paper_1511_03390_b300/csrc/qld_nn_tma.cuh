@@ -59,6 +59,15 @@ __device__ __forceinline__ uint64_t umma_desc_sw(uint32_t saddr) {
     return d;
 }
 
+// The descriptor of the same layout at byte offset `off` (a multiple of 16)
+// past the one given: the start address is the low 14-bit field in 16-byte
+// units, and shared addresses stay below 2^18 bytes, so the field never
+// carries into the next one. With `off` a compile-time constant this is one
+// 64-bit add per MMA instead of building the descriptor again.
+__device__ __forceinline__ uint64_t desc_at(uint64_t desc, uint32_t off) {
+    return desc + (uint64_t)(off >> 4);
+}
+
 __device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
     asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(smem_u32(bar)), "r"(bytes)
                  : "memory");
@@ -164,12 +173,24 @@ struct ConvEpi {
     float* pred;
 };
 
+// Ties 16 registers written by tcgen05.ld to the point after the
+// tcgen05.wait::ld before it: the empty statement "redefines" them, so no use
+// can be scheduled above the wait.
+__device__ __forceinline__ void tc_tie16(uint32_t* r) {
+    asm volatile(""
+                 : "+r"(r[0]), "+r"(r[1]), "+r"(r[2]), "+r"(r[3]), "+r"(r[4]), "+r"(r[5]), "+r"(r[6]), "+r"(r[7]),
+                   "+r"(r[8]), "+r"(r[9]), "+r"(r[10]), "+r"(r[11]), "+r"(r[12]), "+r"(r[13]), "+r"(r[14]),
+                   "+r"(r[15]));
+}
+
 // Epilogue warps (4 of them, warp w reads TMEM lanes 32 (w mod 4) ..) of the
 // persistent TMA convolutions: per tile, wait for its accumulator, add the
 // bias, apply ReLU, write the outputs `epi` asks for, release the accumulator.
 // Pixel m = 32 (w mod 4) + lane of the tile is (y, x) = (m / 16, m mod 16), so
 // a warp holds two whole rows and the 2x2 pooling partners of lane l are the
-// lanes l ^ 1, l ^ 16 and l ^ 17.
+// lanes l ^ 1, l ^ 16 and l ^ 17. The accumulator is read in groups of up to
+// 64 columns (all loads of a group issued before one wait); with N <= 64 the
+// bias stays in registers for all tiles.
 template <int N>
 __device__ __forceinline__ void conv_epilogue(uint32_t tmem, uint64_t* tfull, uint64_t* tempty, volatile int* fail,
                                               int warp, int lane, int ntiles, int tiles_x, int tiles_y, int H, int W,
@@ -185,6 +206,12 @@ __device__ __forceinline__ void conv_epilogue(uint32_t tmem, uint64_t* tfull, ui
     if (epi.pool) epi.pool += co0;
     if (epi.up) epi.up += co0;
     const bool pool_writer = (lane & 17) == 0;  // even x, even y
+    constexpr int G = N < 64 ? N : 64;  // accumulator columns per tcgen05.wait::ld
+    float bres[N <= 64 ? N : 1];        // the bias (or 0), when N <= 64
+    if constexpr (N <= 64) {
+#pragma unroll
+        for (int j = 0; j < N; ++j) bres[j] = bias ? bias[j] : 0.f;
+    }
     int it = 0;
     for (int t = blockIdx.x / nsplit; t < ntiles; t += gridDim.x / nsplit) {
         const int acc = it & 1;
@@ -198,74 +225,85 @@ __device__ __forceinline__ void conv_epilogue(uint32_t tmem, uint64_t* tfull, ui
         const uint32_t taddr = tmem + ((uint32_t)(qw * 32) << 16) + (uint32_t)(acc * N);
         float hacc = epi.head_w ? *epi.head_b : 0.f;
 #pragma unroll 1
-        for (int c0 = 0; c0 < N; c0 += 16) {
-            uint32_t rr[16];
-            tc_ld16(taddr + (uint32_t)c0, rr);
+        for (int g0 = 0; g0 < N; g0 += G) {
+            uint32_t rg[G];
+#pragma unroll
+            for (int c = 0; c < G; c += 16) tc_ld16(taddr + (uint32_t)(g0 + c), rg + c);
             asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
-            float v[16];
 #pragma unroll
-            for (int j = 0; j < 16; ++j) {
-                v[j] = __uint_as_float(rr[j]) + (bias ? bias[c0 + j] : 0.f);
-                if (relu) v[j] = fmaxf(v[j], 0.f);
-            }
-            uint32_t pk[8];
+            for (int c = 0; c < G; c += 16) tc_tie16(rg + c);
 #pragma unroll
-            for (int j = 0; j < 8; ++j) {
-                const __nv_bfloat162 h2 = __floats2bfloat162_rn(v[2 * j], v[2 * j + 1]);
-                pk[j] = *reinterpret_cast<const uint32_t*>(&h2);
-            }
-            if (epi.out && inside) {
-                uint4* o = reinterpret_cast<uint4*>(epi.out + p * epi.ldo + c0);
-                o[0] = make_uint4(pk[0], pk[1], pk[2], pk[3]);
-                o[1] = make_uint4(pk[4], pk[5], pk[6], pk[7]);
-            }
-            if (epi.out_f && inside) {
-                float4* o = reinterpret_cast<float4*>(epi.out_f + p * Cout + c0);
+            for (int c = 0; c < G; c += 16) {
+                const int c0 = g0 + c;
+                const uint32_t* rr = rg + c;
+                float v[16];
 #pragma unroll
-                for (int j = 0; j < 4; ++j) o[j] = make_float4(v[4 * j], v[4 * j + 1], v[4 * j + 2], v[4 * j + 3]);
-            }
-            if (epi.up && inside) {
+                for (int j = 0; j < 16; ++j) {
+                    float bj;
+                    if constexpr (N <= 64) bj = bres[c + j];  // g0 == 0
+                    else bj = bias ? bias[c0 + j] : 0.f;
+                    v[j] = __uint_as_float(rr[j]) + bj;
+                    if (relu) v[j] = fmaxf(v[j], 0.f);
+                }
+                uint32_t pk[8];
 #pragma unroll
-                for (int d = 0; d < 4; ++d) {
-                    const long long q = ((long long)b * 2 * H + 2 * y + (d >> 1)) * (2ll * W) + 2 * x + (d & 1);
-                    uint4* o = reinterpret_cast<uint4*>(epi.up + q * epi.ldu + c0);
+                for (int j = 0; j < 8; ++j) {
+                    const __nv_bfloat162 h2 = __floats2bfloat162_rn(v[2 * j], v[2 * j + 1]);
+                    pk[j] = *reinterpret_cast<const uint32_t*>(&h2);
+                }
+                if (epi.out && inside) {
+                    uint4* o = reinterpret_cast<uint4*>(epi.out + p * epi.ldo + c0);
                     o[0] = make_uint4(pk[0], pk[1], pk[2], pk[3]);
                     o[1] = make_uint4(pk[4], pk[5], pk[6], pk[7]);
                 }
-            }
-            if (epi.pool || epi.head_w) {
-                float f[16];  // the stored (bf16) values
+                if (epi.out_f && inside) {
+                    float4* o = reinterpret_cast<float4*>(epi.out_f + p * Cout + c0);
 #pragma unroll
-                for (int j = 0; j < 8; ++j) {
-                    const float2 t2 = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&pk[j]));
-                    f[2 * j] = t2.x;
-                    f[2 * j + 1] = t2.y;
+                    for (int j = 0; j < 4; ++j) o[j] = make_float4(v[4 * j], v[4 * j + 1], v[4 * j + 2], v[4 * j + 3]);
                 }
-                if (epi.pool) {  // warp-uniform: every lane shuffles
-                    float o[16];
+                if (epi.up && inside) {
 #pragma unroll
-                    for (int j = 0; j < 16; ++j) {
-                        const float a1 = __shfl_xor_sync(0xffffffffu, f[j], 1);
-                        const float a2 = __shfl_xor_sync(0xffffffffu, f[j], 16);
-                        const float a3 = __shfl_xor_sync(0xffffffffu, f[j], 17);
-                        o[j] = 0.25f * (f[j] + a1 + a2 + a3);
+                    for (int d = 0; d < 4; ++d) {
+                        const long long q = ((long long)b * 2 * H + 2 * y + (d >> 1)) * (2ll * W) + 2 * x + (d & 1);
+                        uint4* o = reinterpret_cast<uint4*>(epi.up + q * epi.ldu + c0);
+                        o[0] = make_uint4(pk[0], pk[1], pk[2], pk[3]);
+                        o[1] = make_uint4(pk[4], pk[5], pk[6], pk[7]);
                     }
-                    if (pool_writer && inside) {
-                        uint32_t q2[8];
+                }
+                if (epi.pool || epi.head_w) {
+                    float f[16];  // the stored (bf16) values
 #pragma unroll
-                        for (int j = 0; j < 8; ++j) {
-                            const __nv_bfloat162 h2 = __floats2bfloat162_rn(o[2 * j], o[2 * j + 1]);
-                            q2[j] = *reinterpret_cast<const uint32_t*>(&h2);
+                    for (int j = 0; j < 8; ++j) {
+                        const float2 t2 = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&pk[j]));
+                        f[2 * j] = t2.x;
+                        f[2 * j + 1] = t2.y;
+                    }
+                    if (epi.pool) {  // warp-uniform: every lane shuffles
+                        float o[16];
+#pragma unroll
+                        for (int j = 0; j < 16; ++j) {
+                            const float a1 = __shfl_xor_sync(0xffffffffu, f[j], 1);
+                            const float a2 = __shfl_xor_sync(0xffffffffu, f[j], 16);
+                            const float a3 = __shfl_xor_sync(0xffffffffu, f[j], 17);
+                            o[j] = 0.25f * (f[j] + a1 + a2 + a3);
                         }
-                        const long long pp = ((long long)b * (H / 2) + y / 2) * (W / 2) + x / 2;
-                        uint4* po = reinterpret_cast<uint4*>(epi.pool + pp * epi.ldp + c0);
-                        po[0] = make_uint4(q2[0], q2[1], q2[2], q2[3]);
-                        po[1] = make_uint4(q2[4], q2[5], q2[6], q2[7]);
-                    }
-                }
-                if (epi.head_w) {
+                        if (pool_writer && inside) {
+                            uint32_t q2[8];
 #pragma unroll
-                    for (int j = 0; j < 16; ++j) hacc = fmaf(f[j], epi.head_w[c0 + j], hacc);
+                            for (int j = 0; j < 8; ++j) {
+                                const __nv_bfloat162 h2 = __floats2bfloat162_rn(o[2 * j], o[2 * j + 1]);
+                                q2[j] = *reinterpret_cast<const uint32_t*>(&h2);
+                            }
+                            const long long pp = ((long long)b * (H / 2) + y / 2) * (W / 2) + x / 2;
+                            uint4* po = reinterpret_cast<uint4*>(epi.pool + pp * epi.ldp + c0);
+                            po[0] = make_uint4(q2[0], q2[1], q2[2], q2[3]);
+                            po[1] = make_uint4(q2[4], q2[5], q2[6], q2[7]);
+                        }
+                    }
+                    if (epi.head_w) {
+#pragma unroll
+                        for (int j = 0; j < 16; ++j) hacc = fmaf(f[j], epi.head_w[c0 + j], hacc);
+                    }
                 }
             }
         }
@@ -401,17 +439,17 @@ __global__ void __launch_bounds__(192, 1)
                     const int sa = ia % L::SA;
                     if (!(ok = wait_or_fail(&fullA[sa], (uint32_t)((ia / L::SA) & 1), fail))) break;
                     tc_fence_after();
-                    const uint32_t a0 = smem_u32(sA + sa * 3 * L::HALO);
+                    const uint64_t adesc = umma_desc_sw<SWB>(smem_u32(sA + sa * 3 * L::HALO));
+#pragma unroll
                     for (int tap = 0; tap < 9; ++tap) {
                         const int sb = ib % L::SB;
                         if (!(ok = wait_or_fail(&fullB[sb], (uint32_t)((ib / L::SB) & 1), fail))) break;
                         tc_fence_after();
-                        const uint32_t abase = a0 + (uint32_t)((tap % 3) * L::HALO + (tap / 3) * 16 * SWB);
-                        const uint32_t bbase = smem_u32(sB + sb * L::BSTAGE);
+                        const uint64_t bdesc = umma_desc_sw<SWB>(smem_u32(sB + sb * L::BSTAGE));
 #pragma unroll
                         for (int kk = 0; kk < L::BK / 16; ++kk)
-                            tc_mma(d, umma_desc_sw<SWB>(abase + kk * 32), umma_desc_sw<SWB>(bbase + kk * 32), kIdesc,
-                                   (cc | tap | kk) ? 1u : 0u);
+                            tc_mma(d, desc_at(adesc, (tap % 3) * L::HALO + (tap / 3) * 16 * SWB + kk * 32),
+                                   desc_at(bdesc, kk * 32), kIdesc, (cc | tap | kk) ? 1u : 0u);
                         tc_commit(&emptyB[sb]);
                         ++ib;
                     }
@@ -562,15 +600,14 @@ __global__ void __launch_bounds__(192, 1)
                     const int sa = ia % SA;
                     if (!(ok = wait_or_fail(&fullA[sa], (uint32_t)((ia / SA) & 1), fail))) break;
                     tc_fence_after();
-                    const uint32_t a0 = smem_u32(sA + sa * 3 * L::HALO);
-#pragma unroll 1
+                    const uint64_t adesc = umma_desc_sw<SWB>(smem_u32(sA + sa * 3 * L::HALO));
+                    const uint64_t bdesc = umma_desc_sw<SWB>(w0 + (uint32_t)(cc * 9 * L::BSTAGE));
+#pragma unroll
                     for (int tap = 0; tap < 9; ++tap) {
-                        const uint32_t abase = a0 + (uint32_t)((tap % 3) * L::HALO + (tap / 3) * 16 * SWB);
-                        const uint32_t bbase = w0 + (uint32_t)((cc * 9 + tap) * L::BSTAGE);
 #pragma unroll
                         for (int kk = 0; kk < L::BK / 16; ++kk)
-                            tc_mma(d, umma_desc_sw<SWB>(abase + kk * 32), umma_desc_sw<SWB>(bbase + kk * 32), kIdesc,
-                                   (cc | tap | kk) ? 1u : 0u);
+                            tc_mma(d, desc_at(adesc, (tap % 3) * L::HALO + (tap / 3) * 16 * SWB + kk * 32),
+                                   desc_at(bdesc, tap * L::BSTAGE + kk * 32), kIdesc, (cc | tap | kk) ? 1u : 0u);
                     }
                     tc_commit(&emptyA[sa]);
                     ++ia;
@@ -737,18 +774,17 @@ __global__ void __launch_bounds__(192, 1)
                 const int s = i % L::ST;
                 if (!(ok = wait_or_fail(&full[s], (uint32_t)((i / L::ST) & 1), fail))) break;
                 tc_fence_after();
-                const uint32_t a0 = smem_u32(sA + s * L::ABYTES), b0 = smem_u32(sB + s * L::BBYTES);
                 constexpr uint32_t lboA = STACK ? 16 * SWA : L::HALO;
                 constexpr uint32_t lboB = 128 * L::SWBB;
                 constexpr int kyPerAcc = STACK ? 128 / L::EA : 1;
+                const uint64_t adesc = umma_desc_mn<SWA>(smem_u32(sA + s * L::ABYTES), lboA);
+                const uint64_t bdesc = umma_desc_mn<L::SWBB>(smem_u32(sB + s * L::BBYTES), lboB);
 #pragma unroll
                 for (int acc = 0; acc < L::NACC; ++acc) {
-                    const uint32_t abase = a0 + (uint32_t)(acc * kyPerAcc * 16 * SWA);
 #pragma unroll
                     for (int k = 0; k < 8; ++k)  // 128 pixels = 8 K16 steps of 16 pixel rows
-                        tc_mma(tmem + (uint32_t)(acc * N), umma_desc_mn<SWA>(abase + k * 16 * SWA, lboA),
-                               umma_desc_mn<L::SWBB>(b0 + k * 16 * L::SWBB, lboB), kIdesc,
-                               (i > 0 || k > 0) ? 1u : 0u);
+                        tc_mma(tmem + (uint32_t)(acc * N), desc_at(adesc, (acc * kyPerAcc * 16 + k * 16) * SWA),
+                               desc_at(bdesc, k * 16 * L::SWBB), kIdesc, (i > 0 || k > 0) ? 1u : 0u);
                 }
                 tc_commit(&empty[s]);
             }
