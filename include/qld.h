@@ -130,6 +130,22 @@ int qld_push_image(qld_ctx* ctx, const void* frames, int count, void* stream, fl
  * Returns QLD_E_NOT_READY until N frames have been pushed. */
 int qld_fft_bin(qld_ctx* ctx, int k, float* out);
 
+/* One step of the hot path: qld_push_image(ctx, frames, count, stream, amp,
+ * phase) followed by qld_fft_bin(ctx, k, power), bit for bit the same
+ * results, in ONE kernel for uint16 frames when 1 <= count <= N, the frames
+ * are 16-byte aligned and a frame is a whole number of 16-byte vectors;
+ * otherwise (and for uint8 and packed 12-bit frames, whose DFT bin is bound
+ * by instruction issue, so the push in the same kernel measured slower) as
+ * the two calls. In the single kernel the bin's time slice that later reads
+ * a ring slot is the thread that writes the new frame into it, so the slot is
+ * read back by its writer, and the DFT bin streams the window once per step
+ * with the push riding along. amp and phase may be NULL; power is device float32
+ * [H][W]. Returns QLD_E_INVAL for count < 1, k outside [0, N), a NULL or
+ * misaligned power, or the arguments qld_push_image rejects, and
+ * QLD_E_NOT_READY (nothing done) when the window would not be full. */
+int qld_step(qld_ctx* ctx, const void* frames, int count, void* stream, float* amp, float* phase, int k,
+             float* power);
+
 /* Host-buffer variants: frames are read from, and images written to, HOST
  * memory (SI "Timing sequence" item 3: frames cross the PCI express bus to
  * the GPU). The context keeps device staging (two input stages of up to

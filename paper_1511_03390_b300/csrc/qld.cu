@@ -179,13 +179,19 @@ int enqueue_image(qld_ctx* c, float* amp, float* phase) {
     return cudaGetLastError() == cudaSuccess ? QLD_OK : QLD_E_CUDA;
 }
 
-int enqueue_fft_bin(qld_ctx* c, int k, float* out) {
+// Twiddles of bin k in c->tw (recomputed only when k changes).
+int ensure_twiddles(qld_ctx* c, int k) {
     if (c->tw_k != k) {
         g_launches.fetch_add(1);
         qldk::twiddle_kernel<<<blocks_for(c->N, 256), 256, 0, c->stream>>>(c->tw, c->N, k);
         if (cudaGetLastError() != cudaSuccess) return QLD_E_CUDA;
         c->tw_k = k;
     }
+    return QLD_OK;
+}
+
+int enqueue_fft_bin(qld_ctx* c, int k, float* out) {
+    if (ensure_twiddles(c, k) != QLD_OK) return QLD_E_CUDA;
     g_launches.fetch_add(1);
     if (c->pixfmt == QLD_P12)
         qldk::launch_bin<qldk::p12_t, qldk::kBinPower>(c->ring, c->slot_stride, c->N, c->tw, c->frame_bytes, c->npix,
@@ -197,6 +203,65 @@ int enqueue_fft_bin(qld_ctx* c, int k, float* out) {
         qldk::launch_bin<uint8_t, qldk::kBinPower>(c->ring, c->slot_stride, c->N, c->tw, c->frame_bytes, c->npix,
                                                   out, nullptr, c->stream);
     return cudaGetLastError() == cudaSuccess ? QLD_OK : QLD_E_CUDA;
+}
+
+template <typename B>
+void launch_step_t(const qld_ctx* c, const qldk::PushArgs& a, float* out) {
+    using qldk::bin_kernel;
+    constexpr int P = qldk::kBinPower;
+    const int pv_log = qldk::fftbin_pv_log(a.nvec);
+    const unsigned grid = (unsigned)((a.nvec + (1ll << pv_log) - 1) >> pv_log);
+    const uint8_t* r = c->ring;
+    const long long ss = c->slot_stride;
+    cudaStream_t st = c->stream;
+    switch (pv_log) {
+        case 5: bin_kernel<B, 5, 128, P, true><<<grid, 128, 0, st>>>(r, ss, c->N, c->tw, a.nvec, a.npix, out, nullptr, a);
+            break;
+        case 4: bin_kernel<B, 4, 256, P, true><<<grid, 256, 0, st>>>(r, ss, c->N, c->tw, a.nvec, a.npix, out, nullptr, a);
+            break;
+        case 3: bin_kernel<B, 3, 256, P, true><<<grid, 256, 0, st>>>(r, ss, c->N, c->tw, a.nvec, a.npix, out, nullptr, a);
+            break;
+        default: bin_kernel<B, 2, 256, P, true><<<grid, 256, 0, st>>>(r, ss, c->N, c->tw, a.nvec, a.npix, out, nullptr, a);
+            break;
+    }
+}
+
+// Enqueues push + image + DFT bin of one step (arguments validated, window
+// full afterwards): one bin_kernel with the push folded in (PUSH) for uint16
+// frames with 1 <= count <= N in whole 16-byte vectors, else the push kernel
+// and the bin kernel.
+int enqueue_step(qld_ctx* c, const uint8_t* frames, int count, float* amp, float* phase, int k, float* out) {
+    const long long frame_bytes = c->frame_bytes;
+    // uint16 only: the uint8 and packed 12-bit DFT bins are bound by their
+    // instruction issue, and the push riding in the same kernel made them
+    // about 5 % slower than the two launches (1024^2, N = 1024, 4 frames).
+    const bool one = c->pixfmt == QLD_U16 && count >= 1 && count <= c->N && aligned(frames, 16) &&
+                     (frame_bytes % 16) == 0 && aligned(amp, 4) && aligned(phase, 4);
+    if (!one) {
+        const int rc = enqueue_push(c, frames, count, amp || phase, amp, phase);
+        return rc != QLD_OK ? rc : enqueue_fft_bin(c, k, out);
+    }
+    if (ensure_twiddles(c, k) != QLD_OK) return QLD_E_CUDA;
+    qldk::PushArgs a;
+    a.frames = frames;
+    a.frame_stride = frame_bytes;
+    a.nf = count;
+    a.s_first = c->pushed + 1;
+    a.ring = c->ring;
+    a.slot_stride = c->slot_stride;
+    a.N = c->N;
+    a.S = c->S;
+    a.C = c->C;
+    a.nvec = frame_bytes / 16;
+    a.npix = c->npix;
+    a.amp = amp;
+    a.phase = phase;
+    a.out_aligned = 0;
+    g_launches.fetch_add(1);
+    launch_step_t<uint16_t>(c, a, out);
+    if (cudaGetLastError() != cudaSuccess) return QLD_E_CUDA;
+    c->pushed += count;
+    return QLD_OK;
 }
 
 void free_pipe(HostPipe* hp) {
@@ -410,6 +475,18 @@ int qld_image(qld_ctx* c, float* amp, float* phase) {
     if (!g.ok) return set_err(QLD_E_CUDA);
     if (pending_error() != QLD_OK) return set_err(QLD_E_CUDA);
     return set_err(enqueue_image(c, amp, phase));
+}
+
+int qld_step(qld_ctx* c, const void* frames, int count, void* stream, float* amp, float* phase, int k, float* power) {
+    if (!c || count < 1 || !frames || !power || !aligned(power, 4) || k < 0 || k >= c->N) return set_err(QLD_E_INVAL);
+    if (c->pixfmt == QLD_U16 && !aligned(frames, 2)) return set_err(QLD_E_INVAL);
+    if (!aligned(amp, 4) || !aligned(phase, 4)) return set_err(QLD_E_INVAL);
+    if (c->pushed + count < c->N) return set_err(QLD_E_NOT_READY);
+    DeviceGuard g(c->device);
+    if (!g.ok) return set_err(QLD_E_CUDA);
+    if (pending_error() != QLD_OK) return set_err(QLD_E_CUDA);
+    c->stream = (cudaStream_t)stream;
+    return set_err(enqueue_step(c, (const uint8_t*)frames, count, amp, phase, k, power));
 }
 
 int qld_fft_bin(qld_ctx* c, int k, float* out) {

@@ -656,10 +656,22 @@ enum BinOut { kBinPower = 0, kBinAmpPhase = 1 };
 // PV < 32 one warp holds 32/PV time slices of the same pixels and they are
 // combined with warp shuffles; the warps' partials are then combined in
 // shared memory.
-template <typename T, int PV_LOG, int NT, int OUT>
+//
+// PUSH: one step of the hot path in one launch. Before the DFT bin the
+// kernel pushes a.nf frames (1 <= nf <= N, the window full afterwards; the
+// ring is a.ring with slots slot_stride == a.slot_stride apart) and writes the
+// amplitude / phase image. Time slice ts reads ring slots j = ts, ts + TS,
+// ...; the thread of slice ts pushes exactly the frames whose slot lies in its
+// slice, so every slot it then reads was written by itself (program order)
+// and by no other thread. The changes of S and C (exact int32) are summed over
+// the slices in shared memory before S, C and the image are written. The bin
+// loop is the same code as without PUSH: results are bit-identical to
+// push_vec_kernel with the image epilogue followed by the DFT bin.
+template <typename T, int PV_LOG, int NT, int OUT, bool PUSH = false>
 __global__ void __launch_bounds__(NT) bin_kernel(const uint8_t* __restrict__ ring, long long slot_stride, int N,
                                                  const float2* __restrict__ tw, long long nvec, long long npix,
-                                                 float* __restrict__ out, float* __restrict__ out2) {
+                                                 float* __restrict__ out, float* __restrict__ out2,
+                                                 const PushArgs a) {
     using F = Fmt<T>;
     constexpr int VP = F::VP;
     constexpr int PV = 1 << PV_LOG;
@@ -667,11 +679,51 @@ __global__ void __launch_bounds__(NT) bin_kernel(const uint8_t* __restrict__ rin
     constexpr int NW = NT / 32;
     static_assert(PV >= 4 && PV <= 32 && NT % 32 == 0 && TS >= 1, "bad bin_kernel geometry");
     __shared__ float2 red[NW][PV * VP];
+    __shared__ int2 dsc[PUSH ? TS : 1][PUSH ? PV * VP : 1];  // push changes of (S, C) per slice
 
     const int t = threadIdx.x;
     const int pv = t & (PV - 1);
     const int ts = t >> PV_LOG;
     const long long v = (long long)blockIdx.x * PV + pv;
+
+    if constexpr (PUSH) {
+        int32_t ds[VP], dc[VP];
+#pragma unroll
+        for (int q = 0; q < VP; ++q) ds[q] = dc[q] = 0;
+        if (v < nvec) {
+            const long long off = v * F::VB;
+            const long long slot0 = a.s_first % N;
+            for (int f = 0; f < a.nf; ++f) {
+                long long slot = slot0 + f;
+                if (slot >= N) slot -= N;
+                if ((int)(slot % TS) != ts) continue;
+                const typename F::Vec xn = F::load(a.frames + off + (long long)f * a.frame_stride);
+                const typename F::Vec xo = F::load(a.ring + off + slot * a.slot_stride);
+                F::store(a.ring + off + slot * a.slot_stride, xn);
+                accumulate<T, true>(ds, dc, xn, xo, (int)((a.s_first + f) & 3));
+            }
+        }
+#pragma unroll
+        for (int q = 0; q < VP; ++q) dsc[ts][pv * VP + q] = make_int2(ds[q], dc[q]);
+        __syncthreads();
+        const long long pb = (long long)blockIdx.x * PV * VP;
+        for (int e = t; e < PV * VP; e += NT) {
+            const long long p = pb + e;
+            if (p >= npix) continue;
+            int32_t sum_s = 0, sum_c = 0;
+#pragma unroll
+            for (int k = 0; k < TS; ++k) {
+                const int2 d = dsc[k][e];
+                sum_s += d.x;
+                sum_c += d.y;
+            }
+            const int32_t S = a.S[p] + sum_s, C = a.C[p] + sum_c;
+            a.S[p] = S;
+            a.C[p] = C;
+            if (a.amp) a.amp[p] = amplitude(S, C);
+            if (a.phase) a.phase[p] = phase_of(S, C);
+        }
+    }
 
     // Pixel pairs (2h, 2h+1) share one f32x2 register per accumulator.
     static_assert(VP % 2 == 0, "pixel pairs");
@@ -681,7 +733,9 @@ __global__ void __launch_bounds__(NT) bin_kernel(const uint8_t* __restrict__ rin
     for (int h = 0; h < VH; ++h) re2[h] = im2[h] = 0ull;
 
     if (v < nvec) {
-        const uint8_t* base = ring + v * F::VB;
+        // with PUSH the ring is read through a.ring, the pointer the push
+        // wrote through (the __restrict__ parameter must not alias a store)
+        const uint8_t* base = (PUSH ? (const uint8_t*)a.ring : ring) + v * F::VB;
         f32x2 koff[VH];
 #pragma unroll
         for (int h = 0; h < VH; ++h)
@@ -800,10 +854,10 @@ inline void launch_bin(const uint8_t* base, long long stride, int N, const float
     const int pv_log = fftbin_pv_log(nvec);
     const unsigned grid = (unsigned)((nvec + (1ll << pv_log) - 1) >> pv_log);
     switch (pv_log) {
-        case 5: bin_kernel<B, 5, 128, OUT><<<grid, 128, 0, st>>>(base, stride, N, tw, nvec, npix, out, out2); break;
-        case 4: bin_kernel<B, 4, 256, OUT><<<grid, 256, 0, st>>>(base, stride, N, tw, nvec, npix, out, out2); break;
-        case 3: bin_kernel<B, 3, 256, OUT><<<grid, 256, 0, st>>>(base, stride, N, tw, nvec, npix, out, out2); break;
-        default: bin_kernel<B, 2, 256, OUT><<<grid, 256, 0, st>>>(base, stride, N, tw, nvec, npix, out, out2); break;
+        case 5: bin_kernel<B, 5, 128, OUT><<<grid, 128, 0, st>>>(base, stride, N, tw, nvec, npix, out, out2, {}); break;
+        case 4: bin_kernel<B, 4, 256, OUT><<<grid, 256, 0, st>>>(base, stride, N, tw, nvec, npix, out, out2, {}); break;
+        case 3: bin_kernel<B, 3, 256, OUT><<<grid, 256, 0, st>>>(base, stride, N, tw, nvec, npix, out, out2, {}); break;
+        default: bin_kernel<B, 2, 256, OUT><<<grid, 256, 0, st>>>(base, stride, N, tw, nvec, npix, out, out2, {}); break;
     }
 }
 
