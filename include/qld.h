@@ -267,6 +267,22 @@ int qld_server_submit(qld_server* srv, int ticket, const void* frames, int count
  * on an error none is taken. */
 int qld_server_submit_many(qld_server* srv, int n, const int* tickets, const void* const* frames, const int* counts);
 int qld_server_tick(qld_server* srv, void* stream);
+/* qld_server_tick behind a bounded device wait on a doorbell: first waits
+ * for earlier ticks, then launches, on `stream`, a one-thread kernel that
+ * polls *doorbell (a 4-byte-aligned int the device can read: device memory,
+ * or the device pointer of mapped pinned host memory; written by a copy
+ * engine, e.g. a cudaMemcpyAsync on another non-blocking stream, or by the
+ * host -- never by a kernel that could be queued behind this tick, and not
+ * through a stream that synchronises with `stream`) until it is >= target,
+ * then the tick's
+ * persistent kernel, which starts the moment the doorbell rings with no
+ * host round trip. The wait gives up after timeout_ns (0 < timeout_ns <=
+ * 10 s) of GPU time; the tick then does no work, the submissions stay
+ * pending for a later tick, and the call returns QLD_E_TIMEOUT. Otherwise
+ * it returns, once the tick has completed, the number of streams served (0,
+ * with no wait, when nothing was submitted). QLD_E_INVAL for a NULL or
+ * misaligned doorbell or a timeout out of range. */
+int qld_server_tick_gated(qld_server* srv, void* stream, const int* doorbell, int target, long long timeout_ns);
 int qld_server_image(qld_server* srv, int ticket, float** amp, float** phase);
 int qld_server_iq(qld_server* srv, int ticket, int32_t* S, int32_t* C);
 long long qld_server_frames_pushed(qld_server* srv, int ticket);

@@ -22,7 +22,7 @@ __all__ = [
     "qld_mem_in_use", "qld_launch_count", "qld_fft_bin_frames_noalloc", "QLD_NOALLOC_MAX_N",
     "qld_lockin_table", "qld_lockin_frames", "Server", "QLD_SERVER_MAX_STREAMS", "qld_server_create",
     "qld_server_destroy", "qld_server_request", "qld_server_state", "qld_server_close", "qld_server_submit",
-    "qld_server_submit_many",
+    "qld_server_submit_many", "qld_server_tick_gated",
     "qld_server_tick", "qld_server_image", "qld_server_iq", "qld_server_frames_pushed", "qld_server_mem_in_use",
     "qld_server_sync", "qld_server_autotune", "qld_server_shape", "nn", "LIB_PATH", "lib",
 ]
@@ -104,6 +104,7 @@ _SIGS = {
     "qld_server_submit": ([_p, _i, _p, _i], _i),
     "qld_server_submit_many": ([_p, _i, _p, _p, _p], _i),
     "qld_server_tick": ([_p, _p], _i),
+    "qld_server_tick_gated": ([_p, _p, _p, _i, _ll], _i),
     "qld_server_image": ([_p, _i, ctypes.POINTER(_p), ctypes.POINTER(_p)], _i),
     "qld_server_iq": ([_p, _i, _p, _p], _i),
     "qld_server_frames_pushed": ([_p, _i], _ll),
@@ -440,6 +441,17 @@ def qld_server_tick(srv, stream=None):
     n = lib.qld_server_tick(_sh(srv), _stream(stream))
     if n < 0:
         raise QLDError(n, "qld_server_tick")
+    return n
+
+
+def qld_server_tick_gated(srv, doorbell, target, timeout_ns, stream=None):
+    """qld_server_tick once *doorbell >= target (device or mapped pinned host
+    int32), waiting at most timeout_ns on the GPU; raises QLDError with
+    QLD_E_TIMEOUT when the wait ran out (the submissions stay pending)."""
+    n = lib.qld_server_tick_gated(_sh(srv), _stream(stream), _addr(doorbell, 4, "doorbell"), int(target),
+                                  int(timeout_ns))
+    if n < 0:
+        raise QLDError(n, "qld_server_tick_gated")
     return n
 
 

@@ -25,6 +25,7 @@ struct BatchItem {
 
 struct BatchHeader {
     int nitems;
+    int gated;         // 1: run only if the doorbell gate before it left *gate == 0
     long long ntiles;  // sum over items of ceil(nvec / tile vectors)
 };
 
@@ -44,7 +45,8 @@ __device__ __forceinline__ void push_vector_mode(const PushArgs& a, int reset, i
 // items' tile0 (the same for every thread of the CTA, so no divergence).
 template <int NT, int VPT>
 __global__ void __launch_bounds__(NT) batch_push_kernel(const BatchHeader* __restrict__ hdr,
-                                                        const BatchItem* __restrict__ items) {
+                                                        const BatchItem* __restrict__ items, const int* gate) {
+    if (hdr->gated && *(volatile const int*)gate != 0) return;  // the doorbell wait ran out: no work
     const int n = hdr->nitems;
     const long long ntiles = hdr->ntiles;
     for (long long tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
@@ -85,14 +87,40 @@ constexpr int kNumBatchShapes = (int)(sizeof(kBatchShapes) / sizeof(kBatchShapes
 inline long long batch_tile_vectors(const BatchShape& s) { return (long long)s.threads * s.vpt; }
 
 inline void launch_batch(const BatchShape& s, int num_sms, const BatchHeader* hdr, const BatchItem* items,
-                         cudaStream_t st) {
+                         const int* gate, cudaStream_t st) {
     const unsigned grid = (unsigned)(num_sms * s.ctas_per_sm);
-    if (s.threads == 128 && s.vpt == 1) batch_push_kernel<128, 1><<<grid, 128, 0, st>>>(hdr, items);
-    else if (s.threads == 128 && s.vpt == 2) batch_push_kernel<128, 2><<<grid, 128, 0, st>>>(hdr, items);
-    else if (s.threads == 128 && s.vpt == 4) batch_push_kernel<128, 4><<<grid, 128, 0, st>>>(hdr, items);
-    else if (s.threads == 256 && s.vpt == 1) batch_push_kernel<256, 1><<<grid, 256, 0, st>>>(hdr, items);
-    else if (s.threads == 256 && s.vpt == 2) batch_push_kernel<256, 2><<<grid, 256, 0, st>>>(hdr, items);
-    else batch_push_kernel<64, 2><<<grid, 64, 0, st>>>(hdr, items);
+    if (s.threads == 128 && s.vpt == 1) batch_push_kernel<128, 1><<<grid, 128, 0, st>>>(hdr, items, gate);
+    else if (s.threads == 128 && s.vpt == 2) batch_push_kernel<128, 2><<<grid, 128, 0, st>>>(hdr, items, gate);
+    else if (s.threads == 128 && s.vpt == 4) batch_push_kernel<128, 4><<<grid, 128, 0, st>>>(hdr, items, gate);
+    else if (s.threads == 256 && s.vpt == 1) batch_push_kernel<256, 1><<<grid, 256, 0, st>>>(hdr, items, gate);
+    else if (s.threads == 256 && s.vpt == 2) batch_push_kernel<256, 2><<<grid, 256, 0, st>>>(hdr, items, gate);
+    else batch_push_kernel<64, 2><<<grid, 64, 0, st>>>(hdr, items, gate);
+}
+
+// Bounded device wait on a doorbell before a gated tick: one thread polls
+// *doorbell with volatile loads (re-read every time, so a word in mapped
+// host memory or one a copy engine writes is seen) until it reaches
+// `target`, backing off with __nanosleep, for at most timeout_ns of
+// %globaltimer time. *gate = 0 when the doorbell rang in time, 1 when the
+// wait ran out; the tick launched after it on the same stream then does no
+// work. Nothing else waits on this kernel's threads.
+__global__ void doorbell_gate_kernel(const int* doorbell, int target, long long timeout_ns, int* gate) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    unsigned long long t0;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t0));
+    for (;;) {
+        if (*(volatile const int*)doorbell >= target) {
+            *gate = 0;
+            return;
+        }
+        unsigned long long t;
+        asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+        if ((long long)(t - t0) > timeout_ns) {
+            *gate = 1;
+            return;
+        }
+        __nanosleep(500);
+    }
 }
 
 }  // namespace qldk

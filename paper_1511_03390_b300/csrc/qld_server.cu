@@ -62,6 +62,7 @@ struct qld_server {
     qldk::BatchItem* items_dev;      // inside the hdr_dev block
     qldk::BatchHeader* hdr_host[2];  // pinned
     qldk::BatchItem* items_host[2];  // inside the hdr_host[b] blocks
+    int* gate_dev;                   // outcome of a gated tick's doorbell wait
     cudaEvent_t used[2];
     bool used_valid[2];
     cudaGraphExec_t graph[2];
@@ -72,6 +73,9 @@ struct qld_server {
 };
 
 namespace {
+
+// Longest doorbell wait a gated tick accepts (10 s).
+constexpr long long kMaxGateNs = 10000000000ll;
 
 // Bytes of a descriptor block: the header (rounded up to 16 bytes), then the items.
 constexpr size_t kHdrBytes = (sizeof(qldk::BatchHeader) + 15) / 16 * 16;
@@ -160,6 +164,7 @@ int build_items(qld_server* s, qldk::BatchItem* items, qldk::BatchHeader* hdr, s
         ++n;
     }
     hdr->nitems = n;
+    hdr->gated = 0;
     hdr->ntiles = tiles;
     return n;
 }
@@ -174,7 +179,7 @@ int ensure_graphs(qld_server* s) {
         cudaGraph_t g = nullptr;
         if (cudaStreamBeginCapture(s->cap, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return QLD_E_CUDA;
         cudaMemcpyAsync(s->hdr_dev, s->hdr_host[b], desc_bytes(s->max_streams), cudaMemcpyHostToDevice, s->cap);
-        qldk::launch_batch(qldk::kBatchShapes[s->shape], s->num_sms, s->hdr_dev, s->items_dev, s->cap);
+        qldk::launch_batch(qldk::kBatchShapes[s->shape], s->num_sms, s->hdr_dev, s->items_dev, s->gate_dev, s->cap);
         if (cudaStreamEndCapture(s->cap, &g) != cudaSuccess || !g) {
             cudaGetLastError();
             return QLD_E_CUDA;
@@ -210,6 +215,7 @@ qld_server* qld_server_create(long long hbm_budget_bytes, int max_streams) {
     s->max_streams = max_streams;
     s->hdr_dev = nullptr;
     s->items_dev = nullptr;
+    s->gate_dev = nullptr;
     s->hdr_host[0] = s->hdr_host[1] = nullptr;
     s->items_host[0] = s->items_host[1] = nullptr;
     s->used_valid[0] = s->used_valid[1] = false;
@@ -221,6 +227,7 @@ qld_server* qld_server_create(long long hbm_budget_bytes, int max_streams) {
     bool ok = cudaGetDevice(&s->device) == cudaSuccess &&
               cudaDeviceGetAttribute(&s->num_sms, cudaDevAttrMultiProcessorCount, s->device) == cudaSuccess &&
               cudaMalloc(&s->hdr_dev, desc_bytes(max_streams)) == cudaSuccess &&
+              cudaMalloc(&s->gate_dev, 16) == cudaSuccess && cudaMemset(s->gate_dev, 0, 16) == cudaSuccess &&
               cudaStreamCreateWithFlags(&s->cap, cudaStreamNonBlocking) == cudaSuccess;
     if (ok) s->items_dev = items_of(s->hdr_dev);
     for (int b = 0; ok && b < 2; ++b) {
@@ -250,6 +257,7 @@ void qld_server_destroy(qld_server* s) {
         if (s->used[b]) cudaEventDestroy(s->used[b]);
     }
     if (s->hdr_dev) cudaFree(s->hdr_dev);
+    if (s->gate_dev) cudaFree(s->gate_dev);
     if (s->cap) cudaStreamDestroy(s->cap);
     delete s;
 }
@@ -351,6 +359,42 @@ int qld_server_tick(qld_server* s, void* stream) {
         t.pending_count = 0;
     }
     s->flip ^= 1;
+    return n;
+}
+
+int qld_server_tick_gated(qld_server* s, void* stream, const int* doorbell, int target, long long timeout_ns) {
+    if (!s || !doorbell || ((uintptr_t)doorbell & 3) != 0 || timeout_ns <= 0 || timeout_ns > kMaxGateNs)
+        return set_err(QLD_E_INVAL);
+    const cudaStream_t st = (cudaStream_t)stream;
+    // no earlier tick in flight, so a timed-out tick is undone on the host alone
+    wait_ticks(s);
+    const int b = s->flip;
+    std::vector<int> which;
+    const int n = build_items(s, s->items_host[b], s->hdr_host[b], &which);
+    if (n == 0) return 0;
+    s->hdr_host[b]->gated = 1;
+    int rc = ensure_graphs(s);
+    if (rc != QLD_OK) return set_err(rc);
+    qldk::doorbell_gate_kernel<<<1, 32, 0, st>>>(doorbell, target, timeout_ns, s->gate_dev);
+    if (cudaGetLastError() != cudaSuccess || cudaGraphLaunch(s->graph[b], st) != cudaSuccess ||
+        cudaEventRecord(s->used[b], st) != cudaSuccess)
+        return set_err(QLD_E_CUDA);
+    s->used_valid[b] = true;
+    qldi::count_launches(2);
+    s->flip ^= 1;
+    // the device wait is bounded, so this returns within about timeout_ns
+    int gate = 1;
+    if (cudaEventSynchronize(s->used[b]) != cudaSuccess ||
+        cudaMemcpy(&gate, s->gate_dev, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess)
+        return set_err(QLD_E_CUDA);
+    if (gate != 0) return set_err(QLD_E_TIMEOUT);  // nothing ran; the submissions stay pending
+    for (int id : which) {
+        SrvStream& t = s->streams[id];
+        t.ctx->pushed += t.pending_count;
+        t.ctx->stream = st;
+        t.pending = nullptr;
+        t.pending_count = 0;
+    }
     return n;
 }
 
@@ -463,7 +507,7 @@ int qld_server_autotune(qld_server* s, void* stream, float* best_us) {
                 break;
             }
             cudaEventRecord(e0, st);
-            qldk::launch_batch(qldk::kBatchShapes[k], s->num_sms, hdr, items, st);
+            qldk::launch_batch(qldk::kBatchShapes[k], s->num_sms, hdr, items, s->gate_dev, st);
             cudaEventRecord(e1, st);
             if (cudaEventSynchronize(e1) != cudaSuccess) {
                 rc = QLD_E_CUDA;

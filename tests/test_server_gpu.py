@@ -212,3 +212,100 @@ def test_server_rejects_unbatchable_or_bad_requests():
     assert q.lib.qld_server_submit(srv.handle, t, buf.data_ptr() + 4, 1) == q.QLD_E_INVAL  # misaligned
     assert q.qld_server_tick(srv) == 0  # nothing submitted: no launch
     srv.destroy()
+
+
+# ---- gated ticks: a bounded device wait on a doorbell before the tick ----
+
+def _gated_setup(seed):
+    rng = np.random.default_rng(seed)
+    srv = q.qld_server_create(1 << 34)
+    mix = MIX[:3]
+    tickets = [q.qld_server_request(srv, *m) for m in mix]
+    alone = [q.qld_create(*m) for m in mix]
+    frames = []
+    for (H, W, N, fmt), t, ctx in zip(mix, tickets, alone):
+        x, dev = frames_for(rng, H, W, fmt, N + 3)
+        frames.append((x, dev))
+        q.qld_server_submit(srv, t, dev, N + 3)
+        q.qld_push_frames(ctx, dev, N + 3)
+    torch.cuda.synchronize()
+    return srv, mix, tickets, alone, frames
+
+
+def _check_against_alone(srv, mix, tickets, alone):
+    for (H, W, N, fmt), t, ctx in zip(mix, tickets, alone):
+        S, C, amp, ph = ctx_state(ctx)
+        S2, C2 = server_iq(srv, t, H * W)
+        amp2, ph2 = server_images(srv, t, H * W)
+        assert np.array_equal(S, S2) and np.array_equal(C, C2)
+        assert np.array_equal(amp, amp2) and np.array_equal(ph, ph2)
+
+
+def test_gated_tick_times_out_on_a_doorbell_nothing_rings():
+    srv, mix, tickets, alone, _ = _gated_setup(41)
+    try:
+        bell = torch.zeros(4, dtype=torch.int32, device="cuda")
+        with pytest.raises(q.QLDError) as e:
+            q.qld_server_tick_gated(srv, bell, 1, 20_000_000)  # 20 ms, nothing writes the bell
+        assert e.value.status == q.QLD_E_TIMEOUT
+        assert all(q.qld_server_frames_pushed(srv, t) == 0 for t in tickets)
+        # the submissions are still pending: a plain tick consumes them, and the
+        # server's results equal each stream alone
+        assert q.qld_server_tick(srv) == len(mix)
+        q.qld_server_sync(srv)
+        assert all(q.qld_server_frames_pushed(srv, t) == m[2] + 3 for t, m in zip(tickets, mix))
+        _check_against_alone(srv, mix, tickets, alone)
+        # a bell that already rang lets the tick through at once
+        bell.fill_(7)
+        keep = []  # submitted frames must stay valid until the tick has run
+        for (H, W, N, fmt), t, ctx in zip(mix, tickets, alone):
+            x, dev = frames_for(np.random.default_rng(H), H, W, fmt, 2)
+            keep.append(dev)
+            q.qld_server_submit(srv, t, dev, 2)
+            q.qld_push_frames(ctx, dev, 2)
+        assert q.qld_server_tick_gated(srv, bell, 7, 1_000_000_000) == len(mix)
+        _check_against_alone(srv, mix, tickets, alone)
+        for bad in [(None, 1, 1000), (bell, 1, 0), (bell, 1, 11 * 10 ** 9), (bell.data_ptr() + 2, 1, 1000)]:
+            assert q.lib.qld_server_tick_gated(srv.handle, None, bad[0] if not isinstance(bad[0], torch.Tensor)
+                                               else bad[0].data_ptr(), bad[1], bad[2]) == q.QLD_E_INVAL
+    finally:
+        srv.destroy()
+        for c in alone:
+            c.destroy()
+
+
+def test_gated_tick_runs_when_a_host_thread_rings_the_doorbell():
+    """A host thread rings a device-memory doorbell with a copy on its own
+    non-blocking stream while the calling thread waits in the gated tick,
+    which runs on another non-blocking stream."""
+    import threading
+    import time
+    srv, mix, tickets, alone, _ = _gated_setup(43)
+    try:
+        bell = torch.zeros(4, dtype=torch.int32, device="cuda")
+        three = torch.full((4,), 3, dtype=torch.int32).pin_memory()
+        tick_stream, side = torch.cuda.Stream(), torch.cuda.Stream()
+        torch.cuda.synchronize()
+        rung = []
+
+        def ring():
+            time.sleep(0.05)
+            rung.append(time.perf_counter())
+            with torch.cuda.stream(side):
+                bell.copy_(three, non_blocking=True)
+            side.synchronize()
+
+        th = threading.Thread(target=ring)
+        t0 = time.perf_counter()
+        th.start()
+        n = q.qld_server_tick_gated(srv, bell, 3, 2_000_000_000, stream=tick_stream.cuda_stream)
+        t1 = time.perf_counter()
+        th.join()
+        assert n == len(mix)
+        assert rung and t1 >= rung[0] and t1 - t0 < 1.5  # it waited for the bell, not for the limit
+        assert all(q.qld_server_frames_pushed(srv, t) == m[2] + 3 for t, m in zip(tickets, mix))
+        _check_against_alone(srv, mix, tickets, alone)
+    finally:
+        srv.destroy()
+        for c in alone:
+            c.destroy()
