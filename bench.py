@@ -355,6 +355,18 @@ def run_cuda(args, world, rank, local):
     fft_ms = sum(ev[i][1].elapsed_time(ev[i + 1][0] if i + 1 < KS else ev_s_end) for i in range(KS))
     fft_gbs = ab["fft_bin"] * KS / (fft_ms * 1e-3) / 1e9
     push_gbs = ab["push_image"] * KS / (push_ms * 1e-3) / 1e9
+    # the DFT bin at a k other than N/4 (its own twiddle table; same kernel)
+    K_OTHER = K_BIN + 1
+    q.qld_fft_bin(ctx, K_OTHER, pw)
+    ek0, ek1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ek0.record(st)
+    for _ in range(20):
+        q.qld_fft_bin(ctx, K_OTHER, pw)
+    ek1.record(st)
+    ek1.synchronize()
+    other_ms = ek0.elapsed_time(ek1) / 20
+    fft_other = {"k": K_OTHER, "ms_per_launch": other_ms, "achieved_gbs": ab["fft_bin"] / (other_ms * 1e-3) / 1e9,
+                 "frac": ab["fft_bin"] / (other_ms * 1e-3) / 1e9 / peak}
 
     # frame-to-image latency: host clock from the call of the fused push
     # (frames already in HBM) to the image complete, one sample at a time.
@@ -502,6 +514,7 @@ def run_cuda(args, world, rank, local):
                             "frac": fft_gbs / peak},
                 "share": {"push_image": push_ms / split_ms, "fft_bin": fft_ms / split_ms},
             },
+            "fft_bin_other_k": fft_other,
         },
         "latency_us": {"p50": lat[len(lat) // 2], "p99": lat[min(len(lat) - 1, int(0.99 * len(lat)))],
                        "samples": len(lat),
@@ -912,9 +925,10 @@ def conv_roofline(q, torch, dev, st):
 
 
 def run_e2e(args, q, torch, dev, st, pool):
-    """The same step through the host-buffer C ABI: frames copied from pinned
-    host memory, the three images copied back to pinned host memory, every
-    step; wall-clock over the run, one synchronisation at the end."""
+    """The same step through the host-buffer C ABI (qld_step_host): frames
+    copied from pinned host memory, the three images copied back to pinned
+    host memory, every step; wall-clock over the run, one synchronisation at
+    the end."""
     HP = 256
     host = torch.empty((HP, H, W), dtype=torch.uint16).pin_memory()
     host.copy_(pool[:HP])
@@ -927,9 +941,7 @@ def run_e2e(args, q, torch, dev, st, pool):
 
     def step(i):
         j = (ADV * i) % HP
-        q.qld_push_frames_host(ctx, host[j:j + ADV], ADV, st)
-        q.qld_image_host(ctx, amp_h, ph_h)
-        q.qld_fft_bin_host(ctx, K_BIN, pw_h)
+        q.qld_step_host(ctx, host[j:j + ADV], ADV, K_BIN, pw_h, st, amp_h, ph_h)
 
     for i in range(max(3, args.warmup)):
         step(i)
@@ -943,7 +955,7 @@ def run_e2e(args, q, torch, dev, st, pool):
     ctx.destroy()
     return {"value": H * W * ADV * K / dt / 1e9, "unit": UNIT, "h2d_bytes_per_step": ADV * H * W * 2,
             "d2h_bytes_per_step": 3 * H * W * 4, "steps": K, "ms_per_step": dt / K * 1e3,
-            "api": "qld_push_frames_host + qld_image_host + qld_fft_bin_host, pinned host buffers"}
+            "api": "qld_step_host (frames in, amplitude, phase and power images out), pinned host buffers"}
 
 
 # ------------------------------------------------------ reference arm ---

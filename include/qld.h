@@ -160,6 +160,14 @@ int qld_step(qld_ctx* ctx, const void* frames, int count, void* stream, float* a
 int qld_push_frames_host(qld_ctx* ctx, const void* host_frames, int count, void* stream);
 int qld_image_host(qld_ctx* ctx, float* amp_host, float* phase_host);
 int qld_fft_bin_host(qld_ctx* ctx, int k, float* out_host);
+/* qld_step with host buffers: the frames are copied from host memory into
+ * an input stage, the step runs as in qld_step, and the amplitude, phase
+ * (either may be NULL) and power images are copied back to host memory
+ * through the output ring (valid after qld_sync). Steps of more than 64 MiB
+ * of frames run as qld_push_frames_host, qld_image_host, qld_fft_bin_host.
+ * Errors as qld_step. */
+int qld_step_host(qld_ctx* ctx, const void* host_frames, int count, void* stream, float* amp_host, float* phase_host,
+                  int k, float* power_host);
 
 /* Copies the exact int32 sums S and C (device [H][W]; either may be NULL).
  * Valid at any time (partial sums while the window fills). */

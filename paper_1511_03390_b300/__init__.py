@@ -16,7 +16,7 @@ from . import build as _build
 __all__ = [
     "QLD_U8", "QLD_U16", "QLD_P12", "QLD_OK", "QLD_E_INVAL", "QLD_E_NOMEM", "QLD_E_NOT_READY", "QLD_E_CUDA",
     "QLD_E_TIMEOUT", "QLD_MAX_N", "QLDError", "Context", "qld_create", "qld_destroy", "qld_push_frames",
-    "qld_push_image", "qld_image", "qld_fft_bin", "qld_step", "qld_push_frames_host", "qld_image_host",
+    "qld_push_image", "qld_image", "qld_fft_bin", "qld_step", "qld_step_host", "qld_push_frames_host", "qld_image_host",
     "qld_fft_bin_host", "qld_get_iq", "qld_reset", "qld_frames_pushed", "qld_sync", "qld_stream",
     "qld_strerror", "qld_last_error", "qld_version", "qld_footprint_bytes", "qld_set_mem_budget",
     "qld_mem_in_use", "qld_launch_count", "qld_fft_bin_frames_noalloc", "QLD_NOALLOC_MAX_N",
@@ -59,6 +59,7 @@ _SIGS = {
     "qld_image": ([_p, _p, _p], _i),
     "qld_fft_bin": ([_p, _i, _p], _i),
     "qld_step": ([_p, _p, _i, _p, _p, _p, _i, _p], _i),
+    "qld_step_host": ([_p, _p, _i, _p, _p, _p, _i, _p], _i),
     "qld_push_frames_host": ([_p, _p, _i, _p], _i),
     "qld_image_host": ([_p, _p, _p], _i),
     "qld_fft_bin_host": ([_p, _i, _p], _i),
@@ -272,6 +273,15 @@ def qld_step(ctx, frames, count, k, power, stream=None, amp=None, phase=None):
     return _check(lib.qld_step(_h(ctx), a, n, _stream(stream), _addr(amp, 4 * ctx.npix, "amp"),
                                _addr(phase, 4 * ctx.npix, "phase"), int(k), _addr(power, 4 * ctx.npix, "power")),
                   "qld_step")
+
+
+def qld_step_host(ctx, frames, count, k, power, stream=None, amp=None, phase=None):
+    """qld_step with host frames and host output images (valid after qld_sync)."""
+    n = _count_of(frames, count, ctx.frame_bytes)
+    a = _addr(frames, n * ctx.frame_bytes, "frames")
+    return _check(lib.qld_step_host(_h(ctx), a, n, _stream(stream), _addr(amp, 4 * ctx.npix, "amp"),
+                                    _addr(phase, 4 * ctx.npix, "phase"), int(k), _addr(power, 4 * ctx.npix, "power")),
+                  "qld_step_host")
 
 
 def qld_push_frames_host(ctx, frames, count=None, stream=None):

@@ -565,6 +565,43 @@ int qld_fft_bin_host(qld_ctx* c, int k, float* out_host) {
     return set_err(release_out(c, slot, buf, out_host, nullptr, nullptr));
 }
 
+int qld_step_host(qld_ctx* c, const void* host_frames, int count, void* stream, float* amp_host, float* phase_host,
+                  int k, float* power_host) {
+    if (!c || count < 1 || !host_frames || !power_host || k < 0 || k >= c->N) return set_err(QLD_E_INVAL);
+    if (c->pushed + count < c->N) return set_err(QLD_E_NOT_READY);
+    const long long bytes = (long long)count * c->frame_bytes;
+    if (bytes > (64ll << 20)) {  // more than one input stage: the three host calls
+        int st = qld_push_frames_host(c, host_frames, count, stream);
+        if (st == QLD_OK) st = qld_image_host(c, amp_host, phase_host);
+        return st != QLD_OK ? st : qld_fft_bin_host(c, k, power_host);
+    }
+    DeviceGuard g(c->device);
+    if (!g.ok) return set_err(QLD_E_CUDA);
+    if (pending_error() != QLD_OK) return set_err(QLD_E_CUDA);
+    c->stream = (cudaStream_t)stream;
+    int st = ensure_pipe(c, c->pipe ? c->pipe->stage_bytes : round_up(bytes, 256));
+    if (st == QLD_OK && c->pipe->stage_bytes < bytes) st = ensure_pipe(c, round_up(bytes, 256));
+    if (st != QLD_OK) return set_err(st);
+    HostPipe* hp = c->pipe;
+    const int i = hp->in_idx;
+    hp->in_idx = (i + 1) % HostPipe::kIn;
+    if (cudaStreamWaitEvent(hp->cin, hp->in_free[i], 0) != cudaSuccess ||
+        cudaMemcpyAsync(hp->stage[i], host_frames, (size_t)bytes, cudaMemcpyHostToDevice, hp->cin) != cudaSuccess ||
+        cudaEventRecord(hp->in_ready[i], hp->cin) != cudaSuccess ||
+        cudaStreamWaitEvent(c->stream, hp->in_ready[i], 0) != cudaSuccess)
+        return set_err(QLD_E_CUDA);
+    int s_img = 0, s_pow = 0;
+    float* img = acquire_out(c, &s_img);
+    float* pw = acquire_out(c, &s_pow);
+    float* da = amp_host ? img : nullptr;
+    float* dp = phase_host ? img + c->npad : nullptr;
+    st = enqueue_step(c, hp->stage[i], count, da, dp, k, pw);
+    if (st != QLD_OK) return set_err(st);
+    if (cudaEventRecord(hp->in_free[i], c->stream) != cudaSuccess) return set_err(QLD_E_CUDA);
+    st = release_out(c, s_img, da, amp_host, dp, phase_host);
+    return set_err(st != QLD_OK ? st : release_out(c, s_pow, pw, power_host, nullptr, nullptr));
+}
+
 int qld_get_iq(qld_ctx* c, int32_t* S, int32_t* C) {
     if (!c || !aligned(S, 4) || !aligned(C, 4)) return set_err(QLD_E_INVAL);
     DeviceGuard g(c->device);

@@ -124,3 +124,41 @@ def test_step_full_size_1024x1024_N1024_by_4():
     finally:
         a.destroy()
         b.destroy()
+
+
+@pytest.mark.parametrize("H,W,fmt,N,count", [
+    (256, 256, q.QLD_U16, 16, 4),    # one kernel
+    (256, 256, q.QLD_U8, 16, 3),     # two kernels
+    (128, 256, q.QLD_P12, 8, 2),
+    (1024, 1024, q.QLD_U16, 32, 40),  # 80 MiB of frames: the three host calls
+])
+def test_step_host_equals_step_on_device(H, W, fmt, N, count):
+    rng = np.random.default_rng(H + W + fmt + count)
+    hi = 256 if fmt == q.QLD_U8 else 4096
+    a, b = q.qld_create(H, W, N, fmt), q.qld_create(H, W, N, fmt)
+    npix = H * W
+    try:
+        def raw(x):
+            x = x.astype(np.uint8 if fmt == q.QLD_U8 else np.uint16)
+            return np.ascontiguousarray(pack12(x) if fmt == q.QLD_P12 else x).view(np.uint8).reshape(x.shape[0], -1)
+
+        fill = raw(rng.integers(0, hi, size=(N, npix)))
+        q.qld_push_frames(a, torch.from_numpy(fill).cuda(), N)
+        q.qld_push_frames(b, torch.from_numpy(fill).cuda(), N)
+        host_out = [torch.empty(npix, dtype=torch.float32).pin_memory() for _ in range(3)]
+        dev_out = [torch.empty(npix, dtype=torch.float32, device="cuda") for _ in range(3)]
+        for step in range(3):
+            x = raw(rng.integers(0, hi, size=(count, npix)))
+            xh = torch.from_numpy(x).pin_memory()
+            q.qld_step_host(a, xh, count, N // 4 + step, host_out[2], None, host_out[0], host_out[1])
+            q.qld_step(b, xh.cuda(), count, N // 4 + step, dev_out[2], None, dev_out[0], dev_out[1])
+            q.qld_sync(a)
+            torch.cuda.synchronize()
+            for i in range(3):
+                assert torch.equal(host_out[i], dev_out[i].cpu()), "step %d output %d" % (step, i)
+        Sa, Ca = get_iq(a)
+        Sb, Cb = get_iq(b)
+        assert np.array_equal(Sa, Sb) and np.array_equal(Ca, Cb)
+    finally:
+        a.destroy()
+        b.destroy()
