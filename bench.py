@@ -41,7 +41,7 @@ SEED = 1002
 K_BIN = N // 4
 POOL = 2048  # frames resident in HBM (4 GiB), cycled: every step reads fresh frames from DRAM
 WORKLOAD = ("fog scene OD 6, 1024x1024 uint16 (12-bit), N=1024 sliding window advanced 4 frames/step; "
-            "per step: push + amplitude/phase image + DFT-bin power at k=N/4, one qld_step launch")
+            "per step: push + amplitude/phase image + DFT-bin power at k=N/4")
 FALLBACK_HBM_GBS = 6400.0
 NOMINAL_HBM_GBS = 8000.0  # the ~8 TB/s nominal figure the 70 % target is stated against
 
