@@ -428,10 +428,19 @@ int qldnn_conv3x3_fwd_tma_mode(const void* in, const void* wk, const float* bias
  * [1] = 1 if the second left because of the flag, [2] = the kernel's device
  * time in ns. Nothing faults; the context stays usable. */
 int qldnn_wait_selftest(long long limit_ns, long long* out, void* stream);
+/* flags bit QLDNN_EARLY_LAUNCH of qldnn_conv3x3_fwd_tma_epi: launch with
+ * programmatic stream serialisation. The kernel may then start while the
+ * kernel before it on the stream is still running: it allocates TMEM, sets
+ * up its barriers and loads resident weights, and waits for that kernel to
+ * complete (griddepcontrol.wait) before it reads its input or writes any
+ * output. The caller guarantees that the preceding kernel does not write
+ * this layer's weights or bias (inference); the layer-to-layer gaps of a
+ * network then overlap. Other flag bits: QLD_E_INVAL. */
+#define QLDNN_EARLY_LAUNCH 1
 int qldnn_conv3x3_fwd_tma_epi(const void* in, const void* wk, const float* bias, int B, int H, int W, int Cin,
                               int Cout, int relu, void* out_bf16, long long ldo, void* pool_bf16, void* up_bf16,
                               long long ldu, const float* head_w, const float* head_b, const float* baseline,
-                              float* pred, int* status, void* stream);
+                              float* pred, int* status, int flags, void* stream);
 /* Weight gradient of the 3x3 convolution on the tensor cores: dw [9][Cin][Cout]
  * f32 += sum over pixels of in (shifted by the tap) x g, in [B][H][W][Cin]
  * and g [B][H][W][Cout] bf16 (the caller zeroes dw; 16-byte aligned). Cin is

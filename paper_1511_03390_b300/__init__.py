@@ -94,7 +94,7 @@ _SIGS = {
     "qldnn_conv3x3_fwd_tma_mode": ([_p, _p, _p, _i, _i, _i, _i, _i, _i, _p, _p, _p, _i, _p], _i),
     "qldnn_wait_selftest": ([_ll, _p, _p], _i),
     "qldnn_input_conv3x3": ([_p, _p, _i, _i, _i, ctypes.c_float, _p, _i, _i, _p, _i, _p, _ll, _p, _p], _i),
-    "qldnn_conv3x3_fwd_tma_epi": ([_p, _p, _p, _i, _i, _i, _i, _i, _i, _p, _ll, _p, _p, _ll, _p, _p, _p, _p, _p, _p],
+    "qldnn_conv3x3_fwd_tma_epi": ([_p, _p, _p, _i, _i, _i, _i, _i, _i, _p, _ll, _p, _p, _ll, _p, _p, _p, _p, _p, _i, _p],
                                   _i),
     "qldnn_conv3x3_wgrad_tma": ([_p, _p, _i, _i, _i, _i, _i, _p, _p, _p], _i),
     "qld_server_create": ([_ll, _i], _p),

@@ -566,6 +566,9 @@ __global__ void __launch_bounds__(128) input_conv3x3_kernel(const int32_t* __res
         const int tap = tc / 3, ci = tc - tap * 3;
         wsf[i] = __bfloat162float(w[((long long)tap * Cin + ci) * CO + co]);
     }
+    // the next layer (launched early, qldnn_conv3x3_fwd_tma_epi) may start
+    // its set-up now; it waits for this kernel before reading its output
+    asm volatile("griddepcontrol.launch_dependents;" :::);
     for (long long t0 = blockIdx.x; t0 < ntiles; t0 += gridDim.x) {
         long long t = t0;
         const int bx = (int)(t % tiles_x);
@@ -724,9 +727,28 @@ int sm_count(int dev) {
     return n;
 }
 
+// Launch of `kernel` on `st`; with `early`, with programmatic stream
+// serialisation (the kernel may start before the previous one on the stream
+// has finished, and waits for it with griddepcontrol.wait).
+template <typename... KArgs, typename... Args>
+cudaError_t launch_maybe_early(void (*kernel)(KArgs...), unsigned grid, unsigned block, size_t smem, cudaStream_t st,
+                               bool early, Args... args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(block);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = early ? attr : nullptr;
+    cfg.numAttrs = early ? 1 : 0;
+    return cudaLaunchKernelEx(&cfg, kernel, args...);
+}
+
 template <int N, int SWB>
 int launch_tma(const void* in, const void* wk, const float* bias, int B, int H, int W, int Cin, int Cout, int relu,
-               const qldnn::ConvEpi& epi, int* status, cudaStream_t st, bool force_stream) {
+               const qldnn::ConvEpi& epi, int* status, cudaStream_t st, bool force_stream, bool early) {
     using L = qldnn::TmaConv<N, SWB>;
     EncodeTiledFn enc = encode_tiled();
     int dev = 0;
@@ -768,8 +790,9 @@ int launch_tma(const void* in, const void* wk, const float* bias, int B, int H, 
                 return set_err(QLD_E_CUDA);
             attr_res.fetch_or(1ull << dev);
         }
-        qldnn::conv3x3_fwd_tma_wres_kernel<N, SWB><<<grid, 192, (size_t)R::smem(sa, Cin), st>>>(
-            mi, mw, bias, B, H, W, Cin, Cout, relu, epi, status, sa, nsplit);
+        if (launch_maybe_early(qldnn::conv3x3_fwd_tma_wres_kernel<N, SWB>, grid, 192, (size_t)R::smem(sa, Cin), st,
+                               early, mi, mw, bias, B, H, W, Cin, Cout, relu, epi, status, sa, nsplit) != cudaSuccess)
+            return set_err(QLD_E_CUDA);
         return launched(1);
     }
     static std::atomic<unsigned long long> attr_done{0};  // per instantiation, one bit per device
@@ -779,8 +802,9 @@ int launch_tma(const void* in, const void* wk, const float* bias, int B, int H, 
             return set_err(QLD_E_CUDA);
         attr_done.fetch_or(1ull << dev);
     }
-    qldnn::conv3x3_fwd_tma_kernel<N, SWB><<<grid, 192, L::kSmem, st>>>(mi, mw, bias, B, H, W, Cin, Cout, relu, epi,
-                                                                        status, nsplit);
+    if (launch_maybe_early(qldnn::conv3x3_fwd_tma_kernel<N, SWB>, grid, 192, (size_t)L::kSmem, st, early, mi, mw,
+                           bias, B, H, W, Cin, Cout, relu, epi, status, nsplit) != cudaSuccess)
+        return set_err(QLD_E_CUDA);
     return launched(1);
 }
 
@@ -837,6 +861,7 @@ int conv_tma_dispatch(const void* in, const void* wk, const float* bias, int B, 
                       int relu, const qldnn::ConvEpi& epi, int* status, int mode, cudaStream_t st) {
     const int force_stream = mode & 1;
     const int split_mode = (mode >> 4) & 0xF;
+    const bool early = ((mode >> 8) & 1) != 0;
     if (split_mode != 0 && split_mode != 1 && split_mode != 2 && split_mode != 4) return set_err(QLD_E_INVAL);
     if (!in || !wk || B < 1 || H < 1 || W < 1 || Cin < 16 || Cin % 16 ||
         (Cout != 32 && Cout != 64 && Cout != 128 && Cout != 256) || !al(in, 16) || !al(wk, 16) ||
@@ -865,7 +890,8 @@ int conv_tma_dispatch(const void* in, const void* wk, const float* bias, int B, 
     if (Cout % nsplit || Cout / nsplit < 32) return set_err(QLD_E_INVAL);
     const int nco = Cout / nsplit;
 #define QLD_TMA(NN, SS) \
-    if (nco == NN && swb == SS) return launch_tma<NN, SS>(in, wk, bias, B, H, W, Cin, Cout, relu, epi, status, st, force_stream != 0);
+    if (nco == NN && swb == SS)                                                                                      \
+        return launch_tma<NN, SS>(in, wk, bias, B, H, W, Cin, Cout, relu, epi, status, st, force_stream != 0, early);
     QLD_TMA(32, 32) QLD_TMA(32, 64) QLD_TMA(32, 128)
     QLD_TMA(64, 32) QLD_TMA(64, 64) QLD_TMA(64, 128)
     QLD_TMA(128, 32) QLD_TMA(128, 64) QLD_TMA(128, 128)
@@ -1207,7 +1233,8 @@ int qldnn_conv3x3_fwd_tma_mode(const void* in, const void* wk, const float* bias
 int qldnn_conv3x3_fwd_tma_epi(const void* in, const void* wk, const float* bias, int B, int H, int W, int Cin,
                               int Cout, int relu, void* out_bf16, long long ldo, void* pool_bf16, void* up_bf16,
                               long long ldu, const float* head_w, const float* head_b, const float* baseline,
-                              float* pred, int* status, void* stream) {
+                              float* pred, int* status, int flags, void* stream) {
+    if (flags & ~QLDNN_EARLY_LAUNCH) return set_err(QLD_E_INVAL);
     const bool head = head_w || head_b || baseline || pred;
     if (!out_bf16 && !pool_bf16 && !up_bf16 && !head) return set_err(QLD_E_INVAL);
     if (out_bf16 && (!al(out_bf16, 16) || ldo < Cout || ldo % 8)) return set_err(QLD_E_INVAL);
@@ -1226,8 +1253,8 @@ int qldnn_conv3x3_fwd_tma_epi(const void* in, const void* wk, const float* bias,
     epi.base = baseline;
     epi.pred = pred;
     // the head needs every output channel of a pixel in one CTA
-    return conv_tma_dispatch(in, wk, bias, B, H, W, Cin, Cout, relu, epi, status, head ? (1 << 4) : 0,
-                             (cudaStream_t)stream);
+    const int mode = (head ? (1 << 4) : 0) | ((flags & QLDNN_EARLY_LAUNCH) ? (1 << 8) : 0);
+    return conv_tma_dispatch(in, wk, bias, B, H, W, Cin, Cout, relu, epi, status, mode, (cudaStream_t)stream);
 }
 
 int qldnn_conv3x3_wgrad_tma(const void* in, const void* g, int B, int H, int W, int Cin, int Cout, float* dw,

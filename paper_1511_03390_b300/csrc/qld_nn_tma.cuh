@@ -32,10 +32,14 @@
 //   warps 2-5 epilogue: tcgen05.ld of the accumulator (warp w reads TMEM
 //           lanes 32 (w mod 4) ..), bias, ReLU, bf16/f32 stores, then release
 //           the accumulator, so the next tile's MMAs overlap the read-out.
-// Every wait is bounded (about a second of wall time) and also gives up once
-// another role has flagged a failure; the producer then waits (bounded) for
-// its copies in flight, the MMA thread for its MMAs, and TMEM is freed. A
-// failure records 1 in *status.
+// Launched early (programmatic stream serialisation), a CTA allocates TMEM,
+// sets up its barriers and (weights-resident variant) loads the weights
+// while the previous kernel finishes; the producer waits for that kernel
+// (griddepcontrol.wait) before the first input load, and every global write
+// comes after. Every wait is bounded (about a second of wall time) and also
+// gives up once another role has flagged a failure; the producer then waits
+// (bounded) for its copies in flight, the MMA thread for its MMAs, and TMEM
+// is freed. A failure records 1 in *status.
 
 #pragma once
 
@@ -89,6 +93,14 @@ __device__ __forceinline__ void tma_load_4d(void* dst, const CUtensorMap* map, u
         "l"(reinterpret_cast<uint64_t>(map)), "r"(smem_u32(bar)), "r"(c0), "r"(c1), "r"(c2), "r"(c3)
         : "memory");
 }
+
+// Programmatic dependent launch: a kernel launched with programmatic stream
+// serialisation may start while the kernel before it on the stream is still
+// running. pdl_wait returns once that kernel has completed and its writes are
+// visible (at once when there is no such dependency); pdl_trigger lets the
+// next such kernel launch as soon as every CTA of this one has issued it.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" :::); }
 
 __device__ __forceinline__ uint64_t global_ns() {
     uint64_t t;
@@ -385,11 +397,13 @@ __global__ void __launch_bounds__(192, 1)
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
+    pdl_trigger();
     const uint32_t tmem = *tslot;
 
     if (warp == 0) {
         if (lane == 0) {
             // ------------------------------------------------------------ TMA producer
+            pdl_wait();  // the input (and the output's previous readers) are done
             int ia = 0, ib = 0;
             bool ok = true;
             for (int t = blockIdx.x / nsplit; t < ntiles && ok; t += gridDim.x / nsplit) {
@@ -554,6 +568,7 @@ __global__ void __launch_bounds__(192, 1)
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
+    pdl_trigger();
     const uint32_t tmem = *tslot;
 
     if (warp == 0) {
@@ -563,6 +578,9 @@ __global__ void __launch_bounds__(192, 1)
             for (int cc = 0; cc < csteps; ++cc)
                 for (int tap = 0; tap < 9; ++tap)
                     tma_load_2d(sW + (cc * 9 + tap) * L::BSTAGE, &map_w, wfull, cc * L::BK, tap * Cout + co0);
+            // the weights may load while an earlier kernel still runs (an early
+            // launch requires that it does not write them); the input may not
+            pdl_wait();
             int ia = 0;
             bool ok = true;
             for (int t = blockIdx.x / nsplit; t < ntiles && ok; t += gridDim.x / nsplit) {
@@ -738,6 +756,7 @@ __global__ void __launch_bounds__(192, 1)
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
+    pdl_trigger();
     const uint32_t tmem = *tslot;
 
     if (warp == 0) {

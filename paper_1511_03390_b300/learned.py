@@ -28,6 +28,7 @@ N_LONG = 1024
 IN_SCALE = 1.0 / 200.0
 TARGET_SCALE = IN_SCALE / N_SHORT
 CIN = 16  # input channels: S, C, R, zero padding
+EARLY_LAUNCH = 1  # QLDNN_EARLY_LAUNCH (qld.h)
 
 # (name, input channels, output channels); every convolution is 3x3 + ReLU
 LAYERS = [("c0a", 16, 32), ("c0b", 32, 32), ("c1a", 32, 64), ("c1b", 64, 64), ("c2a", 64, 128), ("c2b", 128, 128),
@@ -208,8 +209,11 @@ class UNet:
         hw = hb = base = pred = None
         if head:
             hw, hb, base, pred = self.prm["head.w"]["p"], self.prm["head.b"]["p"], self.baseline, self.pred
+        # each layer may start its set-up while the previous one finishes (the
+        # weights are constant during inference)
         nn.conv3x3_fwd_tma_epi(x, self.prm[name + ".w"]["wk"], self.prm[name + ".b"]["p"], self.B, h, w, cin, cout, 1,
-                               out, ldo or cout, pool, up, ldu or cout, hw, hb, base, pred, self.status)
+                               out, ldo or cout, pool, up, ldu or cout, hw, hb, base, pred, self.status,
+                               EARLY_LAUNCH)
 
     def _forward_fused(self):
         """The forward pass with pooling, upsample + skip concatenation and the

@@ -165,3 +165,13 @@ def test_input_conv_matches_the_oracle_on_the_packed_input(B, H, W, Cout):
     ref = np.maximum(oracle.conv3x3(xr, wr, bias.cpu().numpy().astype(np.float64)), 0)
     bound = ACC * oracle.conv3x3(np.abs(xr), np.abs(wr)) + 1e-6
     close(out.float().cpu().numpy().reshape(B, H, W, Cout), ref, bound + 2.0 ** -8 * np.abs(ref), "input conv")
+
+
+def test_epi_conv_rejects_unknown_flags():
+    x = torch.zeros(64 * 64 * 32, dtype=torch.bfloat16, device="cuda")
+    w = torch.zeros(9 * 32 * 32, dtype=torch.bfloat16, device="cuda")
+    out = torch.empty_like(x)
+    st = torch.zeros(1, dtype=torch.int32, device="cuda")
+    rc = q.lib.qldnn_conv3x3_fwd_tma_epi(x.data_ptr(), w.data_ptr(), None, 1, 64, 64, 32, 32, 1, out.data_ptr(), 32,
+                                         None, None, 32, None, None, None, None, st.data_ptr(), 2, None)
+    assert rc == q.QLD_E_INVAL
