@@ -746,7 +746,7 @@ cudaError_t launch_maybe_early(void (*kernel)(KArgs...), unsigned grid, unsigned
     return cudaLaunchKernelEx(&cfg, kernel, args...);
 }
 
-template <int N, int SWB>
+template <int N, int SWB, int SUB = 1>
 int launch_tma(const void* in, const void* wk, const float* bias, int B, int H, int W, int Cin, int Cout, int relu,
                const qldnn::ConvEpi& epi, int* status, cudaStream_t st, bool force_stream, bool early) {
     using L = qldnn::TmaConv<N, SWB>;
@@ -760,7 +760,7 @@ int launch_tma(const void* in, const void* wk, const float* bias, int B, int H, 
     CUtensorMap mi, mw;
     const cuuint64_t gdim[4] = {(cuuint64_t)Cin, (cuuint64_t)W, (cuuint64_t)H, (cuuint64_t)B};
     const cuuint64_t gstr[3] = {(cuuint64_t)Cin * 2, (cuuint64_t)W * Cin * 2, (cuuint64_t)H * W * Cin * 2};
-    const cuuint32_t box[4] = {(cuuint32_t)L::BK, 16, 10, 1};
+    const cuuint32_t box[4] = {(cuuint32_t)L::BK, 16, (cuuint32_t)(8 * SUB + 2), 1};  // a tile's halo rows
     const cuuint32_t one[4] = {1, 1, 1, 1};
     if (enc(&mi, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, const_cast<void*>(in), gdim, gstr, box, one,
             CU_TENSOR_MAP_INTERLEAVE_NONE, sw, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
@@ -773,28 +773,30 @@ int launch_tma(const void* in, const void* wk, const float* bias, int B, int H, 
             CU_TENSOR_MAP_INTERLEAVE_NONE, sw, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
         return set_err(QLD_E_CUDA);
-    const long long ntiles = (long long)B * ((H + 7) / 8) * ((W + 15) / 16);
+    const long long ntiles = (long long)B * ((H + 8 * SUB - 1) / (8 * SUB)) * ((W + 15) / 16);
     const int nsplit = Cout / N;  // CTAs per tile, one output-channel slice each
     long long items = ntiles * nsplit;
     const long long cap = (long long)(nsm / nsplit) * nsplit;
     const unsigned grid = (unsigned)(items < cap ? items : cap);
     // weights resident in shared memory when they fit beside two or more halo stages
-    using R = qldnn::TmaConvRes<N, SWB>;
+    using R = qldnn::TmaConvRes<N, SWB, SUB>;
     int sa = 0;
     while (sa < R::kMaxSA && R::smem(sa + 1, Cin) <= 232448) ++sa;
     if (sa >= 2 && !force_stream) {
         static std::atomic<unsigned long long> attr_res{0};
         if (dev < 64 && !(attr_res.load() >> dev & 1ull)) {
-            if (cudaFuncSetAttribute(qldnn::conv3x3_fwd_tma_wres_kernel<N, SWB>,
+            if (cudaFuncSetAttribute(qldnn::conv3x3_fwd_tma_wres_kernel<N, SWB, SUB>,
                                      cudaFuncAttributeMaxDynamicSharedMemorySize, 232448) != cudaSuccess)
                 return set_err(QLD_E_CUDA);
             attr_res.fetch_or(1ull << dev);
         }
-        if (launch_maybe_early(qldnn::conv3x3_fwd_tma_wres_kernel<N, SWB>, grid, 192, (size_t)R::smem(sa, Cin), st,
-                               early, mi, mw, bias, B, H, W, Cin, Cout, relu, epi, status, sa, nsplit) != cudaSuccess)
+        if (launch_maybe_early(qldnn::conv3x3_fwd_tma_wres_kernel<N, SWB, SUB>, grid, 192, (size_t)R::smem(sa, Cin),
+                               st, early, mi, mw, bias, B, H, W, Cin, Cout, relu, epi, status, sa,
+                               nsplit) != cudaSuccess)
             return set_err(QLD_E_CUDA);
         return launched(1);
     }
+    if constexpr (SUB != 1) return set_err(QLD_E_INVAL);  // the weight-streaming kernel has 8-row tiles
     static std::atomic<unsigned long long> attr_done{0};  // per instantiation, one bit per device
     if (dev < 64 && !(attr_done.load() >> dev & 1ull)) {
         if (cudaFuncSetAttribute(qldnn::conv3x3_fwd_tma_kernel<N, SWB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -889,6 +891,23 @@ int conv_tma_dispatch(const void* in, const void* wk, const float* bias, int B, 
     if (split_mode > 0) nsplit = split_mode;
     if (Cout % nsplit || Cout / nsplit < 32) return set_err(QLD_E_INVAL);
     const int nco = Cout / nsplit;
+    // 16 x 16-pixel tiles (two stacked 8 x 16 sub-tiles per pipeline step) for
+    // narrow layers with weights resident beside two 18-row halo stages of at
+    // most 32 channels, when there are at least two such tiles per SM (mode
+    // bit 12 forces them where they apply, bit 13 forbids them). Automatic
+    // only for inputs staged in chunks of at most 32 channels anyway: layers
+    // of 64+ channels would have to drop from 64- to 32-channel chunks, and
+    // measured slower that way (8 x 128^2, 64 -> 64: 554 against 588 TFLOP/s)
+    const int swb2 = swb > 64 ? 64 : swb;
+    const long long tiles16 = (long long)B * ((H + 15) / 16) * ((W + 15) / 16);
+    const bool fits2 = 1024 + 2ll * 3 * 18 * 16 * swb2 + 9ll * Cin * nco * 2 + 256 <= 232448;
+    const bool sub2 = nsplit == 1 && nco <= 64 && !force_stream && !((mode >> 13) & 1) && fits2 &&
+                      (((mode >> 12) & 1) || (tiles16 >= 2ll * nsm && swb2 == swb));
+#define QLD_TMA2(NN, SS)                                                                                            \
+    if (sub2 && nco == NN && swb2 == SS)                                                                               \
+        return launch_tma<NN, SS, 2>(in, wk, bias, B, H, W, Cin, Cout, relu, epi, status, st, false, early);
+    QLD_TMA2(32, 32) QLD_TMA2(32, 64) QLD_TMA2(64, 32) QLD_TMA2(64, 64)
+#undef QLD_TMA2
 #define QLD_TMA(NN, SS) \
     if (nco == NN && swb == SS)                                                                                      \
         return launch_tma<NN, SS>(in, wk, bias, B, H, W, Cin, Cout, relu, epi, status, st, force_stream != 0, early);

@@ -202,8 +202,9 @@ __device__ __forceinline__ void tc_tie16(uint32_t* r) {
 // a warp holds two whole rows and the 2x2 pooling partners of lane l are the
 // lanes l ^ 1, l ^ 16 and l ^ 17. The accumulator is read in groups of up to
 // 64 columns (all loads of a group issued before one wait); with N <= 64 the
-// bias stays in registers for all tiles.
-template <int N>
+// bias stays in registers for all tiles. A tile is SUB sub-tiles of 8 x 16
+// pixels stacked in rows, sub-tile h in accumulator columns (acc SUB + h) N.
+template <int N, int SUB = 1>
 __device__ __forceinline__ void conv_epilogue(uint32_t tmem, uint64_t* tfull, uint64_t* tempty, volatile int* fail,
                                               int warp, int lane, int ntiles, int tiles_x, int tiles_y, int H, int W,
                                               int Cout, const float* __restrict__ bias, int relu, ConvEpi epi,
@@ -231,95 +232,98 @@ __device__ __forceinline__ void conv_epilogue(uint32_t tmem, uint64_t* tfull, ui
         if (!__all_sync(0xffffffffu, got)) break;  // tcgen05.ld below is warp-collective
         tc_fence_after();
         const int tx = t % tiles_x, r = t / tiles_x, ty = r % tiles_y, b = r / tiles_y;
-        const int y = ty * 8 + my, x = tx * 16 + mx;
-        const bool inside = y < H && x < W;
-        const long long p = ((long long)b * H + y) * W + x;
-        const uint32_t taddr = tmem + ((uint32_t)(qw * 32) << 16) + (uint32_t)(acc * N);
-        float hacc = epi.head_w ? *epi.head_b : 0.f;
 #pragma unroll 1
-        for (int g0 = 0; g0 < N; g0 += G) {
-            uint32_t rg[G];
+        for (int h = 0; h < SUB; ++h) {  // the tile's 8-row sub-tiles
+            const int y = (ty * SUB + h) * 8 + my, x = tx * 16 + mx;
+            const bool inside = y < H && x < W;
+            const long long p = ((long long)b * H + y) * W + x;
+            const uint32_t taddr = tmem + ((uint32_t)(qw * 32) << 16) + (uint32_t)((acc * SUB + h) * N);
+            float hacc = epi.head_w ? *epi.head_b : 0.f;
+#pragma unroll 1
+            for (int g0 = 0; g0 < N; g0 += G) {
+                uint32_t rg[G];
 #pragma unroll
-            for (int c = 0; c < G; c += 16) tc_ld16(taddr + (uint32_t)(g0 + c), rg + c);
-            asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
+                for (int c = 0; c < G; c += 16) tc_ld16(taddr + (uint32_t)(g0 + c), rg + c);
+                asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
 #pragma unroll
-            for (int c = 0; c < G; c += 16) tc_tie16(rg + c);
+                for (int c = 0; c < G; c += 16) tc_tie16(rg + c);
 #pragma unroll
-            for (int c = 0; c < G; c += 16) {
-                const int c0 = g0 + c;
-                const uint32_t* rr = rg + c;
-                float v[16];
+                for (int c = 0; c < G; c += 16) {
+                    const int c0 = g0 + c;
+                    const uint32_t* rr = rg + c;
+                    float v[16];
 #pragma unroll
-                for (int j = 0; j < 16; ++j) {
-                    float bj;
-                    if constexpr (N <= 64) bj = bres[c + j];  // g0 == 0
-                    else bj = bias ? bias[c0 + j] : 0.f;
-                    v[j] = __uint_as_float(rr[j]) + bj;
-                    if (relu) v[j] = fmaxf(v[j], 0.f);
-                }
-                uint32_t pk[8];
+                    for (int j = 0; j < 16; ++j) {
+                        float bj;
+                        if constexpr (N <= 64) bj = bres[c + j];  // g0 == 0
+                        else bj = bias ? bias[c0 + j] : 0.f;
+                        v[j] = __uint_as_float(rr[j]) + bj;
+                        if (relu) v[j] = fmaxf(v[j], 0.f);
+                    }
+                    uint32_t pk[8];
 #pragma unroll
-                for (int j = 0; j < 8; ++j) {
-                    const __nv_bfloat162 h2 = __floats2bfloat162_rn(v[2 * j], v[2 * j + 1]);
-                    pk[j] = *reinterpret_cast<const uint32_t*>(&h2);
-                }
-                if (epi.out && inside) {
-                    uint4* o = reinterpret_cast<uint4*>(epi.out + p * epi.ldo + c0);
-                    o[0] = make_uint4(pk[0], pk[1], pk[2], pk[3]);
-                    o[1] = make_uint4(pk[4], pk[5], pk[6], pk[7]);
-                }
-                if (epi.out_f && inside) {
-                    float4* o = reinterpret_cast<float4*>(epi.out_f + p * Cout + c0);
-#pragma unroll
-                    for (int j = 0; j < 4; ++j) o[j] = make_float4(v[4 * j], v[4 * j + 1], v[4 * j + 2], v[4 * j + 3]);
-                }
-                if (epi.up && inside) {
-#pragma unroll
-                    for (int d = 0; d < 4; ++d) {
-                        const long long q = ((long long)b * 2 * H + 2 * y + (d >> 1)) * (2ll * W) + 2 * x + (d & 1);
-                        uint4* o = reinterpret_cast<uint4*>(epi.up + q * epi.ldu + c0);
+                    for (int j = 0; j < 8; ++j) {
+                        const __nv_bfloat162 h2 = __floats2bfloat162_rn(v[2 * j], v[2 * j + 1]);
+                        pk[j] = *reinterpret_cast<const uint32_t*>(&h2);
+                    }
+                    if (epi.out && inside) {
+                        uint4* o = reinterpret_cast<uint4*>(epi.out + p * epi.ldo + c0);
                         o[0] = make_uint4(pk[0], pk[1], pk[2], pk[3]);
                         o[1] = make_uint4(pk[4], pk[5], pk[6], pk[7]);
                     }
-                }
-                if (epi.pool || epi.head_w) {
-                    float f[16];  // the stored (bf16) values
+                    if (epi.out_f && inside) {
+                        float4* o = reinterpret_cast<float4*>(epi.out_f + p * Cout + c0);
 #pragma unroll
-                    for (int j = 0; j < 8; ++j) {
-                        const float2 t2 = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&pk[j]));
-                        f[2 * j] = t2.x;
-                        f[2 * j + 1] = t2.y;
+                        for (int j = 0; j < 4; ++j) o[j] = make_float4(v[4 * j], v[4 * j + 1], v[4 * j + 2], v[4 * j + 3]);
                     }
-                    if (epi.pool) {  // warp-uniform: every lane shuffles
-                        float o[16];
+                    if (epi.up && inside) {
 #pragma unroll
-                        for (int j = 0; j < 16; ++j) {
-                            const float a1 = __shfl_xor_sync(0xffffffffu, f[j], 1);
-                            const float a2 = __shfl_xor_sync(0xffffffffu, f[j], 16);
-                            const float a3 = __shfl_xor_sync(0xffffffffu, f[j], 17);
-                            o[j] = 0.25f * (f[j] + a1 + a2 + a3);
+                        for (int d = 0; d < 4; ++d) {
+                            const long long q = ((long long)b * 2 * H + 2 * y + (d >> 1)) * (2ll * W) + 2 * x + (d & 1);
+                            uint4* o = reinterpret_cast<uint4*>(epi.up + q * epi.ldu + c0);
+                            o[0] = make_uint4(pk[0], pk[1], pk[2], pk[3]);
+                            o[1] = make_uint4(pk[4], pk[5], pk[6], pk[7]);
                         }
-                        if (pool_writer && inside) {
-                            uint32_t q2[8];
+                    }
+                    if (epi.pool || epi.head_w) {
+                        float f[16];  // the stored (bf16) values
 #pragma unroll
-                            for (int j = 0; j < 8; ++j) {
-                                const __nv_bfloat162 h2 = __floats2bfloat162_rn(o[2 * j], o[2 * j + 1]);
-                                q2[j] = *reinterpret_cast<const uint32_t*>(&h2);
+                        for (int j = 0; j < 8; ++j) {
+                            const float2 t2 = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&pk[j]));
+                            f[2 * j] = t2.x;
+                            f[2 * j + 1] = t2.y;
+                        }
+                        if (epi.pool) {  // warp-uniform: every lane shuffles
+                            float o[16];
+#pragma unroll
+                            for (int j = 0; j < 16; ++j) {
+                                const float a1 = __shfl_xor_sync(0xffffffffu, f[j], 1);
+                                const float a2 = __shfl_xor_sync(0xffffffffu, f[j], 16);
+                                const float a3 = __shfl_xor_sync(0xffffffffu, f[j], 17);
+                                o[j] = 0.25f * (f[j] + a1 + a2 + a3);
                             }
-                            const long long pp = ((long long)b * (H / 2) + y / 2) * (W / 2) + x / 2;
-                            uint4* po = reinterpret_cast<uint4*>(epi.pool + pp * epi.ldp + c0);
-                            po[0] = make_uint4(q2[0], q2[1], q2[2], q2[3]);
-                            po[1] = make_uint4(q2[4], q2[5], q2[6], q2[7]);
-                        }
-                    }
-                    if (epi.head_w) {
+                            if (pool_writer && inside) {
+                                uint32_t q2[8];
 #pragma unroll
-                        for (int j = 0; j < 16; ++j) hacc = fmaf(f[j], epi.head_w[c0 + j], hacc);
+                                for (int j = 0; j < 8; ++j) {
+                                    const __nv_bfloat162 h2 = __floats2bfloat162_rn(o[2 * j], o[2 * j + 1]);
+                                    q2[j] = *reinterpret_cast<const uint32_t*>(&h2);
+                                }
+                                const long long pp = ((long long)b * (H / 2) + y / 2) * (W / 2) + x / 2;
+                                uint4* po = reinterpret_cast<uint4*>(epi.pool + pp * epi.ldp + c0);
+                                po[0] = make_uint4(q2[0], q2[1], q2[2], q2[3]);
+                                po[1] = make_uint4(q2[4], q2[5], q2[6], q2[7]);
+                            }
+                        }
+                        if (epi.head_w) {
+#pragma unroll
+                            for (int j = 0; j < 16; ++j) hacc = fmaf(f[j], epi.head_w[c0 + j], hacc);
+                        }
                     }
                 }
             }
+            if (epi.head_w && inside) epi.pred[p] = hacc + epi.base[p];
         }
-        if (epi.head_w && inside) epi.pred[p] = hacc + epi.base[p];
         tc_fence_before();
         mbar_arrive(&tempty[acc]);
         ++it;
@@ -502,28 +506,34 @@ __global__ void __launch_bounds__(192, 1)
 // the halos through an SA-stage ring (SA chosen at launch, at most kMaxSA), so
 // neither the L2 nor the ring depth is spent on weights tile after tile.
 // Same tiles, operand layouts, MMAs, epilogue and failure handling as
-// conv3x3_fwd_tma_kernel.
-template <int N, int SWB>
+// conv3x3_fwd_tma_kernel. SUB = 2: each tile is two 8 x 16 sub-tiles stacked
+// in rows (16 x 16 pixels) that share one 18-row halo load per channel chunk,
+// one barrier round trip and the weights of each MMA step, accumulating into
+// two accumulators of N columns; the per-tile pipeline costs, which dominate
+// narrow (N = 32, 64) layers, are paid once per 256 pixels. With the same
+// channel chunks (SWB) the MMAs of each accumulator, and so the results, are
+// those of SUB = 1.
+template <int N, int SWB, int SUB = 1>
 struct TmaConvRes {
     static constexpr int BK = SWB / 2;
-    static constexpr int HALO = 10 * 16 * SWB;
+    static constexpr int HALO = (8 * SUB + 2) * 16 * SWB;  // one column-shifted halo copy of a tile
     static constexpr int ASTAGE = 3 * HALO;
     static constexpr int BSTAGE = N * SWB;
     static constexpr int kMaxSA = 8;
     static constexpr int kBars = (2 * kMaxSA + 6) * 8;
-    static constexpr int kTmemCols = 2 * N;
+    static constexpr int kTmemCols = 2 * N * SUB;
     // dynamic shared memory for SA halo stages and Cin input channels
     static constexpr long long smem(int SA, int Cin) {
         return 1024 + (long long)SA * ASTAGE + 9ll * (Cin / BK) * BSTAGE + kBars + 16;
     }
 };
 
-template <int N, int SWB>
+template <int N, int SWB, int SUB = 1>
 __global__ void __launch_bounds__(192, 1)
     conv3x3_fwd_tma_wres_kernel(const __grid_constant__ CUtensorMap map_in, const __grid_constant__ CUtensorMap map_w,
                                 const float* __restrict__ bias, int B, int H, int W, int Cin, int Cout, int relu,
                                 const ConvEpi epi, int* status, int SA, int nsplit) {
-    using L = TmaConvRes<N, SWB>;
+    using L = TmaConvRes<N, SWB, SUB>;
     extern __shared__ unsigned char dsm_raw[];
     unsigned char* dsm = dsm_raw + ((1024u - (smem_u32(dsm_raw) & 1023u)) & 1023u);
     const int csteps = Cin / L::BK;
@@ -539,7 +549,7 @@ __global__ void __launch_bounds__(192, 1)
     volatile int* fail = reinterpret_cast<volatile int*>(tslot + 1);
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int tiles_x = (W + 15) >> 4, tiles_y = (H + 7) >> 3;
+    const int tiles_x = (W + 15) >> 4, tiles_y = (H + 8 * SUB - 1) / (8 * SUB);
     const int ntiles = B * tiles_x * tiles_y;
     const int co0 = (blockIdx.x % nsplit) * N;  // this CTA's slice of the output channels
     constexpr uint32_t kIdesc = umma_idesc_bf16(128, N);
@@ -585,7 +595,7 @@ __global__ void __launch_bounds__(192, 1)
             bool ok = true;
             for (int t = blockIdx.x / nsplit; t < ntiles && ok; t += gridDim.x / nsplit) {
                 const int tx = t % tiles_x, r = t / tiles_x, ty = r % tiles_y, b = r / tiles_y;
-                const int x0 = tx * 16, y0 = ty * 8;
+                const int x0 = tx * 16, y0 = ty * 8 * SUB;
                 for (int cc = 0; cc < csteps; ++cc) {
                     const int sa = ia % SA;
                     if (ia >= SA && !(ok = wait_or_fail(&emptyA[sa], (uint32_t)(((ia / SA) - 1) & 1), fail))) break;
@@ -613,7 +623,7 @@ __global__ void __launch_bounds__(192, 1)
                 const int acc = it & 1;
                 if (it >= 2 && !(ok = wait_or_fail(&tempty[acc], (uint32_t)(((it >> 1) - 1) & 1), fail))) break;
                 tc_fence_after();
-                const uint32_t d = tmem + (uint32_t)(acc * N);
+                const uint32_t d = tmem + (uint32_t)(acc * N * SUB);
                 for (int cc = 0; cc < csteps && ok; ++cc) {
                     const int sa = ia % SA;
                     if (!(ok = wait_or_fail(&fullA[sa], (uint32_t)((ia / SA) & 1), fail))) break;
@@ -624,8 +634,11 @@ __global__ void __launch_bounds__(192, 1)
                     for (int tap = 0; tap < 9; ++tap) {
 #pragma unroll
                         for (int kk = 0; kk < L::BK / 16; ++kk)
-                            tc_mma(d, desc_at(adesc, (tap % 3) * L::HALO + (tap / 3) * 16 * SWB + kk * 32),
-                                   desc_at(bdesc, tap * L::BSTAGE + kk * 32), kIdesc, (cc | tap | kk) ? 1u : 0u);
+#pragma unroll
+                            for (int h = 0; h < SUB; ++h)  // sub-tile h: halo rows from 8 h on
+                                tc_mma(d + (uint32_t)(h * N),
+                                       desc_at(adesc, (tap % 3) * L::HALO + (tap / 3 + 8 * h) * 16 * SWB + kk * 32),
+                                       desc_at(bdesc, tap * L::BSTAGE + kk * 32), kIdesc, (cc | tap | kk) ? 1u : 0u);
                     }
                     tc_commit(&emptyA[sa]);
                     ++ia;
@@ -638,8 +651,8 @@ __global__ void __launch_bounds__(192, 1)
             wait_timed(drain, 0, nullptr);
         }
     } else {
-        conv_epilogue<N>(tmem, tfull, tempty, fail, warp, lane, ntiles, tiles_x, tiles_y, H, W, Cout, bias, relu, epi,
-                         nsplit);
+        conv_epilogue<N, SUB>(tmem, tfull, tempty, fail, warp, lane, ntiles, tiles_x, tiles_y, H, W, Cout, bias, relu,
+                              epi, nsplit);
     }
 
     tc_fence_before();

@@ -23,10 +23,12 @@ def _need_gpu():
 # conv3x3_fwd_tma keeps small layers' weights resident in shared memory and
 # splits small layers' output channels over several CTAs per tile;
 # "conv3x3_fwd_tma_stream" forces its weight-streaming variant, "..._split2" /
-# "..._split4" force 2 / 4 CTAs per tile, on every shape they apply to.
+# "..._split4" force 2 / 4 CTAs per tile, "..._sub2" 16 x 16-pixel tiles (two
+# stacked 8 x 16 sub-tiles), on every shape they apply to.
 KERNELS = ["conv3x3_fwd_tc", "conv3x3_fwd_tc2", "conv3x3_fwd_tma", "conv3x3_fwd_tma_stream",
-           "conv3x3_fwd_tma_split2", "conv3x3_fwd_tma_split4"]
-MODES = {"conv3x3_fwd_tma_stream": 1, "conv3x3_fwd_tma_split2": 2 << 4, "conv3x3_fwd_tma_split4": 4 << 4}
+           "conv3x3_fwd_tma_split2", "conv3x3_fwd_tma_split4", "conv3x3_fwd_tma_sub2"]
+MODES = {"conv3x3_fwd_tma_stream": 1, "conv3x3_fwd_tma_split2": 2 << 4, "conv3x3_fwd_tma_split4": 4 << 4,
+         "conv3x3_fwd_tma_sub2": 1 << 12}
 
 
 def _tc(kernel, Cout):
@@ -34,7 +36,7 @@ def _tc(kernel, Cout):
         pytest.skip("the pipelined kernels cover Cout in {32, 64, 128, 256}")
     if kernel in MODES:
         mode = MODES[kernel]
-        if Cout // max(1, mode >> 4) < 32:
+        if Cout // max(1, (mode >> 4) & 0xF) < 32:
             pytest.skip("at least 32 output channels per CTA")
         return lambda *a: q.nn.conv3x3_fwd_tma_mode(*a, mode)
     return getattr(q.nn, kernel)
@@ -166,3 +168,30 @@ def test_bounded_wait_times_out_raises_the_flag_and_leaves_the_context_usable():
     assert status.item() == 0
     with pytest.raises(q.QLDError):
         q.nn.wait_selftest(10, out)  # below the 1 us minimum
+
+
+@pytest.mark.parametrize("B,H,W,Cin,Cout,relu", [(1, 64, 48, 32, 32, 1), (2, 33, 40, 16, 64, 0), (1, 48, 80, 96, 32, 1),
+                                                 (1, 17, 31, 48, 64, 1), (1, 7, 16, 32, 32, 0)])
+def test_tma_16x16_tiles_equal_8x16_tiles(B, H, W, Cin, Cout, relu):
+    """Two stacked sub-tiles per pipeline step run the same MMAs per
+    accumulator as single 8 x 16 tiles when both stage the same channel
+    chunks (inputs of at most 32-channel chunks: Cin not a multiple of 64):
+    identical outputs, bit for bit. (Multiples of 64 channels run in 32-channel
+    chunks with 16 x 16 tiles, 64-channel ones otherwise: the oracle parity
+    test covers those.)"""
+    rng = np.random.default_rng(H * W + Cin + Cout)
+    x, _ = bf16(rng.standard_normal((B, H, W, Cin)))
+    w, _ = bf16(rng.standard_normal((3, 3, Cin, Cout)) / np.sqrt(9 * Cin))
+    bias = torch.from_numpy(rng.standard_normal(Cout).astype(np.float32)).cuda()
+    wk = torch.empty(9 * Cin * Cout, dtype=torch.bfloat16, device="cuda")
+    q.nn.kmajor_weights(w, Cin, Cout, 0, wk)
+    outs = []
+    for mode in (1 << 12, 1 << 13):
+        status = torch.zeros(1, dtype=torch.int32, device="cuda")
+        out_f = torch.full((B, H, W, Cout), float("nan"), dtype=torch.float32, device="cuda")
+        out_b = torch.empty((B, H, W, Cout), dtype=torch.bfloat16, device="cuda")
+        q.nn.conv3x3_fwd_tma_mode(x, wk, bias, B, H, W, Cin, Cout, relu, out_b, out_f, status, mode)
+        torch.cuda.synchronize()
+        assert status.item() == 0
+        outs.append((out_f.cpu(), out_b.cpu()))
+    assert torch.equal(outs[0][0], outs[1][0]) and torch.equal(outs[0][1], outs[1][1])
