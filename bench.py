@@ -739,12 +739,11 @@ def run_serving(q, torch, dev, st, peak, ticks=300, paced_ticks=300, fps=200.0, 
     vals = torch.arange(1, gsamples + 1, dtype=torch.int32).reshape(gsamples, 1).repeat(1, 4).pin_memory()
     gst, side = torch.cuda.Stream(dev), torch.cuda.Stream(dev)
     torch.cuda.synchronize(dev)
-    armed, t_ring = threading.Event(), [0.0] * gsamples
+    armed, t_ring = threading.Semaphore(0), [0.0] * gsamples
 
     def ringer():
         for k in range(gsamples):
-            armed.wait()
-            armed.clear()
+            armed.acquire()
             time.sleep(0.001)  # the gate is polling by now
             t_ring[k] = time.perf_counter()
             with torch.cuda.stream(side):
@@ -756,18 +755,17 @@ def run_serving(q, torch, dev, st, peak, ticks=300, paced_ticks=300, fps=200.0, 
     glat, gerr = [], None
     for k in range(gsamples):
         batches[(20 + ticks + paced_ticks + k) % P].submit(srv, len(tickets))
-        armed.set()
+        armed.release()
         try:
             q.qld_server_tick_gated(srv, bell, k + 1, 1_000_000_000, gst.cuda_stream)
         except q.QLDError as e:  # the bell did not ring within the limit
             gerr = str(e)
-            for j in range(k + 1, gsamples):  # let the ringer finish
-                armed.set()
-                time.sleep(0.003)
+            for _ in range(k + 1, gsamples):  # let the ringer finish
+                armed.release()
             q.qld_server_tick(srv, st)
             break
         glat.append((time.perf_counter() - t_ring[k]) * 1e6)
-    th.join()
+    th.join(timeout=30)
     glat.sort()
     gated = ({"error": gerr} if gerr or not glat else
              {"p50": glat[len(glat) // 2], "p99": glat[min(len(glat) - 1, int(0.99 * len(glat)))],
