@@ -309,3 +309,39 @@ def test_gated_tick_runs_when_a_host_thread_rings_the_doorbell():
         srv.destroy()
         for c in alone:
             c.destroy()
+
+
+def test_gated_tick_doorbell_in_mapped_host_memory():
+    """The doorbell as a word of mapped pinned host memory (device pointer from
+    cudaHostGetDevicePointer), set by the host: the gate's volatile loads see
+    it across the bus and the tick runs."""
+    import ctypes
+    from cuda.bindings import runtime as rt
+    srv, mix, tickets, alone, _ = _gated_setup(47)
+    err, hptr = rt.cudaHostAlloc(16, rt.cudaHostAllocMapped)
+    assert err == rt.cudaError_t.cudaSuccess
+    try:
+        word = ctypes.c_int.from_address(int(hptr))
+        word.value = 5
+        err, dptr = rt.cudaHostGetDevicePointer(hptr, 0)
+        assert err == rt.cudaError_t.cudaSuccess
+        assert q.qld_server_tick_gated(srv, int(dptr), 5, 1_000_000_000) == len(mix)
+        _check_against_alone(srv, mix, tickets, alone)
+        # a target above the word's value times out, nothing consumed
+        keep = []
+        for (H, W, N, fmt), t, ctx in zip(mix, tickets, alone):
+            x, dev = frames_for(np.random.default_rng(W), H, W, fmt, 1)
+            keep.append(dev)
+            q.qld_server_submit(srv, t, dev, 1)
+            q.qld_push_frames(ctx, dev, 1)
+        with pytest.raises(q.QLDError) as e:
+            q.qld_server_tick_gated(srv, int(dptr), 6, 5_000_000)
+        assert e.value.status == q.QLD_E_TIMEOUT
+        word.value = 6
+        assert q.qld_server_tick_gated(srv, int(dptr), 6, 1_000_000_000) == len(mix)
+        _check_against_alone(srv, mix, tickets, alone)
+    finally:
+        srv.destroy()
+        for c in alone:
+            c.destroy()
+        rt.cudaFreeHost(hptr)

@@ -66,7 +66,7 @@ def test_step_equals_push_image_then_fft_bin(H, W, fmt, N, offset):
         fill = rng.integers(0, hi, size=(N - 1, H * W))
         a.push(fill)
         b.push(fill)
-        for count, k in [(1, N // 4), (4, 1), (3, N - 1), (N, 0), (5, N // 2), (2, N // 4)]:
+        for count, k in [(1, N // 4), (4, 1), (3, N - 1), (N, 0), (5, N // 2), (2, N // 4), (N + 3, 1)]:
             step_both(a, b, rng.integers(0, hi, size=(count, H * W)), k, offset)
             a.check(bins=(k,))
     finally:
@@ -162,3 +162,20 @@ def test_step_host_equals_step_on_device(H, W, fmt, N, count):
     finally:
         a.destroy()
         b.destroy()
+
+
+def test_step_fills_a_window_that_was_almost_empty():
+    """qld_step of exactly N frames onto a window holding 2: one kernel whose
+    expiring slots are partly the ring's zeros."""
+    H, W, N = 64, 64, 16
+    rng = np.random.default_rng(5)
+    a, b = Stream(H, W, N, q.QLD_U16), Stream(H, W, N, q.QLD_U16)
+    try:
+        first = rng.integers(0, 4096, size=(2, H * W))
+        a.push(first)
+        b.push(first)
+        step_both(a, b, rng.integers(0, 4096, size=(N, H * W)), 3)
+        a.check(bins=(3, N // 4))
+    finally:
+        a.ctx.destroy()
+        b.ctx.destroy()
