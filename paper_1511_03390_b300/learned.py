@@ -112,14 +112,17 @@ class UNet:
 
     CONVS = ("tma", "tcgen05", "warp_mma")
 
-    def __init__(self, params, B, H, W, inference_only=False, conv="tma", fuse_input=True):
+    def __init__(self, params, B, H, W, inference_only=False, conv="tma", fuse_input=False):
         assert H % 8 == 0 and W % 8 == 0
         assert conv in self.CONVS, conv
         self.prm = params
         self.conv = conv
         # inference with the TMA kernel: pooling, upsampling + skip concat and
         # the head run inside the convolutions' epilogues, and (fuse_input)
-        # the input packing inside the first convolution
+        # the input packing inside a first convolution on the FP32 cores. That
+        # one is off by default: the packing kernel plus the tensor-core layer
+        # (16 x 16-pixel tiles, launched early) measured faster in the graph
+        # at 512^2 (194 against 199 us for the whole forward).
         self.fused = inference_only and conv == "tma"
         self.fuse_input = self.fused and fuse_input
         self._iq = None

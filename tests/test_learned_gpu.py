@@ -131,7 +131,7 @@ def test_fused_inference_forward_matches_the_layer_by_layer_pass(B, H, W):
     assert torch.equal(got, want)
     # the first layer on the FP32 cores (input packing fused) sums in another
     # order: predictions agree to FP32 accumulation and bf16 storage rounding
-    full = learned.UNet(prm, B, H, W, inference_only=True)
+    full = learned.UNet(prm, B, H, W, inference_only=True, fuse_input=True)
     full.pack(S, C)
     got2 = full.forward()
     torch.cuda.synchronize()
