@@ -657,6 +657,9 @@ __global__ void __launch_bounds__(128) input_conv3x3_kernel(const int32_t* __res
 
 __global__ void pack_input_kernel(const int32_t* __restrict__ S, const int32_t* __restrict__ C, long long n,
                                   float scale, __nv_bfloat16* __restrict__ out, float* __restrict__ baseline) {
+    // a first convolution launched early (qldnn_conv3x3_fwd_tma_epi) may set
+    // itself up now; it waits for this kernel before it reads the packed input
+    asm volatile("griddepcontrol.launch_dependents;" :::);
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
         const float s = (float)S[i], c = (float)C[i];
         const float r = sqrtf(s * s + c * c) * scale;
