@@ -7,6 +7,7 @@ untouched), aligned and unaligned frame addresses, and DFT bins anywhere in
 [0, N). Each case is one seed, so a failure names its configuration and
 reruns alone."""
 import math
+import os
 
 import numpy as np
 import pytest
@@ -19,8 +20,9 @@ from test_lockin_gpu import gpu_lockin
 
 pytestmark = pytest.mark.gpu
 
-RING_CASES = 40
-LOCKIN_CASES = 16
+# more cases with QLD_SWEEP_CASES=n (the ring sweep; the lock-in one gets n / 2.5)
+RING_CASES = int(os.environ.get("QLD_SWEEP_CASES", "40"))
+LOCKIN_CASES = max(16, int(RING_CASES / 2.5))
 
 
 @pytest.fixture(autouse=True)
