@@ -752,7 +752,7 @@ def run_serving(q, torch, dev, st, peak, ticks=300, paced_ticks=300, fps=200.0, 
 
     th = threading.Thread(target=ringer)
     th.start()
-    glat, gerr = [], None
+    glat, gdev, gerr = [], [], None
     for k in range(gsamples):
         batches[(20 + ticks + paced_ticks + k) % P].submit(srv, len(tickets))
         armed.release()
@@ -765,13 +765,17 @@ def run_serving(q, torch, dev, st, peak, ticks=300, paced_ticks=300, fps=200.0, 
             q.qld_server_tick(srv, st)
             break
         glat.append((time.perf_counter() - t_ring[k]) * 1e6)
+        gdev.append(q.qld_server_last_gated_us(srv))
     th.join(timeout=30)
     glat.sort()
+    gdev.sort()
     gated = ({"error": gerr} if gerr or not glat else
              {"p50": glat[len(glat) // 2], "p99": glat[min(len(glat) - 1, int(0.99 * len(glat)))],
               "samples": len(glat),
+              "device_p50": gdev[len(gdev) // 2], "device_p99": gdev[min(len(gdev) - 1, int(0.99 * len(gdev)))],
               "what": "qld_server_tick_gated armed before the frames' doorbell; host clock from the doorbell "
-                      "copy's enqueue on another stream to the call's return (all 8 images complete)"})
+                      "copy's enqueue on another stream to the call's return (all 8 images complete); device_* "
+                      "is the GPU time from the gate seeing the doorbell to the images complete (CUDA events)"})
     mem = q.qld_server_mem_in_use(srv)
     srv.destroy()
     del pools

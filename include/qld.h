@@ -291,6 +291,10 @@ int qld_server_tick(qld_server* srv, void* stream);
  * with no wait, when nothing was submitted). QLD_E_INVAL for a NULL or
  * misaligned doorbell or a timeout out of range. */
 int qld_server_tick_gated(qld_server* srv, void* stream, const int* doorbell, int target, long long timeout_ns);
+/* GPU time of the last gated tick that ran, from the end of its doorbell wait
+ * (the doorbell seen) to the tick's images complete, in microseconds (CUDA
+ * events on the tick's stream). QLD_E_NOT_READY before the first one. */
+int qld_server_last_gated_us(const qld_server* srv, float* us);
 int qld_server_image(qld_server* srv, int ticket, float** amp, float** phase);
 int qld_server_iq(qld_server* srv, int ticket, int32_t* S, int32_t* C);
 long long qld_server_frames_pushed(qld_server* srv, int ticket);

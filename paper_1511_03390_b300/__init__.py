@@ -22,7 +22,7 @@ __all__ = [
     "qld_mem_in_use", "qld_launch_count", "qld_fft_bin_frames_noalloc", "QLD_NOALLOC_MAX_N",
     "qld_lockin_table", "qld_lockin_frames", "Server", "QLD_SERVER_MAX_STREAMS", "qld_server_create",
     "qld_server_destroy", "qld_server_request", "qld_server_state", "qld_server_close", "qld_server_submit",
-    "qld_server_submit_many", "qld_server_tick_gated",
+    "qld_server_submit_many", "qld_server_tick_gated", "qld_server_last_gated_us",
     "qld_server_tick", "qld_server_image", "qld_server_iq", "qld_server_frames_pushed", "qld_server_mem_in_use",
     "qld_server_sync", "qld_server_autotune", "qld_server_shape", "nn", "LIB_PATH", "lib",
 ]
@@ -106,6 +106,7 @@ _SIGS = {
     "qld_server_submit_many": ([_p, _i, _p, _p, _p], _i),
     "qld_server_tick": ([_p, _p], _i),
     "qld_server_tick_gated": ([_p, _p, _p, _i, _ll], _i),
+    "qld_server_last_gated_us": ([_p, ctypes.POINTER(ctypes.c_float)], _i),
     "qld_server_image": ([_p, _i, ctypes.POINTER(_p), ctypes.POINTER(_p)], _i),
     "qld_server_iq": ([_p, _i, _p, _p], _i),
     "qld_server_frames_pushed": ([_p, _i], _ll),
@@ -452,6 +453,13 @@ def qld_server_tick(srv, stream=None):
     if n < 0:
         raise QLDError(n, "qld_server_tick")
     return n
+
+
+def qld_server_last_gated_us(srv):
+    """GPU microseconds of the last gated tick, doorbell seen -> images complete."""
+    us = ctypes.c_float()
+    _check(lib.qld_server_last_gated_us(_sh(srv), ctypes.byref(us)), "qld_server_last_gated_us")
+    return us.value
 
 
 def qld_server_tick_gated(srv, doorbell, target, timeout_ns, stream=None):

@@ -63,6 +63,8 @@ struct qld_server {
     qldk::BatchHeader* hdr_host[2];  // pinned
     qldk::BatchItem* items_host[2];  // inside the hdr_host[b] blocks
     int* gate_dev;                   // outcome of a gated tick's doorbell wait
+    cudaEvent_t gate_ev[2];          // after the doorbell wait, after the gated tick (timing)
+    float last_gated_us;             // the last gated tick: doorbell seen -> images complete
     cudaEvent_t used[2];
     bool used_valid[2];
     cudaGraphExec_t graph[2];
@@ -216,6 +218,8 @@ qld_server* qld_server_create(long long hbm_budget_bytes, int max_streams) {
     s->hdr_dev = nullptr;
     s->items_dev = nullptr;
     s->gate_dev = nullptr;
+    s->gate_ev[0] = s->gate_ev[1] = nullptr;
+    s->last_gated_us = -1.f;
     s->hdr_host[0] = s->hdr_host[1] = nullptr;
     s->items_host[0] = s->items_host[1] = nullptr;
     s->used_valid[0] = s->used_valid[1] = false;
@@ -228,6 +232,7 @@ qld_server* qld_server_create(long long hbm_budget_bytes, int max_streams) {
               cudaDeviceGetAttribute(&s->num_sms, cudaDevAttrMultiProcessorCount, s->device) == cudaSuccess &&
               cudaMalloc(&s->hdr_dev, desc_bytes(max_streams)) == cudaSuccess &&
               cudaMalloc(&s->gate_dev, 16) == cudaSuccess && cudaMemset(s->gate_dev, 0, 16) == cudaSuccess &&
+              cudaEventCreate(&s->gate_ev[0]) == cudaSuccess && cudaEventCreate(&s->gate_ev[1]) == cudaSuccess &&
               cudaStreamCreateWithFlags(&s->cap, cudaStreamNonBlocking) == cudaSuccess;
     if (ok) s->items_dev = items_of(s->hdr_dev);
     for (int b = 0; ok && b < 2; ++b) {
@@ -258,6 +263,8 @@ void qld_server_destroy(qld_server* s) {
     }
     if (s->hdr_dev) cudaFree(s->hdr_dev);
     if (s->gate_dev) cudaFree(s->gate_dev);
+    for (int e = 0; e < 2; ++e)
+        if (s->gate_ev[e]) cudaEventDestroy(s->gate_ev[e]);
     if (s->cap) cudaStreamDestroy(s->cap);
     delete s;
 }
@@ -376,7 +383,8 @@ int qld_server_tick_gated(qld_server* s, void* stream, const int* doorbell, int 
     int rc = ensure_graphs(s);
     if (rc != QLD_OK) return set_err(rc);
     qldk::doorbell_gate_kernel<<<1, 32, 0, st>>>(doorbell, target, timeout_ns, s->gate_dev);
-    if (cudaGetLastError() != cudaSuccess || cudaGraphLaunch(s->graph[b], st) != cudaSuccess ||
+    if (cudaGetLastError() != cudaSuccess || cudaEventRecord(s->gate_ev[0], st) != cudaSuccess ||
+        cudaGraphLaunch(s->graph[b], st) != cudaSuccess || cudaEventRecord(s->gate_ev[1], st) != cudaSuccess ||
         cudaEventRecord(s->used[b], st) != cudaSuccess)
         return set_err(QLD_E_CUDA);
     s->used_valid[b] = true;
@@ -388,6 +396,8 @@ int qld_server_tick_gated(qld_server* s, void* stream, const int* doorbell, int 
         cudaMemcpy(&gate, s->gate_dev, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess)
         return set_err(QLD_E_CUDA);
     if (gate != 0) return set_err(QLD_E_TIMEOUT);  // nothing ran; the submissions stay pending
+    float ms = -1.f;
+    s->last_gated_us = cudaEventElapsedTime(&ms, s->gate_ev[0], s->gate_ev[1]) == cudaSuccess ? ms * 1e3f : -1.f;
     for (int id : which) {
         SrvStream& t = s->streams[id];
         t.ctx->pushed += t.pending_count;
@@ -396,6 +406,13 @@ int qld_server_tick_gated(qld_server* s, void* stream, const int* doorbell, int 
         t.pending_count = 0;
     }
     return n;
+}
+
+int qld_server_last_gated_us(const qld_server* s, float* us) {
+    if (!s || !us) return set_err(QLD_E_INVAL);
+    if (s->last_gated_us < 0.f) return set_err(QLD_E_NOT_READY);
+    *us = s->last_gated_us;
+    return QLD_OK;
 }
 
 int qld_server_image(qld_server* s, int ticket, float** amp, float** phase) {

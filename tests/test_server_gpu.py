@@ -248,6 +248,9 @@ def test_gated_tick_times_out_on_a_doorbell_nothing_rings():
         with pytest.raises(q.QLDError) as e:
             q.qld_server_tick_gated(srv, bell, 1, 20_000_000)  # 20 ms, nothing writes the bell
         assert e.value.status == q.QLD_E_TIMEOUT
+        with pytest.raises(q.QLDError) as e:  # no gated tick has run yet
+            q.qld_server_last_gated_us(srv)
+        assert e.value.status == q.QLD_E_NOT_READY
         assert all(q.qld_server_frames_pushed(srv, t) == 0 for t in tickets)
         # the submissions are still pending: a plain tick consumes them, and the
         # server's results equal each stream alone
@@ -265,6 +268,7 @@ def test_gated_tick_times_out_on_a_doorbell_nothing_rings():
             q.qld_push_frames(ctx, dev, 2)
         assert q.qld_server_tick_gated(srv, bell, 7, 1_000_000_000) == len(mix)
         _check_against_alone(srv, mix, tickets, alone)
+        assert 0.0 < q.qld_server_last_gated_us(srv) < 1e5  # the tick alone, not the wait
         for bad in [(None, 1, 1000), (bell, 1, 0), (bell, 1, 11 * 10 ** 9), (bell.data_ptr() + 2, 1, 1000)]:
             assert q.lib.qld_server_tick_gated(srv.handle, None, bad[0] if not isinstance(bad[0], torch.Tensor)
                                                else bad[0].data_ptr(), bad[1], bad[2]) == q.QLD_E_INVAL
