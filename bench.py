@@ -568,7 +568,9 @@ def run_large(q, torch, dev, st, peak, steps=200):
     e1.synchronize()
     us = e0.elapsed_time(e1) * 1e3 / steps
     npix = HL * WL
-    nbytes = npix * (3 * 2 + 16 + 8)
+    # frame, expiring slot, slot write; S and C read (the image needs both);
+    # one of them written (one frame changes S or C, never both); image out
+    nbytes = npix * (3 * 2 + 8 + 4 + 8)
     ring_gb = q.qld_footprint_bytes(HL, WL, NL, 2) / 1e9
     ctx.destroy()
     del pool, amp, ph
@@ -711,7 +713,9 @@ def run_serving(q, torch, dev, st, peak, ticks=300, paced_ticks=300, fps=200.0, 
     e1.synchronize()
     tick_us = e0.elapsed_time(e1) * 1e3 / ticks
     npix_tick = sum(m[0] * m[1] for m in mix)
-    bytes_tick = sum(m[0] * m[1] * (3 * m[3] + 24) for m in mix)
+    # per pixel: frame, expiring slot, slot write (b each); S and C read, one
+    # of them written (one new frame changes S or C, never both); image out
+    bytes_tick = sum(m[0] * m[1] * (3 * m[3] + 20) for m in mix)
 
     lat = []
     ev = torch.cuda.Event()

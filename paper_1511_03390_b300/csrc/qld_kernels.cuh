@@ -425,6 +425,13 @@ __device__ __forceinline__ void push_vector(const PushArgs& a, long long v) {
     const long long off = v * F::VB;
     const long long p0 = v * VP;
 
+    // Frame s moves S when s is odd and C when s is even (accumulate), so a
+    // push of one frame leaves one of the sums as it was: that one is not
+    // stored, and not read unless the image needs it. The same for every
+    // thread of a launch.
+    const bool chS = RESET || a.nf > 1 || (a.s_first & 1);
+    const bool chC = RESET || a.nf > 1 || !(a.s_first & 1);
+
     int32_t sacc[VP], cacc[VP];
     if (RESET) {
 #pragma unroll
@@ -432,8 +439,9 @@ __device__ __forceinline__ void push_vector(const PushArgs& a, long long v) {
     } else {
 #pragma unroll
         for (int q = 0; q < VP; q += 4) {
-            const int4 s4 = *reinterpret_cast<const int4*>(a.S + p0 + q);
-            const int4 c4 = *reinterpret_cast<const int4*>(a.C + p0 + q);
+            int4 s4 = make_int4(0, 0, 0, 0), c4 = make_int4(0, 0, 0, 0);
+            if (EPI || chS) s4 = *reinterpret_cast<const int4*>(a.S + p0 + q);
+            if (EPI || chC) c4 = *reinterpret_cast<const int4*>(a.C + p0 + q);
             sacc[q] = s4.x; sacc[q + 1] = s4.y; sacc[q + 2] = s4.z; sacc[q + 3] = s4.w;
             cacc[q] = c4.x; cacc[q + 1] = c4.y; cacc[q + 2] = c4.z; cacc[q + 3] = c4.w;
         }
@@ -477,8 +485,8 @@ __device__ __forceinline__ void push_vector(const PushArgs& a, long long v) {
 
 #pragma unroll
     for (int q = 0; q < VP; q += 4) {
-        *reinterpret_cast<int4*>(a.S + p0 + q) = make_int4(sacc[q], sacc[q + 1], sacc[q + 2], sacc[q + 3]);
-        *reinterpret_cast<int4*>(a.C + p0 + q) = make_int4(cacc[q], cacc[q + 1], cacc[q + 2], cacc[q + 3]);
+        if (chS) *reinterpret_cast<int4*>(a.S + p0 + q) = make_int4(sacc[q], sacc[q + 1], sacc[q + 2], sacc[q + 3]);
+        if (chC) *reinterpret_cast<int4*>(a.C + p0 + q) = make_int4(cacc[q], cacc[q + 1], cacc[q + 2], cacc[q + 3]);
     }
 
     if (EPI) {
@@ -509,8 +517,14 @@ __device__ __forceinline__ void push_vector(const PushArgs& a, long long v) {
     }
 }
 
+// uint16 pushes are held to 72 registers, seven 128-thread CTAs per SM, so a
+// 1024^2 frame (1024 CTAs) runs in one wave over 148 SMs; the other formats
+// keep the compiler's choice (0 = no minimum).
+template <typename T>
+constexpr int push_min_ctas() { return sizeof(T) == 2 ? 7 : 0; }
+
 template <typename T, bool RESET, bool EPI>
-__global__ void __launch_bounds__(128) push_vec_kernel(const PushArgs a) {
+__global__ void __launch_bounds__(128, push_min_ctas<T>()) push_vec_kernel(const PushArgs a) {
     const long long v = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (v < a.nvec) push_vector<T, RESET, EPI>(a, v);
 }
