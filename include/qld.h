@@ -301,7 +301,15 @@ long long qld_server_frames_pushed(qld_server* srv, int ticket);
 long long qld_server_mem_in_use(const qld_server* srv);
 int qld_server_sync(qld_server* srv);
 int qld_server_autotune(qld_server* srv, void* stream, float* best_us);
+/* The current launch shape; *ctas_per_sm = 0 means one CTA per tile of
+ * threads x vectors_per_thread vectors (a grid covering every admitted
+ * stream) instead of a persistent grid of SMs x ctas_per_sm CTAs. */
 int qld_server_shape(const qld_server* srv, int* threads, int* vectors_per_thread, int* ctas_per_sm);
+/* Number of candidate launch shapes, and a fixed choice of one (0 <= index <
+ * qld_server_num_shapes(), else QLD_E_INVAL) in place of the autotuner's:
+ * waits for the ticks in flight; the next tick runs with it. */
+int qld_server_num_shapes(void);
+int qld_server_set_shape(qld_server* srv, int index);
 
 /* ---- Learned short-window QLD: network kernels --------------------------
  *

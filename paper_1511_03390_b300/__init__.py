@@ -23,6 +23,7 @@ __all__ = [
     "qld_lockin_table", "qld_lockin_frames", "Server", "QLD_SERVER_MAX_STREAMS", "qld_server_create",
     "qld_server_destroy", "qld_server_request", "qld_server_state", "qld_server_close", "qld_server_submit",
     "qld_server_submit_many", "qld_server_tick_gated", "qld_server_last_gated_us",
+    "qld_server_num_shapes", "qld_server_set_shape",
     "qld_server_tick", "qld_server_image", "qld_server_iq", "qld_server_frames_pushed", "qld_server_mem_in_use",
     "qld_server_sync", "qld_server_autotune", "qld_server_shape", "nn", "LIB_PATH", "lib",
 ]
@@ -107,6 +108,8 @@ _SIGS = {
     "qld_server_tick": ([_p, _p], _i),
     "qld_server_tick_gated": ([_p, _p, _p, _i, _ll], _i),
     "qld_server_last_gated_us": ([_p, ctypes.POINTER(ctypes.c_float)], _i),
+    "qld_server_num_shapes": ([], _i),
+    "qld_server_set_shape": ([_p, _i], _i),
     "qld_server_image": ([_p, _i, ctypes.POINTER(_p), ctypes.POINTER(_p)], _i),
     "qld_server_iq": ([_p, _i, _p, _p], _i),
     "qld_server_frames_pushed": ([_p, _i], _ll),
@@ -505,6 +508,15 @@ def qld_server_autotune(srv, stream=None):
     if k < 0:
         raise QLDError(k, "qld_server_autotune")
     return k, us.value
+
+
+def qld_server_num_shapes():
+    return lib.qld_server_num_shapes()
+
+
+def qld_server_set_shape(srv, index):
+    """Fix the batched kernel's launch shape (an index as the autotuner returns)."""
+    return _check(lib.qld_server_set_shape(_sh(srv), index), "qld_server_set_shape")
 
 
 def qld_server_shape(srv):

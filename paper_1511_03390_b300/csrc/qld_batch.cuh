@@ -80,15 +80,23 @@ struct BatchShape {
     int threads, vpt, ctas_per_sm;
 };
 
+// ctas_per_sm = 0: one CTA per tile instead of a persistent grid (the grid
+// is the number of tiles to cover; CTAs past the tick's tile count return at
+// once), so the hardware overlaps consecutive tiles the way it overlaps the
+// CTAs of the single-stream push.
 constexpr BatchShape kBatchShapes[] = {{128, 1, 4}, {128, 2, 4}, {128, 4, 4}, {256, 1, 2}, {256, 2, 2}, {256, 1, 4},
-                                       {128, 1, 8}, {64, 2, 8},  {128, 2, 8}, {256, 2, 4}, {128, 4, 8}};
+                                       {128, 1, 8}, {64, 2, 8},  {128, 2, 8}, {256, 2, 4}, {128, 4, 8}, {128, 1, 0},
+                                       {256, 1, 0}, {128, 2, 0}};
 constexpr int kNumBatchShapes = (int)(sizeof(kBatchShapes) / sizeof(kBatchShapes[0]));
 
 inline long long batch_tile_vectors(const BatchShape& s) { return (long long)s.threads * s.vpt; }
 
-inline void launch_batch(const BatchShape& s, int num_sms, const BatchHeader* hdr, const BatchItem* items,
-                         const int* gate, cudaStream_t st) {
-    const unsigned grid = (unsigned)(num_sms * s.ctas_per_sm);
+// `tiles`: the tiles a one-CTA-per-tile grid covers (unused by persistent
+// shapes).
+inline void launch_batch(const BatchShape& s, int num_sms, long long tiles, const BatchHeader* hdr,
+                         const BatchItem* items, const int* gate, cudaStream_t st) {
+    const unsigned grid = s.ctas_per_sm > 0 ? (unsigned)(num_sms * s.ctas_per_sm)
+                                            : (unsigned)(tiles < 1 ? 1 : (tiles > 0x7FFFFFFF ? 0x7FFFFFFF : tiles));
     if (s.threads == 128 && s.vpt == 1) batch_push_kernel<128, 1><<<grid, 128, 0, st>>>(hdr, items, gate);
     else if (s.threads == 128 && s.vpt == 2) batch_push_kernel<128, 2><<<grid, 128, 0, st>>>(hdr, items, gate);
     else if (s.threads == 128 && s.vpt == 4) batch_push_kernel<128, 4><<<grid, 128, 0, st>>>(hdr, items, gate);

@@ -69,6 +69,7 @@ struct qld_server {
     bool used_valid[2];
     cudaGraphExec_t graph[2];
     bool graph_valid;
+    long long graph_tiles;           // tiles the graphs' grid covers (one-CTA-per-tile shapes)
     cudaStream_t cap;
     int shape;
     int flip;
@@ -171,8 +172,28 @@ int build_items(qld_server* s, qldk::BatchItem* items, qldk::BatchHeader* hdr, s
     return n;
 }
 
+// Tiles of one push of every admitted stream with the current shape: the
+// most a tick can launch.
+long long admitted_tiles(const qld_server* s) {
+    const long long tv = qldk::batch_tile_vectors(qldk::kBatchShapes[s->shape]);
+    long long tiles = 0;
+    for (const SrvStream& t : s->streams)
+        if (t.state == 0 && t.ctx) tiles += (t.ctx->frame_bytes / qldk::batch_vec_bytes(t.ctx->pixfmt) + tv - 1) / tv;
+    return tiles;
+}
+
+// One-CTA-per-tile graphs are rebuilt when a tick has more tiles than their
+// grid covers (streams admitted since they were captured).
+void check_graph_grid(qld_server* s, long long tick_tiles) {
+    if (qldk::kBatchShapes[s->shape].ctas_per_sm == 0 && s->graph_valid && tick_tiles > s->graph_tiles) {
+        wait_ticks(s);
+        s->graph_valid = false;
+    }
+}
+
 int ensure_graphs(qld_server* s) {
     if (s->graph_valid) return QLD_OK;
+    s->graph_tiles = admitted_tiles(s);
     for (int b = 0; b < 2; ++b) {
         if (s->graph[b]) {
             cudaGraphExecDestroy(s->graph[b]);
@@ -181,7 +202,8 @@ int ensure_graphs(qld_server* s) {
         cudaGraph_t g = nullptr;
         if (cudaStreamBeginCapture(s->cap, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return QLD_E_CUDA;
         cudaMemcpyAsync(s->hdr_dev, s->hdr_host[b], desc_bytes(s->max_streams), cudaMemcpyHostToDevice, s->cap);
-        qldk::launch_batch(qldk::kBatchShapes[s->shape], s->num_sms, s->hdr_dev, s->items_dev, s->gate_dev, s->cap);
+        qldk::launch_batch(qldk::kBatchShapes[s->shape], s->num_sms, s->graph_tiles, s->hdr_dev, s->items_dev,
+                           s->gate_dev, s->cap);
         if (cudaStreamEndCapture(s->cap, &g) != cudaSuccess || !g) {
             cudaGetLastError();
             return QLD_E_CUDA;
@@ -225,6 +247,7 @@ qld_server* qld_server_create(long long hbm_budget_bytes, int max_streams) {
     s->used_valid[0] = s->used_valid[1] = false;
     s->graph[0] = s->graph[1] = nullptr;
     s->graph_valid = false;
+    s->graph_tiles = 0;
     s->cap = nullptr;
     s->shape = 0;
     s->flip = 0;
@@ -352,6 +375,7 @@ int qld_server_tick(qld_server* s, void* stream) {
     std::vector<int> which;
     const int n = build_items(s, s->items_host[b], s->hdr_host[b], &which);
     if (n == 0) return 0;
+    check_graph_grid(s, s->hdr_host[b]->ntiles);
     int rc = ensure_graphs(s);
     if (rc != QLD_OK) return set_err(rc);
     if (cudaGraphLaunch(s->graph[b], st) != cudaSuccess || cudaEventRecord(s->used[b], st) != cudaSuccess)
@@ -380,6 +404,7 @@ int qld_server_tick_gated(qld_server* s, void* stream, const int* doorbell, int 
     const int n = build_items(s, s->items_host[b], s->hdr_host[b], &which);
     if (n == 0) return 0;
     s->hdr_host[b]->gated = 1;
+    check_graph_grid(s, s->hdr_host[b]->ntiles);
     int rc = ensure_graphs(s);
     if (rc != QLD_OK) return set_err(rc);
     qldk::doorbell_gate_kernel<<<1, 32, 0, st>>>(doorbell, target, timeout_ns, s->gate_dev);
@@ -443,6 +468,18 @@ int qld_server_sync(qld_server* s) {
     for (int b = 0; b < 2; ++b)
         if (s->used_valid[b] && cudaEventSynchronize(s->used[b]) != cudaSuccess) return set_err(QLD_E_CUDA);
     return cudaGetLastError() == cudaSuccess ? QLD_OK : set_err(QLD_E_CUDA);
+}
+
+int qld_server_num_shapes(void) { return qldk::kNumBatchShapes; }
+
+int qld_server_set_shape(qld_server* s, int index) {
+    if (!s || index < 0 || index >= qldk::kNumBatchShapes) return set_err(QLD_E_INVAL);
+    if (index != s->shape) {
+        wait_ticks(s);  // the graphs are rebuilt at the next tick
+        s->shape = index;
+        s->graph_valid = false;
+    }
+    return QLD_OK;
 }
 
 int qld_server_shape(const qld_server* s, int* threads, int* vectors_per_thread, int* ctas_per_sm) {
@@ -524,7 +561,7 @@ int qld_server_autotune(qld_server* s, void* stream, float* best_us) {
                 break;
             }
             cudaEventRecord(e0, st);
-            qldk::launch_batch(qldk::kBatchShapes[k], s->num_sms, hdr, items, s->gate_dev, st);
+            qldk::launch_batch(qldk::kBatchShapes[k], s->num_sms, hh->ntiles, hdr, items, s->gate_dev, st);
             cudaEventRecord(e1, st);
             if (cudaEventSynchronize(e1) != cudaSuccess) {
                 rc = QLD_E_CUDA;

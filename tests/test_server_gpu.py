@@ -65,21 +65,34 @@ def ctx_state(ctx):
     return S.cpu().numpy(), C.cpu().numpy(), amp.cpu().numpy(), ph.cpu().numpy()
 
 
-def run_mix(autotune=False, ticks=10, seed=0, batched=False):
+def run_mix(autotune=False, ticks=10, seed=0, batched=False, shape=None, late=0):
+    """`shape`: a fixed launch shape; `late`: the last `late` streams of the
+    mix are requested only at tick 3, after the tick graphs were built."""
     rng = np.random.default_rng(seed)
     srv = q.qld_server_create(1 << 36)
-    tickets = [q.qld_server_request(srv, *m) for m in MIX]
-    assert all(q.qld_server_state(srv, t) == 0 for t in tickets)
+    if shape is not None:
+        q.qld_server_set_shape(srv, shape)
+    early = len(MIX) - late
+    tickets = [q.qld_server_request(srv, *m) for m in MIX[:early]] + [None] * late
+    assert all(q.qld_server_state(srv, t) == 0 for t in tickets[:early])
     alone = [q.qld_create(*m) for m in MIX]
     history = [np.zeros((0, m[0] * m[1]), np.uint8 if m[3] == q.QLD_U8 else np.uint16) for m in MIX]
     keep = []
     batch = q.SubmitBatch(len(MIX))
     for tick in range(ticks):
+        if late and tick == 3:
+            for i in range(early, len(MIX)):
+                tickets[i] = q.qld_server_request(srv, *MIX[i])
+                assert q.qld_server_state(srv, tickets[i]) == 0
         nb = 0
         for i, (t, m) in enumerate(zip(tickets, MIX)):
+            if t is None:
+                continue
             H, W, N, fmt = m
             pattern = [1, 2, 0, 3, 1, N + 1, 1, 4, 0, 2]
             count = pattern[(tick + i) % len(pattern)] if tick < ticks - 1 else 1
+            if late and tick == 3 and i >= early:
+                count = N  # a late stream fills its window on the tick it joins
             if count == 0:
                 continue
             x, dev = frames_for(rng, H, W, fmt, count)
@@ -120,6 +133,27 @@ def test_each_stream_in_the_mix_equals_it_alone():
 
 def test_autotuned_shape_gives_the_same_results():
     run_mix(autotune=True, seed=1)
+
+
+@pytest.mark.parametrize("shape", range(16))
+def test_every_launch_shape_gives_the_same_results(shape):
+    """Each candidate shape, persistent or one CTA per tile, with two streams
+    admitted after the tick graphs were built (a one-CTA-per-tile grid must
+    grow to cover them)."""
+    if shape >= q.qld_server_num_shapes():
+        pytest.skip("%d launch shapes" % q.qld_server_num_shapes())
+    run_mix(seed=20 + shape, shape=shape, late=2)
+
+
+def test_set_shape_rejects_bad_indices():
+    srv = q.qld_server_create(1 << 30)
+    try:
+        for bad in (-1, q.qld_server_num_shapes()):
+            assert q.lib.qld_server_set_shape(srv.handle, bad) == q.QLD_E_INVAL
+        q.qld_server_set_shape(srv, q.qld_server_num_shapes() - 1)
+        assert q.qld_server_shape(srv)[2] == 0  # the last shapes are one CTA per tile
+    finally:
+        srv.destroy()
 
 
 def test_submit_many_equals_single_submits():
