@@ -657,7 +657,7 @@ def run_serving(q, torch, dev, st, peak, ticks=300, paced_ticks=300, fps=200.0, 
     """Eight camera streams of uneven size (2 x 640x480 uint8 N=256, 4 x
     1280x1024 uint16 N=1024, 2 x 2048x2048 uint16 N=2048) served by one
     qld_server: admission by HBM footprint, autotuned launch shape, one
-    graph-replayed persistent launch per tick carrying one new frame per
+    graph-replayed launch per tick carrying one new frame per
     stream. Throughput from back-to-back ticks; frame-to-image latency with
     ticks paced at `fps` (frames already in HBM when the tick's clock starts)."""
     from qldscene import DeviceScene, scene_fog, scene_plain
@@ -787,7 +787,7 @@ def run_serving(q, torch, dev, st, peak, ticks=300, paced_ticks=300, fps=200.0, 
     return {"workload": "8 streams: " + ", ".join("%dx%dx%d %s N=%d" % (c, m[1], m[0], "uint8" if m[3] == 1 else "uint16",
                                                                      m[2])
                                                   for m, c in _runs(mix)) +
-                        "; one new frame per stream per tick, one graph-replayed persistent launch per tick",
+                        "; one new frame per stream per tick, one graph-replayed launch per tick",
             "admitted": admitted, "server_mem_gb": mem / 1e9, "budget_gb": budget / 1e9,
             "autotuned_shape": {"index": shape_idx, "threads": shape[0], "vectors_per_thread": shape[1],
                                 "ctas_per_sm": shape[2], "tuning_us_per_tick": tuned_us},

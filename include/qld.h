@@ -251,7 +251,7 @@ int qld_fft_bin_frames_noalloc(const void* frames, int H, int W, int N, int pixf
  *    per stream per tick; QLD_E_NOT_READY while the request waits). The frames
  *    must stay valid until the tick that consumes them has completed.
  *  - qld_server_tick runs every submitted push, with its amplitude/phase image
- *    once the stream's window is full, in ONE persistent kernel launch replayed
+ *    once the stream's window is full, in ONE kernel launch replayed
  *    from a CUDA graph, on `stream`; it returns the number of streams served.
  *    Streams admitted while earlier ticks are still running join the next tick.
  *  - qld_server_image gives the device pointers of a stream's latest images
@@ -283,7 +283,7 @@ int qld_server_tick(qld_server* srv, void* stream);
  * host -- never by a kernel that could be queued behind this tick, and not
  * through a stream that synchronises with `stream`) until it is >= target,
  * then the tick's
- * persistent kernel, which starts the moment the doorbell rings with no
+ * kernel, which starts the moment the doorbell rings with no
  * host round trip. The wait gives up after timeout_ns (0 < timeout_ns <=
  * 10 s) of GPU time; the tick then does no work, the submissions stay
  * pending for a later tick, and the call returns QLD_E_TIMEOUT. Otherwise

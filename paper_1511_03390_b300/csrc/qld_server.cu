@@ -10,7 +10,7 @@
 //     footprint fits the server's HBM budget and a slot is free, and a
 //     request that does not fit waits until closes free enough memory;
 //   * a tick takes the frames submitted since the previous tick and runs all
-//     of their pushes and images in ONE persistent launch (batch_push_kernel)
+//     of their pushes and images in ONE launch (batch_push_kernel)
 //     replayed from a CUDA graph; streams admitted while earlier ticks are
 //     still on the GPU simply join the next tick's batch;
 //   * the launch shape is chosen by timing the candidate shapes on small
