@@ -58,6 +58,8 @@ def parse_args():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-large", action="store_true", help="skip the 4096x4096 N=2048 (68.7 GB ring) stream")
     ap.add_argument("--no-serving", action="store_true", help="skip the 8-stream serving mix (45 GB of rings)")
+    ap.add_argument("--serving-shape", type=int, default=None,
+                    help="fixed launch shape index for the serving mix instead of the autotuner's choice")
     ap.add_argument("--no-learned", action="store_true", help="skip the learned short-window path")
     ap.add_argument("--no-packed", action="store_true", help="skip the packed 12-bit step")
     ap.add_argument("--case", choices=["full", "small"], default="full",
@@ -475,7 +477,7 @@ def run_cuda(args, world, rank, local):
         # the small case keeps the mix's frame sizes (same bytes per tick) with
         # N = 8 windows, so its rings take well under 1 GB
         mix = SERVING_MIX if args.case == "full" else [(h, w, 8, f) for (h, w, n, f) in SERVING_MIX]
-        serving = run_serving(q, torch, dev, st, peak, mix=mix)
+        serving = run_serving(q, torch, dev, st, peak, mix=mix, shape_idx=args.serving_shape)
     learned_res = None
     if not args.no_learned and args.case == "full":
         learned_res = run_learned(q, torch, dev, st)
@@ -653,7 +655,7 @@ def _runs(mix):
     return [(m, c) for m, c in out]
 
 
-def run_serving(q, torch, dev, st, peak, ticks=300, paced_ticks=300, fps=200.0, mix=None):
+def run_serving(q, torch, dev, st, peak, ticks=300, paced_ticks=300, fps=200.0, mix=None, shape_idx=None):
     """Eight camera streams of uneven size (2 x 640x480 uint8 N=256, 4 x
     1280x1024 uint16 N=1024, 2 x 2048x2048 uint16 N=2048) served by one
     qld_server: admission by HBM footprint, autotuned launch shape, one
@@ -686,7 +688,11 @@ def run_serving(q, torch, dev, st, peak, ticks=300, paced_ticks=300, fps=200.0, 
                 pushed[i] += n
         q.qld_server_tick(srv, st)
     q.qld_server_sync(srv)
-    shape_idx, tuned_us = q.qld_server_autotune(srv, st)
+    if shape_idx is None:
+        shape_idx, tuned_us = q.qld_server_autotune(srv, st)
+    else:  # a fixed shape (reproducible profiles: the autotuner's timings change under a profiler)
+        q.qld_server_set_shape(srv, shape_idx)
+        tuned_us = None
     shape = q.qld_server_shape(srv)
 
     # per tick: one frame per stream handed over in one qld_server_submit_many
