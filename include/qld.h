@@ -253,7 +253,9 @@ int qld_fft_bin_frames_noalloc(const void* frames, int H, int W, int N, int pixf
  *  - qld_server_tick runs every submitted push, with its amplitude/phase image
  *    once the stream's window is full, in ONE kernel launch replayed
  *    from a CUDA graph, on `stream`; it returns the number of streams served.
- *    Streams admitted while earlier ticks are still running join the next tick.
+ *    Streams admitted while earlier ticks are still running join the next tick
+ *    (with a one-CTA-per-tile shape, the first tick whose tiles exceed the
+ *    graphs' grid waits for the ticks in flight and rebuilds the graphs).
  *  - qld_server_image gives the device pointers of a stream's latest images
  *    (owned by the server; read them after the tick, in stream order).
  *  - qld_server_autotune times the batched kernel's candidate launch shapes
