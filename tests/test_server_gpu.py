@@ -250,9 +250,11 @@ def test_server_rejects_unbatchable_or_bad_requests():
 
 # ---- gated ticks: a bounded device wait on a doorbell before the tick ----
 
-def _gated_setup(seed):
+def _gated_setup(seed, shape=None):
     rng = np.random.default_rng(seed)
     srv = q.qld_server_create(1 << 34)
+    if shape is not None:
+        q.qld_server_set_shape(srv, shape)
     mix = MIX[:3]
     tickets = [q.qld_server_request(srv, *m) for m in mix]
     alone = [q.qld_create(*m) for m in mix]
@@ -275,8 +277,21 @@ def _check_against_alone(srv, mix, tickets, alone):
         assert np.array_equal(amp, amp2) and np.array_equal(ph, ph2)
 
 
-def test_gated_tick_times_out_on_a_doorbell_nothing_rings():
-    srv, mix, tickets, alone, _ = _gated_setup(41)
+def _per_tile_shape():
+    for k in range(q.qld_server_num_shapes()):
+        srv = q.qld_server_create(1 << 20)
+        try:
+            q.qld_server_set_shape(srv, k)
+            if q.qld_server_shape(srv)[2] == 0:
+                return k
+        finally:
+            srv.destroy()
+    return None
+
+
+@pytest.mark.parametrize("per_tile", [False, True])
+def test_gated_tick_times_out_on_a_doorbell_nothing_rings(per_tile):
+    srv, mix, tickets, alone, _ = _gated_setup(41, _per_tile_shape() if per_tile else None)
     try:
         bell = torch.zeros(4, dtype=torch.int32, device="cuda")
         with pytest.raises(q.QLDError) as e:
