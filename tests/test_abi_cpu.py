@@ -89,3 +89,19 @@ def test_null_context_and_strings():
     assert q.qld_strerror(q.QLD_E_NOT_READY).startswith("window not full")
     assert q.qld_strerror(12345) == "unknown status"
     assert "sm_103a" in q.qld_version()
+
+
+def test_c_program_builds_links_and_runs():
+    """tests/abi_check.c: the header compiles as pedantic C99 and a C program
+    links to libqld.so and gets the right answers from it, no Python or torch
+    involved."""
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    build = os.path.join(root, "_build")
+    os.makedirs(build, exist_ok=True)
+    exe = os.path.join(build, "abi_check")
+    libdir = os.path.dirname(q.LIB_PATH)
+    subprocess.run(["gcc", "-std=c99", "-Wall", "-Wextra", "-pedantic", "-Werror", "-I", os.path.dirname(HEADER),
+                    os.path.join(root, "tests", "abi_check.c"), "-o", exe, "-L", libdir, "-lqld",
+                    "-Wl,-rpath," + libdir], check=True)
+    out = subprocess.run([exe], capture_output=True, text=True, timeout=60)
+    assert out.returncode == 0 and out.stdout.strip() == "ok", out.stdout
