@@ -85,6 +85,26 @@ enum qld_status {
  * (qld_last_error() gives QLD_E_INVAL or QLD_E_NOMEM). Synchronous. */
 qld_ctx* qld_create(int H, int W, int N, int pixfmt);
 
+/* A context for the row band row0 .. row0 + rows - 1 of a stream of
+ * H_total x W frames. Pixels are independent (Methods, "Numerical
+ * simulations": every pixel's time series gives its own R(j,k)), so a frame
+ * split into row bands, each with its own ring and sums (on its own GPU, or
+ * several on one), gives exactly the whole frame's sums, images and DFT bins
+ * row for row, with no exchange between bands.
+ *
+ * The context behaves as qld_create(rows, W, N, pixfmt) -- its images, sums
+ * and bins are rows x W and its footprint is qld_footprint_bytes(rows, W, N,
+ * pixfmt) -- except that pushes take WHOLE frames ([count][H_total][W]; the
+ * host variants too) and read only the band: frame f's band starts
+ * row0 * W * b + f * H_total * W * b bytes into the buffer (b = bytes per
+ * pixel; 3/2 for QLD_P12). A host push copies only the band's rows. The
+ * single-kernel qld_step needs the band's start 16-byte aligned and the
+ * frame pitch a multiple of 16 bytes, as for whole frames. Returns NULL with
+ * QLD_E_INVAL unless 0 <= row0, rows >= 1, row0 + rows <= H_total, both the
+ * band and the whole frame are valid for qld_create, and (QLD_P12) the band
+ * starts on a whole pixel pair; QLD_E_NOMEM as qld_create. */
+qld_ctx* qld_create_band(int H_total, int W, int N, int pixfmt, int row0, int rows);
+
 /* Device bytes qld_create(H, W, N, pixfmt) would allocate, or a negative
  * status for invalid arguments. */
 long long qld_footprint_bytes(int H, int W, int N, int pixfmt);
@@ -226,9 +246,19 @@ int qld_lockin_frames(const void* frames, int H, int W, int N, int pixfmt, const
  * process exits. Each call rewrites the part it uses before reading it, so
  * nothing needs clearing, but all calls share that array: calls that may
  * overlap on the GPU (different streams, no ordering between them) race and
- * can return wrong values. The first call on a device looks up the array's
- * device address (cudaGetSymbolAddress) and caches it; make that first call
- * before any stream capture. */
+ * can return wrong values.
+ *
+ * Set-up: the first call on a device looks up the array's device address
+ * (cudaGetSymbolAddress) and caches it for the life of the process, so a
+ * device reset (cudaDeviceReset) after that first call is not supported.
+ * With lazy module loading (the CUDA default) that first call, and the first
+ * call with each pixel format, may also load the library's code onto the
+ * device, which can allocate device memory and synchronise. Make one call per
+ * device and pixel format as a warm-up before the allocation-free region and
+ * before any stream capture (or set CUDA_MODULE_LOADING=EAGER, which loads
+ * everything when the context is created). Later calls allocate nothing.
+ * An error left by earlier asynchronous work is returned (QLD_E_CUDA) before
+ * anything is queued. */
 int qld_fft_bin_frames_noalloc(const void* frames, int H, int W, int N, int pixfmt, int k, float* out,
                                void* stream);
 

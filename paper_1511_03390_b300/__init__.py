@@ -15,7 +15,8 @@ from . import build as _build
 
 __all__ = [
     "QLD_U8", "QLD_U16", "QLD_P12", "QLD_OK", "QLD_E_INVAL", "QLD_E_NOMEM", "QLD_E_NOT_READY", "QLD_E_CUDA",
-    "QLD_E_TIMEOUT", "QLD_MAX_N", "QLDError", "Context", "qld_create", "qld_destroy", "qld_push_frames",
+    "QLD_E_TIMEOUT", "QLD_MAX_N", "QLDError", "Context", "qld_create", "qld_create_band", "qld_destroy",
+    "qld_push_frames",
     "qld_push_image", "qld_image", "qld_fft_bin", "qld_step", "qld_step_host", "qld_push_frames_host", "qld_image_host",
     "qld_fft_bin_host", "qld_get_iq", "qld_reset", "qld_frames_pushed", "qld_sync", "qld_stream",
     "qld_strerror", "qld_last_error", "qld_version", "qld_footprint_bytes", "qld_set_mem_budget",
@@ -50,6 +51,7 @@ _ll = ctypes.c_longlong
 lib = ctypes.CDLL(LIB_PATH)
 _SIGS = {
     "qld_create": ([_i, _i, _i, _i], _p),
+    "qld_create_band": ([_i, _i, _i, _i, _i, _i], _p),
     "qld_footprint_bytes": ([_i, _i, _i, _i], _ll),
     "qld_set_mem_budget": ([_ll], None),
     "qld_mem_in_use": ([], _ll),
@@ -177,14 +179,22 @@ def _stream(stream):
     return stream.cuda_stream
 
 
+def _frame_bytes(npix, pixfmt):
+    return npix // 2 * 3 if pixfmt == QLD_P12 else npix * pixfmt
+
+
 class Context:
     """A qld_ctx handle with its geometry."""
 
-    def __init__(self, handle, H, W, N, pixfmt):
+    def __init__(self, handle, H, W, N, pixfmt, H_total=None, row0=0):
         self.handle = handle
         self.H, self.W, self.N, self.pixfmt = H, W, N, pixfmt
         self.npix = H * W
-        self.frame_bytes = self.npix // 2 * 3 if pixfmt == QLD_P12 else self.npix * pixfmt
+        self.frame_bytes = _frame_bytes(self.npix, pixfmt)
+        # a row band reads rows row0 .. row0 + H - 1 of H_total x W frames
+        self.H_total = H if H_total is None else H_total
+        self.row0 = row0
+        self.frame_pitch = _frame_bytes(self.H_total * W, pixfmt)
 
     def __del__(self):
         if getattr(self, "handle", None):
@@ -219,6 +229,15 @@ def qld_create(H, W, N, pixfmt):
     return Context(h, int(H), int(W), int(N), int(pixfmt))
 
 
+def qld_create_band(H_total, W, N, pixfmt, row0, rows):
+    """A context for rows row0 .. row0 + rows - 1 of H_total x W frames; its
+    pushes take whole frames and its images, sums and bins are rows x W."""
+    h = lib.qld_create_band(int(H_total), int(W), int(N), int(pixfmt), int(row0), int(rows))
+    if not h:
+        raise QLDError(lib.qld_last_error(), "qld_create_band")
+    return Context(h, int(rows), int(W), int(N), int(pixfmt), H_total=int(H_total), row0=int(row0))
+
+
 def qld_destroy(ctx):
     ctx.destroy()
 
@@ -249,14 +268,14 @@ def _count_of(frames, count, frame_bytes):
 
 
 def qld_push_frames(ctx, frames, count=None, stream=None):
-    n = _count_of(frames, count, ctx.frame_bytes)
-    a = _addr(frames, n * ctx.frame_bytes, "frames")
+    n = _count_of(frames, count, ctx.frame_pitch)
+    a = _addr(frames, n * ctx.frame_pitch, "frames")
     return _check(lib.qld_push_frames(_h(ctx), a, n, _stream(stream)), "qld_push_frames")
 
 
 def qld_push_image(ctx, frames, count=None, stream=None, amp=None, phase=None):
-    n = _count_of(frames, count, ctx.frame_bytes)
-    a = _addr(frames, n * ctx.frame_bytes, "frames")
+    n = _count_of(frames, count, ctx.frame_pitch)
+    a = _addr(frames, n * ctx.frame_pitch, "frames")
     return _check(lib.qld_push_image(_h(ctx), a, n, _stream(stream), _addr(amp, 4 * ctx.npix, "amp"),
                                      _addr(phase, 4 * ctx.npix, "phase")), "qld_push_image")
 
@@ -272,8 +291,8 @@ def qld_fft_bin(ctx, k, out):
 
 def qld_step(ctx, frames, count, k, power, stream=None, amp=None, phase=None):
     """qld_push_image then qld_fft_bin (bin k into `power`) as one kernel."""
-    n = _count_of(frames, count, ctx.frame_bytes)
-    a = _addr(frames, n * ctx.frame_bytes, "frames")
+    n = _count_of(frames, count, ctx.frame_pitch)
+    a = _addr(frames, n * ctx.frame_pitch, "frames")
     return _check(lib.qld_step(_h(ctx), a, n, _stream(stream), _addr(amp, 4 * ctx.npix, "amp"),
                                _addr(phase, 4 * ctx.npix, "phase"), int(k), _addr(power, 4 * ctx.npix, "power")),
                   "qld_step")
@@ -281,16 +300,16 @@ def qld_step(ctx, frames, count, k, power, stream=None, amp=None, phase=None):
 
 def qld_step_host(ctx, frames, count, k, power, stream=None, amp=None, phase=None):
     """qld_step with host frames and host output images (valid after qld_sync)."""
-    n = _count_of(frames, count, ctx.frame_bytes)
-    a = _addr(frames, n * ctx.frame_bytes, "frames")
+    n = _count_of(frames, count, ctx.frame_pitch)
+    a = _addr(frames, n * ctx.frame_pitch, "frames")
     return _check(lib.qld_step_host(_h(ctx), a, n, _stream(stream), _addr(amp, 4 * ctx.npix, "amp"),
                                     _addr(phase, 4 * ctx.npix, "phase"), int(k), _addr(power, 4 * ctx.npix, "power")),
                   "qld_step_host")
 
 
 def qld_push_frames_host(ctx, frames, count=None, stream=None):
-    n = _count_of(frames, count, ctx.frame_bytes)
-    a = _addr(frames, n * ctx.frame_bytes, "host frames")
+    n = _count_of(frames, count, ctx.frame_pitch)
+    a = _addr(frames, n * ctx.frame_pitch, "host frames")
     return _check(lib.qld_push_frames_host(_h(ctx), a, n, _stream(stream)), "qld_push_frames_host")
 
 

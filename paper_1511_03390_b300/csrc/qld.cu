@@ -134,15 +134,17 @@ void launch_push_t(const qld_ctx* c, const qldk::PushArgs& a, bool vec) {
 }
 
 // Enqueues the push of `count` device frames (and, if epi, the image) on
-// c->stream. Arguments are already validated.
-int enqueue_push(qld_ctx* c, const uint8_t* frames, int count, bool epi, float* amp, float* phase) {
+// c->stream. The band of frame f starts at frames + f * pitch (the caller's
+// buffer with the band offset applied, or a contiguous stage). Arguments are
+// already validated.
+int enqueue_push(qld_ctx* c, const uint8_t* frames, long long pitch, int count, bool epi, float* amp, float* phase) {
     if (count == 0) return QLD_OK;
     const long long frame_bytes = c->frame_bytes;
     const bool reset = count >= c->N;
     const int first = reset ? count - c->N : 0;
     qldk::PushArgs a;
-    a.frames = frames + (long long)first * frame_bytes;
-    a.frame_stride = frame_bytes;
+    a.frames = frames + (long long)first * pitch;
+    a.frame_stride = pitch;
     a.nf = reset ? c->N : count;
     a.s_first = c->pushed + first + 1;
     a.ring = c->ring;
@@ -155,7 +157,8 @@ int enqueue_push(qld_ctx* c, const uint8_t* frames, int count, bool epi, float* 
     a.phase = phase;
     a.out_aligned = (aligned(amp, 16) && aligned(phase, 16)) ? 1 : 0;
     const int vb = vec_bytes_of(c->pixfmt);
-    const bool vec = aligned(a.frames, vec_align_of(c->pixfmt)) && (frame_bytes % vb) == 0;
+    const bool vec = aligned(a.frames, vec_align_of(c->pixfmt)) && (frame_bytes % vb) == 0 &&
+                     (pitch % vec_align_of(c->pixfmt)) == 0;
     a.nvec = vec ? frame_bytes / vb : c->npix;
     g_launches.fetch_add(1);
     if (reset) {
@@ -230,21 +233,22 @@ void launch_step_t(const qld_ctx* c, const qldk::PushArgs& a, float* out) {
 // full afterwards): one bin_kernel with the push folded in (PUSH) for uint16
 // frames with 1 <= count <= N in whole 16-byte vectors, else the push kernel
 // and the bin kernel.
-int enqueue_step(qld_ctx* c, const uint8_t* frames, int count, float* amp, float* phase, int k, float* out) {
+int enqueue_step(qld_ctx* c, const uint8_t* frames, long long pitch, int count, float* amp, float* phase, int k,
+                 float* out) {
     const long long frame_bytes = c->frame_bytes;
     // uint16 only: the uint8 and packed 12-bit DFT bins are bound by their
     // instruction issue, and the push riding in the same kernel made them
     // about 5 % slower than the two launches (1024^2, N = 1024, 4 frames).
     const bool one = c->pixfmt == QLD_U16 && count >= 1 && count <= c->N && aligned(frames, 16) &&
-                     (frame_bytes % 16) == 0 && aligned(amp, 4) && aligned(phase, 4);
+                     (frame_bytes % 16) == 0 && (pitch % 16) == 0 && aligned(amp, 4) && aligned(phase, 4);
     if (!one) {
-        const int rc = enqueue_push(c, frames, count, amp || phase, amp, phase);
+        const int rc = enqueue_push(c, frames, pitch, count, amp || phase, amp, phase);
         return rc != QLD_OK ? rc : enqueue_fft_bin(c, k, out);
     }
     if (ensure_twiddles(c, k) != QLD_OK) return QLD_E_CUDA;
     qldk::PushArgs a;
     a.frames = frames;
-    a.frame_stride = frame_bytes;
+    a.frame_stride = pitch;
     a.nf = count;
     a.s_first = c->pushed + 1;
     a.ring = c->ring;
@@ -351,6 +355,73 @@ int release_out(qld_ctx* c, int slot, const float* d0, float* h0, const float* d
     return cudaEventRecord(hp->out_free[slot], hp->cout) == cudaSuccess ? QLD_OK : QLD_E_CUDA;
 }
 
+// Copies the band of host frames first .. first + n - 1 into a contiguous
+// device stage on `st`: one copy for a whole-frame context, a strided copy of
+// the band's rows for a row band (only the band's bytes cross the bus).
+cudaError_t copy_frames_in(const qld_ctx* c, uint8_t* dst, const uint8_t* src, long long first, long long n,
+                           cudaStream_t st) {
+    if (c->band_offset == 0 && c->frame_pitch == c->frame_bytes)
+        return cudaMemcpyAsync(dst, src + first * c->frame_bytes, (size_t)(n * c->frame_bytes), cudaMemcpyHostToDevice,
+                               st);
+    return cudaMemcpy2DAsync(dst, (size_t)c->frame_bytes, src + c->band_offset + first * c->frame_pitch,
+                             (size_t)c->frame_pitch, (size_t)c->frame_bytes, (size_t)n, cudaMemcpyHostToDevice, st);
+}
+
+// Creates a context for rows row0 .. row0 + rows - 1 of H_total x W frames
+// (validated by the caller).
+qld_ctx* create_ctx(int H_total, int W, int N, int pixfmt, int row0, int rows) {
+    const int H = rows;
+    const Layout L = layout_of(H, W, N, pixfmt);
+    // Reserve against the budget before touching the device.
+    const long long budget = g_budget.load();
+    long long prev = g_in_use.fetch_add(L.total);
+    if (budget > 0 && prev + L.total > budget) {
+        g_in_use.fetch_sub(L.total);
+        set_err(QLD_E_NOMEM);
+        return nullptr;
+    }
+    qld_ctx* c = new qld_ctx();
+    std::memset(c, 0, sizeof(*c));
+    c->H = H;
+    c->W = W;
+    c->N = N;
+    c->pixfmt = pixfmt;
+    c->frame_bytes = frame_bytes_of(L.npix, pixfmt);
+    c->H_total = H_total;
+    c->row0 = row0;
+    c->band_offset = frame_bytes_of((long long)row0 * W, pixfmt);
+    c->frame_pitch = frame_bytes_of((long long)H_total * W, pixfmt);
+    c->npix = L.npix;
+    c->npad = L.npad;
+    c->slot_stride = L.slot_stride;
+    c->tw_k = -1;
+    c->footprint = L.total;
+    c->stream = nullptr;
+    int st = QLD_OK;
+    if (cudaGetDevice(&c->device) != cudaSuccess) st = QLD_E_CUDA;
+    if (st == QLD_OK && (cudaMalloc(&c->ring, (size_t)L.ring_bytes) != cudaSuccess ||
+                         cudaMalloc(&c->S, (size_t)L.sums_bytes) != cudaSuccess ||
+                         cudaMalloc(&c->C, (size_t)L.sums_bytes) != cudaSuccess ||
+                         cudaMalloc(&c->tw, (size_t)L.tw_bytes) != cudaSuccess)) {
+        st = QLD_E_NOMEM;
+    }
+    if (st == QLD_OK && (cudaMemset(c->ring, 0, (size_t)L.ring_bytes) != cudaSuccess ||
+                         cudaMemset(c->S, 0, (size_t)L.sums_bytes) != cudaSuccess ||
+                         cudaMemset(c->C, 0, (size_t)L.sums_bytes) != cudaSuccess ||
+                         cudaDeviceSynchronize() != cudaSuccess)) {
+        st = QLD_E_CUDA;
+    }
+    if (st != QLD_OK) {
+        cudaGetLastError();
+        free_ctx_memory(c);
+        delete c;
+        g_in_use.fetch_sub(L.total);
+        set_err(st);
+        return nullptr;
+    }
+    return c;
+}
+
 }  // namespace
 
 extern "C" {
@@ -387,51 +458,18 @@ qld_ctx* qld_create(int H, int W, int N, int pixfmt) {
         set_err(QLD_E_INVAL);
         return nullptr;
     }
-    const Layout L = layout_of(H, W, N, pixfmt);
-    // Reserve against the budget before touching the device.
-    const long long budget = g_budget.load();
-    long long prev = g_in_use.fetch_add(L.total);
-    if (budget > 0 && prev + L.total > budget) {
-        g_in_use.fetch_sub(L.total);
-        set_err(QLD_E_NOMEM);
+    return create_ctx(H, W, N, pixfmt, 0, H);
+}
+
+qld_ctx* qld_create_band(int H_total, int W, int N, int pixfmt, int row0, int rows) {
+    // the band is a valid frame of its own, lies inside the full frame, and
+    // (packed 12-bit) starts on a whole pixel pair
+    if (row0 < 0 || rows < 1 || H_total < 1 || (long long)row0 + rows > H_total || !valid_dims(rows, W, N, pixfmt) ||
+        !valid_dims(H_total, W, N, pixfmt) || (pixfmt == QLD_P12 && ((long long)row0 * W) % 2 != 0)) {
+        set_err(QLD_E_INVAL);
         return nullptr;
     }
-    qld_ctx* c = new qld_ctx();
-    std::memset(c, 0, sizeof(*c));
-    c->H = H;
-    c->W = W;
-    c->N = N;
-    c->pixfmt = pixfmt;
-    c->frame_bytes = frame_bytes_of(L.npix, pixfmt);
-    c->npix = L.npix;
-    c->npad = L.npad;
-    c->slot_stride = L.slot_stride;
-    c->tw_k = -1;
-    c->footprint = L.total;
-    c->stream = nullptr;
-    int st = QLD_OK;
-    if (cudaGetDevice(&c->device) != cudaSuccess) st = QLD_E_CUDA;
-    if (st == QLD_OK && (cudaMalloc(&c->ring, (size_t)L.ring_bytes) != cudaSuccess ||
-                         cudaMalloc(&c->S, (size_t)L.sums_bytes) != cudaSuccess ||
-                         cudaMalloc(&c->C, (size_t)L.sums_bytes) != cudaSuccess ||
-                         cudaMalloc(&c->tw, (size_t)L.tw_bytes) != cudaSuccess)) {
-        st = QLD_E_NOMEM;
-    }
-    if (st == QLD_OK && (cudaMemset(c->ring, 0, (size_t)L.ring_bytes) != cudaSuccess ||
-                         cudaMemset(c->S, 0, (size_t)L.sums_bytes) != cudaSuccess ||
-                         cudaMemset(c->C, 0, (size_t)L.sums_bytes) != cudaSuccess ||
-                         cudaDeviceSynchronize() != cudaSuccess)) {
-        st = QLD_E_CUDA;
-    }
-    if (st != QLD_OK) {
-        cudaGetLastError();
-        free_ctx_memory(c);
-        delete c;
-        g_in_use.fetch_sub(L.total);
-        set_err(st);
-        return nullptr;
-    }
-    return c;
+    return create_ctx(H_total, W, N, pixfmt, row0, rows);
 }
 
 void qld_destroy(qld_ctx* c) {
@@ -452,7 +490,8 @@ int qld_push_frames(qld_ctx* c, const void* frames, int count, void* stream) {
     if (!g.ok) return set_err(QLD_E_CUDA);
     if (pending_error() != QLD_OK) return set_err(QLD_E_CUDA);
     c->stream = (cudaStream_t)stream;
-    return set_err(enqueue_push(c, (const uint8_t*)frames, count, false, nullptr, nullptr));
+    return set_err(enqueue_push(c, (const uint8_t*)frames + c->band_offset, c->frame_pitch, count, false, nullptr,
+                                nullptr));
 }
 
 int qld_push_image(qld_ctx* c, const void* frames, int count, void* stream, float* amp, float* phase) {
@@ -465,7 +504,8 @@ int qld_push_image(qld_ctx* c, const void* frames, int count, void* stream, floa
     if (pending_error() != QLD_OK) return set_err(QLD_E_CUDA);
     c->stream = (cudaStream_t)stream;
     if (count == 0) return set_err(enqueue_image(c, amp, phase));
-    return set_err(enqueue_push(c, (const uint8_t*)frames, count, amp || phase, amp, phase));
+    return set_err(enqueue_push(c, (const uint8_t*)frames + c->band_offset, c->frame_pitch, count, amp || phase, amp,
+                                phase));
 }
 
 int qld_image(qld_ctx* c, float* amp, float* phase) {
@@ -486,7 +526,8 @@ int qld_step(qld_ctx* c, const void* frames, int count, void* stream, float* amp
     if (!g.ok) return set_err(QLD_E_CUDA);
     if (pending_error() != QLD_OK) return set_err(QLD_E_CUDA);
     c->stream = (cudaStream_t)stream;
-    return set_err(enqueue_step(c, (const uint8_t*)frames, count, amp, phase, k, power));
+    return set_err(enqueue_step(c, (const uint8_t*)frames + c->band_offset, c->frame_pitch, count, amp, phase, k,
+                                power));
 }
 
 int qld_fft_bin(qld_ctx* c, int k, float* out) {
@@ -520,12 +561,11 @@ int qld_push_frames_host(qld_ctx* c, const void* host_frames, int count, void* s
         const int i = hp->in_idx;
         hp->in_idx = (i + 1) % HostPipe::kIn;
         if (cudaStreamWaitEvent(hp->cin, hp->in_free[i], 0) != cudaSuccess ||
-            cudaMemcpyAsync(hp->stage[i], src + done * frame_bytes, (size_t)(n * frame_bytes), cudaMemcpyHostToDevice,
-                            hp->cin) != cudaSuccess ||
+            copy_frames_in(c, hp->stage[i], src, done, n, hp->cin) != cudaSuccess ||
             cudaEventRecord(hp->in_ready[i], hp->cin) != cudaSuccess ||
             cudaStreamWaitEvent(c->stream, hp->in_ready[i], 0) != cudaSuccess)
             return set_err(QLD_E_CUDA);
-        st = enqueue_push(c, hp->stage[i], (int)n, false, nullptr, nullptr);
+        st = enqueue_push(c, hp->stage[i], frame_bytes, (int)n, false, nullptr, nullptr);
         if (st != QLD_OK) return set_err(st);
         if (cudaEventRecord(hp->in_free[i], c->stream) != cudaSuccess) return set_err(QLD_E_CUDA);
     }
@@ -586,7 +626,7 @@ int qld_step_host(qld_ctx* c, const void* host_frames, int count, void* stream, 
     const int i = hp->in_idx;
     hp->in_idx = (i + 1) % HostPipe::kIn;
     if (cudaStreamWaitEvent(hp->cin, hp->in_free[i], 0) != cudaSuccess ||
-        cudaMemcpyAsync(hp->stage[i], host_frames, (size_t)bytes, cudaMemcpyHostToDevice, hp->cin) != cudaSuccess ||
+        copy_frames_in(c, hp->stage[i], (const uint8_t*)host_frames, 0, count, hp->cin) != cudaSuccess ||
         cudaEventRecord(hp->in_ready[i], hp->cin) != cudaSuccess ||
         cudaStreamWaitEvent(c->stream, hp->in_ready[i], 0) != cudaSuccess)
         return set_err(QLD_E_CUDA);
@@ -595,7 +635,7 @@ int qld_step_host(qld_ctx* c, const void* host_frames, int count, void* stream, 
     float* pw = acquire_out(c, &s_pow);
     float* da = amp_host ? img : nullptr;
     float* dp = phase_host ? img + c->npad : nullptr;
-    st = enqueue_step(c, hp->stage[i], count, da, dp, k, pw);
+    st = enqueue_step(c, hp->stage[i], c->frame_bytes, count, da, dp, k, pw);
     if (st != QLD_OK) return set_err(st);
     if (cudaEventRecord(hp->in_free[i], c->stream) != cudaSuccess) return set_err(QLD_E_CUDA);
     st = release_out(c, s_img, da, amp_host, dp, phase_host);
@@ -658,6 +698,9 @@ void* qld_stream(const qld_ctx* c) { return c ? (void*)c->stream : nullptr; }
 // array instead of a context. Host code cannot use the array's name as a
 // device address (on the host it names a stand-in object), so the device
 // address is looked up once per device with cudaGetSymbolAddress and cached.
+// The cache lives as long as the process: a device reset (cudaDeviceReset)
+// after the first call would leave it pointing into a destroyed context, so
+// that is not supported.
 
 namespace {
 
@@ -692,6 +735,9 @@ extern "C" int qld_fft_bin_frames_noalloc(const void* frames, int H, int W, int 
     const long long frame_bytes = npix * pixfmt;
     if (npix > (1ll << 31) - 1 || (frame_bytes % qldk::kVecBytes) != 0 || !aligned(frames, 16) || !aligned(out, 4))
         return set_err(QLD_E_INVAL);
+    // A sticky error from earlier asynchronous work: report it before
+    // queueing anything, so a failure here never hides work of this call.
+    if (pending_error() != QLD_OK) return set_err(QLD_E_CUDA);
     int dev = -1;
     if (cudaGetDevice(&dev) != cudaSuccess) return set_err(QLD_E_CUDA);
     float2* tw = noalloc_twiddles(dev);

@@ -9,7 +9,14 @@
 
 struct qld_ctx {
     int H, W, N, pixfmt;
-    long long frame_bytes;  // bytes of one frame in the input format
+    long long frame_bytes;  // bytes of one frame (of the band) in the input format
+    // Row band of a larger frame (qld_create_band): the caller's frames are
+    // H_total x W, this context owns rows row0 .. row0 + H - 1. Frame f of a
+    // device push starts band_offset + f * frame_pitch bytes into the
+    // caller's buffer. A whole-frame context has H_total = H, row0 = 0,
+    // band_offset = 0 and frame_pitch = frame_bytes.
+    int H_total, row0;
+    long long band_offset, frame_pitch;
     long long npix;
     long long npad;         // padded pixel count of S and C
     long long slot_stride;  // bytes

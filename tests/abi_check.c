@@ -19,6 +19,10 @@ static void check(int cond, const char* what) {
 int main(void) {
     check(qld_create(0, 16, 8, QLD_U16) == NULL && qld_last_error() == QLD_E_INVAL, "create rejects H = 0");
     check(qld_create(16, 16, 6, QLD_U16) == NULL && qld_last_error() == QLD_E_INVAL, "create rejects N mod 4 != 0");
+    check(qld_create_band(16, 16, 8, QLD_U16, 12, 8) == NULL && qld_last_error() == QLD_E_INVAL,
+          "band must lie inside the frame");
+    check(qld_create_band(16, 15, 8, QLD_P12, 1, 2) == NULL && qld_last_error() == QLD_E_INVAL,
+          "packed band must start on a pixel pair");
     /* ring of 64 16-KiB slots, two int32 sum planes, 64 float2 twiddles in 512 bytes */
     check(qld_footprint_bytes(128, 128, 64, QLD_U8) == 64LL * 16384 + 2LL * 4 * 16384 + 512, "footprint");
     check(qld_push_frames(NULL, NULL, 0, NULL) == QLD_E_INVAL, "push to no context");

@@ -55,6 +55,31 @@ def test_create_rejects_bad_arguments(H, W, N, fmt):
     assert q.qld_footprint_bytes(H, W, N, fmt) == q.QLD_E_INVAL
 
 
+@pytest.mark.parametrize("H_total,W,N,fmt,row0,rows", [
+    (16, 16, 8, 2, 12, 8),    # band runs past the frame
+    (16, 16, 8, 2, -1, 4),    # negative start
+    (16, 16, 8, 2, 0, 0),     # empty band
+    (16, 16, 6, 2, 0, 8),     # bad window
+    (16, 15, 8, 3, 1, 2),     # packed band starting mid pixel pair
+    (16, 15, 8, 3, 0, 3),     # packed band of an odd pixel count
+    (65536, 65536, 4, 1, 0, 1),  # whole frame too large
+])
+def test_create_band_rejects_bad_arguments(H_total, W, N, fmt, row0, rows):
+    assert q.lib.qld_create_band(H_total, W, N, fmt, row0, rows) is None
+    assert q.qld_last_error() == q.QLD_E_INVAL
+
+
+def test_budget_refuses_a_band_by_its_own_footprint():
+    band = q.qld_footprint_bytes(256, 1024, 1024, 2)
+    q.qld_set_mem_budget(band - 1)
+    try:
+        assert q.lib.qld_create_band(1024, 1024, 1024, 2, 256, 256) is None
+        assert q.qld_last_error() == q.QLD_E_NOMEM
+        assert q.qld_mem_in_use() == 0
+    finally:
+        q.qld_set_mem_budget(0)
+
+
 def test_footprint():
     # ring: N slots of the frame size rounded up to 256 bytes; two int32 sum
     # planes padded to 64 pixels; N float2 twiddles rounded up to 256 bytes.

@@ -57,6 +57,99 @@ def test_unet_gradients_match_the_fp64_reference(conv):
         rel = np.linalg.norm(got - want) / max(np.linalg.norm(want), 1e-30)
         cos = float(got @ want) / max(np.linalg.norm(got) * np.linalg.norm(want), 1e-30)
         assert rel < 2e-2 and cos > 0.999, (k, rel, cos)
+    stagewise_check(net, prm, B, H, W, T)
+
+
+def stagewise_check(net, prm, B, H, W, T):
+    """Every stage of the network's forward and backward pass, elementwise,
+    against FP64 recomputed from the GPU's own inputs to that stage (the
+    stage's bf16 / float32 tensors read back), so each bound is that stage's
+    own arithmetic: a convolution's FP32 accumulation relative to the sum over
+    absolute values (ACC, ACC_W of the per-kernel tests) plus the final bf16
+    rounding (2^-8 relative); pooling, upsampling, concatenation, split and
+    the ReLU mask are emulated exactly. (A bound carried through the whole
+    network over absolute weights grows about sqrt(9 Cin) per layer and says
+    nothing; the end-to-end check above is the norm one.)"""
+    import oracle
+    from test_nn_gpu import ACC, close
+    from test_nn_tc_gpu import ACC_W
+    from unet_reference import LAYERS, bf16r, pool, pool_bwd, up, up_bwd
+
+    U = 2.0 ** -8
+    dims = [(H >> l, W >> l) for l in range(4)]
+    a = {k: v.float().cpu().numpy().astype(np.float64) for k, v in net.a.items()}
+    g = {k: v.cpu().numpy().astype(np.float64) for k, v in net.g.items()}
+    level = {"x": 0, "a0": 0, "e0": 0, "p0": 1, "a1": 1, "e1": 1, "p1": 2, "a2": 2, "e2": 2, "p2": 3, "a3": 3,
+             "u3": 3, "cat2": 2, "ad2": 2, "u2": 2, "cat1": 1, "ad1": 1, "u1": 1, "cat0": 0, "ad0": 0, "u0": 0,
+             "up1": 0, "up2": 1, "up3": 2}
+
+    def t(d, k):
+        h, w = dims[level[k]]
+        return d[k].reshape(B, h, w, -1)
+
+    def wb(name):
+        _, cin, cout = next(l for l in LAYERS if l[0] == name)
+        w = prm[name + ".w"]["p"].cpu().numpy().astype(np.float64)
+        return bf16r(w).reshape(3, 3, cin, cout), prm[name + ".b"]["p"].cpu().numpy().astype(np.float64)
+
+    # forward: conv + bias + ReLU into bf16, pooling, upsample + concat
+    convs = [("c0a", "x", "a0"), ("c0b", "a0", "e0"), ("c1a", "p0", "a1"), ("c1b", "a1", "e1"), ("c2a", "p1", "a2"),
+             ("c2b", "a2", "e2"), ("c3a", "p2", "a3"), ("c3b", "a3", "u3"), ("d2a", "cat2", "ad2"),
+             ("d2b", "ad2", "u2"), ("d1a", "cat1", "ad1"), ("d1b", "ad1", "u1"), ("d0a", "cat0", "ad0"),
+             ("d0b", "ad0", "u0")]
+    for name, src, dst in convs:
+        w, b = wb(name)
+        x = t(a, src)
+        ref = np.maximum(oracle.conv3x3(x, w, b), 0)
+        bound = ACC * (oracle.conv3x3(np.abs(x), np.abs(w)) + np.abs(b)) + 1e-6
+        close(t(a, dst), ref, bound + U * np.abs(ref), "forward " + name)
+    for src, dst in (("e0", "p0"), ("e1", "p1"), ("e2", "p2")):
+        assert np.array_equal(t(a, dst), bf16r(pool(t(a, src)))), "pool " + dst
+    for u, e, dst in (("u3", "e2", "cat2"), ("u2", "e1", "cat1"), ("u1", "e0", "cat0")):
+        assert np.array_equal(t(a, dst), np.concatenate([up(t(a, u)), t(a, e)], axis=3)), "concat " + dst
+    # head and loss gradient (float32)
+    hw = prm["head.w"]["p"].cpu().numpy().astype(np.float64)
+    hb = prm["head.b"]["p"].cpu().numpy().astype(np.float64)
+    u0 = t(a, "u0")
+    base = net.baseline.cpu().numpy().astype(np.float64).reshape(B, H, W)
+    pred = u0 @ hw + hb[0] + base
+    close(net.pred.cpu().numpy().reshape(B, H, W), pred, ACC * (np.abs(u0) @ np.abs(hw) + abs(hb[0]) + np.abs(base))
+          + 1e-6, "head")
+    gp = net.gpred.cpu().numpy().astype(np.float64).reshape(B, H, W)
+    pr = net.pred.cpu().numpy().astype(np.float64).reshape(B, H, W)
+    gref = 2 * (pr - T.cpu().numpy().astype(np.float64).reshape(B, H, W)) / pr.size
+    close(gp, gref, 1e-6 * np.abs(gref) + 1e-12, "loss gradient")
+    close(t(g, "u0"), gp[..., None] * hw, 1e-6 * np.abs(gp[..., None] * hw) + 1e-12, "head data gradient")
+    # sums over pixels: FP32 in any order is within n 2^-24 of the sum of
+    # absolute values
+    nsum = lambda P: P * 2.0 ** -24  # noqa: E731
+    close(prm["head.w"]["g"].cpu().numpy(), np.einsum("bhwc,bhw->c", u0, gp),
+          nsum(B * H * W) * np.einsum("bhwc,bhw->c", np.abs(u0), np.abs(gp)) + 1e-9, "head weight gradient")
+    close(prm["head.b"]["g"].cpu().numpy(), [gp.sum()], nsum(B * H * W) * np.abs(gp).sum() + 1e-9,
+          "head bias gradient")
+    # backward through each convolution: ReLU mask into bf16 (exact), weight,
+    # bias and data gradients within the FP32 accumulation bound
+    for name, src, dst in reversed(convs):
+        w, _ = wb(name)
+        x, y, gy = t(a, src), t(a, dst), t(g, dst)
+        gz = bf16r(np.where(y > 0, gy, 0.0))
+        dx, dw, db = oracle.conv3x3_backward(x, w, gz)
+        mx, mw, mb = oracle.conv3x3_backward(np.abs(x), np.abs(w), np.abs(gz))
+        close(prm[name + ".w"]["g"].cpu().numpy().reshape(dw.shape), dw, ACC_W * mw + 1e-6, "weight gradient " + name)
+        close(prm[name + ".b"]["g"].cpu().numpy(), db, nsum(x.shape[0] * x.shape[1] * x.shape[2]) * mb + 1e-6,
+              "bias gradient " + name)
+        if src != "x":
+            close(t(g, src), dx, ACC * mx + 1e-6, "data gradient " + name)
+    # the gradient plumbing between the convolutions (float32, exact but for
+    # the sums of four in upsample's backward and the pooled adds)
+    for cat, upk, e, uk, c in (("cat0", "up1", "e0", "u1", 32), ("cat1", "up2", "e1", "u2", 64),
+                               ("cat2", "up3", "e2", "u3", 128)):
+        assert np.array_equal(t(g, upk), t(g, cat)[..., :c]), "split " + cat
+        close(t(g, uk), up_bwd(t(g, upk)), 1e-6 * up_bwd(np.abs(t(g, upk))) + 1e-12, "upsample backward " + uk)
+    for e, c, p in (("e2", 128, "p2"), ("e1", 64, "p1"), ("e0", 32, "p0")):
+        cat = {"e0": "cat0", "e1": "cat1", "e2": "cat2"}[e]
+        want = t(g, cat)[..., c:] + pool_bwd(t(g, p))
+        close(t(g, e), want, 1e-6 * np.abs(want) + 1e-12, "skip + pooling backward " + e)
 
 
 def test_short_training_run_beats_the_short_window_baseline():

@@ -90,6 +90,44 @@ def test_fog_1024x1024_u16_N1024_sliding_by_4(od):
     ctx.destroy()
 
 
+def test_step_fog_1024x1024_u16_N1024_by_4_one_launch_against_the_oracle():
+    """The kernel bench.py times, at the shape it times it: qld_step (push,
+    image and DFT bin k = N/4 in one launch) on the OD 6 fog scene, 1024^2
+    uint16, N = 1024, 4 frames a step. After each of three steps, the step's
+    own amplitude, phase and power outputs and the context's sums on 2048+
+    sampled pixels against the oracle on frames regenerated on the host."""
+    H = W = 1024
+    N = 1024
+    sc = scene_fog(6, H=H, W=W)
+    ds = DeviceScene(sc)
+    ctx = q.qld_create(H, W, N, q.QLD_U16)
+    fill(ctx, ds, N, 256)
+    pix = sample_pixels(sc, 2048, 1006)
+    step = torch.empty((4, H, W), dtype=torch.uint16, device="cuda")
+    amp = torch.empty(H * W, dtype=torch.float32, device="cuda")
+    ph = torch.empty_like(amp)
+    pw = torch.empty_like(amp)
+    T = N
+    launches0 = q.qld_launch_count()
+    for i in range(3):
+        ds.generate_into(step, T + 1, 4)
+        q.qld_step(ctx, step, 4, N // 4, pw, None, amp, ph)
+        T += 4
+        q.qld_sync(ctx)
+        s0 = T - N + 1
+        win = sc.frames(s0, N, pix=pix)
+        S_r, C_r = oracle.quadrature_sums(win, s0=s0)
+        S_g, C_g = get_iq(ctx)
+        check_sums(S_g[pix], C_g[pix], S_r, C_r, "step %d" % i)
+        R, phr = oracle.amplitude_phase(S_r, C_r)
+        check_amp_phase(amp.cpu().numpy()[pix], ph.cpu().numpy()[pix], R, phr, "step %d" % i)
+        check_power(pw.cpu().numpy()[pix], oracle.dft_bin(win, N // 4, s0=s0)[2],
+                    win.astype(np.int64).sum(axis=0), "step %d" % i)
+    # one launch per step after the first (which also fills the twiddle table)
+    assert q.qld_launch_count() - launches0 == 3 + 1
+    ctx.destroy()
+
+
 def _pack12_device(x):
     """[n, H, W] uint16 (values < 4096) -> [n, H*W*3/2] uint8, two pixels in
     three bytes, least significant bits first (the QLD_P12 layout)."""
