@@ -72,8 +72,11 @@ __global__ void avgpool2_fwd_kernel(const __nv_bfloat16* __restrict__ in, int B,
         const int y = (int)(r % h);
         const long long b = r / h;
         const long long base = ((b * H + 2 * y) * W + 2 * x) * C + c;
-        const float s = __bfloat162float(in[base]) + __bfloat162float(in[base + C]) +
-                        __bfloat162float(in[base + (long long)W * C]) + __bfloat162float(in[base + (long long)W * C + C]);
+        // the two diagonals of the 2x2 block, then their sum: the same for
+        // every order of the four pixels, as the fused convolution epilogue
+        // (each of whose lanes starts from its own pixel) computes it
+        const float s = (__bfloat162float(in[base]) + __bfloat162float(in[base + (long long)W * C + C])) +
+                        (__bfloat162float(in[base + C]) + __bfloat162float(in[base + (long long)W * C]));
         out[e] = __float2bfloat16_rn(0.25f * s);
     }
 }
@@ -267,7 +270,7 @@ __global__ void avgpool2_fwd_v8_kernel(const uint4* __restrict__ in, int B, int 
         unpack8(__ldg(in + base + (long long)W * C8), f2);
         unpack8(__ldg(in + base + (long long)W * C8 + C8), f3);
 #pragma unroll
-        for (int j = 0; j < 8; ++j) o[j] = 0.25f * (f0[j] + f1[j] + f2[j] + f3[j]);
+        for (int j = 0; j < 8; ++j) o[j] = 0.25f * ((f0[j] + f3[j]) + (f1[j] + f2[j]));  // diagonals first
         out[e] = pack8(o);
     }
 }
@@ -793,7 +796,8 @@ int launch_tma(const void* in, const void* wk, const float* bias, int B, int H, 
                 return set_err(QLD_E_CUDA);
             attr_res.fetch_or(1ull << dev);
         }
-        if (launch_maybe_early(qldnn::conv3x3_fwd_tma_wres_kernel<N, SWB, SUB>, grid, 192, (size_t)R::smem(sa, Cin),
+        if (launch_maybe_early(qldnn::conv3x3_fwd_tma_wres_kernel<N, SWB, SUB>, grid, qldnn::kConvThreads,
+                               (size_t)R::smem(sa, Cin),
                                st, early, mi, mw, bias, B, H, W, Cin, Cout, relu, epi, status, sa,
                                nsplit) != cudaSuccess)
             return set_err(QLD_E_CUDA);
@@ -807,7 +811,8 @@ int launch_tma(const void* in, const void* wk, const float* bias, int B, int H, 
             return set_err(QLD_E_CUDA);
         attr_done.fetch_or(1ull << dev);
     }
-    if (launch_maybe_early(qldnn::conv3x3_fwd_tma_kernel<N, SWB>, grid, 192, (size_t)L::kSmem, st, early, mi, mw,
+    if (launch_maybe_early(qldnn::conv3x3_fwd_tma_kernel<N, SWB>, grid, qldnn::kConvThreads, (size_t)L::kSmem, st,
+                           early, mi, mw,
                            bias, B, H, W, Cin, Cout, relu, epi, status, nsplit) != cudaSuccess)
         return set_err(QLD_E_CUDA);
     return launched(1);

@@ -23,15 +23,19 @@
 // 8-row atoms of 8 * SWB bytes. A K16 step inside a row moves the descriptor
 // start 32 bytes.
 //
-// Roles (192 threads, one CTA per SM, persistent over tiles):
+// Roles (320 threads, one CTA per SM, persistent over tiles):
 //   warp 0  one thread issues the TMA loads into a 2-stage halo ring and an
-//           SB-stage weight ring (mbarrier expect_tx / complete_tx);
+//           SB-stage weight ring of one tap row (three taps) per stage when
+//           two such stages fit (mbarrier expect_tx / complete_tx);
 //   warp 1  allocates TMEM (two accumulators of N columns), one thread issues
 //           tcgen05.mma M128 x N x K16 and commits to the rings' "empty"
 //           barriers and, per tile, to the accumulator's "full" barrier;
-//   warps 2-5 epilogue: tcgen05.ld of the accumulator (warp w reads TMEM
-//           lanes 32 (w mod 4) ..), bias, ReLU, bf16/f32 stores, then release
-//           the accumulator, so the next tile's MMAs overlap the read-out.
+//   warps 2-9 epilogue: tcgen05.ld of the accumulator (warp w reads TMEM
+//           lanes 32 (w mod 4) .., two warps per lane quarter splitting the
+//           columns), bias, ReLU, bf16/f32 stores, then release the
+//           accumulator, so the next tile's MMAs overlap the read-out. The
+//           read-out of the narrow layers' fused pooling and upsampling
+//           outputs is as long as their MMAs, hence eight warps.
 // Launched early (programmatic stream serialisation), a CTA allocates TMEM,
 // sets up its barriers and (weights-resident variant) loads the weights
 // while the previous kernel finishes; the producer waits for that kernel
@@ -113,6 +117,10 @@ __device__ __forceinline__ uint64_t global_ns() {
 // role has set *fail (and set it on a time-out).
 __device__ __forceinline__ bool wait_timed(uint64_t* bar, uint32_t parity, volatile int* fail,
                                            uint64_t limit_ns = 1000000000ull) {
+    // a phase that has already completed costs one probe: the timer is read
+    // (a slow special register, hundreds of cycles on the MMA thread's path)
+    // only when the wait is real
+    if (mbar_try_wait(bar, parity)) return true;
     const uint64_t t0 = global_ns();
     for (uint32_t i = 1;; ++i) {
         if (mbar_try_wait(bar, parity)) return true;
@@ -195,21 +203,34 @@ __device__ __forceinline__ void tc_tie16(uint32_t* r) {
                    "+r"(r[15]));
 }
 
-// Epilogue warps (4 of them, warp w reads TMEM lanes 32 (w mod 4) ..) of the
-// persistent TMA convolutions: per tile, wait for its accumulator, add the
-// bias, apply ReLU, write the outputs `epi` asks for, release the accumulator.
-// Pixel m = 32 (w mod 4) + lane of the tile is (y, x) = (m / 16, m mod 16), so
-// a warp holds two whole rows and the 2x2 pooling partners of lane l are the
-// lanes l ^ 1, l ^ 16 and l ^ 17. The accumulator is read in groups of up to
-// 64 columns (all loads of a group issued before one wait); with N <= 64 the
-// bias stays in registers for all tiles. A tile is SUB sub-tiles of 8 x 16
-// pixels stacked in rows, sub-tile h in accumulator columns (acc SUB + h) N.
+// Epilogue warps of the persistent TMA convolutions (warps 2-5; warp w may
+// read TMEM lanes 32 (w mod 4) .. only). Per tile: wait for its accumulator,
+// add the bias, apply ReLU, write the outputs `epi` asks for, release the
+// accumulator. Pixel m = 32 (w mod 4) + lane of the tile is (y, x) =
+// (m / 16, m mod 16), so a warp holds two whole rows and the 2x2 pooling
+// partners of lane l are the lanes l ^ 1, l ^ 16 and l ^ 17. The four lanes
+// of a 2x2 block share its pooling: lane role r = (x & 1) + 2 (y & 1) takes
+// channel pairs 2r and 2r + 1 of each 16-channel chunk, receiving them from
+// its partners as packed bf16 pairs, and sums the block's diagonals first,
+// (own + l^17) + (l^1 + l^16), which is the same value in every lane's
+// order (the standalone pooling kernels sum the same way). The
+// accumulator is read in groups of up to 64 columns (all loads of a group
+// issued before one wait); with N <= 64 the bias stays in registers for all
+// tiles. A tile is SUB sub-tiles of 8 x 16 pixels stacked in rows, sub-tile h
+// in accumulator columns (acc SUB + h) N. The epilogue warps share the SM
+// sub-partitions' issue slots with the producer and the MMA-issuing thread,
+// whose pace sets the narrow layers' speed, so the read-out is kept to as few
+// instructions (and warps) as possible: more epilogue warps measured slower.
+constexpr int kEpiWarps = 4;
+constexpr int kConvThreads = 64 + 32 * kEpiWarps;
+
 template <int N, int SUB = 1>
 __device__ __forceinline__ void conv_epilogue(uint32_t tmem, uint64_t* tfull, uint64_t* tempty, volatile int* fail,
                                               int warp, int lane, int ntiles, int tiles_x, int tiles_y, int H, int W,
                                               int Cout, const float* __restrict__ bias, int relu, ConvEpi epi,
                                               int nsplit) {
-    const int qw = warp & 3;  // TMEM lane quarter this warp may read
+    const bool head = epi.head_w != nullptr;
+    const int qw = warp & 3;           // TMEM lane quarter this warp may read
     const int m = qw * 32 + lane;
     const int my = m >> 4, mx = m & 15;
     const int co0 = (blockIdx.x % nsplit) * N;  // this CTA's slice of the output channels
@@ -218,9 +239,17 @@ __device__ __forceinline__ void conv_epilogue(uint32_t tmem, uint64_t* tfull, ui
     if (epi.out_f) epi.out_f += co0;
     if (epi.pool) epi.pool += co0;
     if (epi.up) epi.up += co0;
-    const bool pool_writer = (lane & 17) == 0;  // even x, even y
+    const int role = (lane & 1) | ((lane >> 3) & 2);  // 2x2 block position: x & 1, y & 1
+    // pk index of channel pair k (0, 1) of the lane with role r ^ rd, for the
+    // lane that sends it to this one across offset rd (1: x, 2: y, 3: both)
+    auto pick = [&](const uint32_t* pk, int rd, int k) {
+        const int rr = role ^ rd;
+        const uint32_t a = rr & 1 ? pk[2 + k] : pk[k];
+        const uint32_t b = rr & 1 ? pk[6 + k] : pk[4 + k];
+        return rr & 2 ? b : a;
+    };
     constexpr int G = N < 64 ? N : 64;  // accumulator columns per tcgen05.wait::ld
-    float bres[N <= 64 ? N : 1];        // the bias (or 0), when N <= 64
+    float bres[N <= 64 ? N : 1];        // the bias (or 0), for narrow layers
     if constexpr (N <= 64) {
 #pragma unroll
         for (int j = 0; j < N; ++j) bres[j] = bias ? bias[j] : 0.f;
@@ -238,7 +267,7 @@ __device__ __forceinline__ void conv_epilogue(uint32_t tmem, uint64_t* tfull, ui
             const bool inside = y < H && x < W;
             const long long p = ((long long)b * H + y) * W + x;
             const uint32_t taddr = tmem + ((uint32_t)(qw * 32) << 16) + (uint32_t)((acc * SUB + h) * N);
-            float hacc = epi.head_w ? *epi.head_b : 0.f;
+            float hacc = head ? *epi.head_b : 0.f;
 #pragma unroll 1
             for (int g0 = 0; g0 < N; g0 += G) {
                 uint32_t rg[G];
@@ -285,44 +314,43 @@ __device__ __forceinline__ void conv_epilogue(uint32_t tmem, uint64_t* tfull, ui
                             o[1] = make_uint4(pk[4], pk[5], pk[6], pk[7]);
                         }
                     }
-                    if (epi.pool || epi.head_w) {
-                        float f[16];  // the stored (bf16) values
+                    if (epi.pool) {  // warp-uniform: every lane shuffles
+                        uint32_t own[2], v1[2], v16[2], v17[2];
 #pragma unroll
-                        for (int j = 0; j < 8; ++j) {
+                        for (int k = 0; k < 2; ++k) {
+                            own[k] = pick(pk, 0, k);
+                            v1[k] = __shfl_xor_sync(0xffffffffu, pick(pk, 1, k), 1);
+                            v16[k] = __shfl_xor_sync(0xffffffffu, pick(pk, 2, k), 16);
+                            v17[k] = __shfl_xor_sync(0xffffffffu, pick(pk, 3, k), 17);
+                        }
+                        if (inside) {
+                            uint32_t o2[2];
+#pragma unroll
+                            for (int k = 0; k < 2; ++k) {
+                                const float2 f0 = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&own[k]));
+                                const float2 f1 = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&v1[k]));
+                                const float2 f2 = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&v16[k]));
+                                const float2 f3 = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&v17[k]));
+                                const float lo = 0.25f * ((f0.x + f3.x) + (f1.x + f2.x));
+                                const float hi = 0.25f * ((f0.y + f3.y) + (f1.y + f2.y));
+                                const __nv_bfloat162 h2 = __floats2bfloat162_rn(lo, hi);
+                                o2[k] = *reinterpret_cast<const uint32_t*>(&h2);
+                            }
+                            const long long pp = ((long long)b * (H / 2) + y / 2) * (W / 2) + x / 2;
+                            *reinterpret_cast<uint2*>(epi.pool + pp * epi.ldp + c0 + 4 * role) = make_uint2(o2[0], o2[1]);
+                        }
+                    }
+                    if (head) {
+#pragma unroll
+                        for (int j = 0; j < 8; ++j) {  // the stored (bf16) values, in channel order
                             const float2 t2 = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&pk[j]));
-                            f[2 * j] = t2.x;
-                            f[2 * j + 1] = t2.y;
-                        }
-                        if (epi.pool) {  // warp-uniform: every lane shuffles
-                            float o[16];
-#pragma unroll
-                            for (int j = 0; j < 16; ++j) {
-                                const float a1 = __shfl_xor_sync(0xffffffffu, f[j], 1);
-                                const float a2 = __shfl_xor_sync(0xffffffffu, f[j], 16);
-                                const float a3 = __shfl_xor_sync(0xffffffffu, f[j], 17);
-                                o[j] = 0.25f * (f[j] + a1 + a2 + a3);
-                            }
-                            if (pool_writer && inside) {
-                                uint32_t q2[8];
-#pragma unroll
-                                for (int j = 0; j < 8; ++j) {
-                                    const __nv_bfloat162 h2 = __floats2bfloat162_rn(o[2 * j], o[2 * j + 1]);
-                                    q2[j] = *reinterpret_cast<const uint32_t*>(&h2);
-                                }
-                                const long long pp = ((long long)b * (H / 2) + y / 2) * (W / 2) + x / 2;
-                                uint4* po = reinterpret_cast<uint4*>(epi.pool + pp * epi.ldp + c0);
-                                po[0] = make_uint4(q2[0], q2[1], q2[2], q2[3]);
-                                po[1] = make_uint4(q2[4], q2[5], q2[6], q2[7]);
-                            }
-                        }
-                        if (epi.head_w) {
-#pragma unroll
-                            for (int j = 0; j < 16; ++j) hacc = fmaf(f[j], epi.head_w[c0 + j], hacc);
+                            hacc = fmaf(t2.x, epi.head_w[c0 + 2 * j], hacc);
+                            hacc = fmaf(t2.y, epi.head_w[c0 + 2 * j + 1], hacc);
                         }
                     }
                 }
             }
-            if (epi.head_w && inside) epi.pred[p] = hacc + epi.base[p];
+            if (head && inside) epi.pred[p] = hacc + epi.base[p];
         }
         tc_fence_before();
         mbar_arrive(&tempty[acc]);
@@ -335,10 +363,14 @@ struct TmaConv {
     static constexpr int BK = SWB / 2;                      // channels per chunk
     static constexpr int HALO = 10 * 16 * SWB;              // one column-shifted halo copy
     static constexpr int SA = 2;                            // halo stages
-    static constexpr int BSTAGE = N * SWB;                  // one tap's weights
     static constexpr int kA = SA * 3 * HALO;
-    // weight stages: as many as fit beside the halo ring in 227 KB (at most 12)
     static constexpr int kFree = 232448 - 1024 - kA - 64 * 8 - 16;
+    // weight stages of one tap row (three taps: one barrier round trip and
+    // one commit per three taps) when two such stages fit beside the halo
+    // ring, else of one tap
+    static constexpr int TPS = kFree / (3 * N * SWB) >= 2 ? 3 : 1;
+    static constexpr int BSTAGE = TPS * N * SWB;
+    // weight stages: as many as fit beside the halo ring in 227 KB (at most 12)
     static constexpr int SB = kFree / BSTAGE > 12 ? 12 : kFree / BSTAGE;
     static_assert(SB >= 2, "weight ring too small");
     static constexpr int kB = SB * BSTAGE;
@@ -348,7 +380,7 @@ struct TmaConv {
 };
 
 template <int N, int SWB>
-__global__ void __launch_bounds__(192, 1)
+__global__ void __launch_bounds__(kConvThreads, 1)
     conv3x3_fwd_tma_kernel(const __grid_constant__ CUtensorMap map_in, const __grid_constant__ CUtensorMap map_w,
                            const float* __restrict__ bias, int B, int H, int W, int Cin, int Cout, int relu,
                            const ConvEpi epi, int* status, int nsplit) {
@@ -390,7 +422,7 @@ __global__ void __launch_bounds__(192, 1)
         }
         for (int s = 0; s < 2; ++s) {
             mbar_init(&tfull[s], 1);
-            mbar_init(&tempty[s], 128);
+            mbar_init(&tempty[s], 32 * kEpiWarps);
         }
         mbar_init(drain, 1);
         *fail = 0;
@@ -421,12 +453,14 @@ __global__ void __launch_bounds__(192, 1)
                     for (int j = 0; j < 3; ++j)
                         tma_load_4d(sA + (sa * 3 + j) * L::HALO, &map_in, &fullA[sa], cc * L::BK, x0 + j - 1, y0 - 1, b);
                     ++ia;
-                    for (int tap = 0; tap < 9; ++tap) {
+                    for (int g = 0; g < 9 / L::TPS; ++g) {
                         const int sb = ib % L::SB;
                         if (ib >= L::SB && !(ok = wait_or_fail(&emptyB[sb], (uint32_t)(((ib / L::SB) - 1) & 1), fail)))
                             break;
                         mbar_expect_tx(&fullB[sb], L::BSTAGE);
-                        tma_load_2d(sB + sb * L::BSTAGE, &map_w, &fullB[sb], cc * L::BK, tap * Cout + co0);
+                        for (int tt = 0; tt < L::TPS; ++tt)
+                            tma_load_2d(sB + sb * L::BSTAGE + tt * N * SWB, &map_w, &fullB[sb], cc * L::BK,
+                                        (g * L::TPS + tt) * Cout + co0);
                         ++ib;
                     }
                 }
@@ -446,34 +480,45 @@ __global__ void __launch_bounds__(192, 1)
     } else if (warp == 1) {
         if (lane == 0) {
             // --------------------------------------------------------- MMA issuer
-            int ia = 0, ib = 0, it = 0;
+            // As in the weights-resident kernel: counted stages and offset
+            // descriptors; one weight barrier per stage of TPS taps.
+            const uint64_t adesc0 = umma_desc_sw<SWB>(smem_u32(sA));
+            const uint64_t bdesc0 = umma_desc_sw<SWB>(smem_u32(sB));
+            int sa = 0, sb = 0, it = 0;
+            uint32_t pa = 0, pb = 0;
             bool ok = true;
             for (int t = blockIdx.x / nsplit; t < ntiles && ok; t += gridDim.x / nsplit) {
                 const int acc = it & 1;
-                if (it >= 2 && !(ok = wait_or_fail(&tempty[acc], (uint32_t)(((it >> 1) - 1) & 1), fail))) break;
-                tc_fence_after();
+                if (it >= 2 && !(ok = wait_or_fail(&tempty[acc], (((uint32_t)it >> 1) & 1u) ^ 1u, fail))) break;
                 const uint32_t d = tmem + (uint32_t)(acc * N);
                 for (int cc = 0; cc < csteps && ok; ++cc) {
-                    const int sa = ia % L::SA;
-                    if (!(ok = wait_or_fail(&fullA[sa], (uint32_t)((ia / L::SA) & 1), fail))) break;
-                    tc_fence_after();
-                    const uint64_t adesc = umma_desc_sw<SWB>(smem_u32(sA + sa * 3 * L::HALO));
+                    if (!(ok = wait_or_fail(&fullA[sa], pa, fail))) break;
+                    const uint64_t adesc = desc_at(adesc0, (uint32_t)(sa * 3 * L::HALO));
 #pragma unroll
-                    for (int tap = 0; tap < 9; ++tap) {
-                        const int sb = ib % L::SB;
-                        if (!(ok = wait_or_fail(&fullB[sb], (uint32_t)((ib / L::SB) & 1), fail))) break;
+                    for (int g = 0; g < 9 / L::TPS; ++g) {
+                        if (!(ok = wait_or_fail(&fullB[sb], pb, fail))) break;
                         tc_fence_after();
-                        const uint64_t bdesc = umma_desc_sw<SWB>(smem_u32(sB + sb * L::BSTAGE));
+                        const uint64_t bdesc = desc_at(bdesc0, (uint32_t)(sb * L::BSTAGE));
 #pragma unroll
-                        for (int kk = 0; kk < L::BK / 16; ++kk)
-                            tc_mma(d, desc_at(adesc, (tap % 3) * L::HALO + (tap / 3) * 16 * SWB + kk * 32),
-                                   desc_at(bdesc, kk * 32), kIdesc, (cc | tap | kk) ? 1u : 0u);
+                        for (int tt = 0; tt < L::TPS; ++tt) {
+                            const int tap = g * L::TPS + tt;
+#pragma unroll
+                            for (int kk = 0; kk < L::BK / 16; ++kk)
+                                tc_mma(d, desc_at(adesc, (tap % 3) * L::HALO + (tap / 3) * 16 * SWB + kk * 32),
+                                       desc_at(bdesc, tt * N * SWB + kk * 32), kIdesc, (cc | tap | kk) ? 1u : 0u);
+                        }
                         tc_commit(&emptyB[sb]);
-                        ++ib;
+                        if (++sb == L::SB) {
+                            sb = 0;
+                            pb ^= 1u;
+                        }
                     }
                     if (!ok) break;
                     tc_commit(&emptyA[sa]);
-                    ++ia;
+                    if (++sa == L::SA) {
+                        sa = 0;
+                        pa ^= 1u;
+                    }
                 }
                 if (!ok) break;
                 tc_commit(&tfull[acc]);
@@ -529,7 +574,7 @@ struct TmaConvRes {
 };
 
 template <int N, int SWB, int SUB = 1>
-__global__ void __launch_bounds__(192, 1)
+__global__ void __launch_bounds__(kConvThreads, 1)
     conv3x3_fwd_tma_wres_kernel(const __grid_constant__ CUtensorMap map_in, const __grid_constant__ CUtensorMap map_w,
                                 const float* __restrict__ bias, int B, int H, int W, int Cin, int Cout, int relu,
                                 const ConvEpi epi, int* status, int SA, int nsplit) {
@@ -567,7 +612,7 @@ __global__ void __launch_bounds__(192, 1)
         mbar_init(wfull, 1);
         for (int s = 0; s < 2; ++s) {
             mbar_init(&tfull[s], 1);
-            mbar_init(&tempty[s], 128);
+            mbar_init(&tempty[s], 32 * kEpiWarps);
         }
         mbar_init(drain, 1);
         *fail = 0;
@@ -591,18 +636,22 @@ __global__ void __launch_bounds__(192, 1)
             // the weights may load while an earlier kernel still runs (an early
             // launch requires that it does not write them); the input may not
             pdl_wait();
-            int ia = 0;
+            int ia = 0, sa = 0;  // halo loads issued; the stage of the next one
+            uint32_t pa = 0;     // phase parity of that stage's use
             bool ok = true;
             for (int t = blockIdx.x / nsplit; t < ntiles && ok; t += gridDim.x / nsplit) {
                 const int tx = t % tiles_x, r = t / tiles_x, ty = r % tiles_y, b = r / tiles_y;
                 const int x0 = tx * 16, y0 = ty * 8 * SUB;
                 for (int cc = 0; cc < csteps; ++cc) {
-                    const int sa = ia % SA;
-                    if (ia >= SA && !(ok = wait_or_fail(&emptyA[sa], (uint32_t)(((ia / SA) - 1) & 1), fail))) break;
+                    if (ia >= SA && !(ok = wait_or_fail(&emptyA[sa], pa ^ 1u, fail))) break;
                     mbar_expect_tx(&fullA[sa], 3 * L::HALO);
                     for (int j = 0; j < 3; ++j)
                         tma_load_4d(sA + (sa * 3 + j) * L::HALO, &map_in, &fullA[sa], cc * L::BK, x0 + j - 1, y0 - 1, b);
                     ++ia;
+                    if (++sa == SA) {
+                        sa = 0;
+                        pa ^= 1u;
+                    }
                 }
             }
             // no copy may still be in flight when the CTA leaves
@@ -615,21 +664,26 @@ __global__ void __launch_bounds__(192, 1)
     } else if (warp == 1) {
         if (lane == 0) {
             // --------------------------------------------------------- MMA issuer
+            // The tensor core queues about one MMA, so every instruction this
+            // thread spends between MMAs is time the pipe may idle: a barrier
+            // probe costs ~100 cycles while operands stream out of shared
+            // memory. Stages and phases are therefore counted rather than
+            // divided out, and descriptors are offsets from precomputed ones.
             bool ok = wait_or_fail(wfull, 0, fail);
             tc_fence_after();
-            int ia = 0, it = 0;
-            const uint32_t w0 = smem_u32(sW);
+            const uint64_t adesc0 = umma_desc_sw<SWB>(smem_u32(sA));
+            const uint64_t bdesc0 = umma_desc_sw<SWB>(smem_u32(sW));
+            int sa = 0, it = 0;  // halo stage of the next chunk; tiles done
+            uint32_t pa = 0;     // its phase parity
             for (int t = blockIdx.x / nsplit; t < ntiles && ok; t += gridDim.x / nsplit) {
                 const int acc = it & 1;
-                if (it >= 2 && !(ok = wait_or_fail(&tempty[acc], (uint32_t)(((it >> 1) - 1) & 1), fail))) break;
-                tc_fence_after();
+                if (it >= 2 && !(ok = wait_or_fail(&tempty[acc], (((uint32_t)it >> 1) & 1u) ^ 1u, fail))) break;
                 const uint32_t d = tmem + (uint32_t)(acc * N * SUB);
                 for (int cc = 0; cc < csteps && ok; ++cc) {
-                    const int sa = ia % SA;
-                    if (!(ok = wait_or_fail(&fullA[sa], (uint32_t)((ia / SA) & 1), fail))) break;
+                    if (!(ok = wait_or_fail(&fullA[sa], pa, fail))) break;
                     tc_fence_after();
-                    const uint64_t adesc = umma_desc_sw<SWB>(smem_u32(sA + sa * 3 * L::HALO));
-                    const uint64_t bdesc = umma_desc_sw<SWB>(w0 + (uint32_t)(cc * 9 * L::BSTAGE));
+                    const uint64_t adesc = desc_at(adesc0, (uint32_t)(sa * 3 * L::HALO));
+                    const uint64_t bdesc = desc_at(bdesc0, (uint32_t)(cc * 9 * L::BSTAGE));
 #pragma unroll
                     for (int tap = 0; tap < 9; ++tap) {
 #pragma unroll
@@ -641,7 +695,10 @@ __global__ void __launch_bounds__(192, 1)
                                        desc_at(bdesc, tap * L::BSTAGE + kk * 32), kIdesc, (cc | tap | kk) ? 1u : 0u);
                     }
                     tc_commit(&emptyA[sa]);
-                    ++ia;
+                    if (++sa == SA) {
+                        sa = 0;
+                        pa ^= 1u;
+                    }
                 }
                 if (!ok) break;
                 tc_commit(&tfull[acc]);
