@@ -445,9 +445,14 @@ int qldnn_conv3x3_fwd_tma(const void* in, const void* wk, const float* bias, int
  * fit beside two halo stages (loaded once per CTA, only the halos streamed)
  * and streams them per tile otherwise; when a layer has at most half as many
  * output tiles as there are SMs it splits each tile's output channels over 2
- * or 4 CTAs (at least 32 channels each, weights resident). mode bit 0 set: always stream the weights; mode >> 4
- * (0 = automatic, else 1, 2 or 4): the CTAs per tile. For tests and
- * measurements of every variant. */
+ * or 4 CTAs (at least 32 channels each, weights resident); 32-channel
+ * layers whose weights and two halo stages fit in half the shared memory run
+ * two CTAs per SM when each gets at least two tiles (one CTA's MMAs fill the
+ * other's pauses for barriers). mode bit 0 set: always stream the weights;
+ * mode >> 4 (0 = automatic, else 1, 2 or 4): the CTAs per tile; bit 12 /
+ * bit 13: force / forbid 16 x 16-pixel tiles where they fit; bit 14 / bit 15:
+ * forbid / force two CTAs per SM where they fit. For tests and measurements
+ * of every variant. */
 int qldnn_conv3x3_fwd_tma_mode(const void* in, const void* wk, const float* bias, int B, int H, int W, int Cin,
                                int Cout, int relu, void* out_bf16, float* out_f32, int* status, int mode,
                                void* stream);

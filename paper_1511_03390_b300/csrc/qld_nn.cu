@@ -752,7 +752,7 @@ cudaError_t launch_maybe_early(void (*kernel)(KArgs...), unsigned grid, unsigned
     return cudaLaunchKernelEx(&cfg, kernel, args...);
 }
 
-template <int N, int SWB, int SUB = 1>
+template <int N, int SWB, int SUB = 1, int MINB = 1>
 int launch_tma(const void* in, const void* wk, const float* bias, int B, int H, int W, int Cin, int Cout, int relu,
                const qldnn::ConvEpi& epi, int* status, cudaStream_t st, bool force_stream, bool early) {
     using L = qldnn::TmaConv<N, SWB>;
@@ -782,28 +782,30 @@ int launch_tma(const void* in, const void* wk, const float* bias, int B, int H, 
     const long long ntiles = (long long)B * ((H + 8 * SUB - 1) / (8 * SUB)) * ((W + 15) / 16);
     const int nsplit = Cout / N;  // CTAs per tile, one output-channel slice each
     long long items = ntiles * nsplit;
-    const long long cap = (long long)(nsm / nsplit) * nsplit;
+    const long long cap = (long long)(MINB * nsm / nsplit) * nsplit;
     const unsigned grid = (unsigned)(items < cap ? items : cap);
-    // weights resident in shared memory when they fit beside two or more halo stages
+    // weights resident in shared memory when they fit beside two or more halo
+    // stages (within half of it for two CTAs per SM)
     using R = qldnn::TmaConvRes<N, SWB, SUB>;
+    const long long smem_cap = MINB == 2 ? qldnn::kTwoPerSmSmem : 232448;
     int sa = 0;
-    while (sa < R::kMaxSA && R::smem(sa + 1, Cin) <= 232448) ++sa;
+    while (sa < R::kMaxSA && R::smem(sa + 1, Cin) <= smem_cap) ++sa;
     if (sa >= 2 && !force_stream) {
         static std::atomic<unsigned long long> attr_res{0};
         if (dev < 64 && !(attr_res.load() >> dev & 1ull)) {
-            if (cudaFuncSetAttribute(qldnn::conv3x3_fwd_tma_wres_kernel<N, SWB, SUB>,
-                                     cudaFuncAttributeMaxDynamicSharedMemorySize, 232448) != cudaSuccess)
+            if (cudaFuncSetAttribute(qldnn::conv3x3_fwd_tma_wres_kernel<N, SWB, SUB, MINB>,
+                                     cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_cap) != cudaSuccess)
                 return set_err(QLD_E_CUDA);
             attr_res.fetch_or(1ull << dev);
         }
-        if (launch_maybe_early(qldnn::conv3x3_fwd_tma_wres_kernel<N, SWB, SUB>, grid, qldnn::kConvThreads,
+        if (launch_maybe_early(qldnn::conv3x3_fwd_tma_wres_kernel<N, SWB, SUB, MINB>, grid, qldnn::kConvThreads,
                                (size_t)R::smem(sa, Cin),
                                st, early, mi, mw, bias, B, H, W, Cin, Cout, relu, epi, status, sa,
                                nsplit) != cudaSuccess)
             return set_err(QLD_E_CUDA);
         return launched(1);
     }
-    if constexpr (SUB != 1) return set_err(QLD_E_INVAL);  // the weight-streaming kernel has 8-row tiles
+    if constexpr (SUB != 1 || MINB != 1) return set_err(QLD_E_INVAL);  // the weight-streaming kernel: 8-row tiles
     static std::atomic<unsigned long long> attr_done{0};  // per instantiation, one bit per device
     if (dev < 64 && !(attr_done.load() >> dev & 1ull)) {
         if (cudaFuncSetAttribute(qldnn::conv3x3_fwd_tma_kernel<N, SWB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -911,6 +913,27 @@ int conv_tma_dispatch(const void* in, const void* wk, const float* bias, int B, 
     const bool fits2 = 1024 + 2ll * 3 * 18 * 16 * swb2 + 9ll * Cin * nco * 2 + 256 <= 232448;
     const bool sub2 = nsplit == 1 && nco <= 64 && !force_stream && !((mode >> 13) & 1) && fits2 &&
                       (((mode >> 12) & 1) || (tiles16 >= 2ll * nsm && swb2 == swb));
+    // two CTAs per SM for 32-channel layers (every CTA's MMA thread leaves
+    // gaps in the tensor-core queue that the other fills) of at least 32 input
+    // channels when the weights and two halo stages fit in half the shared
+    // memory, staged in chunks of at most 32 channels, with 16 x 16 tiles if
+    // those fit too; when each CTA gets at least two 8 x 16 tiles (mode bit
+    // 15 forces it where it fits, bit 14 forbids it). The 16-channel first
+    // layer, and a 256^2 layer with 1.7 tiles per CTA, measured slower that way.
+    auto fits_two = [&](int sub) {
+        return 1024 + 2ll * 3 * (8 * sub + 2) * 16 * swb2 + 9ll * Cin * nco * 2 + 256 <= qldnn::kTwoPerSmSmem;
+    };
+    const long long tiles8 = ntiles;
+    const bool two = nsplit == 1 && nco == 32 && !force_stream && !((mode >> 14) & 1) && fits_two(1) &&
+                     (((mode >> 15) & 1) || (Cin >= 32 && tiles8 >= 4ll * nsm));
+    if (two) {
+        const bool two_sub2 = !((mode >> 13) & 1) && fits_two(2) && (((mode >> 12) & 1) || tiles16 >= 4ll * nsm);
+        if (swb2 == 32)
+            return two_sub2 ? launch_tma<32, 32, 2, 2>(in, wk, bias, B, H, W, Cin, Cout, relu, epi, status, st, false, early)
+                            : launch_tma<32, 32, 1, 2>(in, wk, bias, B, H, W, Cin, Cout, relu, epi, status, st, false, early);
+        return two_sub2 ? launch_tma<32, 64, 2, 2>(in, wk, bias, B, H, W, Cin, Cout, relu, epi, status, st, false, early)
+                        : launch_tma<32, 64, 1, 2>(in, wk, bias, B, H, W, Cin, Cout, relu, epi, status, st, false, early);
+    }
 #define QLD_TMA2(NN, SS)                                                                                            \
     if (sub2 && nco == NN && swb2 == SS)                                                                               \
         return launch_tma<NN, SS, 2>(in, wk, bias, B, H, W, Cin, Cout, relu, epi, status, st, false, early);

@@ -573,8 +573,16 @@ struct TmaConvRes {
     }
 };
 
-template <int N, int SWB, int SUB = 1>
-__global__ void __launch_bounds__(kConvThreads, 1)
+// MINB = 2: two CTAs per SM (each within kTwoPerSmSmem of shared memory):
+// every MMA-issuing thread feeds a tensor-core queue about one MMA deep and
+// pauses for its barriers and commits; with two CTAs on an SM the other
+// CTA's MMAs fill those pauses (the narrow layers' MMAs take ~45 cycles, a
+// barrier probe ~100), and an early-launched next layer can start on an SM
+// while this one's second CTA still runs.
+constexpr int kTwoPerSmSmem = 115712;
+
+template <int N, int SWB, int SUB = 1, int MINB = 1>
+__global__ void __launch_bounds__(kConvThreads, MINB)
     conv3x3_fwd_tma_wres_kernel(const __grid_constant__ CUtensorMap map_in, const __grid_constant__ CUtensorMap map_w,
                                 const float* __restrict__ bias, int B, int H, int W, int Cin, int Cout, int relu,
                                 const ConvEpi epi, int* status, int SA, int nsplit) {

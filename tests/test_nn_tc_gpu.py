@@ -24,11 +24,14 @@ def _need_gpu():
 # splits small layers' output channels over several CTAs per tile;
 # "conv3x3_fwd_tma_stream" forces its weight-streaming variant, "..._split2" /
 # "..._split4" force 2 / 4 CTAs per tile, "..._sub2" 16 x 16-pixel tiles (two
-# stacked 8 x 16 sub-tiles), on every shape they apply to.
+# stacked 8 x 16 sub-tiles), "..._two" two CTAs per SM, on every shape they
+# apply to.
 KERNELS = ["conv3x3_fwd_tc", "conv3x3_fwd_tc2", "conv3x3_fwd_tma", "conv3x3_fwd_tma_stream",
-           "conv3x3_fwd_tma_split2", "conv3x3_fwd_tma_split4", "conv3x3_fwd_tma_sub2"]
+           "conv3x3_fwd_tma_split2", "conv3x3_fwd_tma_split4", "conv3x3_fwd_tma_sub2", "conv3x3_fwd_tma_two",
+           "conv3x3_fwd_tma_two_sub1"]
 MODES = {"conv3x3_fwd_tma_stream": 1, "conv3x3_fwd_tma_split2": 2 << 4, "conv3x3_fwd_tma_split4": 4 << 4,
-         "conv3x3_fwd_tma_sub2": 1 << 12}
+         "conv3x3_fwd_tma_sub2": 1 << 12, "conv3x3_fwd_tma_two": (1 << 15) | (1 << 12),
+         "conv3x3_fwd_tma_two_sub1": (1 << 15) | (1 << 13)}
 
 
 def _tc(kernel, Cout):
@@ -195,3 +198,28 @@ def test_tma_16x16_tiles_equal_8x16_tiles(B, H, W, Cin, Cout, relu):
         assert status.item() == 0
         outs.append((out_f.cpu(), out_b.cpu()))
     assert torch.equal(outs[0][0], outs[1][0]) and torch.equal(outs[0][1], outs[1][1])
+
+
+@pytest.mark.parametrize("B,H,W,Cin,Cout,relu", [(1, 64, 48, 32, 32, 1), (2, 33, 40, 16, 32, 0), (1, 48, 80, 96, 32, 1),
+                                                 (1, 17, 31, 48, 32, 1), (1, 7, 16, 32, 32, 0)])
+def test_tma_two_ctas_per_sm_equal_one(B, H, W, Cin, Cout, relu):
+    """Two CTAs per SM run the same tiles, MMAs and epilogue as one CTA per SM
+    with the same channel chunks and tile height: identical outputs, bit for
+    bit (Cin not a multiple of 64, so both stage chunks of at most 32)."""
+    rng = np.random.default_rng(H * W + Cin + 7)
+    x, _ = bf16(rng.standard_normal((B, H, W, Cin)))
+    w, _ = bf16(rng.standard_normal((3, 3, Cin, Cout)) / np.sqrt(9 * Cin))
+    bias = torch.from_numpy(rng.standard_normal(Cout).astype(np.float32)).cuda()
+    wk = torch.empty(9 * Cin * Cout, dtype=torch.bfloat16, device="cuda")
+    q.nn.kmajor_weights(w, Cin, Cout, 0, wk)
+    for sub in (1 << 12, 1 << 13):
+        outs = []
+        for two in (1 << 15, 1 << 14):
+            status = torch.zeros(1, dtype=torch.int32, device="cuda")
+            out_f = torch.full((B, H, W, Cout), float("nan"), dtype=torch.float32, device="cuda")
+            out_b = torch.empty((B, H, W, Cout), dtype=torch.bfloat16, device="cuda")
+            q.nn.conv3x3_fwd_tma_mode(x, wk, bias, B, H, W, Cin, Cout, relu, out_b, out_f, status, sub | two)
+            torch.cuda.synchronize()
+            assert status.item() == 0
+            outs.append((out_f.cpu(), out_b.cpu()))
+        assert torch.equal(outs[0][0], outs[1][0]) and torch.equal(outs[0][1], outs[1][1])
