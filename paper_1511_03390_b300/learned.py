@@ -359,13 +359,9 @@ def random_scene_tables(rng, H, W, device, bg=2000.0, maxv=4095):
         else:
             m = ((yy - cy) ** 2 + (xx - cx) ** 2) <= (size / 2) ** 2
         mask = torch.maximum(mask, m.float())
-    sig = 20.0
-    r = int(4 * sig)
-    t = torch.arange(-r, r + 1, device=device, dtype=torch.float32)
-    k = torch.exp(-0.5 * (t / sig) ** 2)
-    k = k / k.sum()
-    blur = torch.nn.functional.conv2d(mask[None, None], k[None, None, None, :], padding=(0, r))
-    blur = torch.nn.functional.conv2d(blur, k[None, None, :, None], padding=(r, 0))[0, 0]
+    from qldscene import blur_device
+
+    blur = blur_device(mask, 20.0)  # the scene generator's own separable CUDA blur
     diffuse = bg * (0.5 + 0.5 * blur / blur.max().clamp_min(1e-12))
     od = float(rng.uniform(4.0, 8.0))
     amp = bg * math.exp(-od)

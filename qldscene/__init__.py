@@ -40,6 +40,8 @@ def _load():
         lib.qs_generate.argtypes = [p, ctypes.c_int, ll, ll, ll, ctypes.c_int, p, p, p, p, ctypes.c_int,
                                     ctypes.c_uint, ctypes.c_uint, ctypes.c_int, p]
         lib.qs_generate.restype = ctypes.c_int
+        lib.qs_blur.argtypes = [p, p, p, ctypes.c_int, ctypes.c_int, p, ctypes.c_int, p]
+        lib.qs_blur.restype = ctypes.c_int
         _lib = lib
     return _lib
 
@@ -57,6 +59,31 @@ def generate_from_tables(out, pixfmt, npix, s_first, count, mu0, mu1, sd0, sd1, 
                              int(key[0]), int(key[1]), int(maxv), ctypes.c_void_p(st.cuda_stream))
     if rc != 0:
         raise RuntimeError("qs_generate failed with code %d" % rc)
+    return out
+
+
+def blur_device(img, sigma, stream=None):
+    """Gaussian blur (std `sigma` pixels, truncated at 4 sigma, zero
+    padding) of a contiguous float32 H x W CUDA tensor, by this package's own
+    separable kernel; returns a new tensor."""
+    import torch
+
+    import math
+
+    H, W = img.shape
+    r = int(math.ceil(4 * sigma))
+    t = torch.arange(-r, r + 1, device=img.device, dtype=torch.float64)
+    k = torch.exp(-0.5 * (t / sigma) ** 2)
+    taps = (k / k.sum()).to(torch.float32).contiguous()
+    src = img.contiguous().to(torch.float32)
+    tmp = torch.empty_like(src)
+    out = torch.empty_like(src)
+    st = stream if stream is not None else torch.cuda.current_stream(img.device)
+    rc = _load().qs_blur(ctypes.c_void_p(src.data_ptr()), ctypes.c_void_p(tmp.data_ptr()),
+                         ctypes.c_void_p(out.data_ptr()), int(H), int(W), ctypes.c_void_p(taps.data_ptr()), r,
+                         ctypes.c_void_p(st.cuda_stream))
+    if rc != 0:
+        raise RuntimeError("qs_blur failed with code %d" % rc)
     return out
 
 

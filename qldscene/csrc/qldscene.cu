@@ -65,9 +65,40 @@ __global__ void generate_kernel(T* __restrict__ out, long long npix, long long o
     }
 }
 
+// One pass of a separable blur with zero padding: out[y][x] = sum over
+// t = -r..r of taps[t + r] * in at (y, x + t) (rows) or (y + t, x) (columns).
+__global__ void blur_pass_kernel(const float* __restrict__ in, float* __restrict__ out, int H, int W,
+                                 const float* __restrict__ taps, int r, int along_rows) {
+    const long long n = (long long)H * W;
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x) {
+        const int y = (int)(e / W), x = (int)(e - (long long)y * W);
+        float acc = 0.f;
+        for (int t = -r; t <= r; ++t) {
+            const int yy = along_rows ? y : y + t, xx = along_rows ? x + t : x;
+            if (yy >= 0 && yy < H && xx >= 0 && xx < W) acc = fmaf(taps[t + r], in[(long long)yy * W + xx], acc);
+        }
+        out[e] = acc;
+    }
+}
+
 }  // namespace
 
 extern "C" {
+
+// Separable blur of an H x W float image on the device (zero padding): the
+// row pass into tmp, the column pass into out (each H x W floats; out may not
+// alias in or tmp). taps holds 2r + 1 device floats. Returns 0, -1 on bad
+// arguments, or the CUDA error code of the launches.
+int qs_blur(const float* in, float* tmp, float* out, int H, int W, const float* taps, int r, void* stream) {
+    if (!in || !tmp || !out || !taps || H < 1 || W < 1 || r < 0 || out == in || out == tmp || tmp == in) return -1;
+    const long long n = (long long)H * W;
+    long long blocks = (n + 255) / 256;
+    if (blocks > 148ll * 64) blocks = 148ll * 64;
+    cudaStream_t st = (cudaStream_t)stream;
+    blur_pass_kernel<<<(unsigned)blocks, 256, 0, st>>>(in, tmp, H, W, taps, r, 1);
+    blur_pass_kernel<<<(unsigned)blocks, 256, 0, st>>>(tmp, out, H, W, taps, r, 0);
+    return (int)cudaGetLastError();
+}
 
 // Writes frames s_first .. s_first+count-1 of the scene to out (device),
 // frame i at out + i*out_stride elements. pixfmt 1 = uint8, 2 = uint16.

@@ -53,3 +53,21 @@ def test_gpu_generator_matches_numpy(make):
     for s0, n in [(1, 9), (4093, 5), ((1 << 32) - 2, 4)]:
         got = ds.frames(s0, n).cpu().numpy().reshape(n, -1)
         assert np.array_equal(got, sc.frames(s0, n))
+
+
+@pytest.mark.gpu
+def test_device_blur_matches_the_numpy_blur():
+    """qldscene.blur_device (the learned simulator's blur) against the host
+    scene generator's Gaussian blur of the same mask."""
+    import torch
+
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from qldscene import blur_device
+    from qldscene.scene import _gauss_blur
+
+    rng = np.random.default_rng(3)
+    mask = (rng.random((96, 130)) < 0.1).astype(np.float64)
+    want = _gauss_blur(mask, 20.0)
+    got = blur_device(torch.from_numpy(mask.astype(np.float32)).cuda(), 20.0).cpu().numpy()
+    assert np.allclose(got, want, rtol=1e-4, atol=1e-6 * want.max())
