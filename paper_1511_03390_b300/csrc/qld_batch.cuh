@@ -29,6 +29,20 @@ struct BatchHeader {
     long long ntiles;  // sum over items of ceil(nvec / tile vectors)
 };
 
+// Most items one launch carries.
+constexpr int kMaxBatchItems = 64;
+
+// A tick's descriptors, passed by value as the kernel's parameter: they reach
+// every CTA through the constant cache with the launch itself, so a tick
+// needs no host-to-device copy before its kernel and a CTA's search for its
+// tile's item reads no global memory. ~9.5 KB, inside the 32 KB a kernel's
+// parameters may take.
+struct BatchParams {
+    BatchHeader hdr;
+    BatchItem items[kMaxBatchItems];
+};
+static_assert(sizeof(BatchParams) + 64 <= 32000, "batch descriptors exceed the kernel parameter space");
+
 template <typename T>
 __device__ __forceinline__ void push_vector_mode(const PushArgs& a, int reset, int epi, long long v) {
     if (reset) {
@@ -44,19 +58,18 @@ __device__ __forceinline__ void push_vector_mode(const PushArgs& a, int reset, i
 // b + gridDim.x, ... The item of a tile is found by binary search over the
 // items' tile0 (the same for every thread of the CTA, so no divergence).
 template <int NT, int VPT>
-__global__ void __launch_bounds__(NT) batch_push_kernel(const BatchHeader* __restrict__ hdr,
-                                                        const BatchItem* __restrict__ items, const int* gate) {
-    if (hdr->gated && *(volatile const int*)gate != 0) return;  // the doorbell wait ran out: no work
-    const int n = hdr->nitems;
-    const long long ntiles = hdr->ntiles;
+__global__ void __launch_bounds__(NT) batch_push_kernel(const __grid_constant__ BatchParams p, const int* gate) {
+    if (p.hdr.gated && *(volatile const int*)gate != 0) return;  // the doorbell wait ran out: no work
+    const int n = p.hdr.nitems;
+    const long long ntiles = p.hdr.ntiles;
     for (long long tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
         int lo = 0, hi = n - 1;
         while (lo < hi) {
             const int mid = (lo + hi + 1) >> 1;
-            if (items[mid].tile0 <= tile) lo = mid;
+            if (p.items[mid].tile0 <= tile) lo = mid;
             else hi = mid - 1;
         }
-        const BatchItem& it = items[lo];
+        const BatchItem& it = p.items[lo];
         const PushArgs a = it.a;
         const int fmt = it.fmt, reset = it.reset, epi = it.epi;
         const long long vbase = (tile - it.tile0) * (long long)(NT * VPT);
@@ -93,16 +106,16 @@ inline long long batch_tile_vectors(const BatchShape& s) { return (long long)s.t
 
 // `tiles`: the tiles a one-CTA-per-tile grid covers (unused by persistent
 // shapes).
-inline void launch_batch(const BatchShape& s, int num_sms, long long tiles, const BatchHeader* hdr,
-                         const BatchItem* items, const int* gate, cudaStream_t st) {
+inline void launch_batch(const BatchShape& s, int num_sms, long long tiles, const BatchParams& p, const int* gate,
+                         cudaStream_t st) {
     const unsigned grid = s.ctas_per_sm > 0 ? (unsigned)(num_sms * s.ctas_per_sm)
                                             : (unsigned)(tiles < 1 ? 1 : (tiles > 0x7FFFFFFF ? 0x7FFFFFFF : tiles));
-    if (s.threads == 128 && s.vpt == 1) batch_push_kernel<128, 1><<<grid, 128, 0, st>>>(hdr, items, gate);
-    else if (s.threads == 128 && s.vpt == 2) batch_push_kernel<128, 2><<<grid, 128, 0, st>>>(hdr, items, gate);
-    else if (s.threads == 128 && s.vpt == 4) batch_push_kernel<128, 4><<<grid, 128, 0, st>>>(hdr, items, gate);
-    else if (s.threads == 256 && s.vpt == 1) batch_push_kernel<256, 1><<<grid, 256, 0, st>>>(hdr, items, gate);
-    else if (s.threads == 256 && s.vpt == 2) batch_push_kernel<256, 2><<<grid, 256, 0, st>>>(hdr, items, gate);
-    else batch_push_kernel<64, 2><<<grid, 64, 0, st>>>(hdr, items, gate);
+    if (s.threads == 128 && s.vpt == 1) batch_push_kernel<128, 1><<<grid, 128, 0, st>>>(p, gate);
+    else if (s.threads == 128 && s.vpt == 2) batch_push_kernel<128, 2><<<grid, 128, 0, st>>>(p, gate);
+    else if (s.threads == 128 && s.vpt == 4) batch_push_kernel<128, 4><<<grid, 128, 0, st>>>(p, gate);
+    else if (s.threads == 256 && s.vpt == 1) batch_push_kernel<256, 1><<<grid, 256, 0, st>>>(p, gate);
+    else if (s.threads == 256 && s.vpt == 2) batch_push_kernel<256, 2><<<grid, 256, 0, st>>>(p, gate);
+    else batch_push_kernel<64, 2><<<grid, 64, 0, st>>>(p, gate);
 }
 
 // Bounded device wait on a doorbell before a gated tick: one thread polls

@@ -56,18 +56,18 @@ struct qld_server {
     int max_streams;
     std::vector<SrvStream> streams;  // index = ticket
     std::deque<int> waiting;         // tickets in arrival order
-    // descriptors: one block [header | items] on the device and two pinned
-    // host blocks (alternating ticks), so a tick copies them in one transfer
-    qldk::BatchHeader* hdr_dev;
-    qldk::BatchItem* items_dev;      // inside the hdr_dev block
-    qldk::BatchHeader* hdr_host[2];  // pinned
-    qldk::BatchItem* items_host[2];  // inside the hdr_host[b] blocks
+    // a tick's descriptors (alternating ticks), handed to the batch kernel as
+    // its parameter by updating the graph's kernel node: no copy to the device
+    qldk::BatchParams* prm[2];
     int* gate_dev;                   // outcome of a gated tick's doorbell wait
     cudaEvent_t gate_ev[2];          // after the doorbell wait, after the gated tick (timing)
     float last_gated_us;             // the last gated tick: doorbell seen -> images complete
     cudaEvent_t used[2];
     bool used_valid[2];
     cudaGraphExec_t graph[2];
+    cudaGraph_t graph_def[2];         // kept for their kernel nodes
+    cudaGraphNode_t node[2];          // the batch kernel of graph b
+    cudaKernelNodeParams node_prm[2]; // its function and launch shape
     bool graph_valid;
     long long graph_tiles;           // tiles the graphs' grid covers (one-CTA-per-tile shapes)
     cudaStream_t cap;
@@ -80,12 +80,7 @@ namespace {
 // Longest doorbell wait a gated tick accepts (10 s).
 constexpr long long kMaxGateNs = 10000000000ll;
 
-// Bytes of a descriptor block: the header (rounded up to 16 bytes), then the items.
-constexpr size_t kHdrBytes = (sizeof(qldk::BatchHeader) + 15) / 16 * 16;
-size_t desc_bytes(int max_streams) { return kHdrBytes + sizeof(qldk::BatchItem) * (size_t)max_streams; }
-qldk::BatchItem* items_of(qldk::BatchHeader* h) {
-    return reinterpret_cast<qldk::BatchItem*>(reinterpret_cast<unsigned char*>(h) + kHdrBytes);
-}
+static_assert(QLD_SERVER_MAX_STREAMS <= qldk::kMaxBatchItems, "a tick's descriptors must fit its kernel parameter");
 
 int active_count(const qld_server* s) {
     int n = 0;
@@ -191,32 +186,53 @@ void check_graph_grid(qld_server* s, long long tick_tiles) {
     }
 }
 
+void free_graphs(qld_server* s) {
+    for (int b = 0; b < 2; ++b) {
+        if (s->graph[b]) cudaGraphExecDestroy(s->graph[b]);
+        if (s->graph_def[b]) cudaGraphDestroy(s->graph_def[b]);
+        s->graph[b] = nullptr;
+        s->graph_def[b] = nullptr;
+        s->node[b] = nullptr;
+    }
+}
+
+// Captures the two tick graphs (one batch kernel node each) for the current
+// launch shape; a tick then only sets that node's parameter.
 int ensure_graphs(qld_server* s) {
     if (s->graph_valid) return QLD_OK;
+    free_graphs(s);
     s->graph_tiles = admitted_tiles(s);
     for (int b = 0; b < 2; ++b) {
-        if (s->graph[b]) {
-            cudaGraphExecDestroy(s->graph[b]);
-            s->graph[b] = nullptr;
-        }
         cudaGraph_t g = nullptr;
         if (cudaStreamBeginCapture(s->cap, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return QLD_E_CUDA;
-        cudaMemcpyAsync(s->hdr_dev, s->hdr_host[b], desc_bytes(s->max_streams), cudaMemcpyHostToDevice, s->cap);
-        qldk::launch_batch(qldk::kBatchShapes[s->shape], s->num_sms, s->graph_tiles, s->hdr_dev, s->items_dev,
-                           s->gate_dev, s->cap);
+        qldk::launch_batch(qldk::kBatchShapes[s->shape], s->num_sms, s->graph_tiles, *s->prm[b], s->gate_dev, s->cap);
         if (cudaStreamEndCapture(s->cap, &g) != cudaSuccess || !g) {
             cudaGetLastError();
             return QLD_E_CUDA;
         }
-        const cudaError_t e = cudaGraphInstantiate(&s->graph[b], g, 0);
-        cudaGraphDestroy(g);
-        if (e != cudaSuccess) {
+        s->graph_def[b] = g;
+        size_t nn = 1;
+        cudaGraphNode_t nd = nullptr;
+        if (cudaGraphGetNodes(g, &nd, &nn) != cudaSuccess || nn != 1 || !nd ||
+            cudaGraphKernelNodeGetParams(nd, &s->node_prm[b]) != cudaSuccess ||
+            cudaGraphInstantiate(&s->graph[b], g, 0) != cudaSuccess) {
             cudaGetLastError();
+            free_graphs(s);
             return QLD_E_CUDA;
         }
+        s->node[b] = nd;
     }
     s->graph_valid = true;
     return QLD_OK;
+}
+
+// Hands the descriptors in s->prm[b] to graph b's kernel (copied by the call).
+int set_tick_params(qld_server* s, int b) {
+    void* args[2] = {s->prm[b], &s->gate_dev};
+    cudaKernelNodeParams kp = s->node_prm[b];
+    kp.kernelParams = args;
+    kp.extra = nullptr;
+    return cudaGraphExecKernelNodeSetParams(s->graph[b], s->node[b], &kp) == cudaSuccess ? QLD_OK : QLD_E_CUDA;
 }
 
 SrvStream* get_stream(qld_server* s, int ticket) {
@@ -237,15 +253,14 @@ qld_server* qld_server_create(long long hbm_budget_bytes, int max_streams) {
     s->budget = hbm_budget_bytes;
     s->in_use = 0;
     s->max_streams = max_streams;
-    s->hdr_dev = nullptr;
-    s->items_dev = nullptr;
+    s->prm[0] = s->prm[1] = nullptr;
     s->gate_dev = nullptr;
     s->gate_ev[0] = s->gate_ev[1] = nullptr;
     s->last_gated_us = -1.f;
-    s->hdr_host[0] = s->hdr_host[1] = nullptr;
-    s->items_host[0] = s->items_host[1] = nullptr;
     s->used_valid[0] = s->used_valid[1] = false;
     s->graph[0] = s->graph[1] = nullptr;
+    s->graph_def[0] = s->graph_def[1] = nullptr;
+    s->node[0] = s->node[1] = nullptr;
     s->graph_valid = false;
     s->graph_tiles = 0;
     s->cap = nullptr;
@@ -253,18 +268,13 @@ qld_server* qld_server_create(long long hbm_budget_bytes, int max_streams) {
     s->flip = 0;
     bool ok = cudaGetDevice(&s->device) == cudaSuccess &&
               cudaDeviceGetAttribute(&s->num_sms, cudaDevAttrMultiProcessorCount, s->device) == cudaSuccess &&
-              cudaMalloc(&s->hdr_dev, desc_bytes(max_streams)) == cudaSuccess &&
               cudaMalloc(&s->gate_dev, 16) == cudaSuccess && cudaMemset(s->gate_dev, 0, 16) == cudaSuccess &&
               cudaEventCreate(&s->gate_ev[0]) == cudaSuccess && cudaEventCreate(&s->gate_ev[1]) == cudaSuccess &&
               cudaStreamCreateWithFlags(&s->cap, cudaStreamNonBlocking) == cudaSuccess;
-    if (ok) s->items_dev = items_of(s->hdr_dev);
     for (int b = 0; ok && b < 2; ++b) {
-        ok = cudaHostAlloc(&s->hdr_host[b], desc_bytes(max_streams), cudaHostAllocDefault) == cudaSuccess &&
-             cudaEventCreateWithFlags(&s->used[b], cudaEventDisableTiming) == cudaSuccess;
-        if (ok) {
-            s->items_host[b] = items_of(s->hdr_host[b]);
-            std::memset(s->hdr_host[b], 0, desc_bytes(max_streams));
-        }
+        s->prm[b] = new qldk::BatchParams();
+        std::memset(s->prm[b], 0, sizeof(qldk::BatchParams));
+        ok = cudaEventCreateWithFlags(&s->used[b], cudaEventDisableTiming) == cudaSuccess;
     }
     if (!ok) {
         cudaGetLastError();
@@ -279,12 +289,11 @@ void qld_server_destroy(qld_server* s) {
     if (!s) return;
     wait_ticks(s);
     for (SrvStream& t : s->streams) release_stream(s, t);
+    free_graphs(s);
     for (int b = 0; b < 2; ++b) {
-        if (s->graph[b]) cudaGraphExecDestroy(s->graph[b]);
-        if (s->hdr_host[b]) cudaFreeHost(s->hdr_host[b]);
+        delete s->prm[b];
         if (s->used[b]) cudaEventDestroy(s->used[b]);
     }
-    if (s->hdr_dev) cudaFree(s->hdr_dev);
     if (s->gate_dev) cudaFree(s->gate_dev);
     for (int e = 0; e < 2; ++e)
         if (s->gate_ev[e]) cudaEventDestroy(s->gate_ev[e]);
@@ -373,10 +382,11 @@ int qld_server_tick(qld_server* s, void* stream) {
     const int b = s->flip;
     if (s->used_valid[b] && cudaEventSynchronize(s->used[b]) != cudaSuccess) return set_err(QLD_E_CUDA);
     std::vector<int> which;
-    const int n = build_items(s, s->items_host[b], s->hdr_host[b], &which);
+    const int n = build_items(s, s->prm[b]->items, &s->prm[b]->hdr, &which);
     if (n == 0) return 0;
-    check_graph_grid(s, s->hdr_host[b]->ntiles);
+    check_graph_grid(s, s->prm[b]->hdr.ntiles);
     int rc = ensure_graphs(s);
+    if (rc == QLD_OK) rc = set_tick_params(s, b);
     if (rc != QLD_OK) return set_err(rc);
     if (cudaGraphLaunch(s->graph[b], st) != cudaSuccess || cudaEventRecord(s->used[b], st) != cudaSuccess)
         return set_err(QLD_E_CUDA);
@@ -401,11 +411,12 @@ int qld_server_tick_gated(qld_server* s, void* stream, const int* doorbell, int 
     wait_ticks(s);
     const int b = s->flip;
     std::vector<int> which;
-    const int n = build_items(s, s->items_host[b], s->hdr_host[b], &which);
+    const int n = build_items(s, s->prm[b]->items, &s->prm[b]->hdr, &which);
     if (n == 0) return 0;
-    s->hdr_host[b]->gated = 1;
-    check_graph_grid(s, s->hdr_host[b]->ntiles);
+    s->prm[b]->hdr.gated = 1;
+    check_graph_grid(s, s->prm[b]->hdr.ntiles);
     int rc = ensure_graphs(s);
+    if (rc == QLD_OK) rc = set_tick_params(s, b);
     if (rc != QLD_OK) return set_err(rc);
     qldk::doorbell_gate_kernel<<<1, 32, 0, st>>>(doorbell, target, timeout_ns, s->gate_dev);
     if (cudaGetLastError() != cudaSuccess || cudaEventRecord(s->gate_ev[0], st) != cudaSuccess ||
@@ -526,18 +537,11 @@ int qld_server_autotune(qld_server* s, void* stream, float* best_us) {
         rep.push_back(r);
     }
     if (rep.empty()) return set_err(QLD_E_NOT_READY);
-    qldk::BatchHeader* hdr = nullptr;
-    qldk::BatchItem* items = nullptr;
-    qldk::BatchHeader* hh = nullptr;
-    qldk::BatchItem* ih = nullptr;
+    qldk::BatchParams* pp = new qldk::BatchParams();
+    std::memset(pp, 0, sizeof(*pp));
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     int rc = QLD_OK;
-    if (cudaMalloc(&hdr, sizeof(*hdr)) != cudaSuccess ||
-        cudaMalloc(&items, sizeof(qldk::BatchItem) * rep.size()) != cudaSuccess ||
-        cudaHostAlloc(&hh, sizeof(*hh), cudaHostAllocDefault) != cudaSuccess ||
-        cudaHostAlloc(&ih, sizeof(qldk::BatchItem) * rep.size(), cudaHostAllocDefault) != cudaSuccess ||
-        cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess)
-        rc = QLD_E_NOMEM;
+    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) rc = QLD_E_NOMEM;
     const int saved_shape = s->shape;
     float best = 1e30f;
     int best_shape = saved_shape;
@@ -549,19 +553,14 @@ int qld_server_autotune(qld_server* s, void* stream, float* best_us) {
         const int warm = 3, reps = 12;
         for (int it = 0; it < warm + reps && rc == QLD_OK; ++it) {
             for (SrvStream& r : probe.streams) r.pending_count = 1;
-            build_items(&probe, ih, hh, nullptr);
+            build_items(&probe, pp->items, &pp->hdr, nullptr);
             // frame (it mod 8) of each replica's 8-frame scratch: consecutive
             // launches read different frames and write different slots
-            for (int i = 0; i < hh->nitems; ++i)
-                ih[i].a.frames = (const uint8_t*)probe.streams[i].pending + (it % 8) * probe.streams[i].ctx->frame_bytes;
-            if (cudaMemcpyAsync(hdr, hh, sizeof(*hh), cudaMemcpyHostToDevice, st) != cudaSuccess ||
-                cudaMemcpyAsync(items, ih, sizeof(qldk::BatchItem) * rep.size(), cudaMemcpyHostToDevice, st) !=
-                    cudaSuccess) {
-                rc = QLD_E_CUDA;
-                break;
-            }
+            for (int i = 0; i < pp->hdr.nitems; ++i)
+                pp->items[i].a.frames =
+                    (const uint8_t*)probe.streams[i].pending + (it % 8) * probe.streams[i].ctx->frame_bytes;
             cudaEventRecord(e0, st);
-            qldk::launch_batch(qldk::kBatchShapes[k], s->num_sms, hh->ntiles, hdr, items, s->gate_dev, st);
+            qldk::launch_batch(qldk::kBatchShapes[k], s->num_sms, pp->hdr.ntiles, *pp, s->gate_dev, st);
             cudaEventRecord(e1, st);
             if (cudaEventSynchronize(e1) != cudaSuccess) {
                 rc = QLD_E_CUDA;
@@ -582,10 +581,7 @@ int qld_server_autotune(qld_server* s, void* stream, float* best_us) {
         cudaFree((void*)r.pending);
         release_stream(s, r);
     }
-    if (hdr) cudaFree(hdr);
-    if (items) cudaFree(items);
-    if (hh) cudaFreeHost(hh);
-    if (ih) cudaFreeHost(ih);
+    delete pp;
     if (e0) cudaEventDestroy(e0);
     if (e1) cudaEventDestroy(e1);
     if (rc != QLD_OK) {
