@@ -17,6 +17,7 @@
 #include <cuda_runtime.h>
 
 #include "qld.h"
+#include "qld_block.cuh"
 #include "qld_kernels.cuh"
 
 #include "qld_internal.h"
@@ -159,6 +160,29 @@ int enqueue_push(qld_ctx* c, const uint8_t* frames, long long pitch, int count, 
     const int vb = vec_bytes_of(c->pixfmt);
     const bool vec = aligned(a.frames, vec_align_of(c->pixfmt)) && (frame_bytes % vb) == 0 &&
                      (pitch % vec_align_of(c->pixfmt)) == 0;
+    // A window rebuilt from the pushed frames alone in a frame of at most
+    // 2^20 pixels: the block-mode kernel, whose threads split the frames into
+    // time slices (the vector kernel would have too few threads, each walking
+    // every frame).
+    const int hb = c->pixfmt == QLD_U16 ? 16 : (c->pixfmt == QLD_U8 ? 8 : 12);  // 8-pixel vector bytes
+    if (reset && c->npix <= (1ll << 20) && aligned(a.frames, 16) && (pitch % 16) == 0 && (frame_bytes % hb) == 0) {
+        a.nvec = frame_bytes / hb;
+        const unsigned grid = (unsigned)((a.nvec + qldk::kBlockPV - 1) / qldk::kBlockPV);
+        g_launches.fetch_add(1);
+        if (c->pixfmt == QLD_U16) {
+            if (epi) qldk::block_push_kernel<uint16_t, true><<<grid, qldk::kBlockThreads, 0, c->stream>>>(a);
+            else qldk::block_push_kernel<uint16_t, false><<<grid, qldk::kBlockThreads, 0, c->stream>>>(a);
+        } else if (c->pixfmt == QLD_U8) {
+            if (epi) qldk::block_push_kernel<qldk::u8h_t, true><<<grid, qldk::kBlockThreads, 0, c->stream>>>(a);
+            else qldk::block_push_kernel<qldk::u8h_t, false><<<grid, qldk::kBlockThreads, 0, c->stream>>>(a);
+        } else {
+            if (epi) qldk::block_push_kernel<qldk::p12h_t, true><<<grid, qldk::kBlockThreads, 0, c->stream>>>(a);
+            else qldk::block_push_kernel<qldk::p12h_t, false><<<grid, qldk::kBlockThreads, 0, c->stream>>>(a);
+        }
+        if (cudaGetLastError() != cudaSuccess) return QLD_E_CUDA;
+        c->pushed += count;
+        return QLD_OK;
+    }
     a.nvec = vec ? frame_bytes / vb : c->npix;
     g_launches.fetch_add(1);
     if (reset) {

@@ -301,3 +301,31 @@ def test_pipelined_host_path_many_steps_without_sync():
         assert np.array_equal(outs[i][0].numpy(), amp) and np.array_equal(outs[i][1].numpy(), ph), i
         assert np.array_equal(outs[i][2].numpy(), get_bin(ref.ctx, 3)), i
     ctx.destroy()
+
+
+@pytest.mark.parametrize("H,W,fmt,N", [(128, 128, 1, 64), (37, 40, 2, 16), (30, 64, 3, 8), (64, 96, 1, 256),
+                                       (5, 24, 2, 4), (256, 256, 2, 256)])
+def test_block_push_equals_the_scalar_path_and_the_oracle(H, W, fmt, N):
+    """Pushes of at least N frames into frames of at most 2^20 pixels run the
+    block-mode kernel (time slices reduced in shared memory) when the frames
+    are 16-byte aligned; the same frames a few bytes off run the one-pixel
+    scalar kernel. Sums, images and DFT bins agree bit for bit, and with the
+    oracle; both plain and fused pushes, exactly N and more than N frames, and
+    sliding pushes afterwards."""
+    rng = np.random.default_rng(H * W + N + fmt)
+    a, b = Stream(H, W, N, fmt), Stream(H, W, N, fmt)
+    try:
+        for count, fused in [(N, True), (N + 5, False), (3, False), (2 * N + 1, True), (1, True)]:
+            x = rand_frames(rng, count, H, W, fmt)
+            ra = a.push(x, offset=0, fused=fused)
+            rb = b.push(x, offset={1: 1, 2: 2, 3: 4}[fmt], fused=fused)
+            if fused:
+                assert np.array_equal(ra[0], rb[0]) and np.array_equal(ra[1], rb[1])
+            Sa, Ca = get_iq(a.ctx)
+            Sb, Cb = get_iq(b.ctx)
+            assert np.array_equal(Sa, Sb) and np.array_equal(Ca, Cb)
+            a.check(bins=(N // 4, 1))
+        assert np.array_equal(get_bin(a.ctx, 3 % N), get_bin(b.ctx, 3 % N))
+    finally:
+        a.ctx.destroy()
+        b.ctx.destroy()
