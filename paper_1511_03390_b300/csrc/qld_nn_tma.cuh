@@ -224,7 +224,7 @@ __device__ __forceinline__ void tc_tie16(uint32_t* r) {
 constexpr int kEpiWarps = 4;
 constexpr int kConvThreads = 64 + 32 * kEpiWarps;
 
-template <int N, int SUB = 1>
+template <int N, int SUB = 1, bool BIAS_REG = (N <= 64)>
 __device__ __forceinline__ void conv_epilogue(uint32_t tmem, uint64_t* tfull, uint64_t* tempty, volatile int* fail,
                                               int warp, int lane, int ntiles, int tiles_x, int tiles_y, int H, int W,
                                               int Cout, const float* __restrict__ bias, int relu, ConvEpi epi,
@@ -249,8 +249,8 @@ __device__ __forceinline__ void conv_epilogue(uint32_t tmem, uint64_t* tfull, ui
         return rr & 2 ? b : a;
     };
     constexpr int G = N < 64 ? N : 64;  // accumulator columns per tcgen05.wait::ld
-    float bres[N <= 64 ? N : 1];        // the bias (or 0), for narrow layers
-    if constexpr (N <= 64) {
+    float bres[BIAS_REG ? N : 1];       // the bias (or 0), for narrow layers
+    if constexpr (BIAS_REG) {
 #pragma unroll
         for (int j = 0; j < N; ++j) bres[j] = bias ? bias[j] : 0.f;
     }
@@ -284,7 +284,7 @@ __device__ __forceinline__ void conv_epilogue(uint32_t tmem, uint64_t* tfull, ui
 #pragma unroll
                     for (int j = 0; j < 16; ++j) {
                         float bj;
-                        if constexpr (N <= 64) bj = bres[c + j];  // g0 == 0
+                        if constexpr (BIAS_REG) bj = bres[c + j];  // g0 == 0
                         else bj = bias ? bias[c0 + j] : 0.f;
                         v[j] = __uint_as_float(rr[j]) + bj;
                         if (relu) v[j] = fmaxf(v[j], 0.f);
@@ -716,8 +716,10 @@ __global__ void __launch_bounds__(kConvThreads, MINB)
             wait_timed(drain, 0, nullptr);
         }
     } else {
-        conv_epilogue<N, SUB>(tmem, tfull, tempty, fail, warp, lane, ntiles, tiles_x, tiles_y, H, W, Cout, bias, relu,
-                              epi, nsplit);
+        // two CTAs per SM leave 168 registers a thread: the bias of a 64-column
+        // layer is then read from memory
+        conv_epilogue<N, SUB, (MINB == 1 ? N <= 64 : N <= 32)>(tmem, tfull, tempty, fail, warp, lane, ntiles, tiles_x,
+                                                                tiles_y, H, W, Cout, bias, relu, epi, nsplit);
     }
 
     tc_fence_before();

@@ -201,7 +201,8 @@ def test_tma_16x16_tiles_equal_8x16_tiles(B, H, W, Cin, Cout, relu):
 
 
 @pytest.mark.parametrize("B,H,W,Cin,Cout,relu", [(1, 64, 48, 32, 32, 1), (2, 33, 40, 16, 32, 0), (1, 48, 80, 96, 32, 1),
-                                                 (1, 17, 31, 48, 32, 1), (1, 7, 16, 32, 32, 0)])
+                                                 (1, 17, 31, 48, 32, 1), (1, 7, 16, 32, 32, 0), (1, 64, 48, 32, 64, 1),
+                                                 (2, 33, 40, 16, 64, 0)])
 def test_tma_two_ctas_per_sm_equal_one(B, H, W, Cin, Cout, relu):
     """Two CTAs per SM run the same tiles, MMAs and epilogue as one CTA per SM
     with the same channel chunks and tile height: identical outputs, bit for
