@@ -829,7 +829,7 @@ def run_plain_c1(q, torch, dev, st, peak, calls=2000, samples=1000):
     del pool1
 
     def pct(v, f):
-        return v[min(len(v) - 1, int(f * len(v)))]
+        return v[min(len(v) - 1, int(f * len(v)))] if v else None
 
     return {"workload": "plain scene, 128x128 uint8, N=64 block mode (one image per 64 new frames), seed 1001",
             "eager": {"us_per_call": us_eager, "gpf_s": pf / (us_eager * 1e-6) / 1e9,

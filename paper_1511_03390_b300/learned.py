@@ -535,7 +535,31 @@ def main(argv=None):
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--init", default=None, help="weights to start from")
     ap.add_argument("--out", default=None)
+    ap.add_argument("--forward", type=int, default=0, metavar="SIZE",
+                    help="only time the inference forward of the committed weights on SIZE x SIZE inputs "
+                         "(random short-window sums, the network as one CUDA graph) and exit")
     a = ap.parse_args(argv)
+    if a.forward:
+        dev = torch.device("cuda")
+        prm = load(WEIGHTS, dev)
+        net = UNet(prm, 1, a.forward, a.forward, inference_only=True).capture()
+        g = torch.Generator(device=dev).manual_seed(a.seed)
+        npix = a.forward * a.forward
+        net.S_in.copy_(torch.randint(-3000, 3000, (npix,), dtype=torch.int32, device=dev, generator=g))
+        net.C_in.copy_(torch.randint(-3000, 3000, (npix,), dtype=torch.int32, device=dev, generator=g))
+        for _ in range(3):
+            net.replay()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(20):
+            net.replay()
+        e1.record()
+        e1.synchronize()
+        ms = e0.elapsed_time(e1) / 20
+        flops = 2.0 * npix * sum(9 * ci * co / 4 ** LEVEL[n[:2]] for n, ci, co in LAYERS)
+        print(json.dumps({"event": "forward", "size": a.forward, "ms": ms, "tflops": flops / ms / 1e9,
+                          "status": int(net.status.item())}), flush=True)
+        return
     t0 = time.time()
     S, C, T, ods = make_dataset(a.stacks, a.size, a.size, seed=a.seed)
     Se, Ce, Te, odse = make_dataset(a.eval_stacks, a.size, a.size, seed=a.seed + 99991)
