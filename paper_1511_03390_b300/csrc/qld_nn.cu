@@ -898,6 +898,14 @@ int conv_tma_dispatch(const void* in, const void* wk, const float* bias, int B, 
     int nsplit = 1;
     for (int cand = 2; cand <= 4 && 2 * ntiles <= nsm && ntiles * nsplit < nsm; cand *= 2)
         if (Cout / cand >= 32 && resident(Cout / cand)) nsplit = cand;
+    // 128-column layers of at most 128 input channels with at most one tile
+    // per SM: two CTAs per tile (four when even that leaves 4 tiles per SM
+    // free), measured faster whether or not the 64-column slices' weights
+    // stay resident (128^2 at batch 1: 64 -> 128 8.95 -> 6.7 us, 128 -> 128
+    // 10.5 -> 9.7 us; 8 x 32^2, 128 -> 128 8.5 -> 7.3 us with two instead of
+    // four); layers of 256 input channels and 64-column layers measured
+    // slower split
+    if (Cout == 128 && Cin <= 128 && ntiles <= nsm) nsplit = 4 * ntiles <= nsm ? 4 : 2;
     if (split_mode > 0) nsplit = split_mode;
     if (Cout % nsplit || Cout / nsplit < 32) return set_err(QLD_E_INVAL);
     const int nco = Cout / nsplit;
