@@ -451,24 +451,15 @@ int qldnn_conv3x3_fwd_tma(const void* in, const void* wk, const float* bias, int
  * other's pauses for barriers). mode bit 0 set: always stream the weights;
  * mode >> 4 (0 = automatic, else 1, 2 or 4): the CTAs per tile; bit 12 /
  * bit 13: force / forbid 16 x 16-pixel tiles where they fit; bit 14 / bit 15:
- * forbid / force two CTAs per SM where they fit. For tests and measurements
- * of every variant. */
+ * forbid / force two CTAs per SM where they fit; bit 16 / bit 17: ask for /
+ * forbid the column-stacked form for 32- and 64-channel slices with resident
+ * weights (the three column taps kx of a tap row as one MMA of 3 x the
+ * slice's columns against an unshifted halo, tiles 14 columns wide, the
+ * three column groups added in the epilogue: (D_0 + D_1) + D_2, FP32). For
+ * tests and measurements of every variant. */
 int qldnn_conv3x3_fwd_tma_mode(const void* in, const void* wk, const float* bias, int B, int H, int W, int Cin,
                                int Cout, int relu, void* out_bf16, float* out_f32, int* status, int mode,
                                void* stream);
-/* The persistent TMA convolution with the layer's neighbours fused into its
- * epilogue (inference of the learned network). Any of:
- *   out_bf16  the activation, rows of ldo >= Cout channels (a multiple of 8):
- *             with ldo > Cout it fills a channel slice of a concatenated tensor
- *   pool_bf16 [B][H/2][W/2][Cout], the 2x2 average of the bf16 activation
- *             (H and W even)
- *   up_bf16   [B][2H][2W], rows of ldu channels: the nearest 2x upsampling,
- *             e.g. into the first channels of the next level's skip concat
- *   head      pred [B][H][W] f32 = head_b[0] + sum_c act[c] head_w[c] +
- *             baseline[p] (head_w [Cout], head_b, baseline, pred all given)
- * The pooled, upsampled and head outputs equal qldnn_avgpool2,
- * qldnn_upsample_concat and qldnn_head + qldnn_add on the bf16 activation bit
- * for bit. Pointers 16-byte aligned. */
 /* Self-test of the failure path shared by the tcgen05 kernels' bounded waits
  * (the paper has no counterpart): one role waits on an mbarrier nothing ever
  * arrives on for limit_ns (1 us .. 2 s) and must time out and raise the
@@ -486,10 +477,31 @@ int qldnn_wait_selftest(long long limit_ns, long long* out, void* stream);
  * this layer's weights or bias (inference); the layer-to-layer gaps of a
  * network then overlap. Other flag bits: QLD_E_INVAL. */
 #define QLDNN_EARLY_LAUNCH 1
+/* The persistent TMA convolution with the layer's neighbours fused into its
+ * epilogue (inference of the learned network). Any of:
+ *   out_bf16  the activation, rows of ldo >= Cout channels (a multiple of 8):
+ *             with ldo > Cout it fills a channel slice of a concatenated tensor
+ *   pool_bf16 [B][H/2][W/2][Cout], the 2x2 average of the bf16 activation
+ *             (H and W even)
+ *   up_bf16   [B][2H][2W], rows of ldu channels: the nearest 2x upsampling,
+ *             e.g. into the first channels of the next level's skip concat
+ *   head      pred [B][H][W] f32 = head_b[0] + sum_c act[c] head_w[c] +
+ *             baseline[p] (head_w [Cout], head_b, baseline, pred all given)
+ * The pooled, upsampled and head outputs equal qldnn_avgpool2,
+ * qldnn_upsample_concat and qldnn_head + qldnn_add on the bf16 activation bit
+ * for bit. Pointers 16-byte aligned. */
 int qldnn_conv3x3_fwd_tma_epi(const void* in, const void* wk, const float* bias, int B, int H, int W, int Cin,
                               int Cout, int relu, void* out_bf16, long long ldo, void* pool_bf16, void* up_bf16,
                               long long ldu, const float* head_w, const float* head_b, const float* baseline,
                               float* pred, int* status, int flags, void* stream);
+/* The same with the kernel variant chosen by the caller: mode bit 0 and bits
+ * 12-17 as in qldnn_conv3x3_fwd_tma_mode (the CTAs per tile stay the layer's
+ * own; other bits: QLD_E_INVAL). For tests and measurements of every variant
+ * with fused outputs. */
+int qldnn_conv3x3_fwd_tma_epi_mode(const void* in, const void* wk, const float* bias, int B, int H, int W, int Cin,
+                                   int Cout, int relu, void* out_bf16, long long ldo, void* pool_bf16, void* up_bf16,
+                                   long long ldu, const float* head_w, const float* head_b, const float* baseline,
+                                   float* pred, int* status, int flags, int mode, void* stream);
 /* Weight gradient of the 3x3 convolution on the tensor cores: dw [9][Cin][Cout]
  * f32 += sum over pixels of in (shifted by the tap) x g, in [B][H][W][Cin]
  * and g [B][H][W][Cout] bf16 (the caller zeroes dw; 16-byte aligned). Cin is

@@ -99,6 +99,8 @@ _SIGS = {
     "qldnn_input_conv3x3": ([_p, _p, _i, _i, _i, ctypes.c_float, _p, _i, _i, _p, _i, _p, _ll, _p, _p], _i),
     "qldnn_conv3x3_fwd_tma_epi": ([_p, _p, _p, _i, _i, _i, _i, _i, _i, _p, _ll, _p, _p, _ll, _p, _p, _p, _p, _p, _i, _p],
                                   _i),
+    "qldnn_conv3x3_fwd_tma_epi_mode": ([_p, _p, _p, _i, _i, _i, _i, _i, _i, _p, _ll, _p, _p, _ll, _p, _p, _p, _p, _p,
+                                        _i, _i, _p], _i),
     "qldnn_conv3x3_wgrad_tma": ([_p, _p, _i, _i, _i, _i, _i, _p, _p, _p], _i),
     "qld_server_create": ([_ll, _i], _p),
     "qld_server_destroy": ([_p], None),

@@ -752,7 +752,7 @@ cudaError_t launch_maybe_early(void (*kernel)(KArgs...), unsigned grid, unsigned
     return cudaLaunchKernelEx(&cfg, kernel, args...);
 }
 
-template <int N, int SWB, int SUB = 1, int MINB = 1>
+template <int N, int SWB, int SUB = 1, int MINB = 1, bool XS = false>
 int launch_tma(const void* in, const void* wk, const float* bias, int B, int H, int W, int Cin, int Cout, int relu,
                const qldnn::ConvEpi& epi, int* status, cudaStream_t st, bool force_stream, bool early) {
     using L = qldnn::TmaConv<N, SWB>;
@@ -779,33 +779,34 @@ int launch_tma(const void* in, const void* wk, const float* bias, int B, int H, 
             CU_TENSOR_MAP_INTERLEAVE_NONE, sw, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
         return set_err(QLD_E_CUDA);
-    const long long ntiles = (long long)B * ((H + 8 * SUB - 1) / (8 * SUB)) * ((W + 15) / 16);
+    using R = qldnn::TmaConvRes<N, SWB, SUB, XS>;
+    const long long ntiles = (long long)B * ((H + 8 * SUB - 1) / (8 * SUB)) * ((W + R::TW - 1) / R::TW);
     const int nsplit = Cout / N;  // CTAs per tile, one output-channel slice each
     long long items = ntiles * nsplit;
     const long long cap = (long long)(MINB * nsm / nsplit) * nsplit;
     const unsigned grid = (unsigned)(items < cap ? items : cap);
     // weights resident in shared memory when they fit beside two or more halo
     // stages (within half of it for two CTAs per SM)
-    using R = qldnn::TmaConvRes<N, SWB, SUB>;
     const long long smem_cap = MINB == 2 ? qldnn::kTwoPerSmSmem : 232448;
     int sa = 0;
     while (sa < R::kMaxSA && R::smem(sa + 1, Cin) <= smem_cap) ++sa;
     if (sa >= 2 && !force_stream) {
         static std::atomic<unsigned long long> attr_res{0};
         if (dev < 64 && !(attr_res.load() >> dev & 1ull)) {
-            if (cudaFuncSetAttribute(qldnn::conv3x3_fwd_tma_wres_kernel<N, SWB, SUB, MINB>,
+            if (cudaFuncSetAttribute(qldnn::conv3x3_fwd_tma_wres_kernel<N, SWB, SUB, MINB, XS>,
                                      cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_cap) != cudaSuccess)
                 return set_err(QLD_E_CUDA);
             attr_res.fetch_or(1ull << dev);
         }
-        if (launch_maybe_early(qldnn::conv3x3_fwd_tma_wres_kernel<N, SWB, SUB, MINB>, grid, qldnn::kConvThreads,
+        if (launch_maybe_early(qldnn::conv3x3_fwd_tma_wres_kernel<N, SWB, SUB, MINB, XS>, grid, qldnn::kConvThreads,
                                (size_t)R::smem(sa, Cin),
                                st, early, mi, mw, bias, B, H, W, Cin, Cout, relu, epi, status, sa,
                                nsplit) != cudaSuccess)
             return set_err(QLD_E_CUDA);
         return launched(1);
     }
-    if constexpr (SUB != 1 || MINB != 1) return set_err(QLD_E_INVAL);  // the weight-streaming kernel: 8-row tiles
+    // the weight-streaming kernel: 8 x 16 tiles, unstacked taps
+    if constexpr (SUB != 1 || MINB != 1 || XS) return set_err(QLD_E_INVAL);
     static std::atomic<unsigned long long> attr_done{0};  // per instantiation, one bit per device
     if (dev < 64 && !(attr_done.load() >> dev & 1ull)) {
         if (cudaFuncSetAttribute(qldnn::conv3x3_fwd_tma_kernel<N, SWB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -937,6 +938,56 @@ int conv_tma_dispatch(const void* in, const void* wk, const float* bias, int B, 
         return 1024 + 2ll * 3 * (8 * sub + 2) * 16 * swb2 + 9ll * Cin * nco * 2 + 256 <= qldnn::kTwoPerSmSmem;
     };
     const long long tiles8 = ntiles;
+    // column taps stacked in N (conv3x3_fwd_tma_wres_kernel<..., XS = true>,
+    // 14-column tiles, one unshifted halo copy per channel chunk) for 32- and
+    // 64-column slices: mode bit 16 asks for it, bit 17 forbids it. Bits 12-15
+    // choose its tile height and CTAs per SM as for the unstacked kernel; two
+    // CTAs per SM and 16-row tiles exclude each other (the accumulators of
+    // 3 x 32 columns, two per CTA, take the tensor memory). By default where
+    // the MMAs outweigh its longer epilogue (three column groups read, two
+    // shuffles per channel): 32-column layers of at least 64 input channels
+    // with at least eight of its tiles per SM, 64-column ones of at least 128
+    // with at least two (measured, graphs of 20 launches: 512^2, 64 -> 32
+    // 18.6 -> 13.6 us; 256^2, 128 -> 64 15.7 -> 12.8 us; slower: 512^2,
+    // 16 -> 32 12.0 -> 12.6 us; 256^2, 64 -> 64 9.6 -> 11.6 us; 128^2,
+    // 128 -> 64 (160 stacked tiles for 148 SMs) 7.3 -> 8.1 us; 256^2, 64 -> 32
+    // (4 tiles per SM) 9.0 -> 6.8 us alone but 12.1 -> 13.0 us with the fused
+    // 2x upsampling of the inference network, whose stores dominate). The
+    // choice depends on the shape alone, so a layer gives the same result
+    // with fused and with separate outputs.
+    auto fits_xs = [&](int sub, int sw, long long cap) {  // resident weights and two halo stages
+        return 1024 + 2ll * (8 * sub + 2) * 16 * sw + 9ll * Cin * nco * 2 + 256 <= cap;
+    };
+    const long long tx14 = (W + 13) / 14;
+    const long long xt8 = (long long)B * ((H + 7) / 8) * tx14, xt16 = (long long)B * ((H + 15) / 16) * tx14;
+    const bool xs_auto = (nco == 32 && Cin >= 64 && xt8 * nsplit >= 8ll * nsm) ||
+                         (nco == 64 && Cin >= 128 && xt8 * nsplit >= 2ll * nsm);
+    const bool xs = (nco == 32 || nco == 64) && !force_stream && !((mode >> 17) & 1) && fits_xs(1, swb2, 232448) &&
+                    (((mode >> 16) & 1) || xs_auto);
+    if (xs) {
+        const int sw = fits_xs(1, swb, 232448) ? swb : swb2;
+        const bool xtwo = nco == 32 && !((mode >> 14) & 1) && fits_xs(1, sw, qldnn::kTwoPerSmSmem) &&
+                          (((mode >> 15) & 1) || (Cin >= 32 && xt8 >= 4ll * nsm));
+        const bool xsub2 = nco == 32 && !xtwo && !((mode >> 13) & 1) && fits_xs(2, sw, 232448) &&
+                           (((mode >> 12) & 1) || xt16 >= 2ll * nsm);
+#define QLD_XS(SS)                                                                                                  \
+    if (sw == SS) {                                                                                                 \
+        if (nco == 64)                                                                                              \
+            return launch_tma<64, SS, 1, 1, true>(in, wk, bias, B, H, W, Cin, Cout, relu, epi, status, st, false,   \
+                                                  early);                                                           \
+        if (xtwo)                                                                                                   \
+            return launch_tma<32, SS, 1, 2, true>(in, wk, bias, B, H, W, Cin, Cout, relu, epi, status, st, false,   \
+                                                  early);                                                           \
+        if (xsub2)                                                                                                  \
+            return launch_tma<32, SS, 2, 1, true>(in, wk, bias, B, H, W, Cin, Cout, relu, epi, status, st, false,   \
+                                                  early);                                                           \
+        return launch_tma<32, SS, 1, 1, true>(in, wk, bias, B, H, W, Cin, Cout, relu, epi, status, st, false,       \
+                                              early);                                                               \
+    }
+        QLD_XS(32) QLD_XS(64) QLD_XS(128)
+#undef QLD_XS
+        return set_err(QLD_E_INVAL);
+    }
     const bool two = nsplit == 1 && (nco == 32 || nco == 64) && !force_stream && !((mode >> 14) & 1) && fits_two(1) &&
                      (((mode >> 15) & 1) || (nco == 32 && Cin >= 32 && tiles8 >= 4ll * nsm));
     if (two && nco == 64)  // 8 x 16 tiles only: 16 x 16 ones do not fit twice with 64-column weights
@@ -1300,7 +1351,17 @@ int qldnn_conv3x3_fwd_tma_epi(const void* in, const void* wk, const float* bias,
                               int Cout, int relu, void* out_bf16, long long ldo, void* pool_bf16, void* up_bf16,
                               long long ldu, const float* head_w, const float* head_b, const float* baseline,
                               float* pred, int* status, int flags, void* stream) {
+    return qldnn_conv3x3_fwd_tma_epi_mode(in, wk, bias, B, H, W, Cin, Cout, relu, out_bf16, ldo, pool_bf16, up_bf16,
+                                          ldu, head_w, head_b, baseline, pred, status, flags, 0, stream);
+}
+
+int qldnn_conv3x3_fwd_tma_epi_mode(const void* in, const void* wk, const float* bias, int B, int H, int W, int Cin,
+                                   int Cout, int relu, void* out_bf16, long long ldo, void* pool_bf16, void* up_bf16,
+                                   long long ldu, const float* head_w, const float* head_b, const float* baseline,
+                                   float* pred, int* status, int flags, int mode, void* stream) {
     if (flags & ~QLDNN_EARLY_LAUNCH) return set_err(QLD_E_INVAL);
+    // variant bits only: the channel split is the layer's (one CTA per tile with a head), early launch is a flag
+    if (mode & ~((0xF << 12) | (3 << 16) | 1)) return set_err(QLD_E_INVAL);
     const bool head = head_w || head_b || baseline || pred;
     if (!out_bf16 && !pool_bf16 && !up_bf16 && !head) return set_err(QLD_E_INVAL);
     if (out_bf16 && (!al(out_bf16, 16) || ldo < Cout || ldo % 8)) return set_err(QLD_E_INVAL);
@@ -1319,7 +1380,7 @@ int qldnn_conv3x3_fwd_tma_epi(const void* in, const void* wk, const float* bias,
     epi.base = baseline;
     epi.pred = pred;
     // the head needs every output channel of a pixel in one CTA
-    const int mode = (head ? (1 << 4) : 0) | ((flags & QLDNN_EARLY_LAUNCH) ? (1 << 8) : 0);
+    mode |= (head ? (1 << 4) : 0) | ((flags & QLDNN_EARLY_LAUNCH) ? (1 << 8) : 0);
     return conv_tma_dispatch(in, wk, bias, B, H, W, Cin, Cout, relu, epi, status, mode, (cudaStream_t)stream);
 }
 

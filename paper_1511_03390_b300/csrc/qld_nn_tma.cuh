@@ -224,11 +224,22 @@ __device__ __forceinline__ void tc_tie16(uint32_t* r) {
 constexpr int kEpiWarps = 4;
 constexpr int kConvThreads = 64 + 32 * kEpiWarps;
 
-template <int N, int SUB = 1, bool BIAS_REG = (N <= 64)>
+//
+// XS (column taps stacked in N, conv3x3_fwd_tma_wres_kernel<..., XS = true>):
+// the accumulator of a sub-tile holds 3 N columns, D_kx[m][co] at column
+// kx N + co, for the 16 halo columns x0 - 1 .. x0 + 14 of an output tile 14
+// columns wide; the output at column x0 + c takes D_0 of halo column c (its
+// own lane), D_1 of column c + 1 and D_2 of column c + 2, summed in that order
+// ((D_0 + D_1) + D_2) after two shuffles down within the 16-lane row. Lanes
+// of halo columns 14 and 15 produce no output (and each other's pooling
+// partners, so the pooling exchange stays inside whole 2 x 2 blocks).
+template <int N, int SUB = 1, bool BIAS_REG = (N <= 64), bool XS = false>
 __device__ __forceinline__ void conv_epilogue(uint32_t tmem, uint64_t* tfull, uint64_t* tempty, volatile int* fail,
                                               int warp, int lane, int ntiles, int tiles_x, int tiles_y, int H, int W,
                                               int Cout, const float* __restrict__ bias, int relu, ConvEpi epi,
                                               int nsplit) {
+    constexpr int TW = XS ? 14 : 16;   // output columns per tile
+    constexpr int NA = XS ? 3 * N : N; // accumulator columns per sub-tile
     const bool head = epi.head_w != nullptr;
     const int qw = warp & 3;           // TMEM lane quarter this warp may read
     const int m = qw * 32 + lane;
@@ -248,7 +259,8 @@ __device__ __forceinline__ void conv_epilogue(uint32_t tmem, uint64_t* tfull, ui
         const uint32_t b = rr & 1 ? pk[6 + k] : pk[4 + k];
         return rr & 2 ? b : a;
     };
-    constexpr int G = N < 64 ? N : 64;  // accumulator columns per tcgen05.wait::ld
+    // accumulator columns per tcgen05.wait::ld (XS: 16 output channels = 48 columns)
+    constexpr int G = XS ? 16 : (N < 64 ? N : 64);
     float bres[BIAS_REG ? N : 1];       // the bias (or 0), for narrow layers
     if constexpr (BIAS_REG) {
 #pragma unroll
@@ -263,19 +275,38 @@ __device__ __forceinline__ void conv_epilogue(uint32_t tmem, uint64_t* tfull, ui
         const int tx = t % tiles_x, r = t / tiles_x, ty = r % tiles_y, b = r / tiles_y;
 #pragma unroll 1
         for (int h = 0; h < SUB; ++h) {  // the tile's 8-row sub-tiles
-            const int y = (ty * SUB + h) * 8 + my, x = tx * 16 + mx;
-            const bool inside = y < H && x < W;
+            const int y = (ty * SUB + h) * 8 + my, x = tx * TW + mx;
+            const bool inside = y < H && x < W && (!XS || mx < TW);
             const long long p = ((long long)b * H + y) * W + x;
-            const uint32_t taddr = tmem + ((uint32_t)(qw * 32) << 16) + (uint32_t)((acc * SUB + h) * N);
+            const uint32_t taddr = tmem + ((uint32_t)(qw * 32) << 16) + (uint32_t)((acc * SUB + h) * NA);
             float hacc = head ? *epi.head_b : 0.f;
-#pragma unroll 1
+            // unrolled when XS, so the register-resident bias is indexed
+            // with constants
+#pragma unroll(XS ? 4 : 1)
             for (int g0 = 0; g0 < N; g0 += G) {
                 uint32_t rg[G];
+                if constexpr (XS) {
+                    uint32_t r1[16], r2[16];
+                    tc_ld16(taddr + (uint32_t)g0, rg);
+                    tc_ld16(taddr + (uint32_t)(N + g0), r1);
+                    tc_ld16(taddr + (uint32_t)(2 * N + g0), r2);
+                    asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
+                    tc_tie16(rg);
+                    tc_tie16(r1);
+                    tc_tie16(r2);
 #pragma unroll
-                for (int c = 0; c < G; c += 16) tc_ld16(taddr + (uint32_t)(g0 + c), rg + c);
-                asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
+                    for (int j = 0; j < 16; ++j) {  // every lane shuffles: warp-uniform
+                        const float d1 = __shfl_down_sync(0xffffffffu, __uint_as_float(r1[j]), 1, 16);
+                        const float d2 = __shfl_down_sync(0xffffffffu, __uint_as_float(r2[j]), 2, 16);
+                        rg[j] = __float_as_uint((__uint_as_float(rg[j]) + d1) + d2);
+                    }
+                } else {
 #pragma unroll
-                for (int c = 0; c < G; c += 16) tc_tie16(rg + c);
+                    for (int c = 0; c < G; c += 16) tc_ld16(taddr + (uint32_t)(g0 + c), rg + c);
+                    asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
+#pragma unroll
+                    for (int c = 0; c < G; c += 16) tc_tie16(rg + c);
+                }
 #pragma unroll
                 for (int c = 0; c < G; c += 16) {
                     const int c0 = g0 + c;
@@ -284,7 +315,7 @@ __device__ __forceinline__ void conv_epilogue(uint32_t tmem, uint64_t* tfull, ui
 #pragma unroll
                     for (int j = 0; j < 16; ++j) {
                         float bj;
-                        if constexpr (BIAS_REG) bj = bres[c + j];  // g0 == 0
+                        if constexpr (BIAS_REG) bj = bres[g0 + c + j];
                         else bj = bias ? bias[c0 + j] : 0.f;
                         v[j] = __uint_as_float(rr[j]) + bj;
                         if (relu) v[j] = fmaxf(v[j], 0.f);
@@ -558,15 +589,32 @@ __global__ void __launch_bounds__(kConvThreads, 1)
 // narrow (N = 32, 64) layers, are paid once per 256 pixels. With the same
 // channel chunks (SWB) the MMAs of each accumulator, and so the results, are
 // those of SUB = 1.
-template <int N, int SWB, int SUB = 1>
+//
+// XS = true stacks the three column taps kx of a tap row in the MMA's N
+// dimension: one MMA M128 x 3N x K16 per tap row ky, sub-tile and K16 step,
+// B = the three taps' weight boxes, which lie one after another in shared
+// memory (tap 3 ky + kx at box 9 cc + 3 ky + kx), read as one 3N-row operand.
+// The halo is loaded once, unshifted, 16 columns from x0 - 1, and a tile
+// covers 14 output columns; the epilogue adds the three column groups
+// (conv_epilogue). Narrow layers gain because an M128 x N32 x K16 MMA takes
+// about as long as an M128 x N96 one.
+template <int N, int SWB, int SUB = 1, bool XS = false>
 struct TmaConvRes {
     static constexpr int BK = SWB / 2;
-    static constexpr int HALO = (8 * SUB + 2) * 16 * SWB;  // one column-shifted halo copy of a tile
-    static constexpr int ASTAGE = 3 * HALO;
+    static constexpr int HALO = (8 * SUB + 2) * 16 * SWB;  // one (column-shifted) halo copy of a tile
+    static constexpr int ASTAGE = (XS ? 1 : 3) * HALO;
     static constexpr int BSTAGE = N * SWB;
     static constexpr int kMaxSA = 8;
     static constexpr int kBars = (2 * kMaxSA + 6) * 8;
-    static constexpr int kTmemCols = 2 * N * SUB;
+    static constexpr int NA = (XS ? 3 : 1) * N;             // accumulator columns per sub-tile
+    static constexpr int TW = XS ? 14 : 16;                 // output columns per tile
+    // two accumulators; an allocation is a power of two of at least 32 columns
+    static constexpr int kTmemCols = 2 * NA * SUB <= 32    ? 32
+                                     : 2 * NA * SUB <= 64  ? 64
+                                     : 2 * NA * SUB <= 128 ? 128
+                                     : 2 * NA * SUB <= 256 ? 256
+                                                           : 512;
+    static_assert(2 * NA * SUB <= 512, "accumulators exceed the tensor memory");
     // dynamic shared memory for SA halo stages and Cin input channels
     static constexpr long long smem(int SA, int Cin) {
         return 1024 + (long long)SA * ASTAGE + 9ll * (Cin / BK) * BSTAGE + kBars + 16;
@@ -581,12 +629,12 @@ struct TmaConvRes {
 // while this one's second CTA still runs.
 constexpr int kTwoPerSmSmem = 115712;
 
-template <int N, int SWB, int SUB = 1, int MINB = 1>
+template <int N, int SWB, int SUB = 1, int MINB = 1, bool XS = false>
 __global__ void __launch_bounds__(kConvThreads, MINB)
     conv3x3_fwd_tma_wres_kernel(const __grid_constant__ CUtensorMap map_in, const __grid_constant__ CUtensorMap map_w,
                                 const float* __restrict__ bias, int B, int H, int W, int Cin, int Cout, int relu,
                                 const ConvEpi epi, int* status, int SA, int nsplit) {
-    using L = TmaConvRes<N, SWB, SUB>;
+    using L = TmaConvRes<N, SWB, SUB, XS>;
     extern __shared__ unsigned char dsm_raw[];
     unsigned char* dsm = dsm_raw + ((1024u - (smem_u32(dsm_raw) & 1023u)) & 1023u);
     const int csteps = Cin / L::BK;
@@ -602,10 +650,10 @@ __global__ void __launch_bounds__(kConvThreads, MINB)
     volatile int* fail = reinterpret_cast<volatile int*>(tslot + 1);
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int tiles_x = (W + 15) >> 4, tiles_y = (H + 8 * SUB - 1) / (8 * SUB);
+    const int tiles_x = (W + L::TW - 1) / L::TW, tiles_y = (H + 8 * SUB - 1) / (8 * SUB);
     const int ntiles = B * tiles_x * tiles_y;
     const int co0 = (blockIdx.x % nsplit) * N;  // this CTA's slice of the output channels
-    constexpr uint32_t kIdesc = umma_idesc_bf16(128, N);
+    constexpr uint32_t kIdesc = umma_idesc_bf16(128, L::NA);
 
     if (warp == 1) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(smem_u32(tslot)),
@@ -649,12 +697,13 @@ __global__ void __launch_bounds__(kConvThreads, MINB)
             bool ok = true;
             for (int t = blockIdx.x / nsplit; t < ntiles && ok; t += gridDim.x / nsplit) {
                 const int tx = t % tiles_x, r = t / tiles_x, ty = r % tiles_y, b = r / tiles_y;
-                const int x0 = tx * 16, y0 = ty * 8 * SUB;
+                const int x0 = tx * L::TW, y0 = ty * 8 * SUB;
                 for (int cc = 0; cc < csteps; ++cc) {
                     if (ia >= SA && !(ok = wait_or_fail(&emptyA[sa], pa ^ 1u, fail))) break;
-                    mbar_expect_tx(&fullA[sa], 3 * L::HALO);
-                    for (int j = 0; j < 3; ++j)
-                        tma_load_4d(sA + (sa * 3 + j) * L::HALO, &map_in, &fullA[sa], cc * L::BK, x0 + j - 1, y0 - 1, b);
+                    mbar_expect_tx(&fullA[sa], L::ASTAGE);
+                    for (int j = 0; j < (XS ? 1 : 3); ++j)
+                        tma_load_4d(sA + sa * L::ASTAGE + j * L::HALO, &map_in, &fullA[sa], cc * L::BK, x0 + j - 1,
+                                    y0 - 1, b);
                     ++ia;
                     if (++sa == SA) {
                         sa = 0;
@@ -686,21 +735,35 @@ __global__ void __launch_bounds__(kConvThreads, MINB)
             for (int t = blockIdx.x / nsplit; t < ntiles && ok; t += gridDim.x / nsplit) {
                 const int acc = it & 1;
                 if (it >= 2 && !(ok = wait_or_fail(&tempty[acc], (((uint32_t)it >> 1) & 1u) ^ 1u, fail))) break;
-                const uint32_t d = tmem + (uint32_t)(acc * N * SUB);
+                const uint32_t d = tmem + (uint32_t)(acc * L::NA * SUB);
                 for (int cc = 0; cc < csteps && ok; ++cc) {
                     if (!(ok = wait_or_fail(&fullA[sa], pa, fail))) break;
                     tc_fence_after();
-                    const uint64_t adesc = desc_at(adesc0, (uint32_t)(sa * 3 * L::HALO));
+                    const uint64_t adesc = desc_at(adesc0, (uint32_t)(sa * L::ASTAGE));
                     const uint64_t bdesc = desc_at(bdesc0, (uint32_t)(cc * 9 * L::BSTAGE));
+                    if constexpr (XS) {
 #pragma unroll
-                    for (int tap = 0; tap < 9; ++tap) {
+                        for (int ky = 0; ky < 3; ++ky) {  // taps 3 ky .. 3 ky + 2 in one 3N-row B operand
 #pragma unroll
-                        for (int kk = 0; kk < L::BK / 16; ++kk)
+                            for (int kk = 0; kk < L::BK / 16; ++kk)
 #pragma unroll
-                            for (int h = 0; h < SUB; ++h)  // sub-tile h: halo rows from 8 h on
-                                tc_mma(d + (uint32_t)(h * N),
-                                       desc_at(adesc, (tap % 3) * L::HALO + (tap / 3 + 8 * h) * 16 * SWB + kk * 32),
-                                       desc_at(bdesc, tap * L::BSTAGE + kk * 32), kIdesc, (cc | tap | kk) ? 1u : 0u);
+                                for (int h = 0; h < SUB; ++h)
+                                    tc_mma(d + (uint32_t)(h * L::NA),
+                                           desc_at(adesc, (ky + 8 * h) * 16 * SWB + kk * 32),
+                                           desc_at(bdesc, 3 * ky * L::BSTAGE + kk * 32), kIdesc,
+                                           (cc | ky | kk) ? 1u : 0u);
+                        }
+                    } else {
+#pragma unroll
+                        for (int tap = 0; tap < 9; ++tap) {
+#pragma unroll
+                            for (int kk = 0; kk < L::BK / 16; ++kk)
+#pragma unroll
+                                for (int h = 0; h < SUB; ++h)  // sub-tile h: halo rows from 8 h on
+                                    tc_mma(d + (uint32_t)(h * N),
+                                           desc_at(adesc, (tap % 3) * L::HALO + (tap / 3 + 8 * h) * 16 * SWB + kk * 32),
+                                           desc_at(bdesc, tap * L::BSTAGE + kk * 32), kIdesc, (cc | tap | kk) ? 1u : 0u);
+                        }
                     }
                     tc_commit(&emptyA[sa]);
                     if (++sa == SA) {
@@ -718,8 +781,9 @@ __global__ void __launch_bounds__(kConvThreads, MINB)
     } else {
         // two CTAs per SM leave 168 registers a thread: the bias of a 64-column
         // layer is then read from memory
-        conv_epilogue<N, SUB, (MINB == 1 ? N <= 64 : N <= 32)>(tmem, tfull, tempty, fail, warp, lane, ntiles, tiles_x,
-                                                                tiles_y, H, W, Cout, bias, relu, epi, nsplit);
+        conv_epilogue<N, SUB, (MINB == 1 ? N <= 64 : N <= 32), XS>(tmem, tfull, tempty, fail, warp, lane, ntiles,
+                                                                    tiles_x, tiles_y, H, W, Cout, bias, relu, epi,
+                                                                    nsplit);
     }
 
     tc_fence_before();

@@ -24,14 +24,23 @@ def _need_gpu():
 # splits small layers' output channels over several CTAs per tile;
 # "conv3x3_fwd_tma_stream" forces its weight-streaming variant, "..._split2" /
 # "..._split4" force 2 / 4 CTAs per tile, "..._sub2" 16 x 16-pixel tiles (two
-# stacked 8 x 16 sub-tiles), "..._two" two CTAs per SM, on every shape they
-# apply to.
-KERNELS = ["conv3x3_fwd_tc", "conv3x3_fwd_tc2", "conv3x3_fwd_tma", "conv3x3_fwd_tma_stream",
+# stacked 8 x 16 sub-tiles), "..._two" two CTAs per SM, "..._xs*" the column
+# taps stacked in N (14-column tiles; 8-row tiles, 16-row tiles, two CTAs per
+# SM; with 2 CTAs per tile), on every shape they apply to (the others run the
+# unstacked kernel).
+# The automatic choice stacks the column taps of some layers (those with
+# many input channels per output column); "..._noxs" and the unstacked
+# variants forbid it (mode bit 17).
+XS, NOXS = 1 << 16, 1 << 17
+KERNELS = ["conv3x3_fwd_tc", "conv3x3_fwd_tc2", "conv3x3_fwd_tma", "conv3x3_fwd_tma_noxs", "conv3x3_fwd_tma_stream",
            "conv3x3_fwd_tma_split2", "conv3x3_fwd_tma_split4", "conv3x3_fwd_tma_sub2", "conv3x3_fwd_tma_two",
-           "conv3x3_fwd_tma_two_sub1"]
-MODES = {"conv3x3_fwd_tma_stream": 1, "conv3x3_fwd_tma_split2": 2 << 4, "conv3x3_fwd_tma_split4": 4 << 4,
-         "conv3x3_fwd_tma_sub2": 1 << 12, "conv3x3_fwd_tma_two": (1 << 15) | (1 << 12),
-         "conv3x3_fwd_tma_two_sub1": (1 << 15) | (1 << 13)}
+           "conv3x3_fwd_tma_two_sub1", "conv3x3_fwd_tma_xs_sub1", "conv3x3_fwd_tma_xs_sub2",
+           "conv3x3_fwd_tma_xs_two", "conv3x3_fwd_tma_xs_split2"]
+MODES = {"conv3x3_fwd_tma_noxs": NOXS, "conv3x3_fwd_tma_stream": 1, "conv3x3_fwd_tma_split2": NOXS | (2 << 4),
+         "conv3x3_fwd_tma_split4": NOXS | (4 << 4), "conv3x3_fwd_tma_sub2": NOXS | (1 << 12),
+         "conv3x3_fwd_tma_two": NOXS | (1 << 15) | (1 << 12), "conv3x3_fwd_tma_two_sub1": NOXS | (1 << 15) | (1 << 13),
+         "conv3x3_fwd_tma_xs_sub1": XS | (1 << 13) | (1 << 14), "conv3x3_fwd_tma_xs_sub2": XS | (1 << 12) | (1 << 14),
+         "conv3x3_fwd_tma_xs_two": XS | (1 << 15), "conv3x3_fwd_tma_xs_split2": XS | (2 << 4)}
 
 
 def _tc(kernel, Cout):
@@ -189,7 +198,7 @@ def test_tma_16x16_tiles_equal_8x16_tiles(B, H, W, Cin, Cout, relu):
     wk = torch.empty(9 * Cin * Cout, dtype=torch.bfloat16, device="cuda")
     q.nn.kmajor_weights(w, Cin, Cout, 0, wk)
     outs = []
-    for mode in (1 << 12, 1 << 13):
+    for mode in (NOXS | (1 << 12), NOXS | (1 << 13), XS | (1 << 12) | (1 << 14), XS | (1 << 13) | (1 << 14)):
         status = torch.zeros(1, dtype=torch.int32, device="cuda")
         out_f = torch.full((B, H, W, Cout), float("nan"), dtype=torch.float32, device="cuda")
         out_b = torch.empty((B, H, W, Cout), dtype=torch.bfloat16, device="cuda")
@@ -198,6 +207,8 @@ def test_tma_16x16_tiles_equal_8x16_tiles(B, H, W, Cin, Cout, relu):
         assert status.item() == 0
         outs.append((out_f.cpu(), out_b.cpu()))
     assert torch.equal(outs[0][0], outs[1][0]) and torch.equal(outs[0][1], outs[1][1])
+    # stacked column taps: the same between their own tile heights
+    assert torch.equal(outs[2][0], outs[3][0]) and torch.equal(outs[2][1], outs[3][1])
 
 
 @pytest.mark.parametrize("B,H,W,Cin,Cout,relu", [(1, 64, 48, 32, 32, 1), (2, 33, 40, 16, 32, 0), (1, 48, 80, 96, 32, 1),
@@ -213,7 +224,7 @@ def test_tma_two_ctas_per_sm_equal_one(B, H, W, Cin, Cout, relu):
     bias = torch.from_numpy(rng.standard_normal(Cout).astype(np.float32)).cuda()
     wk = torch.empty(9 * Cin * Cout, dtype=torch.bfloat16, device="cuda")
     q.nn.kmajor_weights(w, Cin, Cout, 0, wk)
-    for sub in (1 << 12, 1 << 13):
+    for sub in (NOXS | (1 << 12), NOXS | (1 << 13), XS | (1 << 13)):
         outs = []
         for two in (1 << 15, 1 << 14):
             status = torch.zeros(1, dtype=torch.int32, device="cuda")
@@ -224,3 +235,50 @@ def test_tma_two_ctas_per_sm_equal_one(B, H, W, Cin, Cout, relu):
             assert status.item() == 0
             outs.append((out_f.cpu(), out_b.cpu()))
         assert torch.equal(outs[0][0], outs[1][0]) and torch.equal(outs[0][1], outs[1][1])
+
+
+@pytest.mark.parametrize("B,H,W,Cin,Cout", [(1, 40, 72, 32, 32), (2, 18, 30, 16, 64), (1, 24, 58, 64, 32)])
+def test_tma_stacked_column_taps_with_fused_outputs(B, H, W, Cin, Cout):
+    """The column-stacked kernel's fused epilogue outputs (2 x 2 average,
+    nearest 2x upsampling, the 1x1 head plus baseline) against the same
+    operations applied on the CPU to its own bf16 activation, which is itself
+    checked against the FP64 oracle; every pooling block and upsampled pixel
+    of a tile edge (14-column tiles, W not a multiple of 14) included."""
+    rng = np.random.default_rng(H * W + Cin + 11)
+    x, xr = bf16(rng.standard_normal((B, H, W, Cin)))
+    w, wr = bf16(rng.standard_normal((3, 3, Cin, Cout)) / np.sqrt(9 * Cin))
+    bias = torch.from_numpy(rng.standard_normal(Cout).astype(np.float32) * 0.1).cuda()
+    wk = torch.empty(9 * Cin * Cout, dtype=torch.bfloat16, device="cuda")
+    q.nn.kmajor_weights(w, Cin, Cout, 0, wk)
+    hw = torch.from_numpy(rng.standard_normal(Cout).astype(np.float32) * 0.3).cuda()
+    hb = torch.tensor([0.25], dtype=torch.float32, device="cuda")
+    base = torch.from_numpy(rng.standard_normal(B * H * W).astype(np.float32)).cuda()
+    for sub in ((1 << 13) | (1 << 14), (1 << 12) | (1 << 14), 1 << 15):
+        out = torch.empty((B, H, W, Cout), dtype=torch.bfloat16, device="cuda")
+        pool = torch.full((B, H // 2, W // 2, Cout), float("nan"), dtype=torch.bfloat16, device="cuda")
+        up = torch.full((B, 2 * H, 2 * W, Cout), float("nan"), dtype=torch.bfloat16, device="cuda")
+        pred = torch.full((B * H * W,), float("nan"), dtype=torch.float32, device="cuda")
+        status = torch.zeros(1, dtype=torch.int32, device="cuda")
+        rc = q.lib.qldnn_conv3x3_fwd_tma_epi_mode(
+            x.data_ptr(), wk.data_ptr(), bias.data_ptr(), B, H, W, Cin, Cout, 1, out.data_ptr(), Cout,
+            pool.data_ptr(), up.data_ptr(), Cout, hw.data_ptr(), hb.data_ptr(), base.data_ptr(),
+            pred.data_ptr(), status.data_ptr(), 0, XS | sub, None)
+        assert rc == 0
+        torch.cuda.synchronize()
+        assert status.item() == 0
+        act = out.float().cpu().numpy().astype(np.float64)
+        ref = np.maximum(oracle.conv3x3(xr, wr, bias.cpu().numpy().astype(np.float64)), 0)
+        bound = ACC * oracle.conv3x3(np.abs(xr), np.abs(wr)) + 1e-6
+        close(act, ref, bound + 2.0 ** -8 * np.abs(ref), "stacked-tap activation")
+        # the fused outputs from the activation as stored
+        a32 = out.float().cpu().numpy()
+        blk = a32[:, :H // 2 * 2, :W // 2 * 2].reshape(B, H // 2, 2, W // 2, 2, Cout)
+        pw = ((blk[:, :, 0, :, 0] + blk[:, :, 1, :, 1]) + (blk[:, :, 0, :, 1] + blk[:, :, 1, :, 0])) * np.float32(0.25)
+        pw = torch.from_numpy(np.ascontiguousarray(pw)).to(torch.bfloat16).float().numpy()
+        assert np.array_equal(pool.float().cpu().numpy(), pw)
+        uw = np.repeat(np.repeat(a32, 2, axis=1), 2, axis=2)
+        assert np.array_equal(up.float().cpu().numpy(), uw)
+        hp = np.einsum("bhwc,c->bhw", act, hw.cpu().numpy().astype(np.float64)) + 0.25
+        hp = hp.reshape(-1) + base.cpu().numpy()
+        scale = np.einsum("bhwc,c->bhw", np.abs(act), np.abs(hw.cpu().numpy())).reshape(-1) + 1
+        assert np.all(np.abs(pred.cpu().numpy() - hp) <= 1e-5 * scale)
