@@ -23,19 +23,21 @@
 // 8-row atoms of 8 * SWB bytes. A K16 step inside a row moves the descriptor
 // start 32 bytes.
 //
-// Roles (320 threads, one CTA per SM, persistent over tiles):
+// Roles (kConvThreads = 192 threads, persistent over tiles; one CTA per SM,
+// or two for some narrow layers):
 //   warp 0  one thread issues the TMA loads into a 2-stage halo ring and an
 //           SB-stage weight ring of one tap row (three taps) per stage when
 //           two such stages fit (mbarrier expect_tx / complete_tx);
 //   warp 1  allocates TMEM (two accumulators of N columns), one thread issues
 //           tcgen05.mma M128 x N x K16 and commits to the rings' "empty"
 //           barriers and, per tile, to the accumulator's "full" barrier;
-//   warps 2-9 epilogue: tcgen05.ld of the accumulator (warp w reads TMEM
-//           lanes 32 (w mod 4) .., two warps per lane quarter splitting the
-//           columns), bias, ReLU, bf16/f32 stores, then release the
-//           accumulator, so the next tile's MMAs overlap the read-out. The
-//           read-out of the narrow layers' fused pooling and upsampling
-//           outputs is as long as their MMAs, hence eight warps.
+//   warps 2-5 epilogue: tcgen05.ld of the accumulator (warp w reads TMEM
+//           lanes 32 (w mod 4) ..), bias, ReLU, bf16/f32 stores and fused
+//           outputs, then release the accumulator, so the next tile's MMAs
+//           overlap the read-out.
+// The weights-resident variant (conv3x3_fwd_tma_wres_kernel) has the same
+// roles, loads all the weights once per CTA, and can stack tiles in height
+// (SUB) or the three column taps in N (XS).
 // Launched early (programmatic stream serialisation), a CTA allocates TMEM,
 // sets up its barriers and (weights-resident variant) loads the weights
 // while the previous kernel finishes; the producer waits for that kernel
