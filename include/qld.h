@@ -455,8 +455,11 @@ int qldnn_conv3x3_fwd_tma(const void* in, const void* wk, const float* bias, int
  * forbid the column-stacked form for 32- and 64-channel slices with resident
  * weights (the three column taps kx of a tap row as one MMA of 3 x the
  * slice's columns against an unshifted halo, tiles 14 columns wide, the
- * three column groups added in the epilogue: (D_0 + D_1) + D_2, FP32). For
- * tests and measurements of every variant. */
+ * three column groups added in the epilogue: (D_0 + D_1) + D_2, FP32); bit
+ * 18 / bit 19: ask for / forbid eight epilogue warps in the weight-streaming
+ * variant for slices of 64+ columns (two warps per accumulator lane quarter,
+ * each reading half the columns; not with a fused head; the default there). For tests and
+ * measurements of every variant. */
 int qldnn_conv3x3_fwd_tma_mode(const void* in, const void* wk, const float* bias, int B, int H, int W, int Cin,
                                int Cout, int relu, void* out_bf16, float* out_f32, int* status, int mode,
                                void* stream);
@@ -495,7 +498,7 @@ int qldnn_conv3x3_fwd_tma_epi(const void* in, const void* wk, const float* bias,
                               long long ldu, const float* head_w, const float* head_b, const float* baseline,
                               float* pred, int* status, int flags, void* stream);
 /* The same with the kernel variant chosen by the caller: mode bit 0 and bits
- * 12-17 as in qldnn_conv3x3_fwd_tma_mode (the CTAs per tile stay the layer's
+ * 12-19 as in qldnn_conv3x3_fwd_tma_mode (the CTAs per tile stay the layer's
  * own; other bits: QLD_E_INVAL). For tests and measurements of every variant
  * with fused outputs. */
 int qldnn_conv3x3_fwd_tma_epi_mode(const void* in, const void* wk, const float* bias, int B, int H, int W, int Cin,

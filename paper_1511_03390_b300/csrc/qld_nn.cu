@@ -754,7 +754,8 @@ cudaError_t launch_maybe_early(void (*kernel)(KArgs...), unsigned grid, unsigned
 
 template <int N, int SWB, int SUB = 1, int MINB = 1, bool XS = false>
 int launch_tma(const void* in, const void* wk, const float* bias, int B, int H, int W, int Cin, int Cout, int relu,
-               const qldnn::ConvEpi& epi, int* status, cudaStream_t st, bool force_stream, bool early) {
+               const qldnn::ConvEpi& epi, int* status, cudaStream_t st, bool force_stream, bool early,
+               bool wide_epi = false) {
     using L = qldnn::TmaConv<N, SWB>;
     EncodeTiledFn enc = encode_tiled();
     int dev = 0;
@@ -807,6 +808,21 @@ int launch_tma(const void* in, const void* wk, const float* bias, int B, int H, 
     }
     // the weight-streaming kernel: 8 x 16 tiles, unstacked taps
     if constexpr (SUB != 1 || MINB != 1 || XS) return set_err(QLD_E_INVAL);
+    if constexpr (N >= 64) {
+        if (wide_epi) {  // eight epilogue warps, two per TMEM lane quarter
+            static std::atomic<unsigned long long> attr8{0};
+            if (dev < 64 && !(attr8.load() >> dev & 1ull)) {
+                if (cudaFuncSetAttribute(qldnn::conv3x3_fwd_tma_kernel<N, SWB, 8>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, L::kSmem) != cudaSuccess)
+                    return set_err(QLD_E_CUDA);
+                attr8.fetch_or(1ull << dev);
+            }
+            if (launch_maybe_early(qldnn::conv3x3_fwd_tma_kernel<N, SWB, 8>, grid, 64 + 32 * 8, (size_t)L::kSmem, st,
+                                   early, mi, mw, bias, B, H, W, Cin, Cout, relu, epi, status, nsplit) != cudaSuccess)
+                return set_err(QLD_E_CUDA);
+            return launched(1);
+        }
+    }
     static std::atomic<unsigned long long> attr_done{0};  // per instantiation, one bit per device
     if (dev < 64 && !(attr_done.load() >> dev & 1ull)) {
         if (cudaFuncSetAttribute(qldnn::conv3x3_fwd_tma_kernel<N, SWB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -1006,9 +1022,21 @@ int conv_tma_dispatch(const void* in, const void* wk, const float* bias, int B, 
         return launch_tma<NN, SS, 2>(in, wk, bias, B, H, W, Cin, Cout, relu, epi, status, st, false, early);
     QLD_TMA2(32, 32) QLD_TMA2(32, 64) QLD_TMA2(64, 32) QLD_TMA2(64, 64)
 #undef QLD_TMA2
+    // weight-streaming layers of 64+ columns without a head: eight epilogue
+    // warps, two per accumulator lane quarter, each reading half the columns
+    // (mode bit 19 forbids them; bit 18 is the default here). Measured, graphs
+    // of 20 launches, four against eight warps: 8 x 64^2, 64 -> 128 12.8 ->
+    // 10.0 us, 128 -> 128 14.9 -> 13.05 us, 256 -> 128 20.9 -> 20.2 us;
+    // 128^2, 256 -> 128 14.1 -> 12.7 us; no shape slower. Their read-out, one
+    // warp per lane quarter, had been the last tile's tail (cycle stamps: 7,000
+    // cycles for a 128-column tile after its last MMA). The weights-resident
+    // kernel's 64- and 128-column layers measured no faster with eight
+    // (256^2, 64 -> 64 9.7 -> 10.2 us; 8 x 128^2, 64 -> 64 13.9 -> 14.3 us).
+    const bool wide_epi = nco >= 64 && !epi.head_w && !((mode >> 19) & 1);
 #define QLD_TMA(NN, SS) \
     if (nco == NN && swb == SS)                                                                                      \
-        return launch_tma<NN, SS>(in, wk, bias, B, H, W, Cin, Cout, relu, epi, status, st, force_stream != 0, early);
+        return launch_tma<NN, SS>(in, wk, bias, B, H, W, Cin, Cout, relu, epi, status, st, force_stream != 0, early, \
+                                  wide_epi);
     QLD_TMA(32, 32) QLD_TMA(32, 64) QLD_TMA(32, 128)
     QLD_TMA(64, 32) QLD_TMA(64, 64) QLD_TMA(64, 128)
     QLD_TMA(128, 32) QLD_TMA(128, 64) QLD_TMA(128, 128)
@@ -1361,7 +1389,7 @@ int qldnn_conv3x3_fwd_tma_epi_mode(const void* in, const void* wk, const float* 
                                    float* pred, int* status, int flags, int mode, void* stream) {
     if (flags & ~QLDNN_EARLY_LAUNCH) return set_err(QLD_E_INVAL);
     // variant bits only: the channel split is the layer's (one CTA per tile with a head), early launch is a flag
-    if (mode & ~((0xF << 12) | (3 << 16) | 1)) return set_err(QLD_E_INVAL);
+    if (mode & ~((0xF << 12) | (0xF << 16) | 1)) return set_err(QLD_E_INVAL);
     const bool head = head_w || head_b || baseline || pred;
     if (!out_bf16 && !pool_bf16 && !up_bf16 && !head) return set_err(QLD_E_INVAL);
     if (out_bf16 && (!al(out_bf16, 16) || ldo < Cout || ldo % 8)) return set_err(QLD_E_INVAL);

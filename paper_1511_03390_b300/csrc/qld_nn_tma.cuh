@@ -253,7 +253,10 @@ constexpr int kConvThreads = 64 + 32 * kEpiWarps;
 // ((D_0 + D_1) + D_2) after two shuffles down within the 16-lane row. Lanes
 // of halo columns 14 and 15 produce no output (and each other's pooling
 // partners, so the pooling exchange stays inside whole 2 x 2 blocks).
-template <int N, int SUB = 1, bool BIAS_REG = (N <= 64), bool XS = false>
+//
+// EW = 8 (wide layers without a head): two warps per TMEM lane quarter, warp
+// w taking accumulator columns [h N/2, (h + 1) N/2) with h = (w - 2) / 4.
+template <int N, int SUB = 1, bool BIAS_REG = (N <= 64), bool XS = false, int EW = kEpiWarps>
 __device__ __forceinline__ void conv_epilogue(uint32_t tmem, uint64_t* tfull, uint64_t* tempty, volatile int* fail,
                                               int warp, int lane, int ntiles, int tiles_x, int tiles_y, int H, int W,
                                               int Cout, const float* __restrict__ bias, int relu, ConvEpi epi,
@@ -280,7 +283,10 @@ __device__ __forceinline__ void conv_epilogue(uint32_t tmem, uint64_t* tfull, ui
         return rr & 2 ? b : a;
     };
     // accumulator columns per tcgen05.wait::ld (XS: 16 output channels = 48 columns)
-    constexpr int G = XS ? 16 : (N < 64 ? N : 64);
+    static_assert(EW == 4 || (EW == 8 && !XS && !BIAS_REG && N >= 64), "eight epilogue warps: wide layers only");
+    constexpr int NW = N * 4 / EW;                     // accumulator columns this warp reads
+    const int cb = EW == 8 ? ((warp - 2) >> 2) * NW : 0;  // the first of them
+    constexpr int G = XS ? 16 : (NW < 64 ? NW : 64);
     float bres[BIAS_REG ? N : 1];       // the bias (or 0), for narrow layers
     // wide layers read the bias per 16-channel chunk as four 16-byte
     // read-only loads, issued together, where one scalar load per channel
@@ -314,7 +320,7 @@ __device__ __forceinline__ void conv_epilogue(uint32_t tmem, uint64_t* tfull, ui
             // unrolled when XS, so the register-resident bias is indexed
             // with constants
 #pragma unroll(XS ? 4 : 1)
-            for (int g0 = 0; g0 < N; g0 += G) {
+            for (int g0 = cb; g0 < cb + NW; g0 += G) {
                 uint32_t rg[G];
                 if constexpr (XS) {
                     uint32_t r1[16], r2[16];
@@ -451,8 +457,8 @@ struct TmaConv {
     static constexpr int kTmemCols = 2 * N;
 };
 
-template <int N, int SWB>
-__global__ void __launch_bounds__(kConvThreads, 1)
+template <int N, int SWB, int EW = kEpiWarps>
+__global__ void __launch_bounds__(64 + 32 * EW, 1)
     conv3x3_fwd_tma_kernel(const __grid_constant__ CUtensorMap map_in, const __grid_constant__ CUtensorMap map_w,
                            const float* __restrict__ bias, int B, int H, int W, int Cin, int Cout, int relu,
                            const ConvEpi epi, int* status, int nsplit) {
@@ -494,7 +500,7 @@ __global__ void __launch_bounds__(kConvThreads, 1)
         }
         for (int s = 0; s < 2; ++s) {
             mbar_init(&tfull[s], 1);
-            mbar_init(&tempty[s], 32 * kEpiWarps);
+            mbar_init(&tempty[s], 32 * EW);
         }
         mbar_init(drain, 1);
         *fail = 0;
@@ -601,7 +607,8 @@ __global__ void __launch_bounds__(kConvThreads, 1)
             wait_timed(drain, 0, nullptr);
         }
     } else {
-        conv_epilogue<N>(tmem, tfull, tempty, fail, warp, lane, ntiles, tiles_x, tiles_y, H, W, Cout, bias, relu, epi,
+        conv_epilogue<N, 1, (EW == 8 ? false : N <= 64), false, EW>(tmem, tfull, tempty, fail, warp, lane, ntiles,
+                                                                     tiles_x, tiles_y, H, W, Cout, bias, relu, epi,
                          nsplit);
     }
 

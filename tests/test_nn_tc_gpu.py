@@ -26,8 +26,10 @@ def _need_gpu():
 # "..._split4" force 2 / 4 CTAs per tile, "..._sub2" 16 x 16-pixel tiles (two
 # stacked 8 x 16 sub-tiles), "..._two" two CTAs per SM, "..._xs*" the column
 # taps stacked in N (14-column tiles; 8-row tiles, 16-row tiles, two CTAs per
-# SM; with 2 CTAs per tile), on every shape they apply to (the others run the
-# unstacked kernel).
+# SM; with 2 CTAs per tile), "..._stream" / "..._stream_wide" the
+# weight-streaming kernel with four / eight epilogue warps (eight: 64+
+# columns, the default there), on every shape they apply to (the others run
+# the unstacked or four-warp kernel).
 # The automatic choice stacks the column taps of some layers (those with
 # many input channels per output column); "..._noxs" and the unstacked
 # variants forbid it (mode bit 17).
@@ -35,12 +37,13 @@ XS, NOXS = 1 << 16, 1 << 17
 KERNELS = ["conv3x3_fwd_tc", "conv3x3_fwd_tc2", "conv3x3_fwd_tma", "conv3x3_fwd_tma_noxs", "conv3x3_fwd_tma_stream",
            "conv3x3_fwd_tma_split2", "conv3x3_fwd_tma_split4", "conv3x3_fwd_tma_sub2", "conv3x3_fwd_tma_two",
            "conv3x3_fwd_tma_two_sub1", "conv3x3_fwd_tma_xs_sub1", "conv3x3_fwd_tma_xs_sub2",
-           "conv3x3_fwd_tma_xs_two", "conv3x3_fwd_tma_xs_split2"]
-MODES = {"conv3x3_fwd_tma_noxs": NOXS, "conv3x3_fwd_tma_stream": 1, "conv3x3_fwd_tma_split2": NOXS | (2 << 4),
+           "conv3x3_fwd_tma_xs_two", "conv3x3_fwd_tma_xs_split2", "conv3x3_fwd_tma_stream_wide"]
+MODES = {"conv3x3_fwd_tma_noxs": NOXS, "conv3x3_fwd_tma_stream": 1 | (1 << 19), "conv3x3_fwd_tma_split2": NOXS | (2 << 4),
          "conv3x3_fwd_tma_split4": NOXS | (4 << 4), "conv3x3_fwd_tma_sub2": NOXS | (1 << 12),
          "conv3x3_fwd_tma_two": NOXS | (1 << 15) | (1 << 12), "conv3x3_fwd_tma_two_sub1": NOXS | (1 << 15) | (1 << 13),
          "conv3x3_fwd_tma_xs_sub1": XS | (1 << 13) | (1 << 14), "conv3x3_fwd_tma_xs_sub2": XS | (1 << 12) | (1 << 14),
-         "conv3x3_fwd_tma_xs_two": XS | (1 << 15), "conv3x3_fwd_tma_xs_split2": XS | (2 << 4)}
+         "conv3x3_fwd_tma_xs_two": XS | (1 << 15), "conv3x3_fwd_tma_xs_split2": XS | (2 << 4),
+         "conv3x3_fwd_tma_stream_wide": NOXS | 1 | (1 << 18)}
 
 
 def _tc(kernel, Cout):
