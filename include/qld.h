@@ -458,8 +458,8 @@ int qldnn_conv3x3_fwd_tma(const void* in, const void* wk, const float* bias, int
  * three column groups added in the epilogue: (D_0 + D_1) + D_2, FP32); bit
  * 18 / bit 19: ask for / forbid eight epilogue warps in the weight-streaming
  * variant for slices of 64+ columns (two warps per accumulator lane quarter,
- * each reading half the columns; not with a fused head; the default there). For tests and
- * measurements of every variant. */
+ * each reading half the columns; not with a fused head; the default there). Other bits:
+ * QLD_E_INVAL. For tests and measurements of every variant. */
 int qldnn_conv3x3_fwd_tma_mode(const void* in, const void* wk, const float* bias, int B, int H, int W, int Cin,
                                int Cout, int relu, void* out_bf16, float* out_f32, int* status, int mode,
                                void* stream);

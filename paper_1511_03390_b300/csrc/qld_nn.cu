@@ -1365,7 +1365,9 @@ int qldnn_conv3x3_fwd_tma_mode(const void* in, const void* wk, const float* bias
                                int Cout, int relu, void* out_bf16, float* out_f32, int* status, int mode,
                                void* stream) {
     // mode: bit 0 forces the weight-streaming variant; bits 4.. (if non-zero)
-    // force the number of CTAs per tile (1, 2 or 4)
+    // force the number of CTAs per tile (1, 2 or 4); bit 8 early launch;
+    // bits 12-19 the variant choices documented in qld.h; no other bits
+    if (mode & ~(1 | (0xF << 4) | (1 << 8) | (0xFF << 12))) return set_err(QLD_E_INVAL);
     if (!out_bf16 && !out_f32) return set_err(QLD_E_INVAL);
     if (!al(out_bf16, 16) || !al(out_f32, 16)) return set_err(QLD_E_INVAL);
     qldnn::ConvEpi epi{};
