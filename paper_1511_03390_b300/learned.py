@@ -9,7 +9,7 @@ U-Net with 32 base channels (1.06 M parameters) whose convolutions, pooling,
 upsampling, head, loss and Adam steps all run in the library's kernels
 (qldnn_* in include/qld.h): BF16 tensor-core implicit-GEMM convolutions with
 FP32 accumulation, forward and backward. Plain QLD stays the fallback and the
-judge: the training targets are plain-QLD amplitudes of simulated stacks, and
+reference: the training targets are plain-QLD amplitudes of simulated stacks, and
 the network predicts a correction to the short-window estimate 32 R_32.
 
 Units: network input channels are (S_32, C_32, R_32) * IN_SCALE; targets are
