@@ -445,10 +445,17 @@ int qldnn_conv3x3_fwd_tma(const void* in, const void* wk, const float* bias, int
  * fit beside two halo stages (loaded once per CTA, only the halos streamed)
  * and streams them per tile otherwise; when a layer has at most half as many
  * output tiles as there are SMs it splits each tile's output channels over 2
- * or 4 CTAs (at least 32 channels each, weights resident); 32-channel
- * layers whose weights and two halo stages fit in half the shared memory run
- * two CTAs per SM when each gets at least two tiles (one CTA's MMAs fill the
- * other's pauses for barriers). mode bit 0 set: always stream the weights;
+ * or 4 CTAs (at least 32 channels each, weights resident), and 128-channel
+ * layers of at most 128 input channels with at most one tile per SM always
+ * split; 32-channel layers whose weights and two halo stages fit in half the
+ * shared memory run two CTAs per SM when each gets at least two tiles (one
+ * CTA's MMAs fill the other's pauses for barriers); 32-channel slices of 64+
+ * input channels with at least 8 tiles per SM, and 64-channel slices of 128+
+ * input channels with at least 2, stack the column taps (bit 16 below);
+ * weight-streaming slices of 64+ columns read out with eight epilogue warps
+ * (bit 18 below). The choice depends on the shape (and a fused head) only, so
+ * a layer gives the same result with fused and with separate outputs. mode bit
+ * 0 set: always stream the weights;
  * mode >> 4 (0 = automatic, else 1, 2 or 4): the CTAs per tile; bit 12 /
  * bit 13: force / forbid 16 x 16-pixel tiles where they fit; bit 14 / bit 15:
  * forbid / force two CTAs per SM where they fit; bit 16 / bit 17: ask for /
