@@ -447,8 +447,9 @@ int qldnn_conv3x3_fwd_tma(const void* in, const void* wk, const float* bias, int
  * output tiles as there are SMs it splits each tile's output channels over 2
  * or 4 CTAs (at least 32 channels each, weights resident), and 128-channel
  * layers of at most 128 input channels with at most one tile per SM always
- * split; 32-channel layers whose weights and two halo stages fit in half the
- * shared memory run two CTAs per SM when each gets at least two tiles (one
+ * split; 32-channel layers (any input width) whose weights and two halo
+ * stages fit in half the shared memory run two CTAs per SM when each gets at
+ * least two tiles (one
  * CTA's MMAs fill the other's pauses for barriers); 32-channel slices of 64+
  * input channels with at least 8 tiles per SM, and 64-channel slices of 128+
  * input channels with at least 2, stack the column taps (bit 16 below);

@@ -939,15 +939,16 @@ int conv_tma_dispatch(const void* in, const void* wk, const float* bias, int B, 
     const bool sub2 = nsplit == 1 && nco <= 64 && !force_stream && !((mode >> 13) & 1) && fits2 &&
                       (((mode >> 12) & 1) || (tiles16 >= 2ll * nsm && swb2 == swb));
     // two CTAs per SM for 32- and 64-channel layers (every CTA's MMA thread leaves
-    // gaps in the tensor-core queue that the other fills) of at least 32 input
-    // channels when the weights and two halo stages fit in half the shared
-    // memory, staged in chunks of at most 32 channels, with 16 x 16 tiles if
-    // those fit too; by default for 32-column layers of at least 32 input
-    // channels whose CTAs get at least two 8 x 16 tiles (mode bit 15 forces
-    // it where it fits, 64-column layers included; bit 14 forbids it).
+    // gaps in the tensor-core queue that the other fills) when the weights and
+    // two halo stages fit in half the shared memory, staged in chunks of at
+    // most 32 channels, with 16 x 16 tiles if those fit too; by default for
+    // 32-column layers whose CTAs get at least two 8 x 16 tiles (mode bit 15
+    // forces it where it fits, 64-column layers included; bit 14 forbids it).
     // Measured against one CTA per SM in one process: 512^2 64 -> 32 channels
-    // 21.7 -> 18.6 us, 32 -> 32 13.7 -> 13.2 us; slower for the 16-channel
-    // first layer (12.0 -> 12.4 us) and for 256^2, 32 -> 64 (8.7 -> 11.4 us).
+    // 21.7 -> 18.6 us, 32 -> 32 13.7 -> 13.2 us, and, since the wide bias
+    // loads and 32-byte stores of the epilogue, the 16-channel first layer
+    // too (10.9 -> 9.7 us; 12.0 -> 12.4 us before those); slower for 256^2,
+    // 32 -> 64 (8.7 -> 11.4 us).
     // A second MMA-issuing thread in one CTA, taking every other tile,
     // measured no faster on any layer: the gain is not the second issuer.
     auto fits_two = [&](int sub) {
@@ -1005,7 +1006,7 @@ int conv_tma_dispatch(const void* in, const void* wk, const float* bias, int B, 
         return set_err(QLD_E_INVAL);
     }
     const bool two = nsplit == 1 && (nco == 32 || nco == 64) && !force_stream && !((mode >> 14) & 1) && fits_two(1) &&
-                     (((mode >> 15) & 1) || (nco == 32 && Cin >= 32 && tiles8 >= 4ll * nsm));
+                     (((mode >> 15) & 1) || (nco == 32 && tiles8 >= 4ll * nsm));
     if (two && nco == 64)  // 8 x 16 tiles only: 16 x 16 ones do not fit twice with 64-column weights
         return swb2 == 32 ? launch_tma<64, 32, 1, 2>(in, wk, bias, B, H, W, Cin, Cout, relu, epi, status, st, false, early)
                           : launch_tma<64, 64, 1, 2>(in, wk, bias, B, H, W, Cin, Cout, relu, epi, status, st, false, early);
