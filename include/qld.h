@@ -451,8 +451,9 @@ int qldnn_conv3x3_fwd_tma(const void* in, const void* wk, const float* bias, int
  * stages fit in half the shared memory run two CTAs per SM when each gets at
  * least two tiles (one
  * CTA's MMAs fill the other's pauses for barriers); 32-channel slices of 64+
- * input channels with at least 8 tiles per SM, and 64-channel slices of 128+
- * input channels with at least 2, stack the column taps (bit 16 below);
+ * input channels with at least 8 tiles per SM or of 128+ input channels, and
+ * 64-channel slices of 128+ input channels with at least 2 tiles per SM,
+ * stack the column taps (bit 16 below);
  * weight-streaming slices of 64+ columns read out with eight epilogue warps
  * (bit 18 below). The choice depends on the shape (and a fused head) only, so
  * a layer gives the same result with fused and with separate outputs. mode bit
