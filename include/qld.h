@@ -446,8 +446,8 @@ int qldnn_conv3x3_fwd_tma(const void* in, const void* wk, const float* bias, int
  * and streams them per tile otherwise; when a layer has at most half as many
  * output tiles as there are SMs it splits each tile's output channels over 2
  * or 4 CTAs (at least 32 channels each, weights resident), and 128-channel
- * layers of at most 128 input channels with at most one tile per SM always
- * split; 32-channel layers (any input width) whose weights and two halo
+ * layers of at most 128 input channels and 64-channel layers of 128+ input
+ * channels with at most one tile per SM always split; 32-channel layers (any input width) whose weights and two halo
  * stages fit in half the shared memory run two CTAs per SM when each gets at
  * least two tiles (one
  * CTA's MMAs fill the other's pauses for barriers); 32-channel slices of 64+
@@ -506,10 +506,10 @@ int qldnn_conv3x3_fwd_tma_epi(const void* in, const void* wk, const float* bias,
                               int Cout, int relu, void* out_bf16, long long ldo, void* pool_bf16, void* up_bf16,
                               long long ldu, const float* head_w, const float* head_b, const float* baseline,
                               float* pred, int* status, int flags, void* stream);
-/* The same with the kernel variant chosen by the caller: mode bit 0 and bits
- * 12-19 as in qldnn_conv3x3_fwd_tma_mode (the CTAs per tile stay the layer's
- * own; other bits: QLD_E_INVAL). For tests and measurements of every variant
- * with fused outputs. */
+/* The same with the kernel variant chosen by the caller: mode bits 0, 4-7
+ * and 12-19 as in qldnn_conv3x3_fwd_tma_mode (4-7, the CTAs per tile, only
+ * without a head; other bits: QLD_E_INVAL). For tests and measurements of
+ * every variant with fused outputs. */
 int qldnn_conv3x3_fwd_tma_epi_mode(const void* in, const void* wk, const float* bias, int B, int H, int W, int Cin,
                                    int Cout, int relu, void* out_bf16, long long ldo, void* pool_bf16, void* up_bf16,
                                    long long ldu, const float* head_w, const float* head_b, const float* baseline,

@@ -920,9 +920,13 @@ int conv_tma_dispatch(const void* in, const void* wk, const float* bias, int B, 
     // free), measured faster whether or not the 64-column slices' weights
     // stay resident (128^2 at batch 1: 64 -> 128 8.95 -> 6.7 us, 128 -> 128
     // 10.5 -> 9.7 us; 8 x 32^2, 128 -> 128 8.5 -> 7.3 us with two instead of
-    // four); layers of 256 input channels and 64-column layers measured
-    // slower split
+    // four); layers of 256 input channels measured slower split
     if (Cout == 128 && Cin <= 128 && ntiles <= nsm) nsplit = 4 * ntiles <= nsm ? 4 : 2;
+    // 64-column layers of 128+ input channels with at most one tile per SM:
+    // two 32-column slices, which then stack their column taps (128^2,
+    // 128 -> 64 with its fused 2x upsampling 7.8 -> 7.4 us; 8.3 us split
+    // without the stacking)
+    if (Cout == 64 && Cin >= 128 && ntiles <= nsm) nsplit = 2;
     if (split_mode > 0) nsplit = split_mode;
     if (Cout % nsplit || Cout / nsplit < 32) return set_err(QLD_E_INVAL);
     const int nco = Cout / nsplit;
@@ -1394,9 +1398,11 @@ int qldnn_conv3x3_fwd_tma_epi_mode(const void* in, const void* wk, const float* 
                                    long long ldu, const float* head_w, const float* head_b, const float* baseline,
                                    float* pred, int* status, int flags, int mode, void* stream) {
     if (flags & ~QLDNN_EARLY_LAUNCH) return set_err(QLD_E_INVAL);
-    // variant bits only: the channel split is the layer's (one CTA per tile with a head), early launch is a flag
-    if (mode & ~((0xF << 12) | (0xF << 16) | 1)) return set_err(QLD_E_INVAL);
+    // variant bits and (without a head, which needs one CTA per tile) the
+    // CTAs per tile; early launch is a flag
+    if (mode & ~((0xF << 4) | (0xF << 12) | (0xF << 16) | 1)) return set_err(QLD_E_INVAL);
     const bool head = head_w || head_b || baseline || pred;
+    if (head && (mode & (0xF << 4))) return set_err(QLD_E_INVAL);
     if (!out_bf16 && !pool_bf16 && !up_bf16 && !head) return set_err(QLD_E_INVAL);
     if (out_bf16 && (!al(out_bf16, 16) || ldo < Cout || ldo % 8)) return set_err(QLD_E_INVAL);
     if (pool_bf16 && (!al(pool_bf16, 16) || H % 2 || W % 2)) return set_err(QLD_E_INVAL);
