@@ -290,8 +290,9 @@ int qld_fft_bin_frames_noalloc(const void* frames, int H, int W, int N, int pixf
  *    (owned by the server; read them after the tick, in stream order).
  *  - qld_server_autotune times the batched kernel's candidate launch shapes
  *    on small-window replicas of the active streams (same bytes per pushed
- *    frame; temporary memory outside the budget), keeps the fastest and
- *    returns its index (best time per tick in *best_us).
+ *    frame; temporary memory outside the budget), each as the best of three
+ *    runs of eight launches back to back (as ticks run), keeps the fastest
+ *    and returns its index (best time per tick in *best_us).
  * One host thread must drive a server at a time. */
 #define QLD_SERVER_MAX_STREAMS 64
 typedef struct qld_server qld_server;

@@ -547,20 +547,31 @@ int qld_server_autotune(qld_server* s, void* stream, float* best_us) {
     int best_shape = saved_shape;
     qld_server probe = *s;  // build_items on the replicas with each candidate shape
     probe.streams = rep;
+    // Each shape: 3 launches of warm-up, then the best of 3 runs of 8 launches
+    // back to back, as ticks run (timing launches one at a time, with a
+    // synchronisation after each, measured their latency more than the
+    // shape's throughput and let the choice vary from run to run).
+    const int warm = 3, run = 8, runs = 3;
+    int it = 0;
+    auto launch_one = [&](int k) {
+        for (SrvStream& r : probe.streams) r.pending_count = 1;
+        build_items(&probe, pp->items, &pp->hdr, nullptr);
+        // frame (it mod 8) of each replica's 8-frame scratch: consecutive
+        // launches read different frames and write different slots
+        for (int i = 0; i < pp->hdr.nitems; ++i)
+            pp->items[i].a.frames =
+                (const uint8_t*)probe.streams[i].pending + (it % 8) * probe.streams[i].ctx->frame_bytes;
+        qldk::launch_batch(qldk::kBatchShapes[k], s->num_sms, pp->hdr.ntiles, *pp, s->gate_dev, st);
+        for (SrvStream& r : probe.streams) r.ctx->pushed += 1;
+        ++it;
+    };
     for (int k = 0; rc == QLD_OK && k < qldk::kNumBatchShapes; ++k) {
         probe.shape = k;
-        float total = 0.f;
-        const int warm = 3, reps = 12;
-        for (int it = 0; it < warm + reps && rc == QLD_OK; ++it) {
-            for (SrvStream& r : probe.streams) r.pending_count = 1;
-            build_items(&probe, pp->items, &pp->hdr, nullptr);
-            // frame (it mod 8) of each replica's 8-frame scratch: consecutive
-            // launches read different frames and write different slots
-            for (int i = 0; i < pp->hdr.nitems; ++i)
-                pp->items[i].a.frames =
-                    (const uint8_t*)probe.streams[i].pending + (it % 8) * probe.streams[i].ctx->frame_bytes;
+        for (int w = 0; w < warm; ++w) launch_one(k);
+        float us = 1e30f;
+        for (int q = 0; q < runs && rc == QLD_OK; ++q) {
             cudaEventRecord(e0, st);
-            qldk::launch_batch(qldk::kBatchShapes[k], s->num_sms, pp->hdr.ntiles, *pp, s->gate_dev, st);
+            for (int l = 0; l < run; ++l) launch_one(k);
             cudaEventRecord(e1, st);
             if (cudaEventSynchronize(e1) != cudaSuccess) {
                 rc = QLD_E_CUDA;
@@ -568,10 +579,8 @@ int qld_server_autotune(qld_server* s, void* stream, float* best_us) {
             }
             float ms = 0.f;
             cudaEventElapsedTime(&ms, e0, e1);
-            if (it >= warm) total += ms;
-            for (SrvStream& r : probe.streams) r.ctx->pushed += 1;
+            if (ms * 1e3f / run < us) us = ms * 1e3f / run;
         }
-        const float us = total / reps * 1e3f;
         if (rc == QLD_OK && us < best) {
             best = us;
             best_shape = k;
@@ -588,7 +597,7 @@ int qld_server_autotune(qld_server* s, void* stream, float* best_us) {
         cudaGetLastError();
         return set_err(rc);
     }
-    qldi::count_launches(qldk::kNumBatchShapes * 15);
+    qldi::count_launches(qldk::kNumBatchShapes * (warm + run * runs));
     if (best_shape != s->shape) {
         s->shape = best_shape;
         s->graph_valid = false;
