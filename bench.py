@@ -1144,6 +1144,10 @@ def run_learned(q, torch, dev, st, samples=200, fps=200.0):
     Cd = torch.empty_like(Sd)
     net = L.UNet(prm, 1, Hs, Ws, inference_only=True)
     gnet = L.UNet(prm, 1, Hs, Ws, inference_only=True).capture()
+    # the same network captured to read the short-window context's own sums
+    # in place (qld_iq_pointers): no copy between the push and the network
+    Sp, Cp = q.qld_iq_pointers(ctx_s)
+    gnet_iq = L.UNet(prm, 1, Hs, Ws, inference_only=True).capture(Sp, Cp)
 
     def plain():
         q.qld_push_image(ctx_l, frames, L.N_LONG, st, amp, None)
@@ -1156,8 +1160,7 @@ def run_learned(q, torch, dev, st, samples=200, fps=200.0):
 
     def learned_graph():
         q.qld_push_frames(ctx_s, frames[-L.N_SHORT:], L.N_SHORT, st)
-        q.qld_get_iq(ctx_s, gnet.S_in, gnet.C_in)
-        gnet.replay()
+        gnet_iq.replay()
 
     out = {}
     for name, fn, nfr in [("plain_qld_n1024", plain, L.N_LONG), ("learned_n32", learned_path, L.N_SHORT),

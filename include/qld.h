@@ -193,6 +193,14 @@ int qld_step_host(qld_ctx* ctx, const void* host_frames, int count, void* stream
  * Valid at any time (partial sums while the window fills). */
 int qld_get_iq(qld_ctx* ctx, int32_t* S, int32_t* C);
 
+/* The device addresses of the context's own sums S and C (int32 [H][W],
+ * owned by the context, valid until qld_destroy), for kernels that read them
+ * in place instead of a copy (the paper has no counterpart: a zero-copy
+ * accessor). Their contents change with every push: read them in the
+ * context's stream order. Either output may be NULL. QLD_E_INVAL for a NULL
+ * context. */
+int qld_iq_pointers(qld_ctx* ctx, const int32_t** S, const int32_t** C);
+
 /* Empties the window: zeroes the ring and the sums, frames_pushed = 0. */
 int qld_reset(qld_ctx* ctx);
 

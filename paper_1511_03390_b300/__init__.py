@@ -18,7 +18,7 @@ __all__ = [
     "QLD_E_TIMEOUT", "QLD_MAX_N", "QLDError", "Context", "qld_create", "qld_create_band", "qld_destroy",
     "qld_push_frames",
     "qld_push_image", "qld_image", "qld_fft_bin", "qld_step", "qld_step_host", "qld_push_frames_host", "qld_image_host",
-    "qld_fft_bin_host", "qld_get_iq", "qld_reset", "qld_frames_pushed", "qld_sync", "qld_stream",
+    "qld_fft_bin_host", "qld_get_iq", "qld_iq_pointers", "qld_reset", "qld_frames_pushed", "qld_sync", "qld_stream",
     "qld_strerror", "qld_last_error", "qld_version", "qld_footprint_bytes", "qld_set_mem_budget",
     "qld_mem_in_use", "qld_launch_count", "qld_fft_bin_frames_noalloc", "QLD_NOALLOC_MAX_N",
     "qld_lockin_table", "qld_lockin_frames", "Server", "QLD_SERVER_MAX_STREAMS", "qld_server_create",
@@ -123,6 +123,7 @@ _SIGS = {
     "qld_server_shape": ([_p, ctypes.POINTER(_i), ctypes.POINTER(_i), ctypes.POINTER(_i)], _i),
     "qld_lockin_frames": ([_p, _i, _i, _i, _i, _p, _p, _p, _p], _i),
     "qld_get_iq": ([_p, _p, _p], _i),
+    "qld_iq_pointers": ([_p, ctypes.POINTER(_p), ctypes.POINTER(_p)], _i),
     "qld_reset": ([_p], _i),
     "qld_frames_pushed": ([_p], _ll),
     "qld_sync": ([_p], _i),
@@ -348,6 +349,14 @@ def qld_lockin_frames(frames, H, W, N, pixfmt, table, amp=None, phase=None, stre
 
 def qld_get_iq(ctx, S=None, C=None):
     return _check(lib.qld_get_iq(_h(ctx), _addr(S, 4 * ctx.npix, "S"), _addr(C, 4 * ctx.npix, "C")), "qld_get_iq")
+
+
+def qld_iq_pointers(ctx):
+    """Device addresses (ints) of the context's own sums S and C (int32
+    [H*W]); their contents change with every push."""
+    S, C = _p(), _p()
+    _check(lib.qld_iq_pointers(_h(ctx), ctypes.byref(S), ctypes.byref(C)), "qld_iq_pointers")
+    return S.value, C.value
 
 
 def qld_reset(ctx):

@@ -680,6 +680,13 @@ int qld_get_iq(qld_ctx* c, int32_t* S, int32_t* C) {
     return QLD_OK;
 }
 
+int qld_iq_pointers(qld_ctx* c, const int32_t** S, const int32_t** C) {
+    if (!c) return set_err(QLD_E_INVAL);
+    if (S) *S = c->S;
+    if (C) *C = c->C;
+    return QLD_OK;
+}
+
 int qld_reset(qld_ctx* c) {
     if (!c) return set_err(QLD_E_INVAL);
     DeviceGuard g(c->device);

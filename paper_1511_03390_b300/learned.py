@@ -172,15 +172,20 @@ class UNet:
             nn.conv3x3_fwd(x, self.prm[name + ".w"]["bf"], self.prm[name + ".b"]["p"], self.B, h, w, cin, cout, 1, y,
                            None)
 
-    def capture(self):
+    def capture(self, S=None, C=None):
         """Record input packing and the forward pass as one CUDA graph over
         this object's fixed buffers (inputs: self.S_in, self.C_in, int32
         [B*H*W]); replay() then runs the whole network as one launch on the
-        current stream. The first, uncaptured pass sets the kernels'
-        launch attributes."""
+        current stream. With S and C given (int32 device tensors, or device
+        addresses such as qld_iq_pointers' of a QLD context of the same
+        frame size), the graph reads those in place instead. The first,
+        uncaptured pass sets the kernels' launch attributes."""
         d = self.prm.device
-        self.S_in = torch.zeros(self.P[0], dtype=torch.int32, device=d)
-        self.C_in = torch.zeros_like(self.S_in)
+        if S is None or C is None:
+            self.S_in = torch.zeros(self.P[0], dtype=torch.int32, device=d)
+            self.C_in = torch.zeros_like(self.S_in)
+        else:
+            self.S_in, self.C_in = S, C
         side = torch.cuda.Stream(d)
         side.wait_stream(torch.cuda.current_stream(d))
         with torch.cuda.stream(side):

@@ -109,6 +109,7 @@ def test_null_context_and_strings():
     assert q.lib.qld_push_frames(None, None, 0, None) == q.QLD_E_INVAL
     assert q.lib.qld_image(None, None, None) == q.QLD_E_INVAL
     assert q.lib.qld_fft_bin(None, 0, None) == q.QLD_E_INVAL
+    assert q.lib.qld_iq_pointers(None, None, None) == q.QLD_E_INVAL
     assert q.lib.qld_sync(None) == q.QLD_E_INVAL
     assert q.lib.qld_frames_pushed(None) == -1
     assert q.qld_strerror(q.QLD_E_NOT_READY).startswith("window not full")

@@ -268,3 +268,35 @@ def test_epi_conv_rejects_unknown_flags():
     rc = q.lib.qldnn_conv3x3_fwd_tma_epi(x.data_ptr(), w.data_ptr(), None, 1, 64, 64, 32, 32, 1, out.data_ptr(), 32,
                                          None, None, 32, None, None, None, None, st.data_ptr(), 2, None)
     assert rc == q.QLD_E_INVAL
+
+
+def test_network_reading_the_context_sums_in_place_equals_the_copied_input():
+    """A network captured on a QLD context's own sums (qld_iq_pointers) gives
+    the same prediction, bit for bit, as one fed copies of them (qld_get_iq),
+    after each of several pushes; the accessor returns the context's live
+    buffers."""
+    from qldscene import DeviceScene, scene_fog
+
+    H = W = 64
+    prm = learned.Params(seed=3)
+    ctx = q.qld_create(H, W, learned.N_SHORT, q.QLD_U16)
+    try:
+        frames = torch.empty((3 * learned.N_SHORT, H, W), dtype=torch.uint16, device="cuda")
+        DeviceScene(scene_fog(6, seed=77, H=H, W=W), torch.device("cuda")).generate_into(frames, 1, 3 * learned.N_SHORT)
+        Sp, Cp = q.qld_iq_pointers(ctx)
+        inplace = learned.UNet(prm, 1, H, W, inference_only=True).capture(Sp, Cp)
+        copied = learned.UNet(prm, 1, H, W, inference_only=True).capture()
+        st = torch.cuda.current_stream()
+        for k in range(3):
+            q.qld_push_frames(ctx, frames[k * learned.N_SHORT:(k + 1) * learned.N_SHORT], learned.N_SHORT, st)
+            got = inplace.replay().clone()
+            q.qld_get_iq(ctx, copied.S_in, copied.C_in)
+            want = copied.replay().clone()
+            torch.cuda.synchronize()
+            assert torch.equal(got, want)
+        S = torch.empty(H * W, dtype=torch.int32, device="cuda")
+        q.qld_get_iq(ctx, S, None)
+        torch.cuda.synchronize()
+        assert q.qld_iq_pointers(ctx)[0] == Sp
+    finally:
+        q.qld_destroy(ctx)
